@@ -1,0 +1,291 @@
+"""Seeded synthetic sparse inputs shared by the CUDA path and the CPU oracle.
+
+This module holds no SpGEMM arithmetic: it only draws random sparse matrices
+in CSR form (int64 row_ptr, int32 col, typed values) with numpy's PCG64, so
+that both sides of a parity test see the same bytes.  Every matrix it emits
+has strictly increasing column indices within a row (sorted, no duplicates).
+
+Shapes follow the paper's workloads:
+  * R-MAT with Graph500-style quadrant probabilities (Section 4.3 uses a
+    1M x 1M R-MAT with the Graph500 parameters), symmetrised, duplicates
+    removed, vertices randomly permuted (Section 3.1: random permutation at
+    assembly for load balance);
+  * Erdos-Renyi rows with an exact number of distinct uniform columns;
+  * banded matrices (a family with strong locality).
+The paper's own matrices (Table 4) are not available; these stand in for them.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+MASTER_SEED = 20210628
+_M64 = (1 << 64) - 1
+
+# Semiring value types, by name.  bool values are stored as uint8 0/1.
+VALUE_DTYPE = {
+    "plus_times_i64": np.int64,
+    "plus_times_f64": np.float64,
+    "min_plus_u32": np.uint32,
+    "or_and_bool": np.uint8,
+    "sel2nd_min_i32": np.int32,
+}
+SEMIRINGS = tuple(VALUE_DTYPE)
+
+
+def splitmix64(x: int) -> int:
+    """One step of the splitmix64 output function (Steele, Lea, Flood 2014)."""
+    x = (x + 0x9E3779B97F4A7C15) & _M64
+    z = x
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def subseed(*parts: int) -> int:
+    """Derive a 64-bit seed from a tuple of integers by chained splitmix64."""
+    h = MASTER_SEED
+    for p in parts:
+        h = splitmix64(h ^ (int(p) & _M64))
+    return h
+
+
+def rng_for(*parts: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(subseed(*parts)))
+
+
+@dataclass
+class CSR:
+    """Host CSR matrix: row_ptr int64[nrows+1], col int32[nnz], val typed[nnz] (or None)."""
+    nrows: int
+    ncols: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray | None = None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def with_values(self, val: np.ndarray) -> "CSR":
+        assert val.shape == (self.nnz,)
+        return CSR(self.nrows, self.ncols, self.row_ptr, self.col, val)
+
+    def row_lengths(self) -> np.ndarray:
+        return np.diff(self.row_ptr)
+
+
+def _csr_from_sorted_keys(keys: np.ndarray, nrows: int, ncols: int) -> CSR:
+    rows = keys // ncols
+    cols = (keys - rows * ncols).astype(np.int32)
+    counts = np.bincount(rows, minlength=nrows).astype(np.int64)
+    row_ptr = np.zeros(nrows + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return CSR(nrows, ncols, row_ptr, cols)
+
+
+def csr_from_coo(rows: np.ndarray, cols: np.ndarray, nrows: int, ncols: int) -> CSR:
+    """Sorted, de-duplicated CSR pattern from COO coordinates."""
+    keys = np.unique(rows.astype(np.int64) * ncols + cols.astype(np.int64))
+    return _csr_from_sorted_keys(keys, nrows, ncols)
+
+
+def rmat(scale: int, edgefactor: int, a: float, b: float, c: float, seed: int,
+         symmetrize: bool = True, permute: bool = True) -> CSR:
+    """R-MAT pattern on n = 2**scale vertices with n*edgefactor directed edges.
+
+    Each edge descends `scale` levels of the adjacency quadtree, picking the
+    quadrants (0,0), (0,1), (1,0), (1,1) with probabilities a, b, c, d=1-a-b-c
+    and no per-level noise.  Then (optionally) the transpose is added, the
+    vertices are relabelled by one seeded random permutation, and duplicate
+    edges are dropped.  Self-loops are kept.
+    """
+    n = 1 << scale
+    m = n * edgefactor
+    rng = rng_for(seed, 1)
+    i = np.zeros(m, dtype=np.int64)
+    j = np.zeros(m, dtype=np.int64)
+    ab = a + b
+    abc = a + b + c
+    for _ in range(scale):
+        u = rng.random(m)
+        ibit = u >= ab
+        jbit = ((u >= a) & (u < ab)) | (u >= abc)
+        i <<= 1
+        j <<= 1
+        i |= ibit
+        j |= jbit
+        del u, ibit, jbit
+    if permute:
+        perm = rng_for(seed, 2).permutation(n).astype(np.int64)
+        i = perm[i]
+        j = perm[j]
+    if symmetrize:
+        i, j = np.concatenate([i, j]), np.concatenate([j, i])
+    keys = np.unique(i * n + j)
+    del i, j
+    return _csr_from_sorted_keys(keys, n, n)
+
+
+def er_exact(nrows: int, ncols: int, deg: int, seed: int) -> CSR:
+    """Each row gets exactly min(deg, ncols) distinct uniformly random columns."""
+    d = min(deg, ncols)
+    rng = rng_for(seed, 3)
+    cols = np.sort(rng.integers(0, ncols, size=(nrows, d), dtype=np.int64), axis=1)
+    if d > 1:
+        bad = np.nonzero((np.diff(cols, axis=1) == 0).any(axis=1))[0]
+        for r in bad:
+            # Sequential rejection: the first d distinct draws form a uniform d-subset.
+            got: list[int] = []
+            seen: set[int] = set()
+            while len(got) < d:
+                for x in rng.integers(0, ncols, size=2 * d):
+                    x = int(x)
+                    if x not in seen:
+                        seen.add(x)
+                        got.append(x)
+                        if len(got) == d:
+                            break
+            cols[r] = np.sort(np.array(got, dtype=np.int64))
+    row_ptr = np.arange(nrows + 1, dtype=np.int64) * d
+    return CSR(nrows, ncols, row_ptr, cols.reshape(-1).astype(np.int32))
+
+
+def banded(n: int, bw: int, deg: int, seed: int) -> CSR:
+    """Row i gets min(deg, |window|) distinct random columns in [i-bw, i+bw] clipped to [0, n)."""
+    rng = rng_for(seed, 4)
+    width = 2 * bw + 1
+    k = min(deg, width)
+    offsets = np.arange(width, dtype=np.int64) - bw
+    rows_out, cols_out = [], []
+    for r0 in range(0, n, 4096):
+        r1 = min(n, r0 + 4096)
+        rows = np.arange(r0, r1, dtype=np.int64)
+        cand = rows[:, None] + offsets[None, :]
+        key = rng.random((r1 - r0, width))
+        key[(cand < 0) | (cand >= n)] = 2.0          # positions outside [0, n) never win
+        pick = np.argpartition(key, k - 1, axis=1)[:, :k] if k < width else np.tile(np.arange(width), (r1 - r0, 1))
+        ok = np.take_along_axis(key, pick, axis=1) < 2.0
+        c = np.take_along_axis(cand, pick, axis=1)
+        rows_out.append(np.broadcast_to(rows[:, None], c.shape)[ok])
+        cols_out.append(c[ok])
+    return csr_from_coo(np.concatenate(rows_out), np.concatenate(cols_out), n, n)
+
+
+def random_values(semiring: str, nnz: int, seed: int, lo=None, hi=None) -> np.ndarray:
+    """Value streams per semiring (bounds inclusive for integers, [lo, hi) for floats)."""
+    rng = rng_for(seed, 5)
+    if semiring == "plus_times_i64":
+        lo, hi = (1, 10) if lo is None else (lo, hi)
+        return rng.integers(lo, hi + 1, size=nnz, dtype=np.int64)
+    if semiring == "plus_times_f64":
+        lo, hi = (0.0, 1.0) if lo is None else (lo, hi)
+        return lo + (hi - lo) * rng.random(nnz)
+    if semiring == "min_plus_u32":
+        lo, hi = (1, 255) if lo is None else (lo, hi)
+        return rng.integers(lo, hi + 1, size=nnz, dtype=np.uint32)
+    if semiring == "or_and_bool":
+        if lo is None:
+            return np.ones(nnz, dtype=np.uint8)
+        return rng.integers(0, 2, size=nnz, dtype=np.uint8)
+    if semiring == "sel2nd_min_i32":
+        lo, hi = (0, (1 << 30) - 1) if lo is None else (lo, hi)
+        return rng.integers(lo, hi + 1, size=nnz, dtype=np.int32)
+    raise ValueError(semiring)
+
+
+# ---------------------------------------------------------------------------
+# The workloads.  Each returns (semiring, A, B) triples; A and B share the
+# pattern when the product is a square (C = A.A).
+# ---------------------------------------------------------------------------
+
+RMAT_ABCD = (0.57, 0.19, 0.19)
+
+
+def er_square(n: int = 16384, deg: int = 8, cfg: int = 1):
+    """Plain C = A.A over (+,x) int64; A is ER with exactly `deg` distinct columns per row."""
+    A = er_exact(n, n, deg, subseed(cfg, 0))
+    A = A.with_values(random_values("plus_times_i64", A.nnz, subseed(cfg, 1)))
+    return [("plus_times_i64", A, A)]
+
+
+def rmat_square(scale: int = 18, edgefactor: int = 16, cfg: int = 2,
+                semirings=("plus_times_f64", "min_plus_u32", "or_and_bool")):
+    """C = A.A on a symmetrised R-MAT, one value stream per semiring."""
+    P = rmat(scale, edgefactor, *RMAT_ABCD, seed=subseed(cfg, 0))
+    out = []
+    for k, sr in enumerate(semirings):
+        if sr == "sel2nd_min_i32":
+            A = P.with_values(np.ones(P.nnz, dtype=np.int32))
+            B = P.with_values(random_values(sr, P.nnz, subseed(cfg, 10 + k)))
+        else:
+            A = P.with_values(random_values(sr, P.nnz, subseed(cfg, 10 + k)))
+            B = A
+        out.append((sr, A, B))
+    return out
+
+
+def training_family(index: int, cfg: int = 5) -> CSR:
+    """Matrix `index` of the learned-sizer training mix (R-MAT / ER / banded, 2000 in all).
+
+    Indices 0..666 are R-MAT (scale 12..16, a in [0.45, 0.65], d = 0.05,
+    b = c = (0.95 - a)/2, edgefactor 16), 667..1333 are ER (n log-uniform in
+    [2^12, 2^16], degree 4..64), 1334..1999 are banded (bandwidth 8..256,
+    degree 4..64).  All are squared (C = A.A).
+    """
+    rng = rng_for(cfg, 100, index)
+    if index < 667:
+        scale = int(rng.integers(12, 17))
+        a = float(rng.uniform(0.45, 0.65))
+        bc = (0.95 - a) / 2
+        return rmat(scale, 16, a, bc, bc, seed=subseed(cfg, 101, index))
+    if index < 1334:
+        n = int(math.exp(rng.uniform(math.log(1 << 12), math.log(1 << 16))))
+        deg = int(rng.integers(4, 65))
+        return er_exact(n, n, deg, seed=subseed(cfg, 102, index))
+    n = int(math.exp(rng.uniform(math.log(1 << 12), math.log(1 << 16))))
+    bw = int(rng.integers(8, 257))
+    deg = int(rng.integers(4, 65))
+    return banded(n, bw, deg, seed=subseed(cfg, 103, index))
+
+
+def random_csr(nrows: int, ncols: int, density: float, seed: int, semiring: str | None = None,
+               duplicates: bool = False, shuffle: bool = False, empty_rows: float = 0.0,
+               full_rows: float = 0.0, lo=None, hi=None) -> CSR:
+    """Small adversarial CSR inputs for parity tests.
+
+    Each row independently is empty (prob. empty_rows), full (prob.
+    full_rows) or Bernoulli(density) per column.  With `duplicates`, some
+    stored entries are repeated (same coordinate, new value); with `shuffle`
+    the columns inside a row are left in random order.  Values come from
+    random_values(semiring, ...).
+    """
+    rng = rng_for(seed, 6)
+    rows, cols = [], []
+    for i in range(nrows):
+        u = rng.random()
+        if u < empty_rows:
+            c = np.zeros(0, dtype=np.int64)
+        elif u < empty_rows + full_rows:
+            c = np.arange(ncols, dtype=np.int64)
+        else:
+            c = np.nonzero(rng.random(ncols) < density)[0].astype(np.int64)
+        if duplicates and c.size:
+            extra = rng.choice(c, size=int(rng.integers(0, c.size + 1)), replace=True)
+            c = np.concatenate([c, extra])
+        if shuffle:
+            rng.shuffle(c)
+        else:
+            c = np.sort(c, kind="stable")
+        rows.append(np.full(c.size, i, dtype=np.int64))
+        cols.append(c)
+    counts = np.array([c.size for c in cols], dtype=np.int64)
+    row_ptr = np.zeros(nrows + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    col = np.concatenate(cols).astype(np.int32) if nrows else np.zeros(0, np.int32)
+    out = CSR(nrows, ncols, row_ptr, col)
+    if semiring is not None:
+        out = out.with_values(random_values(semiring, out.nnz, subseed(seed, 7), lo, hi))
+    return out
