@@ -1,0 +1,184 @@
+/*
+ * cb.h -- C ABI of the GB300 semiring SpGEMM library (libcb.so).
+ *
+ * Operation (paper Sec. 2.3, "Notation"; Sec. 5.1, "Multithreaded SpGEMM"):
+ *   C = A (+).(x) B  with A in S^{m x n}, B in S^{n x k}, C in S^{m x k},
+ *   computed row by row with Gustavson's formulation: row i of C merges the
+ *   rows of B selected by the stored entries of row i of A.  The pattern of C
+ *   is structural: (i,j) is stored iff some stored A(i,p) meets some stored
+ *   B(p,j); every such pair contributes one (x)-product, and products are
+ *   (+)-combined (entries equal to zero or to the (+)-identity are kept).
+ *   Sec. 5.1 splits the work into (1) a flops estimate and load balance,
+ *   (2) a symbolic phase that sizes C, (3) a numeric phase with a hash
+ *   accumulator; Sec. 7.2 forms C in column batches when it does not fit.
+ *
+ * Data layout (all matrices): CSR by rows.
+ *   row_ptr  int64[nrows + 1], row_ptr[0] = 0, non-decreasing, row_ptr[nrows] = nnz
+ *   col      int32[nnz], 0 <= col < ncols (ncols <= INT32_MAX)
+ *   val      nnz values of the semiring's type (bool stored as uint8 0/1;
+ *            any nonzero input byte counts as true)
+ * Inputs may have unsorted and duplicate columns within a row (duplicates
+ * contribute separately).  Output rows always have strictly increasing
+ * columns.  All cb_csr pointers are DEVICE pointers unless a function says
+ * otherwise.
+ *
+ * Errors: every function returns an int status (CB_OK = 0).  Nothing throws
+ * across the ABI, nothing aborts, no kernel traps.  On error the output
+ * cb_csr is left zeroed and owns nothing; cb_last_error(ctx) gives a message.
+ *
+ * Streams: a cb_ctx is bound to one CUDA stream; all work is ordered on it.
+ * Functions that must learn a size on the host (the total nnz of C, to
+ * allocate it) synchronise that stream once; the functions marked "async"
+ * never synchronise.
+ */
+#ifndef CB_H_
+#define CB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Semirings and their value types. */
+typedef enum {
+  CB_PLUS_TIMES_I64 = 1, /* (+,x) over int64, wrapping two's complement          */
+  CB_PLUS_TIMES_F64 = 2, /* (+,x) over IEEE fp64 (any summation order, FMA ok)   */
+  CB_MIN_PLUS_U32 = 3,   /* (min,+) over uint32, + saturates at UINT32_MAX (inf) */
+  CB_OR_AND_BOOL = 4,    /* (or,and) over bool stored as uint8                   */
+  CB_SEL2ND_MIN_I32 = 5  /* (select2nd,min) over int32: (x)(a,b) = b, (+) = min  */
+} cb_semiring;
+
+/* Status codes. */
+enum {
+  CB_OK = 0,
+  CB_ERR_ARG = 1,       /* null pointer, negative size, bad option             */
+  CB_ERR_SHAPE = 2,     /* A.ncols != B.nrows                                  */
+  CB_ERR_SEMIRING = 3,  /* unknown semiring                                    */
+  CB_ERR_INDEX = 4,     /* ncols > INT32_MAX, bad row_ptr, column out of range */
+  CB_ERR_OOM = 5,       /* device allocation failed                            */
+  CB_ERR_BUDGET = 6,    /* one output row (or batch unit) exceeds the budget   */
+  CB_ERR_TIMEOUT = 7,   /* a bounded device-side wait expired                  */
+  CB_ERR_CUDA = 8,      /* a CUDA runtime call failed                          */
+  CB_ERR_CAPACITY = 9   /* caller-provided output too small; C->nnz = needed   */
+};
+
+typedef struct {
+  int64_t nrows, ncols, nnz;
+  int64_t *row_ptr; /* device, int64[nrows + 1] */
+  int32_t *col;     /* device, int32[nnz]        */
+  void *val;        /* device, nnz values        */
+} cb_csr;
+
+typedef struct cb_ctx cb_ctx;
+
+/* How C's per-row sizes are obtained before the numeric phase. */
+typedef enum {
+  CB_SIZING_EXACT = 0,       /* symbolic phase (paper Sec. 5.1 phase (2))       */
+  CB_SIZING_LEARNED = 1,     /* MLP prediction, exact fallback on overflow      */
+  CB_SIZING_UPPER_BOUND = 2  /* min(flops_i, ncols) per row, exact fallback     */
+} cb_sizing;
+
+/* Consumer of one column batch C[:, col_lo:col_hi) (paper Sec. 7.2: batched
+ * SpGEMM forms the output in batches that the application consumes).  Cb is
+ * valid only during the call (device pointers, columns are global indices).
+ * Return nonzero to stop early (cb_spgemm_ex then returns CB_OK). */
+typedef int (*cb_batch_fn)(int batch, int64_t col_lo, int64_t col_hi,
+                           const cb_csr *Cb, void *user);
+
+/* Learned sizer weights (see cb_mlp_* below). */
+typedef struct cb_mlp cb_mlp;
+
+typedef struct {
+  int32_t sizing;       /* cb_sizing; default CB_SIZING_EXACT                        */
+  int32_t validate;     /* nonzero (default): check A and B on the device first      */
+  int64_t out_capacity; /* >0: C->row_ptr/col/val are caller buffers of this capacity */
+  int64_t budget_bytes; /* >0: column-batched; each batch's C (row_ptr+col+val) fits  */
+  cb_batch_fn on_batch; /* required when budget_bytes > 0                             */
+  void *user;           /* passed to on_batch                                         */
+  const cb_mlp *mlp;    /* required when sizing == CB_SIZING_LEARNED                   */
+  float margin;         /* learned sizing: table capacity = pred * (1 + margin)       */
+  int32_t flags;        /* CB_FLAG_* bits, default 0                                  */
+} cb_opts;
+
+/* cb_opts.flags bits. */
+enum {
+  CB_FLAG_CHECK = 1,  /* synchronise at the end and fail (CB_ERR_CUDA) if a kernel's
+                         internal consistency word is set (debug)                   */
+  CB_FLAG_TIMING = 2  /* record CUDA events between the phases on ctx's stream and
+                         report their durations in cb_stats (synchronises at the end) */
+};
+
+/* Fill *opt with defaults (exact sizing, validation on, library-allocated C). */
+void cb_opts_default(cb_opts *opt);
+
+/* Create a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream) on the current device.  The context owns a reusable device
+ * workspace.  Returns CB_OK or CB_ERR_CUDA / CB_ERR_OOM. */
+int cb_ctx_create(cb_ctx **ctx, void *cuda_stream);
+void cb_ctx_destroy(cb_ctx *ctx);
+/* Rebind the context to another stream. */
+int cb_ctx_set_stream(cb_ctx *ctx, void *cuda_stream);
+const char *cb_last_error(const cb_ctx *ctx);
+const char *cb_status_str(int status);
+
+/* C = A (+).(x) B, synchronous convenience form: creates a temporary context
+ * on the default stream, allocates C (free with cb_csr_free), validates the
+ * inputs, and returns when C is complete. */
+int cb_spgemm(cb_semiring sr, const cb_csr *A, const cb_csr *B, cb_csr *C);
+
+/* C = A (+).(x) B on ctx's stream with options (NULL = defaults).
+ *   - If opt->out_capacity > 0, C->row_ptr (nrows+1), C->col and C->val
+ *     (out_capacity entries) are caller-provided device buffers; if nnz(C)
+ *     exceeds out_capacity the call returns CB_ERR_CAPACITY with C->nnz set
+ *     to the required size and nothing written to C->col/val.
+ *   - Otherwise the library allocates C's arrays with stream-ordered
+ *     allocation on ctx's stream; release them with cb_csr_free.
+ *   - If opt->budget_bytes > 0, C is formed in column batches (Sec. 7.2):
+ *     each batch is handed to opt->on_batch and released afterwards; *C
+ *     receives only the shape and the total nnz.
+ * The stream is synchronised once (to learn nnz(C)); on return the output is
+ * complete only in stream order (synchronise before reading it from the host
+ * through another stream). */
+int cb_spgemm_ex(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B,
+                 cb_csr *C, const cb_opts *opt);
+
+/* Release arrays that the library allocated for C; zeroes *C. */
+void cb_csr_free(cb_csr *C);
+
+/* ---- individual steps of the path (device outputs, async) ---------------
+ * cb_row_stats: paper Sec. 5.1 phase (1) and Table 1 ("flops").  For each row
+ *   i of A: flops[i] = sum over stored A(i,p) of nnz(B(p,:)) (int64[m]),
+ *   maxb[i] = max of those B row lengths (int32[m], 0 for empty rows).
+ *   Either output may be NULL.
+ * cb_row_nnz: paper Sec. 5.1 phase (2) ("symbolic phase ... computes the
+ *   pattern").  nnz_out[i] = number of distinct columns in row i of A.B
+ *   (int64[m]).
+ * cb_exclusive_scan: row pointers from row sizes: out[0] = 0,
+ *   out[i+1] = out[i] + in[i] for i < n (int64 in[n], out[n+1]).
+ */
+int cb_row_stats(cb_ctx *ctx, const cb_csr *A, const cb_csr *B, int64_t *flops,
+                 int32_t *maxb);
+int cb_row_nnz(cb_ctx *ctx, const cb_csr *A, const cb_csr *B, int64_t *nnz_out);
+int cb_exclusive_scan(cb_ctx *ctx, const int64_t *in, int64_t n, int64_t *out);
+
+/* Statistics of the most recent cb_spgemm_ex on this context (host memory). */
+typedef struct {
+  int64_t flops;        /* number of (x)-products                              */
+  int64_t nnz;          /* nnz(C)                                              */
+  int64_t heavy_rows;   /* rows computed with the dense column-slice path      */
+  int64_t heavy_units;  /* (row, column slice) units launched for heavy rows   */
+  int64_t overflow_rows;/* rows recomputed exactly after a sizing overflow     */
+  int32_t batches;      /* column batches (1 when not batched)                 */
+  int32_t kernels;      /* kernel launches issued by the call                  */
+  /* phase durations in ms (CB_FLAG_TIMING only, else 0): K1+K2 flops and
+   * binning; K3 symbolic; K4 scan + numeric binning; K5-K7 numeric. */
+  float ms_stats, ms_symbolic, ms_scan, ms_numeric;
+} cb_stats;
+int cb_last_stats(const cb_ctx *ctx, cb_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CB_H_ */

@@ -1,0 +1,330 @@
+"""Python binding of libcb.so (include/cb.h): argument marshalling only.
+
+Every step of the SpGEMM runs in the library's CUDA kernels; PyTorch only
+provides device memory for the inputs and the current CUDA stream.  There is
+no CPU fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+c_int64 = ctypes.c_int64
+c_void_p = ctypes.c_void_p
+
+SEMIRING = {
+    "plus_times_i64": (1, torch.int64),
+    "plus_times_f64": (2, torch.float64),
+    "min_plus_u32": (3, torch.uint32),
+    "or_and_bool": (4, torch.uint8),
+    "sel2nd_min_i32": (5, torch.int32),
+}
+
+SIZING = {"exact": 0, "learned": 1, "upper_bound": 2}
+
+STATUS = {0: "CB_OK", 1: "CB_ERR_ARG", 2: "CB_ERR_SHAPE", 3: "CB_ERR_SEMIRING", 4: "CB_ERR_INDEX",
+          5: "CB_ERR_OOM", 6: "CB_ERR_BUDGET", 7: "CB_ERR_TIMEOUT", 8: "CB_ERR_CUDA",
+          9: "CB_ERR_CAPACITY"}
+
+
+class cb_csr(ctypes.Structure):
+    _fields_ = [("nrows", c_int64), ("ncols", c_int64), ("nnz", c_int64),
+                ("row_ptr", c_void_p), ("col", c_void_p), ("val", c_void_p)]
+
+
+BATCH_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int, c_int64, c_int64, ctypes.POINTER(cb_csr),
+                            c_void_p)
+
+
+class cb_opts(ctypes.Structure):
+    _fields_ = [("sizing", ctypes.c_int32), ("validate", ctypes.c_int32),
+                ("out_capacity", c_int64), ("budget_bytes", c_int64),
+                ("on_batch", BATCH_FN), ("user", c_void_p), ("mlp", c_void_p),
+                ("margin", ctypes.c_float), ("flags", ctypes.c_int32)]
+
+
+class cb_stats(ctypes.Structure):
+    _fields_ = [("flops", c_int64), ("nnz", c_int64), ("heavy_rows", c_int64),
+                ("heavy_units", c_int64), ("overflow_rows", c_int64), ("batches", ctypes.c_int32),
+                ("kernels", ctypes.c_int32), ("ms_stats", ctypes.c_float),
+                ("ms_symbolic", ctypes.c_float), ("ms_scan", ctypes.c_float),
+                ("ms_numeric", ctypes.c_float)]
+
+
+class CBError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+# exported symbol -> (argtypes, restype)
+_SIGS = {
+    "cb_opts_default": ([ctypes.POINTER(cb_opts)], None),
+    "cb_ctx_create": ([ctypes.POINTER(c_void_p), c_void_p], ctypes.c_int),
+    "cb_ctx_destroy": ([c_void_p], None),
+    "cb_ctx_set_stream": ([c_void_p, c_void_p], ctypes.c_int),
+    "cb_last_error": ([c_void_p], ctypes.c_char_p),
+    "cb_status_str": ([ctypes.c_int], ctypes.c_char_p),
+    "cb_spgemm": ([ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr),
+                   ctypes.POINTER(cb_csr)], ctypes.c_int),
+    "cb_spgemm_ex": ([c_void_p, ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr),
+                      ctypes.POINTER(cb_csr), ctypes.POINTER(cb_opts)], ctypes.c_int),
+    "cb_csr_free": ([ctypes.POINTER(cb_csr)], None),
+    "cb_row_stats": ([c_void_p, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr), c_void_p, c_void_p],
+                     ctypes.c_int),
+    "cb_row_nnz": ([c_void_p, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr), c_void_p], ctypes.c_int),
+    "cb_exclusive_scan": ([c_void_p, c_void_p, c_int64, c_void_p], ctypes.c_int),
+    "cb_last_stats": ([c_void_p, ctypes.POINTER(cb_stats)], ctypes.c_int),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcb.so (building it first if allowed); raises if it is unavailable."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError(f"libcb.so not built at {path}")
+                _build.build()
+            lib = ctypes.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return tuple(_SIGS)
+
+
+# ---------------------------------------------------------------------------
+# device matrices
+# ---------------------------------------------------------------------------
+
+@dataclass
+class DeviceCSR:
+    nrows: int
+    ncols: int
+    row_ptr: torch.Tensor   # int64 [nrows + 1]
+    col: torch.Tensor       # int32 [nnz]
+    val: torch.Tensor       # typed [nnz]
+    _owner: object = None   # keeps library-allocated memory alive
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    @staticmethod
+    def from_host(M, semiring: str, device="cuda") -> "DeviceCSR":
+        dt = SEMIRING[semiring][1]
+        val = torch.from_numpy(np.ascontiguousarray(M.val).view(_np_view(dt)))
+        return DeviceCSR(M.nrows, M.ncols,
+                         torch.from_numpy(np.ascontiguousarray(M.row_ptr, dtype=np.int64)).to(device),
+                         torch.from_numpy(np.ascontiguousarray(M.col, dtype=np.int32)).to(device),
+                         val.to(device).view(dt))
+
+    def to_host(self):
+        v = self.val
+        if v.dtype == torch.uint32:
+            v = v.view(torch.int32)
+        val = v.cpu().numpy()
+        if self.val.dtype == torch.uint32:
+            val = val.view(np.uint32)
+        return self.row_ptr.cpu().numpy(), self.col.cpu().numpy(), val
+
+    def as_struct(self) -> cb_csr:
+        return cb_csr(self.nrows, self.ncols, self.nnz, self.row_ptr.data_ptr(),
+                      self.col.data_ptr() if self.nnz else None,
+                      self.val.data_ptr() if self.nnz else None)
+
+
+def _np_view(dt):
+    return {torch.int64: np.int64, torch.float64: np.float64, torch.uint32: np.int32,
+            torch.uint8: np.uint8, torch.int32: np.int32}[dt]
+
+
+_TYPESTR = {torch.int64: "<i8", torch.float64: "<f8", torch.uint32: "<u4", torch.uint8: "|u1",
+            torch.int32: "<i4"}
+
+
+class _Owner:
+    """Frees library-allocated C arrays when the last tensor viewing them dies."""
+
+    def __init__(self, lib, csr: cb_csr):
+        self.lib = lib
+        self.csr = csr
+
+    def __del__(self):
+        try:
+            self.lib.cb_csr_free(ctypes.byref(self.csr))
+        except Exception:
+            pass
+
+
+class _Buf:
+    def __init__(self, ptr: int, n: int, dtype, owner):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": _TYPESTR[dtype],
+                                         "data": (ptr, False), "version": 3, "strides": None}
+        self.owner = owner
+
+
+def _wrap(ptr, n, dtype, owner, device):
+    if n == 0 or not ptr:
+        return torch.empty(0, dtype=dtype, device=device)
+    if dtype == torch.uint32:
+        t = torch.as_tensor(_Buf(ptr, n, torch.int32, owner), device=device)
+        return t.view(torch.uint32)
+    return torch.as_tensor(_Buf(ptr, n, dtype, owner), device=device)
+
+
+# ---------------------------------------------------------------------------
+# contexts (one per device and stream)
+# ---------------------------------------------------------------------------
+
+class Context:
+    def __init__(self, stream: torch.cuda.Stream | None = None):
+        self.lib = load()
+        self.stream = stream or torch.cuda.current_stream()
+        self.handle = c_void_p()
+        rc = self.lib.cb_ctx_create(ctypes.byref(self.handle), c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise CBError(rc, "cb_ctx_create failed")
+
+    def __del__(self):
+        try:
+            if self.handle:
+                self.lib.cb_ctx_destroy(self.handle)
+                self.handle = c_void_p()
+        except Exception:
+            pass
+
+    def error(self) -> str:
+        msg = self.lib.cb_last_error(self.handle)
+        return msg.decode() if msg else ""
+
+    def check(self, rc: int):
+        if rc != 0:
+            raise CBError(rc, self.error())
+
+    def stats(self) -> dict:
+        s = cb_stats()
+        self.check(self.lib.cb_last_stats(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in cb_stats._fields_}
+
+
+_ctx_cache: dict = {}
+
+
+def context(stream: torch.cuda.Stream | None = None) -> Context:
+    stream = stream or torch.cuda.current_stream()
+    key = (stream.device.index, stream.cuda_stream)
+    ctx = _ctx_cache.get(key)
+    if ctx is None:
+        ctx = Context(stream)
+        _ctx_cache[key] = ctx
+    return ctx
+
+
+def make_opts(sizing="exact", validate=True, out_capacity=0, budget_bytes=0, on_batch=None,
+              margin=0.25, flags=0) -> cb_opts:
+    lib = load()
+    o = cb_opts()
+    lib.cb_opts_default(ctypes.byref(o))
+    o.sizing = SIZING[sizing]
+    o.validate = 1 if validate else 0
+    o.out_capacity = int(out_capacity)
+    o.budget_bytes = int(budget_bytes)
+    if on_batch is not None:
+        o.on_batch = on_batch
+    o.margin = float(margin)
+    o.flags = int(flags)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# the calls
+# ---------------------------------------------------------------------------
+
+FLAG_CHECK = 1
+FLAG_TIMING = 2
+
+
+def spgemm(semiring: str, A: DeviceCSR, B: DeviceCSR, *, validate: bool = True, check: bool = False,
+           ctx: Context | None = None, out: DeviceCSR | None = None, sizing: str = "exact",
+           timing: bool = False) -> DeviceCSR:
+    """C = A (+).(x) B on the GPU (cb_spgemm_ex).
+
+    With `out` (a DeviceCSR whose col/val tensors are large enough), C is
+    written into those buffers and a DeviceCSR viewing the first nnz(C)
+    entries is returned; otherwise the library allocates C.
+    `check` adds a synchronising self-consistency check of the kernels.
+    """
+    code, dt = SEMIRING[semiring]
+    ctx = ctx or context()
+    sa, sb = A.as_struct(), B.as_struct()
+    opts = make_opts(sizing=sizing, validate=validate,
+                     flags=(FLAG_CHECK if check else 0) | (FLAG_TIMING if timing else 0))
+    if out is not None:
+        opts.out_capacity = max(1, min(out.col.numel(), out.val.numel()))
+        sc = cb_csr(0, 0, 0, out.row_ptr.data_ptr(), out.col.data_ptr(), out.val.data_ptr())
+        ctx.check(ctx.lib.cb_spgemm_ex(ctx.handle, code, ctypes.byref(sa), ctypes.byref(sb),
+                                       ctypes.byref(sc), ctypes.byref(opts)))
+        n = sc.nnz
+        return DeviceCSR(sc.nrows, sc.ncols, out.row_ptr[:sc.nrows + 1], out.col[:n], out.val[:n])
+    sc = cb_csr()
+    ctx.check(ctx.lib.cb_spgemm_ex(ctx.handle, code, ctypes.byref(sa), ctypes.byref(sb),
+                                   ctypes.byref(sc), ctypes.byref(opts)))
+    owner = _Owner(ctx.lib, cb_csr(sc.nrows, sc.ncols, sc.nnz, sc.row_ptr, sc.col, sc.val))
+    dev = A.row_ptr.device
+    return DeviceCSR(sc.nrows, sc.ncols, _wrap(sc.row_ptr, sc.nrows + 1, torch.int64, owner, dev),
+                     _wrap(sc.col, sc.nnz, torch.int32, owner, dev),
+                     _wrap(sc.val, sc.nnz, dt, owner, dev), owner)
+
+
+def row_stats(A: DeviceCSR, B: DeviceCSR, ctx: Context | None = None):
+    """(flops[m] int64, maxb[m] int32) on the device (cb_row_stats)."""
+    ctx = ctx or context()
+    dev = A.row_ptr.device
+    flops = torch.empty(A.nrows, dtype=torch.int64, device=dev)
+    maxb = torch.empty(A.nrows, dtype=torch.int32, device=dev)
+    sa, sb = A.as_struct(), B.as_struct()
+    ctx.check(ctx.lib.cb_row_stats(ctx.handle, ctypes.byref(sa), ctypes.byref(sb),
+                                   c_void_p(flops.data_ptr()), c_void_p(maxb.data_ptr())))
+    return flops, maxb
+
+
+def row_nnz(A: DeviceCSR, B: DeviceCSR, ctx: Context | None = None) -> torch.Tensor:
+    """Exact nnz of every row of A.B on the device (cb_row_nnz, the symbolic phase)."""
+    ctx = ctx or context()
+    out = torch.empty(A.nrows, dtype=torch.int64, device=A.row_ptr.device)
+    sa, sb = A.as_struct(), B.as_struct()
+    ctx.check(ctx.lib.cb_row_nnz(ctx.handle, ctypes.byref(sa), ctypes.byref(sb),
+                                 c_void_p(out.data_ptr())))
+    return out
+
+
+def exclusive_scan(x: torch.Tensor, ctx: Context | None = None) -> torch.Tensor:
+    ctx = ctx or context()
+    assert x.dtype == torch.int64 and x.is_contiguous()
+    out = torch.empty(x.numel() + 1, dtype=torch.int64, device=x.device)
+    ctx.check(ctx.lib.cb_exclusive_scan(ctx.handle, c_void_p(x.data_ptr()), x.numel(),
+                                        c_void_p(out.data_ptr())))
+    return out

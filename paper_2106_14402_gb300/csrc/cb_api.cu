@@ -1,0 +1,493 @@
+// C ABI of the semiring SpGEMM (include/cb.h): argument checks, workspace
+// management and the host-side plan that orders the kernels of the path on
+// one stream:
+//   validate? -> K1 flops + tiers -> K2 scatter -> [sync: tier sizes]
+//   -> K3 symbolic (hash tiers + heavy bitmap slices) -> K4 scan -> numeric
+//   binning + heavy units -> [sync: nnz(C)] -> allocate C -> K5-K7 numeric.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/cb.h"
+#include "cb_common.cuh"
+#include "cb_kernels.h"
+
+struct cb_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sms = 0;
+  void* ws = nullptr;   // workspace for per-row arrays
+  size_t ws_cap = 0;
+  void* ws2 = nullptr;  // workspace for heavy-row slice arrays
+  size_t ws2_cap = 0;
+  int64_t* host = nullptr;  // pinned read-back buffer
+  cudaEvent_t ev[6] = {};   // phase boundaries (CB_FLAG_TIMING)
+  std::string err;
+  cb_stats stats{};
+};
+
+namespace {
+
+using cb::DevCSR;
+
+struct Fail {
+  int code;
+};
+
+#define CB_CUDA(call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+      throw Fail{e_ == cudaErrorMemoryAllocation ? CB_ERR_OOM : CB_ERR_CUDA};         \
+    }                                                                                 \
+  } while (0)
+
+#define CB_LAUNCHED()                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = cudaGetLastError();                                              \
+    if (e_ != cudaSuccess) {                                                          \
+      ctx->err = std::string("kernel launch: ") + cudaGetErrorString(e_);             \
+      throw Fail{CB_ERR_CUDA};                                                        \
+    }                                                                                 \
+  } while (0)
+
+void fail(cb_ctx* ctx, int code, const std::string& msg) {
+  ctx->err = msg;
+  throw Fail{code};
+}
+
+size_t value_size(int sr) {
+  switch (sr) {
+    case CB_PLUS_TIMES_I64: return 8;
+    case CB_PLUS_TIMES_F64: return 8;
+    case CB_MIN_PLUS_U32: return 4;
+    case CB_OR_AND_BOOL: return 1;
+    case CB_SEL2ND_MIN_I32: return 4;
+  }
+  return 0;
+}
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Bump allocator over a workspace buffer.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t n) {
+    T* p = reinterpret_cast<T*>(base + off);
+    off += align_up(n * sizeof(T));
+    return p;
+  }
+};
+
+void ensure(cb_ctx* ctx, void** buf, size_t* cap, size_t need) {
+  if (need <= *cap) return;
+  size_t want = need + need / 4 + (1 << 20);
+  if (*buf) CB_CUDA(cudaFreeAsync(*buf, ctx->stream));
+  *buf = nullptr;
+  *cap = 0;
+  CB_CUDA(cudaMallocAsync(buf, want, ctx->stream));
+  *cap = want;
+}
+
+void check_operand(cb_ctx* ctx, const cb_csr* M, const char* name) {
+  if (M->nrows < 0 || M->ncols < 0 || M->nnz < 0)
+    fail(ctx, CB_ERR_ARG, std::string(name) + ": negative size");
+  if (!M->row_ptr) fail(ctx, CB_ERR_ARG, std::string(name) + ": null row_ptr");
+  if (M->nnz > 0 && (!M->col || !M->val))
+    fail(ctx, CB_ERR_ARG, std::string(name) + ": null col/val with nnz > 0");
+  if (M->ncols > INT32_MAX || M->nrows >= INT32_MAX)
+    fail(ctx, CB_ERR_INDEX, std::string(name) + ": dimension beyond int32 indices");
+}
+
+DevCSR dev(const cb_csr* M) { return DevCSR{M->nrows, M->ncols, M->row_ptr, M->col, M->val}; }
+
+void read_counters(cb_ctx* ctx, const int64_t* counters, const int64_t* extra, int n_extra) {
+  CB_CUDA(cudaMemcpyAsync(ctx->host, counters, sizeof(int64_t) * cb::kCounters,
+                          cudaMemcpyDeviceToHost, ctx->stream));
+  if (n_extra)
+    CB_CUDA(cudaMemcpyAsync(ctx->host + cb::kCounters, extra, sizeof(int64_t) * n_extra,
+                            cudaMemcpyDeviceToHost, ctx->stream));
+  CB_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+void run_validation(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, int64_t* counters) {
+  CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+  cb::launch_validate(dev(A), A->nnz, 0, counters, ctx->stream, ctx->sms);
+  cb::launch_validate(dev(B), B->nnz, 10, counters, ctx->stream, ctx->sms);
+  CB_LAUNCHED();
+  ctx->stats.kernels += 2;
+  read_counters(ctx, counters, nullptr, 0);
+  const int64_t e = ctx->host[cb::kError];
+  if (e) {
+    char msg[160];
+    std::snprintf(msg, sizeof msg, "%s: %s invalid at index %lld", e >= 10 ? "B" : "A",
+                  (e % 10) == 1 ? "row_ptr" : "column index",
+                  (long long)ctx->host[cb::kErrDetail]);
+    fail(ctx, CB_ERR_INDEX, msg);
+  }
+}
+
+void mark(cb_ctx* ctx, const cb_opts& opt, int k) {
+  if (!(opt.flags & CB_FLAG_TIMING)) return;
+  if (!ctx->ev[k]) CB_CUDA(cudaEventCreate(&ctx->ev[k]));
+  CB_CUDA(cudaEventRecord(ctx->ev[k], ctx->stream));
+}
+
+void collect_times(cb_ctx* ctx, const cb_opts& opt, bool numeric_ran) {
+  if (!(opt.flags & CB_FLAG_TIMING)) return;
+  CB_CUDA(cudaEventSynchronize(ctx->ev[numeric_ran ? 5 : 3]));
+  float t = 0.f;
+  CB_CUDA(cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[1]));
+  ctx->stats.ms_stats = t;
+  CB_CUDA(cudaEventElapsedTime(&t, ctx->ev[1], ctx->ev[2]));
+  ctx->stats.ms_symbolic = t;
+  CB_CUDA(cudaEventElapsedTime(&t, ctx->ev[2], ctx->ev[3]));
+  ctx->stats.ms_scan = t;
+  if (numeric_ran) {
+    CB_CUDA(cudaEventElapsedTime(&t, ctx->ev[4], ctx->ev[5]));
+    ctx->stats.ms_numeric = t;
+  }
+}
+
+// Everything from K1 to the allocation of C and the numeric phase.
+void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_csr* C,
+                  const cb_opts& opt) {
+  const int64_t m = A->nrows, ncols = B->ncols;
+  const bool caller_buf = opt.out_capacity > 0;
+  const size_t vsz = value_size(sr);
+
+  // stage-1 workspace: counters, per-row arrays, scan partials
+  size_t need = align_up(sizeof(int64_t) * cb::kCounters) + 3 * align_up(8 * (size_t)m + 8) +
+                2 * align_up(4 * (size_t)m + 4) + align_up(8 * (size_t)cb::scan_partials(m));
+  ensure(ctx, &ctx->ws, &ctx->ws_cap, need);
+  Carver cv{static_cast<char*>(ctx->ws)};
+  int64_t* counters = cv.take<int64_t>(cb::kCounters);
+  int64_t* flops = cv.take<int64_t>(m + 1);
+  int64_t* nnz = cv.take<int64_t>(m + 1);
+  int32_t* maxb = cv.take<int32_t>(m + 1);
+  int32_t* perm_sym = cv.take<int32_t>(m + 1);
+  int32_t* perm_num = cv.take<int32_t>(m + 1);
+  int64_t* partial = cv.take<int64_t>(cb::scan_partials(m));
+  (void)maxb;
+
+  if (opt.validate) run_validation(ctx, A, B, counters);
+
+  C->nrows = m;
+  C->ncols = ncols;
+  C->nnz = 0;
+  if (!caller_buf) {
+    C->row_ptr = nullptr;
+    C->col = nullptr;
+    C->val = nullptr;
+    CB_CUDA(cudaMallocAsync((void**)&C->row_ptr, sizeof(int64_t) * (size_t)(m + 1), ctx->stream));
+  }
+  if (m == 0) {
+    CB_CUDA(cudaMemsetAsync(C->row_ptr, 0, sizeof(int64_t), ctx->stream));
+    return;
+  }
+
+  const DevCSR dA = dev(A), dB = dev(B);
+  CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+  mark(ctx, opt, 0);
+  cb::launch_classify_sym(dA, dB, flops, maxb, counters, ctx->stream, ctx->sms);
+  cb::launch_scatter_sym(m, ncols, flops, perm_sym, nnz, counters, ctx->stream, ctx->sms);
+  CB_LAUNCHED();
+  mark(ctx, opt, 1);
+  ctx->stats.kernels += 2;
+  read_counters(ctx, counters, nullptr, 0);
+
+  int64_t sym_cnt[cb::kSymTiers], sym_beg[cb::kSymTiers];
+  for (int t = 0; t < cb::kSymTiers; ++t) sym_cnt[t] = ctx->host[cb::kCntSym + t];
+  sym_beg[0] = 0;
+  sym_beg[1] = 0;
+  for (int t = 2; t < cb::kSymTiers; ++t) sym_beg[t] = sym_beg[t - 1] + sym_cnt[t - 1];
+  ctx->stats.flops = ctx->host[cb::kTotalFlops];
+  const int64_t n_heavy = sym_cnt[cb::kSymHeavy];
+  const int64_t wnum = cb::num_slice_width(sr);
+  const int64_t num_slices = (ncols + wnum - 1) / wnum;
+
+  size_t need2 = align_up(4 * (size_t)(n_heavy * num_slices) + 4) +
+                 align_up(8 * (size_t)(n_heavy * num_slices) + 8);
+  ensure(ctx, &ctx->ws2, &ctx->ws2_cap, need2);
+  Carver cv2{static_cast<char*>(ctx->ws2)};
+  int32_t* slice_counts = cv2.take<int32_t>(n_heavy * num_slices + 1);
+  int2* units = cv2.take<int2>(n_heavy * num_slices + 1);
+  const int32_t* heavy_rows = perm_sym + sym_beg[cb::kSymHeavy];
+
+  int launches = 0;
+  cb::launch_symbolic(dA, dB, perm_sym, sym_beg, sym_cnt, flops, nnz, slice_counts, wnum,
+                      num_slices, ctx->stream, ctx->sms, &launches);
+  mark(ctx, opt, 2);
+  cb::launch_exclusive_scan(nnz, m, C->row_ptr, partial, ctx->stream);
+  cb::launch_classify_num(sr, m, nnz, perm_num, counters, ctx->stream, ctx->sms);
+  cb::launch_build_units(sr, n_heavy, heavy_rows, nnz, slice_counts, num_slices, units, counters,
+                         ctx->stream);
+  CB_LAUNCHED();
+  mark(ctx, opt, 3);
+  ctx->stats.kernels += launches + 3 + 2 + (n_heavy ? 1 : 0);
+  read_counters(ctx, counters, C->row_ptr + m, 1);
+
+  const int64_t total = ctx->host[cb::kCounters];
+  int64_t num_cnt[cb::kNumTiers], num_beg[cb::kNumTiers];
+  for (int t = 0; t < cb::kNumTiers; ++t) num_cnt[t] = ctx->host[cb::kCntNum + t];
+  num_beg[0] = 0;
+  num_beg[1] = 0;
+  for (int t = 2; t < cb::kNumTiers; ++t) num_beg[t] = num_beg[t - 1] + num_cnt[t - 1];
+  const int64_t n_units = ctx->host[cb::kUnits];
+  ctx->stats.nnz = total;
+  ctx->stats.heavy_rows = num_cnt[cb::kNumHeavy];
+  ctx->stats.heavy_units = n_units;
+  C->nnz = total;
+
+  if (caller_buf) {
+    if (total > opt.out_capacity) {
+      char msg[128];
+      std::snprintf(msg, sizeof msg, "output needs %lld entries, capacity %lld",
+                    (long long)total, (long long)opt.out_capacity);
+      ctx->err = msg;
+      throw Fail{CB_ERR_CAPACITY};
+    }
+  } else if (total > 0) {
+    CB_CUDA(cudaMallocAsync((void**)&C->col, sizeof(int32_t) * (size_t)total, ctx->stream));
+    CB_CUDA(cudaMallocAsync(&C->val, vsz * (size_t)total, ctx->stream));
+  }
+  if (total == 0) {
+    collect_times(ctx, opt, false);
+    return;
+  }
+
+  launches = 0;
+  mark(ctx, opt, 4);
+  cb::launch_numeric(sr, dA, dB, perm_num, num_beg, num_cnt, flops, nnz, heavy_rows, units,
+                     n_units, slice_counts, num_slices, C->row_ptr, C->col, C->val,
+                     counters + cb::kError, ctx->stream, ctx->sms, &launches);
+  CB_LAUNCHED();
+  mark(ctx, opt, 5);
+  ctx->stats.kernels += launches;
+  collect_times(ctx, opt, true);
+
+  if (opt.flags & 1) {  // debug: check the kernels' internal consistency word
+    read_counters(ctx, counters, nullptr, 0);
+    if (ctx->host[cb::kError]) {
+      char msg[96];
+      std::snprintf(msg, sizeof msg, "internal consistency check failed (code %lld)",
+                    (long long)ctx->host[cb::kError]);
+      fail(ctx, CB_ERR_CUDA, msg);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void cb_opts_default(cb_opts* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof *opt);
+  opt->sizing = CB_SIZING_EXACT;
+  opt->validate = 1;
+  opt->margin = 0.25f;
+}
+
+int cb_ctx_create(cb_ctx** out, void* stream) {
+  if (!out) return CB_ERR_ARG;
+  *out = nullptr;
+  cb_ctx* ctx = new (std::nothrow) cb_ctx();
+  if (!ctx) return CB_ERR_OOM;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess ||
+      cudaMallocHost((void**)&ctx->host, sizeof(int64_t) * (cb::kCounters + 64)) != cudaSuccess) {
+    delete ctx;
+    return CB_ERR_CUDA;
+  }
+  *out = ctx;
+  return CB_OK;
+}
+
+void cb_ctx_destroy(cb_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->ws || ctx->ws2) cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->ws2) cudaFree(ctx->ws2);
+  if (ctx->host) cudaFreeHost(ctx->host);
+  for (cudaEvent_t e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+}
+
+int cb_ctx_set_stream(cb_ctx* ctx, void* stream) {
+  if (!ctx) return CB_ERR_ARG;
+  if (ctx->stream != static_cast<cudaStream_t>(stream)) {
+    // Workspace was allocated in the old stream's order; finish that work first.
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return CB_ERR_CUDA;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+  }
+  return CB_OK;
+}
+
+const char* cb_last_error(const cb_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+const char* cb_status_str(int s) {
+  switch (s) {
+    case CB_OK: return "ok";
+    case CB_ERR_ARG: return "invalid argument";
+    case CB_ERR_SHAPE: return "shape mismatch (A.ncols != B.nrows)";
+    case CB_ERR_SEMIRING: return "unknown semiring";
+    case CB_ERR_INDEX: return "invalid CSR index data";
+    case CB_ERR_OOM: return "device out of memory";
+    case CB_ERR_BUDGET: return "output budget too small";
+    case CB_ERR_TIMEOUT: return "bounded device wait expired";
+    case CB_ERR_CUDA: return "CUDA error";
+    case CB_ERR_CAPACITY: return "caller-provided output too small";
+  }
+  return "unknown status";
+}
+
+int cb_spgemm_ex(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, cb_csr* C,
+                 const cb_opts* opt_in) {
+  if (!ctx) return CB_ERR_ARG;
+  ctx->err.clear();
+  ctx->stats = cb_stats{};
+  ctx->stats.batches = 1;
+  cb_opts opt;
+  if (opt_in) opt = *opt_in;
+  else cb_opts_default(&opt);
+  const bool caller_buf = opt.out_capacity > 0;
+  cb_csr saved{};
+  if (C) saved = *C;
+  try {
+    if (!A || !B || !C) fail(ctx, CB_ERR_ARG, "null matrix argument");
+    if (value_size(sr) == 0) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
+    check_operand(ctx, A, "A");
+    check_operand(ctx, B, "B");
+    if (A->ncols != B->nrows) fail(ctx, CB_ERR_SHAPE, "A.ncols != B.nrows");
+    if (caller_buf && (!C->row_ptr || !C->col || !C->val))
+      fail(ctx, CB_ERR_ARG, "out_capacity > 0 needs C->row_ptr, C->col and C->val");
+    if (opt.sizing != CB_SIZING_EXACT) fail(ctx, CB_ERR_ARG, "sizing mode not supported");
+    if (opt.budget_bytes > 0) fail(ctx, CB_ERR_ARG, "column batching not supported");
+    spgemm_plain(ctx, (int)sr, A, B, C, opt);
+    return CB_OK;
+  } catch (const Fail& f) {
+    if (!caller_buf && C) {
+      cudaStreamSynchronize(ctx->stream);
+      if (C->row_ptr && C->row_ptr != saved.row_ptr) cudaFree(C->row_ptr);
+      if (C->col && C->col != saved.col) cudaFree(C->col);
+      if (C->val && C->val != saved.val) cudaFree(C->val);
+      std::memset(C, 0, sizeof *C);
+    }
+    return f.code;
+  }
+}
+
+int cb_spgemm(cb_semiring sr, const cb_csr* A, const cb_csr* B, cb_csr* C) {
+  cb_ctx* ctx = nullptr;
+  int rc = cb_ctx_create(&ctx, nullptr);
+  if (rc != CB_OK) return rc;
+  rc = cb_spgemm_ex(ctx, sr, A, B, C, nullptr);
+  if (rc == CB_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    rc = CB_ERR_CUDA;
+    cb_csr_free(C);
+  }
+  cb_ctx_destroy(ctx);
+  return rc;
+}
+
+void cb_csr_free(cb_csr* C) {
+  if (!C) return;
+  if (C->row_ptr) cudaFree(C->row_ptr);
+  if (C->col) cudaFree(C->col);
+  if (C->val) cudaFree(C->val);
+  std::memset(C, 0, sizeof *C);
+}
+
+int cb_row_stats(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, int64_t* flops, int32_t* maxb) {
+  if (!ctx) return CB_ERR_ARG;
+  ctx->err.clear();
+  try {
+    if (!A || !B) fail(ctx, CB_ERR_ARG, "null matrix argument");
+    check_operand(ctx, A, "A");
+    check_operand(ctx, B, "B");
+    if (A->ncols != B->nrows) fail(ctx, CB_ERR_SHAPE, "A.ncols != B.nrows");
+    const int64_t m = A->nrows;
+    size_t need = align_up(sizeof(int64_t) * cb::kCounters) + align_up(8 * (size_t)m + 8);
+    ensure(ctx, &ctx->ws, &ctx->ws_cap, need);
+    Carver cv{static_cast<char*>(ctx->ws)};
+    int64_t* counters = cv.take<int64_t>(cb::kCounters);
+    int64_t* f = flops ? flops : cv.take<int64_t>(m + 1);
+    if (m == 0) return CB_OK;
+    CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+    cb::launch_classify_sym(dev(A), dev(B), f, maxb, counters, ctx->stream, ctx->sms);
+    CB_LAUNCHED();
+    return CB_OK;
+  } catch (const Fail& f) {
+    return f.code;
+  }
+}
+
+int cb_row_nnz(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, int64_t* nnz_out) {
+  if (!ctx) return CB_ERR_ARG;
+  ctx->err.clear();
+  try {
+    if (!A || !B || !nnz_out) fail(ctx, CB_ERR_ARG, "null argument");
+    check_operand(ctx, A, "A");
+    check_operand(ctx, B, "B");
+    if (A->ncols != B->nrows) fail(ctx, CB_ERR_SHAPE, "A.ncols != B.nrows");
+    const int64_t m = A->nrows, ncols = B->ncols;
+    if (m == 0) return CB_OK;
+    size_t need = align_up(sizeof(int64_t) * cb::kCounters) + align_up(8 * (size_t)m + 8) +
+                  align_up(4 * (size_t)m + 4);
+    ensure(ctx, &ctx->ws, &ctx->ws_cap, need);
+    Carver cv{static_cast<char*>(ctx->ws)};
+    int64_t* counters = cv.take<int64_t>(cb::kCounters);
+    int64_t* flops = cv.take<int64_t>(m + 1);
+    int32_t* perm = cv.take<int32_t>(m + 1);
+    const DevCSR dA = dev(A), dB = dev(B);
+    CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+    cb::launch_classify_sym(dA, dB, flops, nullptr, counters, ctx->stream, ctx->sms);
+    cb::launch_scatter_sym(m, ncols, flops, perm, nnz_out, counters, ctx->stream, ctx->sms);
+    CB_LAUNCHED();
+    read_counters(ctx, counters, nullptr, 0);
+    int64_t cnt[cb::kSymTiers], beg[cb::kSymTiers];
+    for (int t = 0; t < cb::kSymTiers; ++t) cnt[t] = ctx->host[cb::kCntSym + t];
+    beg[0] = beg[1] = 0;
+    for (int t = 2; t < cb::kSymTiers; ++t) beg[t] = beg[t - 1] + cnt[t - 1];
+    const int64_t n_heavy = cnt[cb::kSymHeavy];
+    const int64_t wnum = cb::num_slice_width(CB_PLUS_TIMES_I64);
+    const int64_t slices = (ncols + wnum - 1) / wnum;
+    ensure(ctx, &ctx->ws2, &ctx->ws2_cap, align_up(4 * (size_t)(n_heavy * slices) + 4));
+    int launches = 0;
+    cb::launch_symbolic(dA, dB, perm, beg, cnt, flops, nnz_out, static_cast<int32_t*>(ctx->ws2),
+                        wnum, slices, ctx->stream, ctx->sms, &launches);
+    CB_LAUNCHED();
+    return CB_OK;
+  } catch (const Fail& f) {
+    return f.code;
+  }
+}
+
+int cb_exclusive_scan(cb_ctx* ctx, const int64_t* in, int64_t n, int64_t* out) {
+  if (!ctx) return CB_ERR_ARG;
+  ctx->err.clear();
+  try {
+    if (n < 0 || !out || (n > 0 && !in)) fail(ctx, CB_ERR_ARG, "bad scan arguments");
+    ensure(ctx, &ctx->ws, &ctx->ws_cap, align_up(8 * (size_t)cb::scan_partials(n)));
+    cb::launch_exclusive_scan(in, n, out, static_cast<int64_t*>(ctx->ws), ctx->stream);
+    CB_LAUNCHED();
+    return CB_OK;
+  } catch (const Fail& f) {
+    return f.code;
+  }
+}
+
+int cb_last_stats(const cb_ctx* ctx, cb_stats* out) {
+  if (!ctx || !out) return CB_ERR_ARG;
+  *out = ctx->stats;
+  return CB_OK;
+}
+
+}  // extern "C"

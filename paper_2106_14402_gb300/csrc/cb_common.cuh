@@ -1,0 +1,168 @@
+// Device-side building blocks shared by the SpGEMM kernels: semiring
+// traits, the shared-memory hash probe, team synchronisation and the
+// tier limits that the host dispatcher and the kernels agree on.
+#pragma once
+
+#include <cstdint>
+#include <climits>
+#include <cuda_runtime.h>
+
+namespace cb {
+
+// ---------------------------------------------------------------------------
+// Semirings (paper Sec. 1: user-defined (+) and (x); the five below are the
+// ones this library instantiates).  A = accumulator type held in shared
+// memory; T = value type in the CSR arrays.  Every (+) here is commutative
+// and associative on A, so products may be combined in any order with
+// atomics; for fp64 that changes rounding only.
+// ---------------------------------------------------------------------------
+template <int SR> struct Sem;
+
+template <> struct Sem<1> {  // (+,x) over int64, wrapping
+  typedef int64_t T;
+  typedef unsigned long long A;
+  static constexpr bool kUsesA = true;
+  __device__ static __forceinline__ A ident() { return 0ull; }
+  __device__ static __forceinline__ A mul(T a, T b) { return (A)a * (A)b; }
+  __device__ static __forceinline__ A add(A x, A y) { return x + y; }
+  __device__ static __forceinline__ void atomic(A* p, A v) { atomicAdd(p, v); }
+  __device__ static __forceinline__ T out(A x) { return (T)x; }
+};
+
+template <> struct Sem<2> {  // (+,x) over fp64
+  typedef double T;
+  typedef double A;
+  static constexpr bool kUsesA = true;
+  __device__ static __forceinline__ A ident() { return 0.0; }
+  __device__ static __forceinline__ A mul(T a, T b) { return __dmul_rn(a, b); }
+  __device__ static __forceinline__ A add(A x, A y) { return __dadd_rn(x, y); }
+  __device__ static __forceinline__ void atomic(A* p, A v) { atomicAdd(p, v); }
+  __device__ static __forceinline__ T out(A x) { return x; }
+};
+
+template <> struct Sem<3> {  // (min,+) over uint32, + saturating at UINT32_MAX
+  typedef uint32_t T;
+  typedef unsigned A;
+  static constexpr bool kUsesA = true;
+  __device__ static __forceinline__ A ident() { return 0xFFFFFFFFu; }
+  __device__ static __forceinline__ A mul(T a, T b) {
+    unsigned s = a + b;
+    return s < a ? 0xFFFFFFFFu : s;
+  }
+  __device__ static __forceinline__ A add(A x, A y) { return x < y ? x : y; }
+  __device__ static __forceinline__ void atomic(A* p, A v) { atomicMin(p, v); }
+  __device__ static __forceinline__ T out(A x) { return x; }
+};
+
+template <> struct Sem<4> {  // (or,and) over bool (uint8 storage)
+  typedef uint8_t T;
+  typedef unsigned A;
+  static constexpr bool kUsesA = true;
+  __device__ static __forceinline__ A ident() { return 0u; }
+  __device__ static __forceinline__ A mul(T a, T b) { return (a != 0 && b != 0) ? 1u : 0u; }
+  __device__ static __forceinline__ A add(A x, A y) { return x | y; }
+  __device__ static __forceinline__ void atomic(A* p, A v) { if (v) atomicOr(p, v); }
+  __device__ static __forceinline__ T out(A x) { return x ? 1 : 0; }
+};
+
+template <> struct Sem<5> {  // (select2nd,min) over int32
+  typedef int32_t T;
+  typedef int A;
+  static constexpr bool kUsesA = false;
+  __device__ static __forceinline__ A ident() { return INT_MAX; }
+  __device__ static __forceinline__ A mul(T, T b) { return b; }
+  __device__ static __forceinline__ A add(A x, A y) { return x < y ? x : y; }
+  __device__ static __forceinline__ void atomic(A* p, A v) { atomicMin(p, v); }
+  __device__ static __forceinline__ T out(A x) { return x; }
+};
+
+// ---------------------------------------------------------------------------
+// Tier limits.  Symbolic tiers are chosen by u_i = min(flops_i, ncols) (an
+// upper bound of nnz(C_i)); numeric tiers by the exact nnz(C_i).  A row
+// whose bound exceeds kSymHashMax is counted with a dense bitmap instead of
+// a hash table; a row whose nnz exceeds the numeric hash limit is computed
+// by dense column slices.  kSymHashMax <= every numeric hash limit, so each
+// numeric-heavy row was counted slice by slice in the symbolic phase.
+// ---------------------------------------------------------------------------
+constexpr int kEmptyKey = -1;
+
+constexpr int kSymWarpMax = 128;     // warp team, table <= 256 slots
+constexpr int kSymSmallMax = 1024;   // 256-thread team, table <= 2048
+constexpr int kSymHashMax = 4096;    // 1024-thread team, table <= 8192
+constexpr int kSymSliceBits = 1 << 20;  // dense bitmap slice (128 KB)
+
+constexpr int kNumWarpMax = 64;      // warp team, table <= 128
+constexpr int kNumSmallMax = 512;    // 256-thread team, table <= 1024
+template <int SR> struct NumLimits {
+  // The large hash tier keeps keys + accumulators for <= kHashMax entries at
+  // a load factor <= 1/2; the dense slice keeps kSlice accumulators + bitmap.
+  static constexpr int kHashMax = sizeof(typename Sem<SR>::A) == 8 ? 4096 : 8192;
+  static constexpr int kSlice = sizeof(typename Sem<SR>::A) == 8 ? 16384 : 32768;
+};
+
+enum SymTier { kSymEmpty = 0, kSymWarp = 1, kSymSmall = 2, kSymLarge = 3, kSymHeavy = 4, kSymTiers = 5 };
+enum NumTier { kNumEmpty = 0, kNumWarp = 1, kNumSmall = 2, kNumLarge = 3, kNumHeavy = 4, kNumTiers = 5 };
+
+__device__ __forceinline__ int sym_tier(int64_t u) {
+  return u == 0 ? kSymEmpty : u <= kSymWarpMax ? kSymWarp : u <= kSymSmallMax ? kSymSmall
+         : u <= kSymHashMax ? kSymLarge : kSymHeavy;
+}
+
+template <int SR>
+__device__ __forceinline__ int num_tier(int64_t nz) {
+  return nz == 0 ? kNumEmpty : nz <= kNumWarpMax ? kNumWarp : nz <= kNumSmallMax ? kNumSmall
+         : nz <= NumLimits<SR>::kHashMax ? kNumLarge : kNumHeavy;
+}
+
+// Smallest power of two >= x (x >= 1), as log2.
+__host__ __device__ __forceinline__ int ceil_log2(int64_t x) {
+  int l = 0;
+  while ((int64_t(1) << l) < x) ++l;
+  return l;
+}
+
+// Fibonacci hashing into a table of 2^bits slots (bits in [1, 31]).
+__device__ __forceinline__ uint32_t hash_slot(int32_t c, int shift) {
+  return ((uint32_t)c * 2654435769u) >> shift;
+}
+
+// Find the slot of key c in an open-addressing (linear probing) table of
+// mask+1 slots, inserting it if absent.  Returns the slot, or -1 if the
+// table is full (never happens for tables sized >= 2x the row bound).
+// `inserted` reports whether this call created the key.
+__device__ __forceinline__ int probe_insert(int* keys, uint32_t mask, int shift, int c,
+                                           bool& inserted) {
+  uint32_t s = hash_slot(c, shift);
+  inserted = false;
+  for (uint32_t n = 0; n <= mask; ++n) {
+    int k = *(volatile int*)&keys[s];
+    if (k == c) return (int)s;
+    if (k == kEmptyKey) {
+      int old = atomicCAS(&keys[s], kEmptyKey, c);
+      if (old == kEmptyKey) { inserted = true; return (int)s; }
+      if (old == c) return (int)s;
+    }
+    s = (s + 1) & mask;
+  }
+  return -1;
+}
+
+template <int TEAM>
+__device__ __forceinline__ void team_sync() {
+  if (TEAM == 32) __syncwarp();
+  else __syncthreads();
+}
+
+// Group size (lanes per stored A entry) for a row: the power of two nearest
+// below the mean B-row length, clamped to [1, TEAM_MAX].
+template <int TEAM_MAX>
+__device__ __forceinline__ int group_log2(int64_t flops, int64_t nnz_a) {
+  if (nnz_a <= 0) return 0;
+  int64_t avg = flops / nnz_a;
+  int g = 0;
+  while (g < 5 && (int64_t(2) << g) <= avg) ++g;
+  int lim = TEAM_MAX >= 32 ? 5 : ceil_log2(TEAM_MAX);
+  return g < lim ? g : lim;
+}
+
+}  // namespace cb

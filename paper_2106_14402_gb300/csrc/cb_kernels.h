@@ -1,0 +1,75 @@
+// Host-side launch wrappers for the SpGEMM kernels (no templates cross this
+// header, so the C ABI layer compiles without the device code).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cb {
+
+struct DevCSR {
+  int64_t nrows, ncols;
+  const int64_t* rp;
+  const int32_t* col;
+  const void* val;
+};
+
+// Counters block in device memory (int64 each).
+enum Counter {
+  kCntSym = 0,          // [5] rows per symbolic tier
+  kCurSym = 5,          // [5] scatter cursors
+  kCntNum = 10,         // [5] rows per numeric tier
+  kCurNum = 15,         // [5]
+  kTotalFlops = 20,
+  kUnits = 21,          // heavy (row, slice) units
+  kError = 22,          // validation / overflow error word
+  kErrDetail = 23,
+  kCounters = 32
+};
+
+// Validation of one CSR operand: row_ptr[0] == 0, non-decreasing,
+// row_ptr[n] == nnz, 0 <= col < ncols.  Sets counters[kError] to a nonzero
+// code on failure (1 = row_ptr, 2 = column), kErrDetail to an offending index.
+void launch_validate(const DevCSR& M, int64_t nnz, int code_base, int64_t* counters,
+                     cudaStream_t s, int sms);
+
+// K1: flops_i, maxB_i and the symbolic tier histogram; total flops.
+void launch_classify_sym(const DevCSR& A, const DevCSR& B, int64_t* flops, int32_t* maxb,
+                         int64_t* counters, cudaStream_t s, int sms);
+// K2: rows into per-tier segments of perm; heavy rows also get nnz[i] = 0.
+void launch_scatter_sym(int64_t m, int64_t ncols, const int64_t* flops, int32_t* perm,
+                        int64_t* nnz, int64_t* counters, cudaStream_t s, int sms);
+
+// K4: out[0] = 0, out[i+1] = out[i] + in[i]; partial needs scan_partials(n) int64.
+int64_t scan_partials(int64_t n);
+void launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* partial,
+                           cudaStream_t s);
+
+// Numeric binning by exact row size, and heavy (row, slice) unit list.
+void launch_classify_num(int sr, int64_t m, const int64_t* nnz, int32_t* perm,
+                         int64_t* counters, cudaStream_t s, int sms);
+void launch_build_units(int sr, int64_t n_heavy, const int32_t* heavy_rows, const int64_t* nnz,
+                        const int32_t* slice_counts, int64_t slices, int2* units,
+                        int64_t* counters, cudaStream_t s);
+
+// K3: symbolic phase, all tiers.  perm holds the tier segments in order;
+// seg_begin[t] / seg_count[t] are host copies of the tier layout.
+// slice_counts: int32[n_heavy * num_slices] per numeric slice of width
+// num_slice_w.
+void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,
+                     const int64_t* seg_begin, const int64_t* seg_count, const int64_t* flops,
+                     int64_t* nnz, int32_t* slice_counts, int64_t num_slice_w,
+                     int64_t num_slices, cudaStream_t s, int sms, int* launches);
+
+// K5-K7: numeric phase over the numeric tier segments + heavy units, writing
+// sorted rows of C at Crp.
+int num_slice_width(int sr);
+int num_hash_max(int sr);
+void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* perm,
+                    const int64_t* seg_begin, const int64_t* seg_count, const int64_t* flops,
+                    const int64_t* nnz, const int32_t* heavy_rows, const int2* units,
+                    int64_t n_units, const int32_t* slice_counts, int64_t num_slices,
+                    const int64_t* Crp, int32_t* Ccol, void* Cval, int64_t* err, cudaStream_t s,
+                    int sms, int* launches);
+
+}  // namespace cb

@@ -1,0 +1,352 @@
+// K5-K7: numeric phase (paper Sec. 5.1 phase (3): "performs the actual
+// multiplication using the ... hash table"), with the in-row sort that makes
+// every output row strictly increasing in column.
+//
+// Tiers by the exact row size nz = nnz(C_i) from the symbolic phase:
+//   * nz <= 64:   one warp per row, keys + accumulators in a per-warp table
+//   * nz <= 512:  one 256-thread team per row
+//   * nz <= H:    one 1024-thread team per row (H = 4096 for 8-byte
+//                 accumulators, 8192 for 4-byte ones)
+//   For these, the table has 2^ceil(log2 2nz) slots (load factor <= 1/2);
+//   after accumulation the team compacts the occupied slots, bitonic-sorts
+//   them by column in shared memory and writes the row with coalesced stores.
+//   * heavier:    dense column slices.  One CTA per (row, slice of W columns)
+//                 keeps W accumulators plus a W-bit occupancy bitmap in shared
+//                 memory, scans the whole product stream of the row and keeps
+//                 the products that land in its slice; the bitmap is then
+//                 read in column order, so the slice comes out sorted without
+//                 a sort.  Slice offsets come from the symbolic slice counts.
+// Products are combined with the semiring's atomic (+) on shared memory.
+#include "cb_common.cuh"
+#include "cb_kernels.h"
+
+namespace cb {
+
+namespace {
+
+__device__ __forceinline__ void flag_error(int64_t* err, int64_t code) {
+  if (err) atomicCAS((unsigned long long*)err, 0ull, (unsigned long long)code);
+}
+
+// Exclusive scan of one int per thread across a team of TEAM threads.
+template <int TEAM>
+__device__ __forceinline__ int team_exclusive_scan(int x, int* scratch /* >= 33 ints */, int& total) {
+  const int lane = threadIdx.x & 31;
+  int incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (TEAM == 32) {
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - x;
+  }
+  const int w = threadIdx.x >> 5;
+  constexpr int NW = TEAM / 32;
+  if (lane == 31) scratch[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int v = lane < NW ? scratch[lane] : 0;
+    int vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, vi, o);
+      if (lane >= o) vi += y;
+    }
+    if (lane < NW) scratch[lane] = vi - v;
+    if (lane == NW - 1) scratch[32] = vi;
+  }
+  __syncthreads();
+  total = scratch[32];
+  const int r = scratch[w] + incl - x;
+  __syncthreads();
+  return r;
+}
+
+template <int SR, int CTA, int TEAM, int TABLE_MAX>
+__global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int32_t* rows,
+                                                  int64_t nrows_tier, const int64_t* flops,
+                                                  const int64_t* nnz, const int64_t* Crp,
+                                                  int32_t* Ccol, typename Sem<SR>::T* Cval,
+                                                  int64_t* err) {
+  typedef Sem<SR> S;
+  typedef typename S::A Acc;
+  typedef typename S::T T;
+  constexpr int TEAMS = CTA / TEAM;
+  constexpr int PER = TABLE_MAX / TEAM;
+  extern __shared__ __align__(16) unsigned char num_smem[];
+  __shared__ int scan_scratch[TEAMS][33];
+  const int team = threadIdx.x / TEAM, lane = threadIdx.x % TEAM;
+  Acc* vals = reinterpret_cast<Acc*>(num_smem) + team * TABLE_MAX;
+  int* keys = reinterpret_cast<int*>(reinterpret_cast<Acc*>(num_smem) + TEAMS * TABLE_MAX) + team * TABLE_MAX;
+  const T* Aval = reinterpret_cast<const T*>(A.val);
+  const T* Bval = reinterpret_cast<const T*>(B.val);
+
+  for (int64_t r = (int64_t)blockIdx.x * TEAMS + team; r < nrows_tier;
+       r += (int64_t)gridDim.x * TEAMS) {
+    const int i = rows[r];
+    const int64_t nz = nnz[i];
+    const int bits = max(ceil_log2(2 * nz), 5);
+    const int tsize = 1 << bits;
+    const uint32_t mask = (uint32_t)tsize - 1;
+    const int shift = 32 - bits;
+    for (int s = lane; s < tsize; s += TEAM) {
+      keys[s] = kEmptyKey;
+      vals[s] = S::ident();
+    }
+    team_sync<TEAM>();
+
+    // accumulate every product of row i
+    const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
+    const int gl = group_log2<TEAM>(flops[i], a1 - a0);
+    const int G = 1 << gl, gq = lane & (G - 1), groups = TEAM >> gl;
+    for (int64_t p = a0 + (lane >> gl); p < a1; p += groups) {
+      const int k = A.col[p];
+      const T a = S::kUsesA ? Aval[p] : T();
+      const int64_t b1 = B.rp[k + 1];
+      for (int64_t q = B.rp[k] + gq; q < b1; q += G) {
+        bool ins;
+        const int slot = probe_insert(keys, mask, shift, B.col[q], ins);
+        if (slot >= 0) S::atomic(&vals[slot], S::mul(a, Bval[q]));
+        else flag_error(err, 20);
+      }
+    }
+    team_sync<TEAM>();
+
+    // compact occupied slots (registers first, so the table can be overwritten)
+    int mk[PER];
+    Acc mv[PER];
+    int mc = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int s = lane + j * TEAM;
+      mk[j] = kEmptyKey;
+      if (s < tsize) {
+        mk[j] = keys[s];
+        mv[j] = vals[s];
+      }
+      mc += mk[j] != kEmptyKey;
+    }
+    int total;
+    int pos = team_exclusive_scan<TEAM>(mc, scan_scratch[team], total);
+    team_sync<TEAM>();
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      if (mk[j] != kEmptyKey) {
+        keys[pos] = mk[j];
+        vals[pos] = mv[j];
+        ++pos;
+      }
+    }
+    const int P = 1 << ceil_log2(total > 0 ? total : 1);
+    for (int t = total + lane; t < P; t += TEAM) keys[t] = INT_MAX;
+    team_sync<TEAM>();
+
+    // bitonic sort of P (key, value) pairs by key
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = lane; t < (P >> 1); t += TEAM) {
+          const int lo = ((t / j) * (j << 1)) + (t % j);
+          const int hi = lo + j;
+          const bool asc = (lo & k) == 0;
+          const int ka = keys[lo], kb = keys[hi];
+          if ((ka > kb) == asc) {
+            keys[lo] = kb;
+            keys[hi] = ka;
+            const Acc va = vals[lo];
+            vals[lo] = vals[hi];
+            vals[hi] = va;
+          }
+        }
+        team_sync<TEAM>();
+      }
+    }
+
+    // write the sorted row
+    if (total != nz && lane == 0) flag_error(err, 21);
+    const int nw = total < nz ? total : (int)nz;
+    const int64_t off = Crp[i];
+    for (int t = lane; t < nw; t += TEAM) {
+      Ccol[off + t] = keys[t];
+      Cval[off + t] = S::out(vals[t]);
+    }
+    team_sync<TEAM>();
+  }
+}
+
+// Dense column-slice units for heavy rows.
+template <int SR>
+__global__ void __launch_bounds__(1024) k_num_heavy(DevCSR A, DevCSR B, const int32_t* heavy_rows,
+                                                    const int2* units, int64_t n_units,
+                                                    const int32_t* slice_counts, int64_t num_slices,
+                                                    const int64_t* flops, const int64_t* Crp,
+                                                    int32_t* Ccol, typename Sem<SR>::T* Cval,
+                                                    int64_t* err) {
+  typedef Sem<SR> S;
+  typedef typename S::A Acc;
+  typedef typename S::T T;
+  constexpr int W = NumLimits<SR>::kSlice;
+  constexpr int NW = W / 32;
+  static_assert(NW <= 1024, "one bitmap word per thread");
+  extern __shared__ __align__(16) unsigned char heavy_smem[];
+  Acc* vals = reinterpret_cast<Acc*>(heavy_smem);
+  unsigned* bm = reinterpret_cast<unsigned*>(vals + W);
+  __shared__ int scratch[33];
+  __shared__ long long s_off;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const T* Aval = reinterpret_cast<const T*>(A.val);
+  const T* Bval = reinterpret_cast<const T*>(B.val);
+
+  for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const int2 un = units[u];
+    const int64_t h = un.x, sl = un.y;
+    const int i = heavy_rows[h];
+    const int64_t lo = sl * (int64_t)W;
+    const int64_t hi = min(lo + (int64_t)W, B.ncols);
+    const unsigned width = (unsigned)(hi - lo);
+    const int nwords = (int)((width + 31) / 32);
+    for (int t = tid; t < (int)width; t += 1024) vals[t] = S::ident();
+    for (int w = tid; w < nwords; w += 1024) bm[w] = 0u;
+    if (tid < 32) {
+      long long o = 0;
+      for (int64_t t = lane; t < sl; t += 32) o += slice_counts[h * num_slices + t];
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) o += __shfl_down_sync(0xffffffffu, o, d);
+      if (lane == 0) s_off = o;
+    }
+    __syncthreads();
+
+    const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
+    const int gl = group_log2<1024>(flops[i], a1 - a0);
+    const int G = 1 << gl, gq = tid & (G - 1), groups = 1024 >> gl;
+    for (int64_t p = a0 + (tid >> gl); p < a1; p += groups) {
+      const int k = A.col[p];
+      const T a = S::kUsesA ? Aval[p] : T();
+      const int64_t b1 = B.rp[k + 1];
+      for (int64_t q = B.rp[k] + gq; q < b1; q += G) {
+        const unsigned off = (unsigned)((int64_t)B.col[q] - lo);
+        if (off < width) {
+          S::atomic(&vals[off], S::mul(a, Bval[q]));
+          const unsigned bit = 1u << (off & 31);
+          if (!(bm[off >> 5] & bit)) atomicOr(&bm[off >> 5], bit);
+        }
+      }
+    }
+    __syncthreads();
+
+    unsigned word = tid < nwords ? bm[tid] : 0u;
+    int total;
+    const int ex = team_exclusive_scan<1024>(__popc(word), scratch, total);
+    if (tid == 0 && total != slice_counts[h * num_slices + sl]) flag_error(err, 22);
+    int64_t o = Crp[i] + s_off + ex;
+    const int64_t row_end = Crp[i + 1];
+    while (word) {
+      const int b = __ffs(word) - 1;
+      word &= word - 1;
+      if (o < row_end) {
+        const int c = tid * 32 + b;
+        Ccol[o] = (int32_t)(lo + c);
+        Cval[o] = S::out(vals[c]);
+      }
+      ++o;
+    }
+    __syncthreads();
+  }
+}
+
+template <class K>
+void set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+inline int capped(int64_t want, int64_t cap) {
+  if (want < 1) want = 1;
+  return (int)(want < cap ? want : cap);
+}
+
+template <int SR>
+void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int64_t* seg_begin,
+                const int64_t* seg_count, const int64_t* flops, const int64_t* nnz,
+                const int32_t* heavy_rows, const int2* units, int64_t n_units,
+                const int32_t* slice_counts, int64_t num_slices, const int64_t* Crp,
+                int32_t* Ccol, void* Cval_, int64_t* err, cudaStream_t s, int sms, int* launches) {
+  typedef typename Sem<SR>::A Acc;
+  typedef typename Sem<SR>::T T;
+  T* Cval = reinterpret_cast<T*>(Cval_);
+  constexpr size_t slot = sizeof(Acc) + sizeof(int);
+  if (seg_count[kNumWarp]) {
+    constexpr int CTA = 256, TEAM = 32, TBL = 2 * kNumWarpMax;
+    const size_t smem = (CTA / TEAM) * TBL * slot;
+    k_num_hash<SR, CTA, TEAM, TBL><<<capped((seg_count[kNumWarp] + 7) / 8, sms * 8), CTA, smem, s>>>(
+        A, B, perm + seg_begin[kNumWarp], seg_count[kNumWarp], flops, nnz, Crp, Ccol, Cval, err);
+    ++*launches;
+  }
+  if (seg_count[kNumSmall]) {
+    constexpr int CTA = 256, TEAM = 256, TBL = 2 * kNumSmallMax;
+    const size_t smem = TBL * slot;
+    k_num_hash<SR, CTA, TEAM, TBL><<<capped(seg_count[kNumSmall], sms * 8), CTA, smem, s>>>(
+        A, B, perm + seg_begin[kNumSmall], seg_count[kNumSmall], flops, nnz, Crp, Ccol, Cval, err);
+    ++*launches;
+  }
+  if (seg_count[kNumLarge]) {
+    constexpr int CTA = 1024, TEAM = 1024, TBL = 2 * NumLimits<SR>::kHashMax;
+    const size_t smem = TBL * slot;
+    set_smem(k_num_hash<SR, CTA, TEAM, TBL>, smem);
+    k_num_hash<SR, CTA, TEAM, TBL><<<capped(seg_count[kNumLarge], sms), CTA, smem, s>>>(
+        A, B, perm + seg_begin[kNumLarge], seg_count[kNumLarge], flops, nnz, Crp, Ccol, Cval, err);
+    ++*launches;
+  }
+  if (n_units) {
+    constexpr int W = NumLimits<SR>::kSlice;
+    const size_t smem = W * sizeof(Acc) + (W / 32) * sizeof(unsigned);
+    set_smem(k_num_heavy<SR>, smem);
+    k_num_heavy<SR><<<capped(n_units, sms), 1024, smem, s>>>(A, B, heavy_rows, units, n_units,
+                                                             slice_counts, num_slices, flops, Crp,
+                                                             Ccol, Cval, err);
+    ++*launches;
+  }
+}
+
+}  // namespace
+
+int num_slice_width(int sr) {
+  switch (sr) {
+    case 1: return NumLimits<1>::kSlice;
+    case 2: return NumLimits<2>::kSlice;
+    case 3: return NumLimits<3>::kSlice;
+    case 4: return NumLimits<4>::kSlice;
+    default: return NumLimits<5>::kSlice;
+  }
+}
+
+int num_hash_max(int sr) {
+  switch (sr) {
+    case 1: return NumLimits<1>::kHashMax;
+    case 2: return NumLimits<2>::kHashMax;
+    case 3: return NumLimits<3>::kHashMax;
+    case 4: return NumLimits<4>::kHashMax;
+    default: return NumLimits<5>::kHashMax;
+  }
+}
+
+void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* perm,
+                    const int64_t* seg_begin, const int64_t* seg_count, const int64_t* flops,
+                    const int64_t* nnz, const int32_t* heavy_rows, const int2* units,
+                    int64_t n_units, const int32_t* slice_counts, int64_t num_slices,
+                    const int64_t* Crp, int32_t* Ccol, void* Cval, int64_t* err, cudaStream_t s,
+                    int sms, int* launches) {
+#define CB_NUM(SRV)                                                                        \
+  numeric_sr<SRV>(A, B, perm, seg_begin, seg_count, flops, nnz, heavy_rows, units, n_units, \
+                  slice_counts, num_slices, Crp, Ccol, Cval, err, s, sms, launches)
+  switch (sr) {
+    case 1: CB_NUM(1); break;
+    case 2: CB_NUM(2); break;
+    case 3: CB_NUM(3); break;
+    case 4: CB_NUM(4); break;
+    case 5: CB_NUM(5); break;
+  }
+#undef CB_NUM
+}
+
+}  // namespace cb

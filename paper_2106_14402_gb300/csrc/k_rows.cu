@@ -1,0 +1,282 @@
+// Row-level kernels of the SpGEMM path: input validation, the per-row flops
+// estimate and load-balance binning (paper Sec. 5.1 phase (1)), the int64
+// exclusive scan that turns row sizes into row pointers, and the list of
+// heavy-row column-slice work units.
+#include "cb_common.cuh"
+#include "cb_kernels.h"
+
+namespace cb {
+
+namespace {
+
+__device__ __forceinline__ void set_error(int64_t* counters, int64_t code, int64_t detail) {
+  if (atomicCAS((unsigned long long*)&counters[kError], 0ull, (unsigned long long)code) == 0ull)
+    counters[kErrDetail] = detail;
+}
+
+__global__ void k_validate(DevCSR M, int64_t nnz, int code_base, int64_t* counters) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (tid == 0 && (M.rp[0] != 0 || M.rp[M.nrows] != nnz)) set_error(counters, code_base + 1, 0);
+  for (int64_t i = tid; i < M.nrows; i += stride)
+    if (M.rp[i + 1] < M.rp[i]) set_error(counters, code_base + 1, i);
+  for (int64_t q = tid; q < nnz; q += stride) {
+    int32_t c = M.col[q];
+    if (c < 0 || (int64_t)c >= M.ncols) set_error(counters, code_base + 2, q);
+  }
+}
+
+// K1: one warp per row of A.  flops_i = sum of B row lengths over the row's
+// stored entries (Table 1's flops), maxb_i = the longest of them.
+__global__ void __launch_bounds__(256) k_classify_sym(DevCSR A, DevCSR B, int64_t* flops,
+                                                      int32_t* maxb, int64_t* counters) {
+  __shared__ unsigned long long hist[kSymTiers];
+  __shared__ unsigned long long total;
+  if (threadIdx.x < kSymTiers) hist[threadIdx.x] = 0;
+  if (threadIdx.x == 0) total = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < A.nrows;
+       i += nwarps) {
+    const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
+    long long f = 0;
+    int mx = 0;
+    for (int64_t p = a0 + lane; p < a1; p += 32) {
+      const int k = A.col[p];
+      const int64_t len = B.rp[k + 1] - B.rp[k];
+      f += len;
+      mx = max(mx, (int)min(len, (int64_t)INT_MAX));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      f += __shfl_down_sync(0xffffffffu, f, o);
+      mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+      flops[i] = f;
+      if (maxb) maxb[i] = mx;
+      atomicAdd(&hist[sym_tier(min((int64_t)f, B.ncols))], 1ull);
+      atomicAdd(&total, (unsigned long long)f);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kSymTiers && hist[threadIdx.x])
+    atomicAdd((unsigned long long*)&counters[kCntSym + threadIdx.x], hist[threadIdx.x]);
+  if (threadIdx.x == 0 && total) atomicAdd((unsigned long long*)&counters[kTotalFlops], total);
+}
+
+struct TierBySize {
+  const int64_t* v;
+  int64_t cap, t1, t2, t3;
+  __device__ __forceinline__ int operator()(int64_t i) const {
+    const int64_t u = min(v[i], cap);
+    return u == 0 ? 0 : u <= t1 ? 1 : u <= t2 ? 2 : u <= t3 ? 3 : 4;
+  }
+};
+
+__global__ void __launch_bounds__(256) k_tier_count(int64_t m, TierBySize tier, int64_t* cnt) {
+  __shared__ unsigned long long hist[5];
+  if (threadIdx.x < 5) hist[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&hist[tier(i)], 1ull);
+  __syncthreads();
+  if (threadIdx.x < 5 && hist[threadIdx.x])
+    atomicAdd((unsigned long long*)&cnt[threadIdx.x], hist[threadIdx.x]);
+}
+
+// K2: place row i into the segment of its tier inside perm (tiers 1..4 in
+// order; tier 0 rows are empty and get no slot).  zero_nnz (optional): rows
+// of tier 0 and 4 get nnz = 0 (tier 4 rows are summed slice by slice later).
+__global__ void __launch_bounds__(256) k_tier_scatter(int64_t m, TierBySize tier, int32_t* perm,
+                                                      const int64_t* cnt, int64_t* cur,
+                                                      int64_t* zero_nnz) {
+  __shared__ int local[5];
+  __shared__ long long base[5];
+  if (threadIdx.x < 5) local[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int t = -1, slot = 0;
+  if (i < m) {
+    t = tier(i);
+    if (zero_nnz && (t == 0 || t == 4)) zero_nnz[i] = 0;
+    if (t > 0) slot = atomicAdd(&local[t], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x > 0 && threadIdx.x < 5 && local[threadIdx.x]) {
+    long long seg = 0;
+    for (int u = 1; u < (int)threadIdx.x; ++u) seg += cnt[u];
+    base[threadIdx.x] =
+        seg + (long long)atomicAdd((unsigned long long*)&cur[threadIdx.x], (unsigned long long)local[threadIdx.x]);
+  }
+  __syncthreads();
+  if (t > 0) perm[base[t] + slot] = (int32_t)i;
+}
+
+// K4: three-pass exclusive scan (tile reduce, scan of tile sums, apply).
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ long long block_exclusive_scan(long long x, long long* warp_tot,
+                                                         long long& block_total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  long long incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    long long v = lane < nw ? warp_tot[lane] : 0;
+    long long vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, vi, o);
+      if (lane >= o) vi += y;
+    }
+    if (lane < nw) warp_tot[lane] = vi - v;
+    if (lane == nw - 1) warp_tot[32] = vi;
+  }
+  __syncthreads();
+  block_total = warp_tot[32];
+  const long long r = warp_tot[w] + incl - x;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int64_t* in, int64_t n,
+                                                              int64_t* partial) {
+  __shared__ long long wt[33];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  long long s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j)
+    if (base + j < n) s += in[base + j];
+  long long tot;
+  block_exclusive_scan(s, wt, tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(int64_t* partial, int64_t nb,
+                                                                int64_t* out_total) {
+  __shared__ long long wt[33];
+  long long carry = 0;
+  for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
+    const int64_t b = b0 + threadIdx.x;
+    const long long v = b < nb ? partial[b] : 0;
+    long long tot;
+    const long long ex = block_exclusive_scan(v, wt, tot);
+    if (b < nb) partial[b] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *out_total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int64_t* in, int64_t n,
+                                                             const int64_t* partial, int64_t* out) {
+  __shared__ long long wt[33];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  long long v[kScanItems];
+  long long s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    v[j] = base + j < n ? in[base + j] : 0;
+    s += v[j];
+  }
+  long long tot;
+  long long run = block_exclusive_scan(s, wt, tot) + partial[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    if (base + j < n) out[base + j] = run;
+    run += v[j];
+  }
+}
+
+// Heavy rows that the numeric phase computes by dense column slices: one
+// unit (h, s) per slice s of heavy row h holding at least one entry.  One
+// warp per heavy row, lanes over its slices.
+__global__ void __launch_bounds__(256) k_build_units(int64_t n_heavy, const int32_t* heavy_rows,
+                                                     const int64_t* nnz, int64_t hash_max,
+                                                     const int32_t* slice_counts, int64_t slices,
+                                                     int2* units, int64_t* counters) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t h = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); h < n_heavy;
+       h += nwarps) {
+    if (nnz[heavy_rows[h]] <= hash_max) continue;
+    for (int64_t s0 = 0; s0 < slices; s0 += 32) {
+      const int64_t s = s0 + lane;
+      const bool live = s < slices && slice_counts[h * slices + s] > 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, live);
+      if (!bal) continue;
+      long long base = 0;
+      if (lane == 0)
+        base = (long long)atomicAdd((unsigned long long*)&counters[kUnits], (unsigned long long)__popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (live) units[base + __popc(bal & ((1u << lane) - 1))] = make_int2((int)h, (int)s);
+    }
+  }
+}
+
+inline int grid_for(int64_t work, int per_block, int cap) {
+  int64_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  return (int)(g < cap ? g : cap);
+}
+
+}  // namespace
+
+void launch_validate(const DevCSR& M, int64_t nnz, int code_base, int64_t* counters,
+                     cudaStream_t s, int sms) {
+  k_validate<<<grid_for(nnz + M.nrows, 256, sms * 8), 256, 0, s>>>(M, nnz, code_base, counters);
+}
+
+void launch_classify_sym(const DevCSR& A, const DevCSR& B, int64_t* flops, int32_t* maxb,
+                         int64_t* counters, cudaStream_t s, int sms) {
+  k_classify_sym<<<grid_for(A.nrows, 8, sms * 8), 256, 0, s>>>(A, B, flops, maxb, counters);
+}
+
+void launch_scatter_sym(int64_t m, int64_t ncols, const int64_t* flops, int32_t* perm,
+                        int64_t* nnz, int64_t* counters, cudaStream_t s, int) {
+  TierBySize t{flops, ncols, kSymWarpMax, kSymSmallMax, kSymHashMax};
+  k_tier_scatter<<<grid_for(m, 256, 1 << 30), 256, 0, s>>>(m, t, perm, counters + kCntSym,
+                                                            counters + kCurSym, nnz);
+}
+
+int64_t scan_partials(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+void launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* partial,
+                           cudaStream_t s) {
+  if (n == 0) {
+    cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+    return;
+  }
+  const int64_t nb = (n + kScanTile - 1) / kScanTile;
+  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial);
+  k_scan_partials<<<1, kScanThreads, 0, s>>>(partial, nb, out + n);
+  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial, out);
+}
+
+void launch_classify_num(int sr, int64_t m, const int64_t* nnz, int32_t* perm, int64_t* counters,
+                         cudaStream_t s, int sms) {
+  TierBySize t{nnz, INT64_MAX, kNumWarpMax, kNumSmallMax, (int64_t)num_hash_max(sr)};
+  k_tier_count<<<grid_for(m, 256, sms * 8), 256, 0, s>>>(m, t, counters + kCntNum);
+  k_tier_scatter<<<grid_for(m, 256, 1 << 30), 256, 0, s>>>(m, t, perm, counters + kCntNum,
+                                                            counters + kCurNum, nullptr);
+}
+
+void launch_build_units(int sr, int64_t n_heavy, const int32_t* heavy_rows, const int64_t* nnz,
+                        const int32_t* slice_counts, int64_t slices, int2* units,
+                        int64_t* counters, cudaStream_t s) {
+  if (n_heavy == 0) return;
+  k_build_units<<<grid_for(n_heavy, 8, 4096), 256, 0, s>>>(
+      n_heavy, heavy_rows, nnz, num_hash_max(sr), slice_counts, slices, units, counters);
+}
+
+}  // namespace cb

@@ -1,0 +1,75 @@
+"""Shared helpers for the parity tests: run the CUDA path and the oracle on
+the same seeded inputs and compare them element by element.
+
+The bar (per semiring):
+  * integer, bool and min/select semirings: bit-exact row pointers, columns
+    and values;
+  * (+,x) fp64: identical pattern and |c - c_ref| <= 1e-12 * sum|a_ik b_kj|
+    per entry (sum of |products| accumulated by the oracle).  For an entry
+    with m products any two summation orders differ by at most about
+    2(m-1)u*sum|ab| with u = 2^-53, so 1e-12 holds up to m ~ 4500 products
+    per entry, above every entry of the test workloads.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+FP64_TOL = 1e-12
+
+
+def compare_rows(sr, got, want, rows=None, tol=FP64_TOL):
+    """got = (row_ptr, col, val) over all rows (host arrays); want = oracle output
+    over `rows` (all rows when None).  Raises AssertionError on the first mismatch."""
+    g_rp, g_col, g_val = got
+    w_rp, w_col, w_val, w_abs = want
+    if rows is None:
+        assert np.array_equal(g_rp, w_rp), _first_diff("row_ptr", g_rp, w_rp)
+        assert np.array_equal(g_col, w_col), _first_diff("col", g_col, w_col)
+        gv, wv, ab = g_val, w_val, w_abs
+    else:
+        rows = np.asarray(rows, dtype=np.int64)
+        lens = g_rp[rows + 1] - g_rp[rows]
+        assert np.array_equal(lens, np.diff(w_rp)), "row sizes differ on sampled rows"
+        idx = np.concatenate([np.arange(g_rp[r], g_rp[r + 1]) for r in rows]) if len(rows) else \
+            np.zeros(0, np.int64)
+        assert np.array_equal(g_col[idx], w_col), _first_diff("col", g_col[idx], w_col)
+        gv, wv, ab = g_val[idx], w_val, w_abs
+    if sr == "plus_times_f64":
+        err = np.abs(gv - wv)
+        bad = err > tol * ab
+        assert not bad.any(), f"fp64 tolerance exceeded at {np.nonzero(bad)[0][:5]}: " \
+                              f"{gv[bad][:5]} vs {wv[bad][:5]}"
+        return float(np.max(err / np.where(ab > 0, ab, 1.0))) if err.size else 0.0
+    assert np.array_equal(gv, wv), _first_diff("val", gv, wv)
+    return 0.0
+
+
+def _first_diff(name, a, b):
+    if a.shape != b.shape:
+        return f"{name}: shape {a.shape} vs {b.shape}"
+    i = np.nonzero(a != b)[0]
+    return f"{name}: first difference at {i[:5]}: {a[i[:5]]} vs {b[i[:5]]}"
+
+
+def check_structure(rp, col, ncols):
+    """Properties that hold at any size: monotone row pointers, columns in
+    range and strictly increasing inside each row."""
+    assert rp[0] == 0 and np.all(np.diff(rp) >= 0)
+    assert col.size == rp[-1]
+    if col.size:
+        assert col.min() >= 0 and col.max() < ncols
+        d = np.diff(col.astype(np.int64))
+        starts = rp[1:-1]
+        boundary = np.zeros(col.size - 1, dtype=bool) if col.size > 1 else np.zeros(0, bool)
+        inner = starts[(starts > 0) & (starts < col.size)] - 1
+        boundary[inner] = True
+        assert np.all((d > 0) | boundary), "columns not strictly increasing inside a row"
+
+
+def sample_rows(m, flops, frac=0.01, top=100, seed=0):
+    """A seeded fraction of the rows plus the `top` rows with most products."""
+    rng = np.random.default_rng(seed)
+    k = max(1, int(m * frac))
+    pick = rng.choice(m, size=min(k, m), replace=False)
+    heavy = np.argsort(-np.asarray(flops), kind="stable")[:top]
+    return np.unique(np.concatenate([pick, heavy])).astype(np.int64)
