@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Throughput of the semiring SpGEMM C = A (+).(x) B on one GB300.
+
+One step = the whole path (flops + binning, symbolic, scan, numeric with
+in-row sort) for every product of the workload:
+
+  rmat18 (default): R-MAT scale 18, edgefactor 16, a=0.57 b=c=0.19 d=0.05,
+          symmetrised, duplicates removed, vertices permuted; C = A.A over
+          (+,x) fp64 U(0,1), (min,+) uint32 U{1..255} and (or,and) bool.
+  er16k:  ER n=16384 with exactly 8 distinct columns per row, (+,x) int64
+          U{1..10}; C = A.A.
+
+Inputs are seeded synthetic matrices resident in HBM; outputs go to
+pre-reserved device buffers; validation is off inside the timed loop.  L2
+is flushed (a 512 MB device write) before every timed step.  Each rank of a
+multi-GPU launch runs an independent replica (weak scaling).
+
+`--impl reference` times the CPU oracle on the host cores instead, on a
+bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "semiring SpGEMM flops/s & nnz(C)/s on 1 GB300, learned/batched vs plain two-phase"
+UNIT = "products/s"
+VAL_BYTES = {"plus_times_i64": 8, "plus_times_f64": 8, "min_plus_u32": 4, "or_and_bool": 1,
+             "sel2nd_min_i32": 4}
+DTYPE_NAME = {"plus_times_i64": "int64", "plus_times_f64": "f64", "min_plus_u32": "u32",
+              "or_and_bool": "u8", "sel2nd_min_i32": "i32"}
+
+
+def workload(name: str):
+    from paper_2106_14402_gb300 import gen
+    if name == "rmat18":
+        desc = ("R-MAT s18 ef16 (0.57/0.19/0.19/0.05) symmetrised+dedup+permuted; C=A.A over "
+                "(+,x) f64, (min,+) u32, (or,and) bool")
+        return desc, gen.rmat_square(18, 16, cfg=2)
+    if name == "er16k":
+        desc = "ER n=16384, 8 distinct cols/row, (+,x) int64 U{1..10}; C=A.A"
+        return desc, gen.er_square()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def compulsory_bytes(sr, A, B, nnz_c, m):
+    """bytes(A) + bytes(B rows touched, once) + bytes(C): row_ptr 8 B/row, col 4 B, val by type."""
+    v = VAL_BYTES[sr]
+    a = 8 * (A.nrows + 1) + A.nnz * (4 + v)
+    touched = np.unique(A.col)
+    blen = np.diff(B.row_ptr)[touched]
+    b = 8 * (touched.size + 1) + int(blen.sum()) * (4 + v)
+    c = 8 * (m + 1) + nnz_c * (4 + v)
+    return int(a + b + c)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        med = statistics.median(sm) if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded row sample (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_rate(problems, target_s: float = 12.0, seed: int = 0):
+    """Time the oracle on a seeded row sample of each product, sized to ~target_s in total.
+
+    Returns (products/s, nnz/s, cores, description, seconds)."""
+    import oracle
+    cores = oracle.max_threads()
+    rng = np.random.default_rng(seed)
+    samples = []
+    for sr, A, B in problems:
+        flops, _ = oracle.row_stats(A, B)
+        perm = rng.permutation(A.nrows)
+        samples.append((sr, A, B, flops, perm))
+    # calibrate on 0.2% of rows
+    probe_prod, probe_t = 0, 0.0
+    for sr, A, B, flops, perm in samples:
+        rows = np.sort(perm[: max(1, A.nrows // 500)])
+        t0 = time.perf_counter()
+        oracle.spgemm(sr, A, B, rows=rows)
+        probe_t += time.perf_counter() - t0
+        probe_prod += int(flops[rows].sum())
+    rate = probe_prod / max(probe_t, 1e-6)
+    total_prod = sum(int(f.sum()) for _, _, _, f, _ in samples)
+    frac = min(1.0, target_s * rate / max(total_prod, 1))
+    prod, nnz, t = 0, 0, 0.0
+    for sr, A, B, flops, perm in samples:
+        rows = np.sort(perm[: max(1, int(A.nrows * frac))])
+        t0 = time.perf_counter()
+        rp, _, _, _ = oracle.spgemm(sr, A, B, rows=rows)
+        t += time.perf_counter() - t0
+        prod += int(flops[rows].sum())
+        nnz += int(rp[-1])
+    desc = (f"seeded {frac * 100:.2f}% row sample of every product "
+            f"({prod:.3e} products, {nnz:.3e} nnz(C)), oracle std::map Gustavson, OpenMP")
+    return prod / t, nnz / t, cores, desc, t
+
+
+def run_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    desc, problems = workload(args.workload)
+    steps = []
+    for _ in range(args.warmup):
+        oracle_sample_rate(problems, target_s=2.0)
+    for _ in range(args.steps):
+        steps.append(oracle_sample_rate(problems, target_s=args.ref_seconds))
+    rate = statistics.median(s[0] for s in steps)
+    nnz_rate = statistics.median(s[1] for s in steps)
+    cores, sample = steps[0][2], steps[0][3]
+    out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * statistics.median(s[4] for s in steps),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": ",".join(DTYPE_NAME[sr] for sr, _, _ in problems), "data": "synthetic",
+           "config": {"workload": desc, "sample": sample}, "nnz_per_s": nnz_rate,
+           "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main_gpu(args):
+    import torch
+
+    from paper_2106_14402_gb300 import cb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cb.load()
+    desc, problems = workload(args.workload)
+    dev = torch.device("cuda", local)
+
+    # device-resident inputs, pre-reserved outputs sized by one untimed call
+    dprob = []
+    for sr, A, B in problems:
+        dA = cb.DeviceCSR.from_host(A, sr, dev)
+        dB = dA if B is A else cb.DeviceCSR.from_host(B, sr, dev)
+        C = cb.spgemm(sr, dA, dB, validate=True)
+        nnz = C.nnz
+        del C
+        out = cb.DeviceCSR(A.nrows, B.ncols, torch.empty(A.nrows + 1, dtype=torch.int64, device=dev),
+                           torch.empty(max(nnz, 1), dtype=torch.int32, device=dev),
+                           torch.empty(max(nnz, 1), dtype=cb.SEMIRING[sr][1], device=dev))
+        dprob.append((sr, A, B, dA, dB, out, nnz))
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ctx = cb.context()
+
+    def step(collect):
+        launches = 0
+        for sr, A, B, dA, dB, out, nnz in dprob:
+            cb.spgemm(sr, dA, dB, validate=False, out=out, timing=True, ctx=ctx)
+            st = ctx.stats()
+            launches += st["kernels"]
+            if collect is not None:
+                collect.setdefault(sr, []).append(st)
+        return launches
+
+    for _ in range(args.warmup):
+        step(None)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    stats: dict = {}
+    times = []
+    launches = 0
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        launches += step(stats)
+        ev1.record()
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    ms_step = sum(times) / len(times)
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+        dist.barrier()
+
+    products = sum(st[0]["flops"] for st in stats.values())
+    nnz_c = sum(st[0]["nnz"] for st in stats.values())
+    value = world * products / (ms_step * 1e-3)
+    nnz_rate = world * nnz_c / (ms_step * 1e-3)
+
+    # per-semiring breakdown and the numeric-phase roofline
+    per_sr = {}
+    num_bytes = 0
+    num_ms = 0.0
+    phase_tot = {"ms_stats": 0.0, "ms_symbolic": 0.0, "ms_scan": 0.0, "ms_numeric": 0.0}
+    for sr, A, B, dA, dB, out, nnz in dprob:
+        sts = stats[sr]
+        ph = {k: statistics.median(s[k] for s in sts) for k in phase_tot}
+        for k in phase_tot:
+            phase_tot[k] += ph[k]
+        cbytes = compulsory_bytes(sr, A, B, nnz, A.nrows)
+        num_bytes += cbytes
+        num_ms += ph["ms_numeric"]
+        per_sr[sr] = {"products": sts[0]["flops"], "nnz_c": sts[0]["nnz"],
+                      "heavy_rows": sts[0]["heavy_rows"], "heavy_units": sts[0]["heavy_units"],
+                      "compulsory_bytes": cbytes, **{k: round(v, 4) for k, v in ph.items()}}
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            peak = float(json.load(f)["hbm_gbs"])
+        peak_src = "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    achieved = num_bytes / (num_ms * 1e-3) / 1e9 if num_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "numeric phase (K5-K7: hash tiers + dense heavy slices), per SpGEMM",
+                "peak_source": peak_src,
+                "algorithmic_bytes_per_step": num_bytes, "ms_per_step_in_kernel": round(num_ms, 4)}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, cb, ctx, dprob, dev, world, dist, products)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, nr, cores, sample, _ = oracle_sample_rate(problems, target_s=args.ref_seconds)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": ",".join(DTYPE_NAME[sr] for sr, *_ in dprob), "data": "synthetic",
+                "config": {"workload": desc, "sizing": "exact (plain two-phase)",
+                           "l2": "flushed by a 512 MB device write before every timed step",
+                           "products_per_step": products, "nnz_c_per_step": nnz_c,
+                           "validation": "off in the timed loop",
+                           "parallelism": f"replicas x{world}"},
+                "nnz_per_s": nnz_rate, "per_semiring": per_sr, "phase_ms_per_step":
+                    {k: round(v, 4) for k, v in phase_tot.items()},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks, "wall_s_timed": round(wall, 3)}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, cb, ctx, dprob, dev, world, dist, products):
+    """Same metric through the public call with host buffers: per step the
+    inputs are copied from pinned host memory, C is computed, and C is read
+    back into pinned host memory, all inside the timed region."""
+    import torch
+    hosts = []
+    for sr, A, B, dA, dB, out, nnz in dprob:
+        hA = [t.cpu().pin_memory() for t in (dA.row_ptr, dA.col, dA.val)]
+        hB = None if dB is dA else [t.cpu().pin_memory() for t in (dB.row_ptr, dB.col, dB.val)]
+        hosts.append((hA, hB))
+    max_nnz = max(p[6] for p in dprob)
+    max_rows = max(p[1].nrows for p in dprob)
+    vmax = max(VAL_BYTES[p[0]] for p in dprob)
+    hC = (torch.empty(max_rows + 1, dtype=torch.int64, pin_memory=True),
+          torch.empty(max(max_nnz, 1), dtype=torch.int32, pin_memory=True),
+          torch.empty(max(max_nnz, 1) * vmax, dtype=torch.uint8, pin_memory=True))
+    moved = {"h2d": 0, "d2h": 0}
+
+    def one(count):
+        for (sr, A, B, dA, dB, out, nnz), (hA, hB) in zip(dprob, hosts):
+            pairs = list(zip((dA.row_ptr, dA.col, dA.val), hA))
+            if hB is not None:
+                pairs += list(zip((dB.row_ptr, dB.col, dB.val), hB))
+            for dst, src in pairs:
+                dst.copy_(src, non_blocking=True)
+                if count:
+                    moved["h2d"] += src.numel() * src.element_size()
+            C = cb.spgemm(sr, dA, dB, validate=False, out=out, ctx=ctx)
+            n = C.nnz
+            val = C.val.view(torch.int32) if C.val.dtype == torch.uint32 else C.val
+            vb = val.view(torch.uint8)
+            hC[0][: C.nrows + 1].copy_(C.row_ptr, non_blocking=True)
+            hC[1][:n].copy_(C.col, non_blocking=True)
+            hC[2][: vb.numel()].copy_(vb, non_blocking=True)
+            if count:
+                moved["d2h"] += (C.nrows + 1) * 8 + n * 4 + vb.numel()
+        torch.cuda.synchronize()
+
+    one(False)
+    if dist:
+        dist.barrier()
+    steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one(True)
+    el = (time.perf_counter() - t0) / steps
+    if dist:
+        t = torch.tensor([el], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    return {"value": world * products / el, "unit": UNIT,
+            "h2d_bytes_per_step": moved["h2d"] // steps, "d2h_bytes_per_step": moved["d2h"] // steps,
+            "ms_per_step": el * 1e3, "steps": steps, "timing": "host wall clock, synchronised"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="rmat18", choices=("rmat18", "er16k"))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return main_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

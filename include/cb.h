@@ -1,14 +1,14 @@
 /*
  * cb.h -- C ABI of the GB300 semiring SpGEMM library (libcb.so).
  *
- * Operation (paper Sec. 2.3, "Notation"; Sec. 5.1, "Multithreaded SpGEMM"):
+ * Operation (paper Sec. 3.1, the SpGEMM notation; Sec. 4.1, multithreaded SpGEMM):
  *   C = A (+).(x) B  with A in S^{m x n}, B in S^{n x k}, C in S^{m x k},
  *   computed row by row with Gustavson's formulation: row i of C merges the
  *   rows of B selected by the stored entries of row i of A.  The pattern of C
  *   is structural: (i,j) is stored iff some stored A(i,p) meets some stored
  *   B(p,j); every such pair contributes one (x)-product, and products are
  *   (+)-combined (entries equal to zero or to the (+)-identity are kept).
- *   Sec. 5.1 splits the work into (1) a flops estimate and load balance,
+ *   Sec. 4.1 splits the work into (1) a flops estimate and load balance,
  *   (2) a symbolic phase that sizes C, (3) a numeric phase with a hash
  *   accumulator; Sec. 7.2 forms C in column batches when it does not fit.
  *
@@ -75,7 +75,7 @@ typedef struct cb_ctx cb_ctx;
 
 /* How C's per-row sizes are obtained before the numeric phase. */
 typedef enum {
-  CB_SIZING_EXACT = 0,       /* symbolic phase (paper Sec. 5.1 phase (2))       */
+  CB_SIZING_EXACT = 0,       /* symbolic phase (paper Sec. 4.1, phase (2))      */
   CB_SIZING_LEARNED = 1,     /* MLP prediction, exact fallback on overflow      */
   CB_SIZING_UPPER_BOUND = 2  /* min(flops_i, ncols) per row, exact fallback     */
 } cb_sizing;
@@ -144,16 +144,22 @@ int cb_spgemm(cb_semiring sr, const cb_csr *A, const cb_csr *B, cb_csr *C);
 int cb_spgemm_ex(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B,
                  cb_csr *C, const cb_opts *opt);
 
-/* Release arrays that the library allocated for C; zeroes *C. */
+/* Release arrays that the library allocated for C; zeroes *C.  Waits for all
+ * work on the device to finish first, so it is safe right after an
+ * asynchronous cb_spgemm_ex. */
 void cb_csr_free(cb_csr *C);
+/* Stream-ordered release on ctx's stream: the arrays are freed after the work
+ * already queued on that stream (e.g. the kernels that write C) completes.
+ * The caller must not use C's arrays on other streams afterwards. */
+int cb_csr_free_async(cb_ctx *ctx, cb_csr *C);
 
 /* ---- individual steps of the path (device outputs, async) ---------------
- * cb_row_stats: paper Sec. 5.1 phase (1) and Table 1 ("flops").  For each row
+ * cb_row_stats: paper Sec. 4.1, phase (1), and Table 1 (flops).  For each row
  *   i of A: flops[i] = sum over stored A(i,p) of nnz(B(p,:)) (int64[m]),
  *   maxb[i] = max of those B row lengths (int32[m], 0 for empty rows).
  *   Either output may be NULL.
- * cb_row_nnz: paper Sec. 5.1 phase (2) ("symbolic phase ... computes the
- *   pattern").  nnz_out[i] = number of distinct columns in row i of A.B
+ * cb_row_nnz: paper Sec. 4.1, phase (2) (the symbolic phase that finds the
+ *   pattern of C).  nnz_out[i] = number of distinct columns in row i of A.B
  *   (int64[m]).
  * cb_exclusive_scan: row pointers from row sizes: out[0] = 0,
  *   out[i+1] = out[i] + in[i] for i < n (int64 in[n], out[n+1]).

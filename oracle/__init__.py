@@ -6,8 +6,8 @@ and this package imports nothing from the library (it shares no code with
 the CUDA path).
 
 `spgemm` wraps oracle.cpp: a plain Gustavson SpGEMM with one ordered map per
-output row (paper Sec. 5.1), over the five semirings named below.
-`row_stats` gives flops_i and max_p nnz(B(p,:)) per row (Sec. 5.1 phase (1);
+output row (paper Sec. 4.1), over the five semirings named below.
+`row_stats` gives flops_i and max_p nnz(B(p,:)) per row (Sec. 4.1, phase (1);
 Table 1 defines flops).  `mlp` holds the FP64 reference of the learned row
 size predictor.
 """

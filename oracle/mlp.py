@@ -1,9 +1,9 @@
 """FP64 reference of the learned per-row nnz(C) predictor -- TEST INFRASTRUCTURE ONLY.
 
-The paper replaces exact memory-requirement estimation by "faster memory
-requirement estimation that involves approximate algorithms" (Sec. 6,
-"Optimizations"), and sizes batched SpGEMM from a symbolic step (Sec. 7.2,
-Fig. 8 caption).  The predictor here is that approximate estimator: a
+The paper's GPU path speeds up the estimate of the output's memory needs
+with approximate algorithms (Sec. 5, the optimizations paragraph), and it
+sizes batched SpGEMM from a symbolic step (Sec. 7.4, caption of the CA
+SpGEMM strong-scaling figure).  The predictor here is that approximate estimator: a
 3 -> 64 -> 64 -> 1 MLP over three per-row features of the product.  The paper
 fixes none of its details; this file is the plain statement of the reading
 used (every step written out in numpy float64):

@@ -5,14 +5,14 @@
 // CPU-baseline leg may load it; the library's product path never does.  It
 // shares no code, header, table or constant with the CUDA sources.
 //
-// Definition followed (paper Sec. 2.3 and Sec. 5.1):
-//   * C = A B with A in S^{m x n}, B in S^{n x k}, C in S^{m x k} (Sec. 2.3).
-//   * Gustavson's formulation (Sec. 5.1, "Multithreaded SpGEMM"): output
+// Definition followed (paper Sec. 3.1 and Sec. 4.1):
+//   * C = A B with A in S^{m x n}, B in S^{n x k}, C in S^{m x k} (Sec. 3.1).
+//   * Gustavson's formulation (Sec. 4.1, multithreaded SpGEMM): output
 //     line i of C is the merge of the B lines selected by the nonzeros of
 //     A's line i.  The paper states it column-wise on CSC; on CSR rows the
 //     same statement holds for C^T = B^T A^T, so here rows play the role of
 //     the paper's columns.
-//   * The pattern of C is structural (the symbolic phase of Sec. 5.1 computes
+//   * The pattern of C is structural (the symbolic phase of Sec. 4.1 derives
 //     it from the input patterns alone): (i,j) is stored iff some stored
 //     A(i,p) meets some stored B(p,j).  An entry is kept even when its value
 //     equals the (+)-identity or zero.
@@ -20,7 +20,7 @@
 //     products of an entry are (+)-combined in storage order: A's row i in
 //     storage order, and for each of its entries, B's row in storage order.
 //     Duplicate coordinates in A or B therefore contribute separately.
-//   * flops (Table 1: "the number of nonzero arithmetic operations") is the
+//   * flops (Table 1: the count of arithmetic operations on nonzeros) is the
 //     number of (x)-products, flops_i = sum over A(i,p) of nnz(B(p,:)).
 //
 // Semirings (the paper allows any; these five are the ones exercised):
@@ -168,7 +168,7 @@ int run(int64_t m, const int64_t* Arp, const int32_t* Acol, const void* Aval_,
 
 extern "C" {
 
-// Per-row statistics of the product A.B (Sec. 5.1 phase (1), Table 1):
+// Per-row statistics of the product A.B (Sec. 4.1, phase (1); Table 1):
 // flops[i] = sum over stored A(i,p) of nnz(B(p,:)); maxb[i] = max of those
 // nnz(B(p,:)) (0 for an empty row).
 int orc_row_stats(int64_t m, const int64_t* Arp, const int32_t* Acol,

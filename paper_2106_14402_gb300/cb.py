@@ -80,6 +80,7 @@ _SIGS = {
     "cb_spgemm_ex": ([c_void_p, ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr),
                       ctypes.POINTER(cb_csr), ctypes.POINTER(cb_opts)], ctypes.c_int),
     "cb_csr_free": ([ctypes.POINTER(cb_csr)], None),
+    "cb_csr_free_async": ([c_void_p, ctypes.POINTER(cb_csr)], ctypes.c_int),
     "cb_row_stats": ([c_void_p, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr), c_void_p, c_void_p],
                      ctypes.c_int),
     "cb_row_nnz": ([c_void_p, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr), c_void_p], ctypes.c_int),
@@ -166,15 +167,16 @@ _TYPESTR = {torch.int64: "<i8", torch.float64: "<f8", torch.uint32: "<u4", torch
 
 
 class _Owner:
-    """Frees library-allocated C arrays when the last tensor viewing them dies."""
+    """Frees library-allocated C arrays when the last tensor viewing them dies,
+    in stream order on the context's stream (after the kernels writing them)."""
 
-    def __init__(self, lib, csr: cb_csr):
-        self.lib = lib
+    def __init__(self, ctx, csr: cb_csr):
+        self.ctx = ctx
         self.csr = csr
 
     def __del__(self):
         try:
-            self.lib.cb_csr_free(ctypes.byref(self.csr))
+            self.ctx.lib.cb_csr_free_async(self.ctx.handle, ctypes.byref(self.csr))
         except Exception:
             pass
 
@@ -292,7 +294,7 @@ def spgemm(semiring: str, A: DeviceCSR, B: DeviceCSR, *, validate: bool = True, 
     sc = cb_csr()
     ctx.check(ctx.lib.cb_spgemm_ex(ctx.handle, code, ctypes.byref(sa), ctypes.byref(sb),
                                    ctypes.byref(sc), ctypes.byref(opts)))
-    owner = _Owner(ctx.lib, cb_csr(sc.nrows, sc.ncols, sc.nnz, sc.row_ptr, sc.col, sc.val))
+    owner = _Owner(ctx, cb_csr(sc.nrows, sc.ncols, sc.nnz, sc.row_ptr, sc.col, sc.val))
     dev = A.row_ptr.device
     return DeviceCSR(sc.nrows, sc.ncols, _wrap(sc.row_ptr, sc.nrows + 1, torch.int64, owner, dev),
                      _wrap(sc.col, sc.nnz, torch.int32, owner, dev),

@@ -374,10 +374,10 @@ int cb_spgemm_ex(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, 
     return CB_OK;
   } catch (const Fail& f) {
     if (!caller_buf && C) {
+      if (C->row_ptr && C->row_ptr != saved.row_ptr) cudaFreeAsync(C->row_ptr, ctx->stream);
+      if (C->col && C->col != saved.col) cudaFreeAsync(C->col, ctx->stream);
+      if (C->val && C->val != saved.val) cudaFreeAsync(C->val, ctx->stream);
       cudaStreamSynchronize(ctx->stream);
-      if (C->row_ptr && C->row_ptr != saved.row_ptr) cudaFree(C->row_ptr);
-      if (C->col && C->col != saved.col) cudaFree(C->col);
-      if (C->val && C->val != saved.val) cudaFree(C->val);
       std::memset(C, 0, sizeof *C);
     }
     return f.code;
@@ -399,10 +399,20 @@ int cb_spgemm(cb_semiring sr, const cb_csr* A, const cb_csr* B, cb_csr* C) {
 
 void cb_csr_free(cb_csr* C) {
   if (!C) return;
+  if (C->row_ptr || C->col || C->val) cudaDeviceSynchronize();
   if (C->row_ptr) cudaFree(C->row_ptr);
   if (C->col) cudaFree(C->col);
   if (C->val) cudaFree(C->val);
   std::memset(C, 0, sizeof *C);
+}
+
+int cb_csr_free_async(cb_ctx* ctx, cb_csr* C) {
+  if (!ctx || !C) return CB_ERR_ARG;
+  int rc = CB_OK;
+  for (void* p : {(void*)C->row_ptr, (void*)C->col, C->val})
+    if (p && cudaFreeAsync(p, ctx->stream) != cudaSuccess) rc = CB_ERR_CUDA;
+  std::memset(C, 0, sizeof *C);
+  return rc;
 }
 
 int cb_row_stats(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, int64_t* flops, int32_t* maxb) {

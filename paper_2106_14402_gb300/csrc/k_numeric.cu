@@ -1,5 +1,5 @@
-// K5-K7: numeric phase (paper Sec. 5.1 phase (3): "performs the actual
-// multiplication using the ... hash table"), with the in-row sort that makes
+// K5-K7: numeric phase (paper Sec. 4.1, phase (3): the products are formed
+// and combined in a hash-table accumulator), with the in-row sort that makes
 // every output row strictly increasing in column.
 //
 // Tiers by the exact row size nz = nnz(C_i) from the symbolic phase:

@@ -1,5 +1,5 @@
 // Row-level kernels of the SpGEMM path: input validation, the per-row flops
-// estimate and load-balance binning (paper Sec. 5.1 phase (1)), the int64
+// estimate and load-balance binning (paper Sec. 4.1, phase (1)), the int64
 // exclusive scan that turns row sizes into row pointers, and the list of
 // heavy-row column-slice work units.
 #include "cb_common.cuh"
@@ -27,7 +27,7 @@ __global__ void k_validate(DevCSR M, int64_t nnz, int code_base, int64_t* counte
 }
 
 // K1: one warp per row of A.  flops_i = sum of B row lengths over the row's
-// stored entries (Table 1's flops), maxb_i = the longest of them.
+// stored entries (the flops count of Table 1), maxb_i = the longest of them.
 __global__ void __launch_bounds__(256) k_classify_sym(DevCSR A, DevCSR B, int64_t* flops,
                                                       int32_t* maxb, int64_t* counters) {
   __shared__ unsigned long long hist[kSymTiers];

@@ -1,5 +1,5 @@
-// K3: symbolic phase (paper Sec. 5.1 phase (2): "computes the pattern" of C
-// to size it).  nnz(C_i) = |union over stored A(i,p) of cols(B(p,:))|.
+// K3: symbolic phase (paper Sec. 4.1, phase (2): the pattern of C is found
+// from the input patterns alone, which sizes C before any value is formed).  nnz(C_i) = |union over stored A(i,p) of cols(B(p,:))|.
 //
 // Rows are processed by tier of u_i = min(flops_i, ncols):
 //   * u <= 128:  one warp per row, insert-only hash of 2^ceil(log2 2u) keys

@@ -6,10 +6,10 @@ that both sides of a parity test see the same bytes.  Every matrix it emits
 has strictly increasing column indices within a row (sorted, no duplicates).
 
 Shapes follow the paper's workloads:
-  * R-MAT with Graph500-style quadrant probabilities (Section 4.3 uses a
-    1M x 1M R-MAT with the Graph500 parameters), symmetrised, duplicates
-    removed, vertices randomly permuted (Section 3.1: random permutation at
-    assembly for load balance);
+  * R-MAT with Graph500-style quadrant probabilities (the sparsity study of
+    Sec. 4.5 uses an R-MAT with the Graph500 parameters), symmetrised,
+    duplicates removed, vertices randomly permuted (Sec. 3.1 balances load by
+    permuting matrices at assembly);
   * Erdos-Renyi rows with an exact number of distinct uniform columns;
   * banded matrices (a family with strong locality).
 The paper's own matrices (Table 4) are not available; these stand in for them.

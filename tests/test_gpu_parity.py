@@ -271,3 +271,18 @@ def test_invalid_inputs_are_rejected(cb):
     assert e.value.code == 4
     # the context is still usable afterwards
     compare_rows(sr, cb.spgemm(sr, dA, dB).to_host(), oracle.spgemm(sr, A, B))
+
+
+def test_drop_result_without_sync(cb):
+    # The library-allocated C is released in stream order, so dropping it
+    # while its kernels are still queued is safe.
+    sr = "plus_times_f64"
+    A = gen.rmat(14, 16, *gen.RMAT_ABCD, seed=90)
+    A = A.with_values(gen.random_values(sr, A.nnz, 91))
+    dA = cb.DeviceCSR.from_host(A, sr)
+    for _ in range(3):
+        C = cb.spgemm(sr, dA, dA)
+        del C
+    got = cb.spgemm(sr, dA, dA).to_host()
+    rows = np.arange(0, A.nrows, 97)
+    compare_rows(sr, got, oracle.spgemm(sr, A, A, rows=rows), rows=rows)
