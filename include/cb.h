@@ -61,7 +61,8 @@ enum {
   CB_ERR_BUDGET = 6,    /* one output row (or batch unit) exceeds the budget   */
   CB_ERR_TIMEOUT = 7,   /* a bounded device-side wait expired                  */
   CB_ERR_CUDA = 8,      /* a CUDA runtime call failed                          */
-  CB_ERR_CAPACITY = 9   /* caller-provided output too small; C->nnz = needed   */
+  CB_ERR_CAPACITY = 9,  /* caller-provided output too small; C->nnz = needed   */
+  CB_ERR_SCRATCH = 10   /* size beyond a fixed static scratch capacity         */
 };
 
 typedef struct {
@@ -168,6 +169,35 @@ int cb_row_stats(cb_ctx *ctx, const cb_csr *A, const cb_csr *B, int64_t *flops,
                  int32_t *maxb);
 int cb_row_nnz(cb_ctx *ctx, const cb_csr *A, const cb_csr *B, int64_t *nnz_out);
 int cb_exclusive_scan(cb_ctx *ctx, const int64_t *in, int64_t n, int64_t *out);
+
+/* ---- allocation-free scan ------------------------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers
+ * that cannot allocate device memory when they need the row-pointer scan: a
+ * process whose device memory is entirely owned by another allocator (for
+ * example a framework's caching pool that reserved the GPU), or a
+ * latency-critical loop that must not pay for cudaMalloc's implicit device
+ * synchronisation.
+ *
+ * cb_exclusive_scan_noalloc: same result as cb_exclusive_scan (out[0] = 0,
+ *   out[i+1] = out[i] + in[i]; device int64 in[n], out[n+1]), enqueued on
+ *   `cuda_stream` (a cudaStream_t, NULL = legacy default stream) of the
+ *   current device.  It takes no context and calls no cudaMalloc, cudaFree or
+ *   other allocating routine: its scratch (one int64 partial sum per 4096
+ *   entries) is a fixed device array of 65,537 int64 (512 KiB + 8 bytes)
+ *   inside the library, which every GPU that loads the library holds until
+ *   the process exits.
+ *   - n may be at most 268,435,456; larger n returns CB_ERR_SCRATCH and
+ *     launches nothing.  Bad pointers or n < 0 return CB_ERR_ARG.
+ *   - The first call on each device looks up the array's device address
+ *     (with that device current) and caches it; make that first call before
+ *     any stream capture.
+ *   - Every call on a device shares the one array, and the array keeps the
+ *     last call's contents (nothing needs clearing: each call writes every
+ *     entry it reads).  Calls whose work overlaps on the GPU (unordered
+ *     streams, or several host threads) race on it and give wrong results:
+ *     order them on one stream or with events.
+ *   Returns CB_OK or CB_ERR_CUDA (launch failure). */
+int cb_exclusive_scan_noalloc(const int64_t *in, int64_t n, int64_t *out, void *cuda_stream);
 
 /* Statistics of the most recent cb_spgemm_ex on this context (host memory). */
 typedef struct {

@@ -31,7 +31,7 @@ SIZING = {"exact": 0, "learned": 1, "upper_bound": 2}
 
 STATUS = {0: "CB_OK", 1: "CB_ERR_ARG", 2: "CB_ERR_SHAPE", 3: "CB_ERR_SEMIRING", 4: "CB_ERR_INDEX",
           5: "CB_ERR_OOM", 6: "CB_ERR_BUDGET", 7: "CB_ERR_TIMEOUT", 8: "CB_ERR_CUDA",
-          9: "CB_ERR_CAPACITY"}
+          9: "CB_ERR_CAPACITY", 10: "CB_ERR_SCRATCH"}
 
 
 class cb_csr(ctypes.Structure):
@@ -85,6 +85,7 @@ _SIGS = {
                      ctypes.c_int),
     "cb_row_nnz": ([c_void_p, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr), c_void_p], ctypes.c_int),
     "cb_exclusive_scan": ([c_void_p, c_void_p, c_int64, c_void_p], ctypes.c_int),
+    "cb_exclusive_scan_noalloc": ([c_void_p, c_int64, c_void_p, c_void_p], ctypes.c_int),
     "cb_last_stats": ([c_void_p, ctypes.POINTER(cb_stats)], ctypes.c_int),
 }
 

@@ -344,6 +344,7 @@ const char* cb_status_str(int s) {
     case CB_ERR_TIMEOUT: return "bounded device wait expired";
     case CB_ERR_CUDA: return "CUDA error";
     case CB_ERR_CAPACITY: return "caller-provided output too small";
+    case CB_ERR_SCRATCH: return "size beyond the static scratch capacity";
   }
   return "unknown status";
 }
