@@ -207,28 +207,27 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_csr*
   for (int t = 2; t < cb::kSymTiers; ++t) sym_beg[t] = sym_beg[t - 1] + sym_cnt[t - 1];
   ctx->stats.flops = ctx->host[cb::kTotalFlops];
   const int64_t n_heavy = sym_cnt[cb::kSymHeavy];
-  const int64_t wnum = cb::num_slice_width(sr);
-  const int64_t num_slices = (ncols + wnum - 1) / wnum;
+  const int64_t spans = (ncols + cb::kSpanCols - 1) / cb::kSpanCols;
+  const int wcut = cb::num_window_cut(sr);
+  // every (row, span) yields at most count/wcut + 1 windows; counts sum to <= flops
+  const int64_t win_cap = n_heavy * spans + ctx->stats.flops / wcut + 1;
 
-  size_t need2 = align_up(4 * (size_t)(n_heavy * num_slices) + 4) +
-                 align_up(8 * (size_t)(n_heavy * num_slices) + 8);
+  size_t need2 = align_up(4 * (size_t)(n_heavy * spans) + 4) + align_up(sizeof(cb::Window) * (size_t)win_cap);
   ensure(ctx, &ctx->ws2, &ctx->ws2_cap, need2);
   Carver cv2{static_cast<char*>(ctx->ws2)};
-  int32_t* slice_counts = cv2.take<int32_t>(n_heavy * num_slices + 1);
-  int2* units = cv2.take<int2>(n_heavy * num_slices + 1);
+  int32_t* span_counts = cv2.take<int32_t>(n_heavy * spans + 1);
+  cb::Window* wins = cv2.take<cb::Window>(win_cap);
   const int32_t* heavy_rows = perm_sym + sym_beg[cb::kSymHeavy];
 
   int launches = 0;
-  cb::launch_symbolic(dA, dB, perm_sym, sym_beg, sym_cnt, flops, nnz, slice_counts, wnum,
-                      num_slices, ctx->stream, ctx->sms, &launches);
+  cb::launch_symbolic(dA, dB, perm_sym, sym_beg, sym_cnt, flops, nnz, span_counts, wcut, wins,
+                      win_cap, counters, ctx->stream, ctx->sms, &launches);
   mark(ctx, opt, 2);
   cb::launch_exclusive_scan(nnz, m, C->row_ptr, partial, ctx->stream);
   cb::launch_classify_num(sr, m, nnz, perm_num, counters, ctx->stream, ctx->sms);
-  cb::launch_build_units(sr, n_heavy, heavy_rows, nnz, slice_counts, num_slices, units, counters,
-                         ctx->stream);
   CB_LAUNCHED();
   mark(ctx, opt, 3);
-  ctx->stats.kernels += launches + 3 + 2 + (n_heavy ? 1 : 0);
+  ctx->stats.kernels += launches + 3 + 2;
   read_counters(ctx, counters, C->row_ptr + m, 1);
 
   const int64_t total = ctx->host[cb::kCounters];
@@ -238,6 +237,12 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_csr*
   num_beg[1] = 0;
   for (int t = 2; t < cb::kNumTiers; ++t) num_beg[t] = num_beg[t - 1] + num_cnt[t - 1];
   const int64_t n_units = ctx->host[cb::kUnits];
+  if (ctx->host[cb::kError]) {
+    char msg[96];
+    std::snprintf(msg, sizeof msg, "symbolic phase consistency check failed (code %lld)",
+                  (long long)ctx->host[cb::kError]);
+    fail(ctx, CB_ERR_CUDA, msg);
+  }
   ctx->stats.nnz = total;
   ctx->stats.heavy_rows = num_cnt[cb::kNumHeavy];
   ctx->stats.heavy_units = n_units;
@@ -262,8 +267,8 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_csr*
 
   launches = 0;
   mark(ctx, opt, 4);
-  cb::launch_numeric(sr, dA, dB, perm_num, num_beg, num_cnt, flops, nnz, heavy_rows, units,
-                     n_units, slice_counts, num_slices, C->row_ptr, C->col, C->val,
+  cb::launch_numeric(sr, dA, dB, perm_num, num_beg, num_cnt, flops, nnz, heavy_rows, wins,
+                     n_units, span_counts, spans, C->row_ptr, C->col, C->val,
                      counters + cb::kError, ctx->stream, ctx->sms, &launches);
   CB_LAUNCHED();
   mark(ctx, opt, 5);
@@ -468,12 +473,12 @@ int cb_row_nnz(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, int64_t* nnz_out) 
     beg[0] = beg[1] = 0;
     for (int t = 2; t < cb::kSymTiers; ++t) beg[t] = beg[t - 1] + cnt[t - 1];
     const int64_t n_heavy = cnt[cb::kSymHeavy];
-    const int64_t wnum = cb::num_slice_width(CB_PLUS_TIMES_I64);
-    const int64_t slices = (ncols + wnum - 1) / wnum;
-    ensure(ctx, &ctx->ws2, &ctx->ws2_cap, align_up(4 * (size_t)(n_heavy * slices) + 4));
+    const int64_t spans = (ncols + cb::kSpanCols - 1) / cb::kSpanCols;
+    ensure(ctx, &ctx->ws2, &ctx->ws2_cap, align_up(4 * (size_t)(n_heavy * spans) + 4));
     int launches = 0;
     cb::launch_symbolic(dA, dB, perm, beg, cnt, flops, nnz_out, static_cast<int32_t*>(ctx->ws2),
-                        wnum, slices, ctx->stream, ctx->sms, &launches);
+                        cb::num_window_cut(CB_PLUS_TIMES_F64), nullptr, 0, counters, ctx->stream,
+                        ctx->sms, &launches);
     CB_LAUNCHED();
     return CB_OK;
   } catch (const Fail& f) {

@@ -78,26 +78,43 @@ template <> struct Sem<5> {  // (select2nd,min) over int32
 
 // ---------------------------------------------------------------------------
 // Tier limits.  Symbolic tiers are chosen by u_i = min(flops_i, ncols) (an
-// upper bound of nnz(C_i)); numeric tiers by the exact nnz(C_i).  A row
-// whose bound exceeds kSymHashMax is counted with a dense bitmap instead of
-// a hash table; a row whose nnz exceeds the numeric hash limit is computed
-// by dense column slices.  kSymHashMax <= every numeric hash limit, so each
-// numeric-heavy row was counted slice by slice in the symbolic phase.
+// upper bound of nnz(C_i)); numeric tiers by the exact nnz(C_i).
+//   * u <= 512: counted with a shared-memory hash table (warp or 256-thread
+//     team); u > 512: counted with a dense bitmap per span of kSpanCols
+//     columns, which also cuts the row into rank windows (below).
+//   * nnz <= 512: numeric in a shared-memory hash table + bitonic sort;
+//     nnz > 512: numeric per rank window.  Every such row has u > 512, so its
+//     windows exist.
+// A rank window is a run of whole bitmap words of one span holding at most
+// NumLimits<SR>::kWcap output entries; inside it an output column's slot is
+// its rank (popcount of the set bits before it), so a dense array of kWcap
+// accumulators indexed by rank holds the window and reads out sorted.
 // ---------------------------------------------------------------------------
 constexpr int kEmptyKey = -1;
 
 constexpr int kSymWarpMax = 128;     // warp team, table <= 256 slots
-constexpr int kSymSmallMax = 1024;   // 256-thread team, table <= 2048
-constexpr int kSymHashMax = 4096;    // 1024-thread team, table <= 8192
-constexpr int kSymSliceBits = 1 << 20;  // dense bitmap slice (128 KB)
+constexpr int kSymSmallMax = 512;    // 256-thread team, table <= 1024
+constexpr int kSymHashMax = 512;     // above: dense bitmap spans
+constexpr int kSpanCols = 1 << 18;   // columns per bitmap span
+constexpr int kSpanWords = kSpanCols / 32;
+constexpr int kMaxWindowsPerSpan = 64;
 
 constexpr int kNumWarpMax = 64;      // warp team, table <= 128
 constexpr int kNumSmallMax = 512;    // 256-thread team, table <= 1024
 template <int SR> struct NumLimits {
-  // The large hash tier keeps keys + accumulators for <= kHashMax entries at
-  // a load factor <= 1/2; the dense slice keeps kSlice accumulators + bitmap.
-  static constexpr int kHashMax = sizeof(typename Sem<SR>::A) == 8 ? 4096 : 8192;
-  static constexpr int kSlice = sizeof(typename Sem<SR>::A) == 8 ? 16384 : 32768;
+  static constexpr int kHashMax = kNumSmallMax;
+  // accumulators per rank window
+  static constexpr int kWcap = sizeof(typename Sem<SR>::A) == 8 ? 16384 : 32768;
+  // window cut: a window starts where the running count crosses a multiple
+  // of kWcut, so it holds at most kWcut + 31 <= kWcap entries
+  static constexpr int kWcut = kWcap - 32;
+};
+
+// One rank window of a heavy row: row index h into the heavy-row list, the
+// span, the word range [w_lo, w_hi) inside the span, its entry count and the
+// rank of its first entry within the span.
+struct Window {
+  int32_t h, span, w_lo, w_hi, count, rank;
 };
 
 enum SymTier { kSymEmpty = 0, kSymWarp = 1, kSymSmall = 2, kSymLarge = 3, kSymHeavy = 4, kSymTiers = 5 };
@@ -163,6 +180,42 @@ __device__ __forceinline__ int group_log2(int64_t flops, int64_t nnz_a) {
   while (g < 5 && (int64_t(2) << g) <= avg) ++g;
   int lim = TEAM_MAX >= 32 ? 5 : ceil_log2(TEAM_MAX);
   return g < lim ? g : lim;
+}
+
+// Exclusive scan of one int per thread across a team of TEAM threads.
+template <int TEAM>
+__device__ __forceinline__ int team_exclusive_scan(int x, int* scratch /* >= 33 ints */, int& total) {
+  const int lane = threadIdx.x & 31;
+  int incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (TEAM == 32) {
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - x;
+  }
+  const int w = threadIdx.x >> 5;
+  constexpr int NW = TEAM / 32;
+  if (lane == 31) scratch[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int v = lane < NW ? scratch[lane] : 0;
+    int vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, vi, o);
+      if (lane >= o) vi += y;
+    }
+    if (lane < NW) scratch[lane] = vi - v;
+    if (lane == NW - 1) scratch[32] = vi;
+  }
+  __syncthreads();
+  total = scratch[32];
+  const int r = scratch[w] + incl - x;
+  __syncthreads();
+  return r;
 }
 
 }  // namespace cb

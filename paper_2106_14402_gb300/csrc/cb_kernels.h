@@ -7,6 +7,8 @@
 
 namespace cb {
 
+struct Window;
+
 struct DevCSR {
   int64_t nrows, ncols;
   const int64_t* rp;
@@ -21,7 +23,7 @@ enum Counter {
   kCntNum = 10,         // [5] rows per numeric tier
   kCurNum = 15,         // [5]
   kTotalFlops = 20,
-  kUnits = 21,          // heavy (row, slice) units
+  kUnits = 21,          // rank windows appended by the symbolic phase
   kError = 22,          // validation / overflow error word
   kErrDetail = 23,
   kCounters = 32
@@ -45,30 +47,29 @@ int64_t scan_partials(int64_t n);
 void launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* partial,
                            cudaStream_t s);
 
-// Numeric binning by exact row size, and heavy (row, slice) unit list.
+// Numeric binning by exact row size.
 void launch_classify_num(int sr, int64_t m, const int64_t* nnz, int32_t* perm,
                          int64_t* counters, cudaStream_t s, int sms);
-void launch_build_units(int sr, int64_t n_heavy, const int32_t* heavy_rows, const int64_t* nnz,
-                        const int32_t* slice_counts, int64_t slices, int2* units,
-                        int64_t* counters, cudaStream_t s);
 
 // K3: symbolic phase, all tiers.  perm holds the tier segments in order;
-// seg_begin[t] / seg_count[t] are host copies of the tier layout.
-// slice_counts: int32[n_heavy * num_slices] per numeric slice of width
-// num_slice_w.
+// seg_begin[t] / seg_count[t] are host copies of the tier layout.  Heavy
+// rows (tier 4) write span_counts[h * spans + span] and, when wins is
+// non-null, append their rank windows (cut every `wcut` entries) to wins
+// (capacity win_cap; counters[kUnits] counts them).
 void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,
                      const int64_t* seg_begin, const int64_t* seg_count, const int64_t* flops,
-                     int64_t* nnz, int32_t* slice_counts, int64_t num_slice_w,
-                     int64_t num_slices, cudaStream_t s, int sms, int* launches);
+                     int64_t* nnz, int32_t* span_counts, int wcut, Window* wins,
+                     int64_t win_cap, int64_t* counters, cudaStream_t s, int sms,
+                     int* launches);
 
-// K5-K7: numeric phase over the numeric tier segments + heavy units, writing
-// sorted rows of C at Crp.
-int num_slice_width(int sr);
+// K5-K7: numeric phase over the numeric tier segments + rank windows,
+// writing sorted rows of C at Crp.
+int num_window_cut(int sr);
 int num_hash_max(int sr);
 void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* perm,
                     const int64_t* seg_begin, const int64_t* seg_count, const int64_t* flops,
-                    const int64_t* nnz, const int32_t* heavy_rows, const int2* units,
-                    int64_t n_units, const int32_t* slice_counts, int64_t num_slices,
+                    const int64_t* nnz, const int32_t* heavy_rows, const Window* wins,
+                    int64_t n_wins, const int32_t* span_counts, int64_t spans,
                     const int64_t* Crp, int32_t* Ccol, void* Cval, int64_t* err, cudaStream_t s,
                     int sms, int* launches);
 

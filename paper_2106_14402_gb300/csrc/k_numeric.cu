@@ -5,17 +5,14 @@
 // Tiers by the exact row size nz = nnz(C_i) from the symbolic phase:
 //   * nz <= 64:   one warp per row, keys + accumulators in a per-warp table
 //   * nz <= 512:  one 256-thread team per row
-//   * nz <= H:    one 1024-thread team per row (H = 4096 for 8-byte
-//                 accumulators, 8192 for 4-byte ones)
 //   For these, the table has 2^ceil(log2 2nz) slots (load factor <= 1/2);
 //   after accumulation the team compacts the occupied slots, bitonic-sorts
 //   them by column in shared memory and writes the row with coalesced stores.
-//   * heavier:    dense column slices.  One CTA per (row, slice of W columns)
-//                 keeps W accumulators plus a W-bit occupancy bitmap in shared
-//                 memory, scans the whole product stream of the row and keeps
-//                 the products that land in its slice; the bitmap is then
-//                 read in column order, so the slice comes out sorted without
-//                 a sort.  Slice offsets come from the symbolic slice counts.
+//   * heavier:    rank windows (cut by the symbolic phase).  One CTA per
+//                 window rebuilds the window's column bitmap from the row's
+//                 product stream, prefix-counts it, and accumulates each
+//                 product at its column's rank in a dense shared-memory array;
+//                 the window then reads out in column order without a sort.
 // Products are combined with the semiring's atomic (+) on shared memory.
 #include "cb_common.cuh"
 #include "cb_kernels.h"
@@ -26,42 +23,6 @@ namespace {
 
 __device__ __forceinline__ void flag_error(int64_t* err, int64_t code) {
   if (err) atomicCAS((unsigned long long*)err, 0ull, (unsigned long long)code);
-}
-
-// Exclusive scan of one int per thread across a team of TEAM threads.
-template <int TEAM>
-__device__ __forceinline__ int team_exclusive_scan(int x, int* scratch /* >= 33 ints */, int& total) {
-  const int lane = threadIdx.x & 31;
-  int incl = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (TEAM == 32) {
-    total = __shfl_sync(0xffffffffu, incl, 31);
-    return incl - x;
-  }
-  const int w = threadIdx.x >> 5;
-  constexpr int NW = TEAM / 32;
-  if (lane == 31) scratch[w] = incl;
-  __syncthreads();
-  if (w == 0) {
-    int v = lane < NW ? scratch[lane] : 0;
-    int vi = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, vi, o);
-      if (lane >= o) vi += y;
-    }
-    if (lane < NW) scratch[lane] = vi - v;
-    if (lane == NW - 1) scratch[32] = vi;
-  }
-  __syncthreads();
-  total = scratch[32];
-  const int r = scratch[w] + incl - x;
-  __syncthreads();
-  return r;
 }
 
 template <int SR, int CTA, int TEAM, int TABLE_MAX>
@@ -175,51 +136,91 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
   }
 }
 
-// Dense column-slice units for heavy rows.
+// Rank windows of heavy rows (nnz > 512).  One CTA per window: rebuild the
+// window's bitmap from the row's product stream, prefix-count its words,
+// then accumulate every product into the dense accumulator at the column's
+// rank and write the window's slice of the row in column order.
 template <int SR>
-__global__ void __launch_bounds__(1024) k_num_heavy(DevCSR A, DevCSR B, const int32_t* heavy_rows,
-                                                    const int2* units, int64_t n_units,
-                                                    const int32_t* slice_counts, int64_t num_slices,
-                                                    const int64_t* flops, const int64_t* Crp,
-                                                    int32_t* Ccol, typename Sem<SR>::T* Cval,
-                                                    int64_t* err) {
+__global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const int32_t* heavy_rows,
+                                                      const Window* wins, int64_t n_wins,
+                                                      const int32_t* span_counts, int64_t spans,
+                                                      const int64_t* flops, const int64_t* nnz,
+                                                      const int64_t* Crp, int32_t* Ccol,
+                                                      typename Sem<SR>::T* Cval, int64_t* err) {
   typedef Sem<SR> S;
   typedef typename S::A Acc;
   typedef typename S::T T;
-  constexpr int W = NumLimits<SR>::kSlice;
-  constexpr int NW = W / 32;
-  static_assert(NW <= 1024, "one bitmap word per thread");
-  extern __shared__ __align__(16) unsigned char heavy_smem[];
-  Acc* vals = reinterpret_cast<Acc*>(heavy_smem);
-  unsigned* bm = reinterpret_cast<unsigned*>(vals + W);
+  constexpr int WCAP = NumLimits<SR>::kWcap;
+  constexpr int WPT = kSpanWords / 1024;
+  extern __shared__ __align__(16) unsigned char rank_smem[];
+  Acc* acc = reinterpret_cast<Acc*>(rank_smem);
+  unsigned* bm = reinterpret_cast<unsigned*>(acc + WCAP);
+  int* pre = reinterpret_cast<int*>(bm + kSpanWords);
   __shared__ int scratch[33];
-  __shared__ long long s_off;
+  __shared__ long long s_base;
   const int tid = threadIdx.x, lane = tid & 31;
   const T* Aval = reinterpret_cast<const T*>(A.val);
   const T* Bval = reinterpret_cast<const T*>(B.val);
 
-  for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
-    const int2 un = units[u];
-    const int64_t h = un.x, sl = un.y;
-    const int i = heavy_rows[h];
-    const int64_t lo = sl * (int64_t)W;
-    const int64_t hi = min(lo + (int64_t)W, B.ncols);
+  for (int64_t u = blockIdx.x; u < n_wins; u += gridDim.x) {
+    const Window wd = wins[u];
+    const int i = heavy_rows[wd.h];
+    if (nnz[i] <= kNumSmallMax || wd.count <= 0) continue;  // hash tiers own small rows
+    const int cnt = wd.count < WCAP ? wd.count : WCAP;
+    const int64_t span_lo = (int64_t)wd.span * kSpanCols;
+    const int64_t lo = span_lo + 32 * (int64_t)wd.w_lo;
+    const int64_t hi = min(span_lo + 32 * (int64_t)wd.w_hi, B.ncols);
     const unsigned width = (unsigned)(hi - lo);
-    const int nwords = (int)((width + 31) / 32);
-    for (int t = tid; t < (int)width; t += 1024) vals[t] = S::ident();
-    for (int w = tid; w < nwords; w += 1024) bm[w] = 0u;
+    const int nw = wd.w_hi - wd.w_lo;
+    for (int w = tid; w < nw; w += 1024) bm[w] = 0u;
+    for (int t = tid; t < cnt; t += 1024) acc[t] = S::ident();
     if (tid < 32) {
       long long o = 0;
-      for (int64_t t = lane; t < sl; t += 32) o += slice_counts[h * num_slices + t];
+      for (int64_t t = lane; t < wd.span; t += 32) o += span_counts[(int64_t)wd.h * spans + t];
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) o += __shfl_down_sync(0xffffffffu, o, d);
-      if (lane == 0) s_off = o;
+      if (lane == 0) s_base = o + wd.rank;
     }
     __syncthreads();
 
     const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
     const int gl = group_log2<1024>(flops[i], a1 - a0);
     const int G = 1 << gl, gq = tid & (G - 1), groups = 1024 >> gl;
+    // pass 1: the window's columns
+    for (int64_t p = a0 + (tid >> gl); p < a1; p += groups) {
+      const int k = A.col[p];
+      const int64_t b1 = B.rp[k + 1];
+      for (int64_t q = B.rp[k] + gq; q < b1; q += G) {
+        const unsigned off = (unsigned)((int64_t)B.col[q] - lo);
+        if (off < width) {
+          const unsigned bit = 1u << (off & 31);
+          if (!(bm[off >> 5] & bit)) atomicOr(&bm[off >> 5], bit);
+        }
+      }
+    }
+    __syncthreads();
+    // exclusive prefix of word popcounts
+    {
+      int c[WPT];
+      int mine = 0;
+#pragma unroll
+      for (int j = 0; j < WPT; ++j) {
+        const int w = tid * WPT + j;
+        c[j] = w < nw ? __popc(bm[w]) : 0;
+        mine += c[j];
+      }
+      int total;
+      int run = team_exclusive_scan<1024>(mine, scratch, total);
+#pragma unroll
+      for (int j = 0; j < WPT; ++j) {
+        const int w = tid * WPT + j;
+        if (w < nw) pre[w] = run;
+        run += c[j];
+      }
+      if (tid == 0 && total != wd.count) flag_error(err, 23);
+    }
+    __syncthreads();
+    // pass 2: accumulate at the rank of each product's column
     for (int64_t p = a0 + (tid >> gl); p < a1; p += groups) {
       const int k = A.col[p];
       const T a = S::kUsesA ? Aval[p] : T();
@@ -227,29 +228,27 @@ __global__ void __launch_bounds__(1024) k_num_heavy(DevCSR A, DevCSR B, const in
       for (int64_t q = B.rp[k] + gq; q < b1; q += G) {
         const unsigned off = (unsigned)((int64_t)B.col[q] - lo);
         if (off < width) {
-          S::atomic(&vals[off], S::mul(a, Bval[q]));
-          const unsigned bit = 1u << (off & 31);
-          if (!(bm[off >> 5] & bit)) atomicOr(&bm[off >> 5], bit);
+          const int w = off >> 5;
+          const int slot = pre[w] + __popc(bm[w] & ((1u << (off & 31)) - 1u));
+          if (slot < cnt) S::atomic(&acc[slot], S::mul(a, Bval[q]));
         }
       }
     }
     __syncthreads();
-
-    unsigned word = tid < nwords ? bm[tid] : 0u;
-    int total;
-    const int ex = team_exclusive_scan<1024>(__popc(word), scratch, total);
-    if (tid == 0 && total != slice_counts[h * num_slices + sl]) flag_error(err, 22);
-    int64_t o = Crp[i] + s_off + ex;
+    // write the window: values by slot (coalesced), columns by word
+    const int64_t out = Crp[i] + s_base;
     const int64_t row_end = Crp[i + 1];
-    while (word) {
-      const int b = __ffs(word) - 1;
-      word &= word - 1;
-      if (o < row_end) {
-        const int c = tid * 32 + b;
-        Ccol[o] = (int32_t)(lo + c);
-        Cval[o] = S::out(vals[c]);
+    for (int t = tid; t < cnt; t += 1024)
+      if (out + t < row_end) Cval[out + t] = S::out(acc[t]);
+    for (int w = tid; w < nw; w += 1024) {
+      unsigned word = bm[w];
+      int64_t o = out + pre[w];
+      while (word) {
+        const int b = __ffs(word) - 1;
+        word &= word - 1;
+        if (o < row_end) Ccol[o] = (int32_t)(lo + 32 * w + b);
+        ++o;
       }
-      ++o;
     }
     __syncthreads();
   }
@@ -268,8 +267,8 @@ inline int capped(int64_t want, int64_t cap) {
 template <int SR>
 void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int64_t* seg_begin,
                 const int64_t* seg_count, const int64_t* flops, const int64_t* nnz,
-                const int32_t* heavy_rows, const int2* units, int64_t n_units,
-                const int32_t* slice_counts, int64_t num_slices, const int64_t* Crp,
+                const int32_t* heavy_rows, const Window* wins, int64_t n_wins,
+                const int32_t* span_counts, int64_t spans, const int64_t* Crp,
                 int32_t* Ccol, void* Cval_, int64_t* err, cudaStream_t s, int sms, int* launches) {
   typedef typename Sem<SR>::A Acc;
   typedef typename Sem<SR>::T T;
@@ -297,26 +296,25 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
         A, B, perm + seg_begin[kNumLarge], seg_count[kNumLarge], flops, nnz, Crp, Ccol, Cval, err);
     ++*launches;
   }
-  if (n_units) {
-    constexpr int W = NumLimits<SR>::kSlice;
-    const size_t smem = W * sizeof(Acc) + (W / 32) * sizeof(unsigned);
-    set_smem(k_num_heavy<SR>, smem);
-    k_num_heavy<SR><<<capped(n_units, sms), 1024, smem, s>>>(A, B, heavy_rows, units, n_units,
-                                                             slice_counts, num_slices, flops, Crp,
-                                                             Ccol, Cval, err);
+  if (n_wins) {
+    constexpr size_t smem = NumLimits<SR>::kWcap * sizeof(Acc) + 2 * kSpanWords * sizeof(unsigned);
+    set_smem(k_num_rank<SR>, smem);
+    k_num_rank<SR><<<capped(n_wins, sms), 1024, smem, s>>>(A, B, heavy_rows, wins, n_wins,
+                                                           span_counts, spans, flops, nnz, Crp,
+                                                           Ccol, Cval, err);
     ++*launches;
   }
 }
 
 }  // namespace
 
-int num_slice_width(int sr) {
+int num_window_cut(int sr) {
   switch (sr) {
-    case 1: return NumLimits<1>::kSlice;
-    case 2: return NumLimits<2>::kSlice;
-    case 3: return NumLimits<3>::kSlice;
-    case 4: return NumLimits<4>::kSlice;
-    default: return NumLimits<5>::kSlice;
+    case 1: return NumLimits<1>::kWcut;
+    case 2: return NumLimits<2>::kWcut;
+    case 3: return NumLimits<3>::kWcut;
+    case 4: return NumLimits<4>::kWcut;
+    default: return NumLimits<5>::kWcut;
   }
 }
 
@@ -332,13 +330,13 @@ int num_hash_max(int sr) {
 
 void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* perm,
                     const int64_t* seg_begin, const int64_t* seg_count, const int64_t* flops,
-                    const int64_t* nnz, const int32_t* heavy_rows, const int2* units,
-                    int64_t n_units, const int32_t* slice_counts, int64_t num_slices,
+                    const int64_t* nnz, const int32_t* heavy_rows, const Window* wins,
+                    int64_t n_wins, const int32_t* span_counts, int64_t spans,
                     const int64_t* Crp, int32_t* Ccol, void* Cval, int64_t* err, cudaStream_t s,
                     int sms, int* launches) {
 #define CB_NUM(SRV)                                                                        \
-  numeric_sr<SRV>(A, B, perm, seg_begin, seg_count, flops, nnz, heavy_rows, units, n_units, \
-                  slice_counts, num_slices, Crp, Ccol, Cval, err, s, sms, launches)
+  numeric_sr<SRV>(A, B, perm, seg_begin, seg_count, flops, nnz, heavy_rows, wins, n_wins,   \
+                  span_counts, spans, Crp, Ccol, Cval, err, s, sms, launches)
   switch (sr) {
     case 1: CB_NUM(1); break;
     case 2: CB_NUM(2); break;

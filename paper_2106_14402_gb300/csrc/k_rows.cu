@@ -198,32 +198,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int64_t* in, 
   }
 }
 
-// Heavy rows that the numeric phase computes by dense column slices: one
-// unit (h, s) per slice s of heavy row h holding at least one entry.  One
-// warp per heavy row, lanes over its slices.
-__global__ void __launch_bounds__(256) k_build_units(int64_t n_heavy, const int32_t* heavy_rows,
-                                                     const int64_t* nnz, int64_t hash_max,
-                                                     const int32_t* slice_counts, int64_t slices,
-                                                     int2* units, int64_t* counters) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t h = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); h < n_heavy;
-       h += nwarps) {
-    if (nnz[heavy_rows[h]] <= hash_max) continue;
-    for (int64_t s0 = 0; s0 < slices; s0 += 32) {
-      const int64_t s = s0 + lane;
-      const bool live = s < slices && slice_counts[h * slices + s] > 0;
-      const unsigned bal = __ballot_sync(0xffffffffu, live);
-      if (!bal) continue;
-      long long base = 0;
-      if (lane == 0)
-        base = (long long)atomicAdd((unsigned long long*)&counters[kUnits], (unsigned long long)__popc(bal));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (live) units[base + __popc(bal & ((1u << lane) - 1))] = make_int2((int)h, (int)s);
-    }
-  }
-}
-
 inline int grid_for(int64_t work, int per_block, int cap) {
   int64_t g = (work + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -269,14 +243,6 @@ void launch_classify_num(int sr, int64_t m, const int64_t* nnz, int32_t* perm, i
   k_tier_count<<<grid_for(m, 256, sms * 8), 256, 0, s>>>(m, t, counters + kCntNum);
   k_tier_scatter<<<grid_for(m, 256, 1 << 30), 256, 0, s>>>(m, t, perm, counters + kCntNum,
                                                             counters + kCurNum, nullptr);
-}
-
-void launch_build_units(int sr, int64_t n_heavy, const int32_t* heavy_rows, const int64_t* nnz,
-                        const int32_t* slice_counts, int64_t slices, int2* units,
-                        int64_t* counters, cudaStream_t s) {
-  if (n_heavy == 0) return;
-  k_build_units<<<grid_for(n_heavy, 8, 4096), 256, 0, s>>>(
-      n_heavy, heavy_rows, nnz, num_hash_max(sr), slice_counts, slices, units, counters);
 }
 
 }  // namespace cb

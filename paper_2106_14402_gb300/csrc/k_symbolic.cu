@@ -3,11 +3,10 @@
 //
 // Rows are processed by tier of u_i = min(flops_i, ncols):
 //   * u <= 128:  one warp per row, insert-only hash of 2^ceil(log2 2u) keys
-//   * u <= 1024: one 256-thread team per row, same table shape
-//   * u <= 4096: one 1024-thread team per row
-//   * heavier:   dense bitmap of the row's columns, one CTA per (row, slice
-//                of 2^20 columns); popcounts are also recorded per numeric
-//                column slice so the numeric phase can place its output.
+//   * u <= 512:  one 256-thread team per row, same table shape
+//   * heavier:   dense bitmap of the row's columns, one CTA per (row, span
+//                of 2^18 columns); the span is also cut into rank windows
+//                that the numeric phase processes one CTA each.
 // Inside a team, lanes form groups of G = 2^g lanes (G ~ mean B-row length
 // of the row); each group walks one stored A entry's B row with coalesced
 // loads while the groups stride over A's row.
@@ -64,27 +63,31 @@ __global__ void __launch_bounds__(CTA) k_sym_hash(DevCSR A, DevCSR B, const int3
   }
 }
 
-// Heavy rows: one CTA per (heavy row h, symbolic slice ss) unit.  The bitmap
-// covers columns [lo, hi) of the slice; counts are recorded per numeric
-// slice of wnum columns (wnum divides kSymSliceBits and is a multiple of 32).
-__global__ void __launch_bounds__(1024) k_sym_heavy(DevCSR A, DevCSR B, const int32_t* heavy_rows,
-                                                    int64_t n_heavy, int64_t sym_slices,
-                                                    const int64_t* flops, int64_t wnum,
-                                                    int64_t num_slices, int64_t* nnz,
-                                                    int32_t* slice_counts) {
+// Heavy rows (u > 512): one CTA per (heavy row h, span) unit.  The bitmap
+// covers the span's columns [lo, hi); after counting, the span is cut into
+// rank windows of at most wcut + 31 entries (see cb_common.cuh), appended to
+// `wins` (when non-null) for the numeric phase.
+__global__ void __launch_bounds__(1024) k_sym_bitmap(DevCSR A, DevCSR B, const int32_t* heavy_rows,
+                                                     int64_t n_heavy, int64_t spans,
+                                                     const int64_t* flops, int wcut, int64_t* nnz,
+                                                     int32_t* span_counts, Window* wins,
+                                                     int64_t win_cap, int64_t* counters) {
   extern __shared__ unsigned sym_bm[];
-  __shared__ int total;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t units = n_heavy * sym_slices;
+  __shared__ int scratch[33];
+  __shared__ int wstart[kMaxWindowsPerSpan];
+  __shared__ int wrank[kMaxWindowsPerSpan];
+  __shared__ long long wbase;
+  constexpr int WPT = kSpanWords / 1024;  // bitmap words per thread in the scan
+  const int tid = threadIdx.x;
+  const int64_t units = n_heavy * spans;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int64_t h = u / sym_slices, ss = u - h * sym_slices;
+    const int64_t h = u / spans, sp = u - h * spans;
     const int i = heavy_rows[h];
-    const int64_t lo = ss * (int64_t)kSymSliceBits;
-    const int64_t hi = min(lo + (int64_t)kSymSliceBits, B.ncols);
+    const int64_t lo = sp * (int64_t)kSpanCols;
+    const int64_t hi = min(lo + (int64_t)kSpanCols, B.ncols);
     const unsigned width = (unsigned)(hi - lo);
     const int nwords = (int)((width + 31) / 32);
     for (int w = tid; w < nwords; w += 1024) sym_bm[w] = 0u;
-    if (tid == 0) total = 0;
     __syncthreads();
     const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
     const int gl = group_log2<1024>(flops[i], a1 - a0);
@@ -101,21 +104,69 @@ __global__ void __launch_bounds__(1024) k_sym_heavy(DevCSR A, DevCSR B, const in
       }
     }
     __syncthreads();
-    const int64_t s0 = lo / wnum;
-    const int nsub = (int)((width + wnum - 1) / wnum);
-    const int wpw = (int)(wnum / 32);
-    for (int t = warp; t < nsub; t += 32) {
-      int c = 0;
-      const int wend = min((t + 1) * wpw, nwords);
-      for (int w = t * wpw + lane; w < wend; w += 32) c += __popc(sym_bm[w]);
-      c = __reduce_add_sync(0xffffffffu, c);
-      if (lane == 0) {
-        slice_counts[h * num_slices + s0 + t] = c;
-        if (c) atomicAdd(&total, c);
+
+    // exclusive prefix of the word popcounts (WPT consecutive words per thread)
+    int c[WPT];
+    int mine = 0;
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) {
+      const int w = tid * WPT + j;
+      c[j] = w < nwords ? __popc(sym_bm[w]) : 0;
+      mine += c[j];
+    }
+    int total;
+    int run = team_exclusive_scan<1024>(mine, scratch, total);  // entries before my first word
+    // Windows: word w belongs to window floor(before(w) / wcut), where
+    // before(w) counts the entries in words < w.  Consecutive words differ by
+    // at most 32 <= wcut entries, so window indices run 0..K-1 without gaps,
+    // every window has a first word, and each holds at most wcut + 31 entries.
+    const int last_before = total - __popc(sym_bm[nwords - 1]);
+    int K = (wins && total > 0) ? last_before / wcut + 1 : 0;
+    if (K > kMaxWindowsPerSpan) {  // wcut too small for this span width
+      if (tid == 0) atomicCAS((unsigned long long*)&counters[kError], 0ull, 31ull);
+      K = 0;
+    }
+    if (tid == 0) {
+      wstart[0] = 0;
+      wrank[0] = 0;
+    }
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) {
+      const int w = tid * WPT + j;
+      if (w > 0 && w < nwords) {
+        const int before = run;
+        const int before_prev = run - (j > 0 ? c[j - 1] : __popc(sym_bm[w - 1]));
+        const int kk = before / wcut;
+        if (kk < K && before_prev / wcut < kk) {
+          wstart[kk] = w;
+          wrank[kk] = before;
+        }
       }
+      run += c[j];
+    }
+    if (tid == 0 && K > 0) {
+      long long b = (long long)atomicAdd((unsigned long long*)&counters[kUnits], (unsigned long long)K);
+      if (b + K > win_cap) {
+        atomicCAS((unsigned long long*)&counters[kError], 0ull, 30ull);
+        b = -1;
+      }
+      wbase = b;
     }
     __syncthreads();
-    if (tid == 0 && total) atomicAdd((unsigned long long*)&nnz[i], (unsigned long long)total);
+    if (tid < K && wbase >= 0) {
+      Window wd;
+      wd.h = (int32_t)h;
+      wd.span = (int32_t)sp;
+      wd.w_lo = wstart[tid];
+      wd.w_hi = tid + 1 < K ? wstart[tid + 1] : nwords;
+      wd.rank = wrank[tid];
+      wd.count = (tid + 1 < K ? wrank[tid + 1] : total) - wrank[tid];
+      wins[wbase + tid] = wd;
+    }
+    if (tid == 0) {
+      span_counts[h * spans + sp] = total;
+      if (total) atomicAdd((unsigned long long*)&nnz[i], (unsigned long long)total);
+    }
     __syncthreads();
   }
 }
@@ -134,8 +185,9 @@ inline int capped(int64_t want, int64_t cap) {
 
 void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,
                      const int64_t* seg_begin, const int64_t* seg_count, const int64_t* flops,
-                     int64_t* nnz, int32_t* slice_counts, int64_t num_slice_w,
-                     int64_t num_slices, cudaStream_t s, int sms, int* launches) {
+                     int64_t* nnz, int32_t* span_counts, int wcut, Window* wins,
+                     int64_t win_cap, int64_t* counters, cudaStream_t s, int sms,
+                     int* launches) {
   if (seg_count[kSymWarp]) {
     constexpr int CTA = 256, TEAM = 32, TBL = 2 * kSymWarpMax;
     const size_t smem = (CTA / TEAM) * TBL * sizeof(int);
@@ -159,15 +211,13 @@ void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,
     ++*launches;
   }
   if (seg_count[kSymHeavy]) {
-    const int64_t ncols = B.ncols;
-    const int64_t sym_slices = (ncols + kSymSliceBits - 1) / kSymSliceBits;
-    const int64_t width = ncols < kSymSliceBits ? ncols : kSymSliceBits;
+    const int64_t spans = (B.ncols + kSpanCols - 1) / kSpanCols;
+    const int64_t width = B.ncols < kSpanCols ? B.ncols : kSpanCols;
     const size_t smem = (size_t)((width + 31) / 32) * sizeof(unsigned);
-    set_smem(k_sym_heavy, smem);
-    const int per_sm = smem <= 64 * 1024 ? 2 : 1;
-    k_sym_heavy<<<capped(seg_count[kSymHeavy] * sym_slices, (int64_t)sms * per_sm), 1024, smem, s>>>(
-        A, B, perm + seg_begin[kSymHeavy], seg_count[kSymHeavy], sym_slices, flops, num_slice_w,
-        num_slices, nnz, slice_counts);
+    set_smem(k_sym_bitmap, smem);
+    k_sym_bitmap<<<capped(seg_count[kSymHeavy] * spans, (int64_t)sms * 2), 1024, smem, s>>>(
+        A, B, perm + seg_begin[kSymHeavy], seg_count[kSymHeavy], spans, flops, wcut, nnz,
+        span_counts, wins, win_cap, counters);
     ++*launches;
   }
 }
