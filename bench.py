@@ -49,6 +49,10 @@ def workload(name: str):
         desc = ("R-MAT s18 ef16 (0.57/0.19/0.19/0.05) symmetrised+dedup+permuted; C=A.A over "
                 "(+,x) f64, (min,+) u32, (or,and) bool")
         return desc, gen.rmat_square(18, 16, cfg=2)
+    if name == "rmat16":
+        desc = ("R-MAT s16 ef16 (0.57/0.19/0.19/0.05) symmetrised+dedup+permuted; C=A.A over (+,x) f64 "
+                "(small profiling case)")
+        return desc, gen.rmat_square(16, 16, cfg=2, semirings=("plus_times_f64",))
     if name == "er16k":
         desc = "ER n=16384, 8 distinct cols/row, (+,x) int64 U{1..10}; C=A.A"
         return desc, gen.er_square()
@@ -388,7 +392,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", default="rmat18", choices=("rmat18", "er16k"))
+    ap.add_argument("--workload", default="rmat18", choices=("rmat18", "rmat16", "er16k"))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=12.0)

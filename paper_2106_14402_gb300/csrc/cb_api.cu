@@ -193,12 +193,14 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_csr*
   const DevCSR dA = dev(A), dB = dev(B);
   CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
   mark(ctx, opt, 0);
+  cb::launch_check_sorted(dB, counters, ctx->stream, ctx->sms);
   cb::launch_classify_sym(dA, dB, flops, maxb, counters, ctx->stream, ctx->sms);
   cb::launch_scatter_sym(m, ncols, flops, perm_sym, nnz, counters, ctx->stream, ctx->sms);
   CB_LAUNCHED();
   mark(ctx, opt, 1);
-  ctx->stats.kernels += 2;
+  ctx->stats.kernels += 3;
   read_counters(ctx, counters, nullptr, 0);
+  const int b_sorted = ctx->host[cb::kUnsorted] == 0 ? 1 : 0;
 
   int64_t sym_cnt[cb::kSymTiers], sym_beg[cb::kSymTiers];
   for (int t = 0; t < cb::kSymTiers; ++t) sym_cnt[t] = ctx->host[cb::kCntSym + t];
@@ -212,16 +214,27 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_csr*
   // every (row, span) yields at most count/wcut + 1 windows; counts sum to <= flops
   const int64_t win_cap = n_heavy * spans + ctx->stats.flops / wcut + 1;
 
-  size_t need2 = align_up(4 * (size_t)(n_heavy * spans) + 4) + align_up(sizeof(cb::Window) * (size_t)win_cap);
+  // Heavy-row bitmaps are kept for the numeric phase when they fit a quarter
+  // of free device memory (capped at 32 GiB); otherwise the numeric phase
+  // rebuilds each window's bitmap from the products.
+  const size_t bits_bytes = (size_t)(n_heavy * spans) * cb::kSpanWords * sizeof(unsigned);
+  size_t free_b = 0, total_b = 0;
+  CB_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const bool keep_bits = n_heavy > 0 && bits_bytes <= free_b / 4 && bits_bytes <= (32ull << 30);
+  size_t need2 = align_up(4 * (size_t)(n_heavy * spans) + 4) +
+                 align_up(8 * (size_t)(n_heavy * spans) + 8) +
+                 align_up(sizeof(cb::Window) * (size_t)win_cap) + (keep_bits ? align_up(bits_bytes) : 0);
   ensure(ctx, &ctx->ws2, &ctx->ws2_cap, need2);
   Carver cv2{static_cast<char*>(ctx->ws2)};
   int32_t* span_counts = cv2.take<int32_t>(n_heavy * spans + 1);
+  int2* span_wins = cv2.take<int2>(n_heavy * spans + 1);
   cb::Window* wins = cv2.take<cb::Window>(win_cap);
+  unsigned* hbits = keep_bits ? cv2.take<unsigned>((size_t)(n_heavy * spans) * cb::kSpanWords) : nullptr;
   const int32_t* heavy_rows = perm_sym + sym_beg[cb::kSymHeavy];
 
   int launches = 0;
-  cb::launch_symbolic(dA, dB, perm_sym, sym_beg, sym_cnt, flops, nnz, span_counts, wcut, wins,
-                      win_cap, counters, ctx->stream, ctx->sms, &launches);
+  cb::launch_symbolic(dA, dB, perm_sym, sym_beg, sym_cnt, flops, nnz, span_counts, span_wins, wcut,
+                      wins, win_cap, hbits, b_sorted, counters, ctx->stream, ctx->sms, &launches);
   mark(ctx, opt, 2);
   cb::launch_exclusive_scan(nnz, m, C->row_ptr, partial, ctx->stream);
   cb::launch_classify_num(sr, m, nnz, perm_num, counters, ctx->stream, ctx->sms);
@@ -268,7 +281,7 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_csr*
   launches = 0;
   mark(ctx, opt, 4);
   cb::launch_numeric(sr, dA, dB, perm_num, num_beg, num_cnt, flops, nnz, heavy_rows, wins,
-                     n_units, span_counts, spans, C->row_ptr, C->col, C->val,
+                     n_units, span_counts, spans, hbits, b_sorted, C->row_ptr, C->col, C->val,
                      counters + cb::kError, ctx->stream, ctx->sms, &launches);
   CB_LAUNCHED();
   mark(ctx, opt, 5);
@@ -464,6 +477,7 @@ int cb_row_nnz(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, int64_t* nnz_out) 
     int32_t* perm = cv.take<int32_t>(m + 1);
     const DevCSR dA = dev(A), dB = dev(B);
     CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+    cb::launch_check_sorted(dB, counters, ctx->stream, ctx->sms);
     cb::launch_classify_sym(dA, dB, flops, nullptr, counters, ctx->stream, ctx->sms);
     cb::launch_scatter_sym(m, ncols, flops, perm, nnz_out, counters, ctx->stream, ctx->sms);
     CB_LAUNCHED();
@@ -477,8 +491,9 @@ int cb_row_nnz(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, int64_t* nnz_out) 
     ensure(ctx, &ctx->ws2, &ctx->ws2_cap, align_up(4 * (size_t)(n_heavy * spans) + 4));
     int launches = 0;
     cb::launch_symbolic(dA, dB, perm, beg, cnt, flops, nnz_out, static_cast<int32_t*>(ctx->ws2),
-                        cb::num_window_cut(CB_PLUS_TIMES_F64), nullptr, 0, counters, ctx->stream,
-                        ctx->sms, &launches);
+                        nullptr, cb::num_window_cut(CB_PLUS_TIMES_F64), nullptr, 0, nullptr,
+                        ctx->host[cb::kUnsorted] == 0 ? 1 : 0, counters, ctx->stream, ctx->sms,
+                        &launches);
     CB_LAUNCHED();
     return CB_OK;
   } catch (const Fail& f) {

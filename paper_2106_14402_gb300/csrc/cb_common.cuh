@@ -7,6 +7,8 @@
 #include <climits>
 #include <cuda_runtime.h>
 
+#include "cb_kernels.h"
+
 namespace cb {
 
 // ---------------------------------------------------------------------------
@@ -180,6 +182,84 @@ __device__ __forceinline__ int group_log2(int64_t flops, int64_t nnz_a) {
   while (g < 5 && (int64_t(2) << g) <= avg) ++g;
   int lim = TEAM_MAX >= 32 ? 5 : ceil_log2(TEAM_MAX);
   return g < lim ? g : lim;
+}
+
+// Lane layout of a group of G = 2^gl lanes inside a warp (G <= 32).
+struct Group {
+  int G, gq, shift;
+  unsigned mask;
+  __device__ __forceinline__ Group(int gl, int thread) {
+    G = 1 << gl;
+    gq = thread & (G - 1);
+    shift = (thread & 31) & ~(G - 1);
+    mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << shift);
+  }
+  // ballot of the group's lanes, as G low bits
+  __device__ __forceinline__ unsigned ballot(bool pred) const {
+    return (__ballot_sync(mask, pred) & mask) >> shift;
+  }
+};
+
+// First index in the sorted run col[q0, q1) whose column is >= x, found
+// cooperatively by a lane group: each round lane j probes the (j+1)-th of
+// G+1 equal cut points, and the number of probes below x narrows the run by
+// a factor of about G+1.  Every lane of the group must call it.
+__device__ __forceinline__ int64_t group_lower_bound(const int32_t* col, int64_t q0, int64_t q1,
+                                                     int64_t x, const Group& g) {
+  int64_t lo = q0, hi = q1;  // the answer lies in [lo, hi]
+  while (hi - lo > g.G) {
+    const int64_t len = hi - lo;
+    const int64_t pos = lo + (len * (g.gq + 1)) / (g.G + 1);
+    const int t = __popc(g.ballot((int64_t)col[pos] < x));
+    const int64_t nlo = t > 0 ? lo + (len * t) / (g.G + 1) + 1 : lo;
+    const int64_t nhi = t < g.G ? lo + (len * (t + 1)) / (g.G + 1) : hi;
+    lo = nlo;
+    hi = nhi;
+  }
+  const int64_t pos = lo + g.gq;
+  return lo + __popc(g.ballot(pos < hi && (int64_t)col[pos] < x));
+}
+
+// Visit every product A(i,p) * B(p,q) of row i whose column lies in
+// [lo, hi): f(p, q, c) is called by the lane that owns it.  Lanes form
+// groups of 2^gl per stored A entry (a team of TEAM threads, `thread` in
+// [0, TEAM)).  `whole` means [lo, hi) covers every column of B (no filter);
+// `sorted` means B's rows are non-decreasing in column, so each B row's
+// slice in [lo, hi) is located by a group search and walked to its end;
+// otherwise whole B rows are read and filtered.  Uniform per team.
+template <int TEAM, class F>
+__device__ __forceinline__ void for_row_products(const DevCSR& A, const DevCSR& B, int64_t i,
+                                                 int64_t lo, int64_t hi, bool whole, bool sorted,
+                                                 int gl, int thread, F&& f) {
+  const Group g(gl, thread);
+  const int groups = TEAM >> gl;
+  const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
+  const unsigned width = (unsigned)(hi - lo);
+  if (whole || !sorted) {
+    for (int64_t p = a0 + (thread >> gl); p < a1; p += groups) {
+      const int k = A.col[p];
+      const int64_t q1 = B.rp[k + 1];
+      for (int64_t q = B.rp[k] + g.gq; q < q1; q += g.G) {
+        const int c = B.col[q];
+        if (whole || (unsigned)((int64_t)c - lo) < width) f(p, q, c);
+      }
+    }
+    return;
+  }
+  for (int64_t p = a0 + (thread >> gl); p < a1; p += groups) {
+    const int k = A.col[p];
+    const int64_t q1 = B.rp[k + 1];
+    int64_t q = group_lower_bound(B.col, B.rp[k], q1, lo, g);
+    while (true) {
+      const int64_t qq = q + g.gq;
+      const int c = qq < q1 ? B.col[qq] : INT_MAX;
+      const bool in = (int64_t)c < hi;
+      const int n = __popc(g.ballot(in));
+      if (in) f(p, qq, c);
+      if (n < g.G) break;
+      q += g.G;
+    }
+  }
 }
 
 // Exclusive scan of one int per thread across a team of TEAM threads.

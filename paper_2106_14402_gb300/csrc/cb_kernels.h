@@ -26,6 +26,7 @@ enum Counter {
   kUnits = 21,          // rank windows appended by the symbolic phase
   kError = 22,          // validation / overflow error word
   kErrDetail = 23,
+  kUnsorted = 24,       // > 0 when some row of B is not non-decreasing
   kCounters = 32
 };
 
@@ -56,11 +57,15 @@ void launch_classify_num(int sr, int64_t m, const int64_t* nnz, int32_t* perm,
 // rows (tier 4) write span_counts[h * spans + span] and, when wins is
 // non-null, append their rank windows (cut every `wcut` entries) to wins
 // (capacity win_cap; counters[kUnits] counts them).
+// (span_wins[h * spans + span] = {first window, window count}; hbits, when
+// non-null, receives each heavy row's bitmap: kSpanWords words per (row, span).)
 void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,
                      const int64_t* seg_begin, const int64_t* seg_count, const int64_t* flops,
-                     int64_t* nnz, int32_t* span_counts, int wcut, Window* wins,
-                     int64_t win_cap, int64_t* counters, cudaStream_t s, int sms,
-                     int* launches);
+                     int64_t* nnz, int32_t* span_counts, int2* span_wins, int wcut,
+                     Window* wins, int64_t win_cap, unsigned* hbits, int b_sorted,
+                     int64_t* counters, cudaStream_t s, int sms, int* launches);
+// Sets counters[kUnsorted] > 0 if some row of B decreases in column.
+void launch_check_sorted(const DevCSR& B, int64_t* counters, cudaStream_t s, int sms);
 
 // K5-K7: numeric phase over the numeric tier segments + rank windows,
 // writing sorted rows of C at Crp.
@@ -70,7 +75,7 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
                     const int64_t* seg_begin, const int64_t* seg_count, const int64_t* flops,
                     const int64_t* nnz, const int32_t* heavy_rows, const Window* wins,
                     int64_t n_wins, const int32_t* span_counts, int64_t spans,
-                    const int64_t* Crp, int32_t* Ccol, void* Cval, int64_t* err, cudaStream_t s,
-                    int sms, int* launches);
+                    const unsigned* hbits, int b_sorted, const int64_t* Crp, int32_t* Ccol,
+                    void* Cval, int64_t* err, cudaStream_t s, int sms, int* launches);
 
 }  // namespace cb

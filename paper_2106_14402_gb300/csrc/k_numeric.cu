@@ -136,14 +136,16 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
   }
 }
 
-// Rank windows of heavy rows (nnz > 512).  One CTA per window: rebuild the
-// window's bitmap from the row's product stream, prefix-count its words,
-// then accumulate every product into the dense accumulator at the column's
-// rank and write the window's slice of the row in column order.
+// Rank windows of heavy rows (nnz > 512).  One CTA per window: take the
+// window's column bitmap (stored by the symbolic phase, or rebuilt from the
+// row's products), prefix-count its words, then accumulate every product
+// into the dense accumulator at its column's rank and write the window's
+// slice of the row in column order.
 template <int SR>
 __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const int32_t* heavy_rows,
                                                       const Window* wins, int64_t n_wins,
                                                       const int32_t* span_counts, int64_t spans,
+                                                      const unsigned* hbits, int b_sorted,
                                                       const int64_t* flops, const int64_t* nnz,
                                                       const int64_t* Crp, int32_t* Ccol,
                                                       typename Sem<SR>::T* Cval, int64_t* err) {
@@ -170,9 +172,15 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
     const int64_t span_lo = (int64_t)wd.span * kSpanCols;
     const int64_t lo = span_lo + 32 * (int64_t)wd.w_lo;
     const int64_t hi = min(span_lo + 32 * (int64_t)wd.w_hi, B.ncols);
-    const unsigned width = (unsigned)(hi - lo);
+    const bool whole = lo == 0 && hi == B.ncols;
     const int nw = wd.w_hi - wd.w_lo;
-    for (int w = tid; w < nw; w += 1024) bm[w] = 0u;
+    const int gl = group_log2<1024>(flops[i], A.rp[i + 1] - A.rp[i]);
+    if (hbits) {
+      const unsigned* src = hbits + (size_t)((int64_t)wd.h * spans + wd.span) * kSpanWords + wd.w_lo;
+      for (int w = tid; w < nw; w += 1024) bm[w] = src[w];
+    } else {
+      for (int w = tid; w < nw; w += 1024) bm[w] = 0u;
+    }
     for (int t = tid; t < cnt; t += 1024) acc[t] = S::ident();
     if (tid < 32) {
       long long o = 0;
@@ -183,22 +191,15 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
     }
     __syncthreads();
 
-    const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
-    const int gl = group_log2<1024>(flops[i], a1 - a0);
-    const int G = 1 << gl, gq = tid & (G - 1), groups = 1024 >> gl;
-    // pass 1: the window's columns
-    for (int64_t p = a0 + (tid >> gl); p < a1; p += groups) {
-      const int k = A.col[p];
-      const int64_t b1 = B.rp[k + 1];
-      for (int64_t q = B.rp[k] + gq; q < b1; q += G) {
-        const unsigned off = (unsigned)((int64_t)B.col[q] - lo);
-        if (off < width) {
-          const unsigned bit = 1u << (off & 31);
-          if (!(bm[off >> 5] & bit)) atomicOr(&bm[off >> 5], bit);
-        }
-      }
+    if (!hbits) {  // pass 1: rebuild the window's columns
+      for_row_products<1024>(A, B, i, lo, hi, whole, b_sorted != 0, gl, tid,
+                             [&](int64_t, int64_t, int c) {
+                               const unsigned off = (unsigned)((int64_t)c - lo);
+                               const unsigned bit = 1u << (off & 31);
+                               if (!(bm[off >> 5] & bit)) atomicOr(&bm[off >> 5], bit);
+                             });
+      __syncthreads();
     }
-    __syncthreads();
     // exclusive prefix of word popcounts
     {
       int c[WPT];
@@ -221,19 +222,14 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
     }
     __syncthreads();
     // pass 2: accumulate at the rank of each product's column
-    for (int64_t p = a0 + (tid >> gl); p < a1; p += groups) {
-      const int k = A.col[p];
-      const T a = S::kUsesA ? Aval[p] : T();
-      const int64_t b1 = B.rp[k + 1];
-      for (int64_t q = B.rp[k] + gq; q < b1; q += G) {
-        const unsigned off = (unsigned)((int64_t)B.col[q] - lo);
-        if (off < width) {
-          const int w = off >> 5;
-          const int slot = pre[w] + __popc(bm[w] & ((1u << (off & 31)) - 1u));
-          if (slot < cnt) S::atomic(&acc[slot], S::mul(a, Bval[q]));
-        }
-      }
-    }
+    for_row_products<1024>(A, B, i, lo, hi, whole, b_sorted != 0, gl, tid,
+                           [&](int64_t p, int64_t q, int c) {
+                             const unsigned off = (unsigned)((int64_t)c - lo);
+                             const int w = off >> 5;
+                             const int slot = pre[w] + __popc(bm[w] & ((1u << (off & 31)) - 1u));
+                             const T a = S::kUsesA ? Aval[p] : T();
+                             if (slot < cnt) S::atomic(&acc[slot], S::mul(a, Bval[q]));
+                           });
     __syncthreads();
     // write the window: values by slot (coalesced), columns by word
     const int64_t out = Crp[i] + s_base;
@@ -268,8 +264,9 @@ template <int SR>
 void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int64_t* seg_begin,
                 const int64_t* seg_count, const int64_t* flops, const int64_t* nnz,
                 const int32_t* heavy_rows, const Window* wins, int64_t n_wins,
-                const int32_t* span_counts, int64_t spans, const int64_t* Crp,
-                int32_t* Ccol, void* Cval_, int64_t* err, cudaStream_t s, int sms, int* launches) {
+                const int32_t* span_counts, int64_t spans, const unsigned* hbits, int b_sorted,
+                const int64_t* Crp, int32_t* Ccol, void* Cval_, int64_t* err, cudaStream_t s,
+                int sms, int* launches) {
   typedef typename Sem<SR>::A Acc;
   typedef typename Sem<SR>::T T;
   T* Cval = reinterpret_cast<T*>(Cval_);
@@ -300,8 +297,8 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
     constexpr size_t smem = NumLimits<SR>::kWcap * sizeof(Acc) + 2 * kSpanWords * sizeof(unsigned);
     set_smem(k_num_rank<SR>, smem);
     k_num_rank<SR><<<capped(n_wins, sms), 1024, smem, s>>>(A, B, heavy_rows, wins, n_wins,
-                                                           span_counts, spans, flops, nnz, Crp,
-                                                           Ccol, Cval, err);
+                                                           span_counts, spans, hbits, b_sorted,
+                                                           flops, nnz, Crp, Ccol, Cval, err);
     ++*launches;
   }
 }
@@ -332,11 +329,11 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
                     const int64_t* seg_begin, const int64_t* seg_count, const int64_t* flops,
                     const int64_t* nnz, const int32_t* heavy_rows, const Window* wins,
                     int64_t n_wins, const int32_t* span_counts, int64_t spans,
-                    const int64_t* Crp, int32_t* Ccol, void* Cval, int64_t* err, cudaStream_t s,
-                    int sms, int* launches) {
+                    const unsigned* hbits, int b_sorted, const int64_t* Crp, int32_t* Ccol,
+                    void* Cval, int64_t* err, cudaStream_t s, int sms, int* launches) {
 #define CB_NUM(SRV)                                                                        \
   numeric_sr<SRV>(A, B, perm, seg_begin, seg_count, flops, nnz, heavy_rows, wins, n_wins,   \
-                  span_counts, spans, Crp, Ccol, Cval, err, s, sms, launches)
+                  span_counts, spans, hbits, b_sorted, Crp, Ccol, Cval, err, s, sms, launches)
   switch (sr) {
     case 1: CB_NUM(1); break;
     case 2: CB_NUM(2); break;

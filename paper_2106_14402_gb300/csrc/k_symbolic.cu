@@ -70,8 +70,10 @@ __global__ void __launch_bounds__(CTA) k_sym_hash(DevCSR A, DevCSR B, const int3
 __global__ void __launch_bounds__(1024) k_sym_bitmap(DevCSR A, DevCSR B, const int32_t* heavy_rows,
                                                      int64_t n_heavy, int64_t spans,
                                                      const int64_t* flops, int wcut, int64_t* nnz,
-                                                     int32_t* span_counts, Window* wins,
-                                                     int64_t win_cap, int64_t* counters) {
+                                                     int32_t* span_counts, int2* span_wins,
+                                                     Window* wins, int64_t win_cap,
+                                                     unsigned* hbits, int b_sorted,
+                                                     int64_t* counters) {
   extern __shared__ unsigned sym_bm[];
   __shared__ int scratch[33];
   __shared__ int wstart[kMaxWindowsPerSpan];
@@ -85,25 +87,21 @@ __global__ void __launch_bounds__(1024) k_sym_bitmap(DevCSR A, DevCSR B, const i
     const int i = heavy_rows[h];
     const int64_t lo = sp * (int64_t)kSpanCols;
     const int64_t hi = min(lo + (int64_t)kSpanCols, B.ncols);
-    const unsigned width = (unsigned)(hi - lo);
-    const int nwords = (int)((width + 31) / 32);
+    const int nwords = (int)((hi - lo + 31) / 32);
     for (int w = tid; w < nwords; w += 1024) sym_bm[w] = 0u;
     __syncthreads();
-    const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
-    const int gl = group_log2<1024>(flops[i], a1 - a0);
-    const int G = 1 << gl, gq = tid & (G - 1), groups = 1024 >> gl;
-    for (int64_t p = a0 + (tid >> gl); p < a1; p += groups) {
-      const int k = A.col[p];
-      const int64_t b1 = B.rp[k + 1];
-      for (int64_t q = B.rp[k] + gq; q < b1; q += G) {
-        const unsigned off = (unsigned)((int64_t)B.col[q] - lo);
-        if (off < width) {
-          const unsigned bit = 1u << (off & 31);
-          if (!(sym_bm[off >> 5] & bit)) atomicOr(&sym_bm[off >> 5], bit);
-        }
-      }
-    }
+    const int gl = group_log2<1024>(flops[i], A.rp[i + 1] - A.rp[i]);
+    for_row_products<1024>(A, B, i, lo, hi, spans == 1, b_sorted != 0, gl, tid,
+                           [&](int64_t, int64_t, int c) {
+                             const unsigned off = (unsigned)((int64_t)c - lo);
+                             const unsigned bit = 1u << (off & 31);
+                             if (!(sym_bm[off >> 5] & bit)) atomicOr(&sym_bm[off >> 5], bit);
+                           });
     __syncthreads();
+    if (hbits) {
+      unsigned* dst = hbits + (size_t)(h * spans + sp) * kSpanWords;
+      for (int w = tid; w < nwords; w += 1024) dst[w] = sym_bm[w];
+    }
 
     // exclusive prefix of the word popcounts (WPT consecutive words per thread)
     int c[WPT];
@@ -144,13 +142,17 @@ __global__ void __launch_bounds__(1024) k_sym_bitmap(DevCSR A, DevCSR B, const i
       }
       run += c[j];
     }
-    if (tid == 0 && K > 0) {
-      long long b = (long long)atomicAdd((unsigned long long*)&counters[kUnits], (unsigned long long)K);
-      if (b + K > win_cap) {
-        atomicCAS((unsigned long long*)&counters[kError], 0ull, 30ull);
-        b = -1;
+    if (tid == 0) {
+      long long b = -1;
+      if (K > 0) {
+        b = (long long)atomicAdd((unsigned long long*)&counters[kUnits], (unsigned long long)K);
+        if (b + K > win_cap) {
+          atomicCAS((unsigned long long*)&counters[kError], 0ull, 30ull);
+          b = -1;
+        }
       }
       wbase = b;
+      if (span_wins) span_wins[h * spans + sp] = make_int2((int)(b >= 0 ? b : 0), b >= 0 ? K : 0);
     }
     __syncthreads();
     if (tid < K && wbase >= 0) {
@@ -171,6 +173,22 @@ __global__ void __launch_bounds__(1024) k_sym_bitmap(DevCSR A, DevCSR B, const i
   }
 }
 
+// Flags (counters[kUnsorted] > 0) when some row of B has a column smaller
+// than its predecessor in the same row; when no row does, window passes may
+// search B rows instead of filtering them.  One warp per row of B.
+__global__ void __launch_bounds__(256) k_check_sorted(DevCSR B, int64_t* counters) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  int bad = 0;
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < B.nrows;
+       r += nwarps) {
+    const int64_t q1 = B.rp[r + 1];
+    for (int64_t q = B.rp[r] + lane; q + 1 < q1; q += 32) bad |= B.col[q + 1] < B.col[q] ? 1 : 0;
+  }
+  bad = __syncthreads_or(bad);
+  if (bad && threadIdx.x == 0) atomicAdd((unsigned long long*)&counters[kUnsorted], 1ull);
+}
+
 template <class K>
 void set_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -183,11 +201,17 @@ inline int capped(int64_t want, int64_t cap) {
 
 }  // namespace
 
+void launch_check_sorted(const DevCSR& B, int64_t* counters, cudaStream_t s, int sms) {
+  if (B.nrows == 0) return;
+  int64_t g = (B.nrows + 7) / 8;
+  k_check_sorted<<<(int)(g < sms * 8 ? g : sms * 8), 256, 0, s>>>(B, counters);
+}
+
 void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,
                      const int64_t* seg_begin, const int64_t* seg_count, const int64_t* flops,
-                     int64_t* nnz, int32_t* span_counts, int wcut, Window* wins,
-                     int64_t win_cap, int64_t* counters, cudaStream_t s, int sms,
-                     int* launches) {
+                     int64_t* nnz, int32_t* span_counts, int2* span_wins, int wcut,
+                     Window* wins, int64_t win_cap, unsigned* hbits, int b_sorted,
+                     int64_t* counters, cudaStream_t s, int sms, int* launches) {
   if (seg_count[kSymWarp]) {
     constexpr int CTA = 256, TEAM = 32, TBL = 2 * kSymWarpMax;
     const size_t smem = (CTA / TEAM) * TBL * sizeof(int);
@@ -217,7 +241,7 @@ void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,
     set_smem(k_sym_bitmap, smem);
     k_sym_bitmap<<<capped(seg_count[kSymHeavy] * spans, (int64_t)sms * 2), 1024, smem, s>>>(
         A, B, perm + seg_begin[kSymHeavy], seg_count[kSymHeavy], spans, flops, wcut, nnz,
-        span_counts, wins, win_cap, counters);
+        span_counts, span_wins, wins, win_cap, hbits, b_sorted, counters);
     ++*launches;
   }
 }

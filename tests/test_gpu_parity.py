@@ -111,6 +111,29 @@ def test_every_tier(cb, sr):
     assert ctx.stats()["heavy_units"] > 0
 
 
+@pytest.mark.parametrize("sr", ("plus_times_f64", "min_plus_u32", "sel2nd_min_i32"))
+def test_heavy_rows_unsorted_b(cb, sr):
+    # B rows shuffled: window passes must filter whole rows instead of searching them
+    A, B = _tiered_inputs(sr, seed=5)
+    rng = np.random.default_rng(6)
+    col = B.col.copy()
+    val = B.val.copy()
+    for r in range(B.nrows):
+        s, e = B.row_ptr[r], B.row_ptr[r + 1]
+        perm = rng.permutation(e - s) + s
+        col[s:e], val[s:e] = col[perm], val[perm]
+    B = gen.CSR(B.nrows, B.ncols, B.row_ptr, col, val)
+    assert_parity(cb, sr, A, B)
+
+
+@pytest.mark.parametrize("sr", ("plus_times_f64", "or_and_bool"))
+def test_heavy_rows_several_spans(cb, sr):
+    # 600000 columns = 3 bitmap spans; the widest rows need several windows per span
+    A, B = _tiered_inputs(sr, seed=7, ncols=600000)
+    assert_parity(cb, sr, A, B)
+    assert cb.context().stats()["heavy_units"] > A.nrows
+
+
 def test_single_hot_column(cb):
     # every product of every row lands in column 7: maximal atomic contention
     n = 5000
