@@ -170,6 +170,45 @@ int cb_row_stats(cb_ctx *ctx, const cb_csr *A, const cb_csr *B, int64_t *flops,
 int cb_row_nnz(cb_ctx *ctx, const cb_csr *A, const cb_csr *B, int64_t *nnz_out);
 int cb_exclusive_scan(cb_ctx *ctx, const int64_t *in, int64_t n, int64_t *out);
 
+/* ---- learned row-size predictor -------------------------------------------
+ * Paper Sec. 5 (optimizations): the GPU path estimates the output's memory
+ * needs with approximate algorithms instead of an exact symbolic pass; Sec.
+ * 7.4 sizes batched SpGEMM from such a step.  Here the estimate is a small
+ * MLP over three row features f_i = (nnz(A_i), flops_i, max_p nnz(B_p)):
+ *   x = bf16((log2(1 + f) - mu) / sigma); h1 = bf16(relu(W1 x + b1));
+ *   h2 = bf16(relu(W2 h1 + b2)); z = w3 . h2 + b3;
+ *   pred_i = clamp(ceil(sigmoid(z) * flops_i), maxB_i, min(flops_i, ncols)).
+ * Weights are used as bf16 copies of fp32 master weights, products are
+ * accumulated in fp32.  Parameters are one fp32 vector of CB_MLP_NPARAM
+ * values laid out W1[64][3], b1[64], W2[64][64], b2[64], w3[64], b3[1];
+ * `norm` is mu[3] followed by sigma[3].  A cb_mlp lives on the device that
+ * was current when it was created. */
+#define CB_MLP_HIDDEN 64
+#define CB_MLP_NPARAM 4481
+/* Create from host parameters and normalisation (copied); CB_ERR_OOM/CUDA. */
+int cb_mlp_create(cb_mlp **out, const float *params, const float *norm);
+void cb_mlp_destroy(cb_mlp *m);
+/* Copy the fp32 master parameters, the normalisation and the Adam step
+ * count back to host memory (checkpointing); any output may be NULL. */
+int cb_mlp_get(const cb_mlp *m, float *params, float *norm, int64_t *step);
+/* Raw features of every row of A.B: feat[3*i + 0..2] = (nnz(A_i), flops_i,
+ * maxB_i) as floats (device float[3*m]). */
+int cb_row_features(cb_ctx *ctx, const cb_csr *A, const cb_csr *B, float *feat);
+/* K8: logits z[i] and sizes pred[i] for nrows feature rows (device; either
+ * output may be NULL); ncols is the width that caps the sizes. */
+int cb_mlp_predict(cb_ctx *ctx, const cb_mlp *m, const float *feat, int64_t nrows, int64_t ncols,
+                   float *z, int64_t *pred);
+/* K9: mean pinball-loss gradient (quantile tau) over rows with flops > 0
+ * against exact sizes nnz[i] (device int64); grad: device float[NPARAM],
+ * loss: device float[1] (may be NULL).  Leaves the model unchanged. */
+int cb_mlp_grad(cb_ctx *ctx, const cb_mlp *m, const float *feat, const int64_t *nnz,
+                int64_t nrows, float tau, float *grad, float *loss);
+/* Train in place with Adam (beta 0.9/0.999, eps 1e-8) for `epochs` passes
+ * over the rows in mini-batches of `batch` rows; epoch_loss (host float
+ * [epochs], may be NULL) receives each epoch's mean loss. */
+int cb_mlp_train(cb_ctx *ctx, cb_mlp *m, const float *feat, const int64_t *nnz, int64_t nrows,
+                 int epochs, int64_t batch, float lr, float tau, float *epoch_loss);
+
 /* ---- allocation-free scan ------------------------------------------------
  * The paper has no counterpart of this entry point; it exists for callers
  * that cannot allocate device memory when they need the row-pointer scan: a

@@ -87,6 +87,17 @@ _SIGS = {
     "cb_exclusive_scan": ([c_void_p, c_void_p, c_int64, c_void_p], ctypes.c_int),
     "cb_exclusive_scan_noalloc": ([c_void_p, c_int64, c_void_p, c_void_p], ctypes.c_int),
     "cb_last_stats": ([c_void_p, ctypes.POINTER(cb_stats)], ctypes.c_int),
+    "cb_mlp_create": ([ctypes.POINTER(c_void_p), c_void_p, c_void_p], ctypes.c_int),
+    "cb_mlp_destroy": ([c_void_p], None),
+    "cb_mlp_get": ([c_void_p, c_void_p, c_void_p, c_void_p], ctypes.c_int),
+    "cb_row_features": ([c_void_p, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr), c_void_p],
+                        ctypes.c_int),
+    "cb_mlp_predict": ([c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p],
+                       ctypes.c_int),
+    "cb_mlp_grad": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int64, ctypes.c_float, c_void_p,
+                     c_void_p], ctypes.c_int),
+    "cb_mlp_train": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int64, ctypes.c_int, c_int64,
+                      ctypes.c_float, ctypes.c_float, c_void_p], ctypes.c_int),
 }
 
 
@@ -331,3 +342,128 @@ def exclusive_scan(x: torch.Tensor, ctx: Context | None = None) -> torch.Tensor:
     ctx.check(ctx.lib.cb_exclusive_scan(ctx.handle, c_void_p(x.data_ptr()), x.numel(),
                                         c_void_p(out.data_ptr())))
     return out
+
+
+def _view(ptr, n, dtype, device):
+    """Tensor view of library memory that stays valid only while the callback runs."""
+    return _wrap(ptr, n, dtype, None, device)
+
+
+def spgemm_column_batches(semiring: str, A: DeviceCSR, B: DeviceCSR, budget_bytes: int, on_batch,
+                          *, validate: bool = True, ctx: Context | None = None,
+                          sizing: str = "exact", timing: bool = False) -> dict:
+    """Column-batched C = A (+).(x) B (cb_spgemm_ex with budget_bytes > 0).
+
+    on_batch(batch, col_lo, col_hi, Cb) is called for each batch with a
+    DeviceCSR view of C[:, col_lo:col_hi) (global column indices) that is
+    valid only during the call; return True to stop early.  Returns the
+    call's statistics (batches, flops, nnz, ...).
+    """
+    code, dt = SEMIRING[semiring]
+    ctx = ctx or context()
+    dev = A.row_ptr.device
+    errors = []
+
+    def _cb(batch, lo, hi, cptr, user):
+        try:
+            c = cptr.contents
+            view = DeviceCSR(c.nrows, c.ncols, _view(c.row_ptr, c.nrows + 1, torch.int64, dev),
+                             _view(c.col, c.nnz, torch.int32, dev), _view(c.val, c.nnz, dt, dev))
+            return 1 if on_batch(batch, lo, hi, view) else 0
+        except Exception as e:  # never raise through the C ABI
+            errors.append(e)
+            return 1
+
+    fn = BATCH_FN(_cb)
+    sa, sb = A.as_struct(), B.as_struct()
+    opts = make_opts(sizing=sizing, validate=validate, budget_bytes=budget_bytes, on_batch=fn,
+                     flags=FLAG_TIMING if timing else 0)
+    sc = cb_csr()
+    ctx.check(ctx.lib.cb_spgemm_ex(ctx.handle, code, ctypes.byref(sa), ctypes.byref(sb),
+                                   ctypes.byref(sc), ctypes.byref(opts)))
+    if errors:
+        raise errors[0]
+    st = ctx.stats()
+    st["nnz_total"] = sc.nnz
+    return st
+
+
+# ---------------------------------------------------------------------------
+# learned row-size predictor
+# ---------------------------------------------------------------------------
+
+MLP_NPARAM = 4481
+
+
+def _ptr_or_none(t):
+    return c_void_p(t.data_ptr()) if t is not None else None
+
+
+class MLP:
+    """Device-resident predictor (cb_mlp): fp32 master weights, bf16 copies, Adam state."""
+
+    def __init__(self, params, norm):
+        self.lib = load()
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        nrm = np.ascontiguousarray(norm, dtype=np.float32)
+        assert p.shape == (MLP_NPARAM,) and nrm.shape == (6,)
+        self.handle = c_void_p()
+        rc = self.lib.cb_mlp_create(ctypes.byref(self.handle), p.ctypes.data, nrm.ctypes.data)
+        if rc != 0:
+            raise CBError(rc, "cb_mlp_create failed")
+
+    def __del__(self):
+        try:
+            if self.handle:
+                self.lib.cb_mlp_destroy(self.handle)
+                self.handle = c_void_p()
+        except Exception:
+            pass
+
+    def get(self):
+        p = np.zeros(MLP_NPARAM, np.float32)
+        nrm = np.zeros(6, np.float32)
+        step = ctypes.c_int64()
+        rc = self.lib.cb_mlp_get(self.handle, p.ctypes.data, nrm.ctypes.data, ctypes.byref(step))
+        if rc != 0:
+            raise CBError(rc, "cb_mlp_get failed")
+        return p, nrm, step.value
+
+    def predict(self, feat: torch.Tensor, ncols: int, ctx: Context | None = None):
+        ctx = ctx or context()
+        m = feat.shape[0]
+        z = torch.empty(m, dtype=torch.float32, device=feat.device)
+        pred = torch.empty(m, dtype=torch.int64, device=feat.device)
+        ctx.check(self.lib.cb_mlp_predict(ctx.handle, self.handle, c_void_p(feat.data_ptr()), m,
+                                          int(ncols), c_void_p(z.data_ptr()),
+                                          c_void_p(pred.data_ptr())))
+        return z, pred
+
+    def grad(self, feat: torch.Tensor, nnz: torch.Tensor, tau: float = 0.9,
+             ctx: Context | None = None):
+        ctx = ctx or context()
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=feat.device)
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+        ctx.check(self.lib.cb_mlp_grad(ctx.handle, self.handle, c_void_p(feat.data_ptr()),
+                                       c_void_p(nnz.data_ptr()), feat.shape[0], float(tau),
+                                       c_void_p(g.data_ptr()), c_void_p(loss.data_ptr())))
+        return g, loss
+
+    def train(self, feat: torch.Tensor, nnz: torch.Tensor, epochs: int, batch: int, lr: float,
+              tau: float = 0.9, ctx: Context | None = None):
+        ctx = ctx or context()
+        losses = np.zeros(max(epochs, 1), np.float32)
+        ctx.check(self.lib.cb_mlp_train(ctx.handle, self.handle, c_void_p(feat.data_ptr()),
+                                        c_void_p(nnz.data_ptr()), feat.shape[0], int(epochs),
+                                        int(batch), float(lr), float(tau), losses.ctypes.data))
+        return losses[:epochs]
+
+
+def row_features(A: DeviceCSR, B: DeviceCSR, ctx: Context | None = None) -> torch.Tensor:
+    """Raw per-row features (nnz(A_i), flops_i, maxB_i) as a float32 [m, 3] device tensor."""
+    ctx = ctx or context()
+    feat = torch.empty((A.nrows, 3), dtype=torch.float32, device=A.row_ptr.device)
+    sa, sb = A.as_struct(), B.as_struct()
+    ctx.check(ctx.lib.cb_row_features(ctx.handle, ctypes.byref(sa), ctypes.byref(sb),
+                                      c_void_p(feat.data_ptr())))
+    return feat

@@ -6,8 +6,11 @@
 //   binning + heavy units -> [sync: nnz(C)] -> allocate C -> K5-K7 numeric.
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <memory>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/cb.h"
 #include "cb_common.cuh"
@@ -114,7 +117,9 @@ void read_counters(cb_ctx* ctx, const int64_t* counters, const int64_t* extra, i
   CB_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
-void run_validation(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, int64_t* counters) {
+void run_validation(cb_ctx* ctx, const cb_csr* A, const cb_csr* B) {
+  ensure(ctx, &ctx->ws, &ctx->ws_cap, align_up(sizeof(int64_t) * cb::kCounters));
+  int64_t* counters = static_cast<int64_t*>(ctx->ws);
   CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
   cb::launch_validate(dev(A), A->nnz, 0, counters, ctx->stream, ctx->sms);
   cb::launch_validate(dev(B), B->nnz, 10, counters, ctx->stream, ctx->sms);
@@ -154,9 +159,11 @@ void collect_times(cb_ctx* ctx, const cb_opts& opt, bool numeric_ran) {
 }
 
 // Everything from K1 to the allocation of C and the numeric phase.
-void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_csr* C,
-                  const cb_opts& opt) {
-  const int64_t m = A->nrows, ncols = B->ncols;
+// The plain (unbatched) path on a possibly windowed view dB of B; C gets
+// C->ncols = out_ncols.  Inputs are assumed valid (validation happens first).
+void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_t out_ncols,
+                  cb_csr* C, const cb_opts& opt) {
+  const int64_t m = A->nrows, ncols = dB.ncols;
   const bool caller_buf = opt.out_capacity > 0;
   const size_t vsz = value_size(sr);
 
@@ -172,12 +179,9 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_csr*
   int32_t* perm_sym = cv.take<int32_t>(m + 1);
   int32_t* perm_num = cv.take<int32_t>(m + 1);
   int64_t* partial = cv.take<int64_t>(cb::scan_partials(m));
-  (void)maxb;
-
-  if (opt.validate) run_validation(ctx, A, B, counters);
 
   C->nrows = m;
-  C->ncols = ncols;
+  C->ncols = out_ncols;
   C->nnz = 0;
   if (!caller_buf) {
     C->row_ptr = nullptr;
@@ -190,7 +194,7 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_csr*
     return;
   }
 
-  const DevCSR dA = dev(A), dB = dev(B);
+  const DevCSR dA = dev(A);
   CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
   mark(ctx, opt, 0);
   cb::launch_check_sorted(dB, counters, ctx->stream, ctx->sms);
@@ -299,9 +303,214 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_csr*
   }
 }
 
+// Symbolic counts only: nnz_out[i] = nnz of row i of A.B (view dB).
+void count_rows(cb_ctx* ctx, const DevCSR& dA, const DevCSR& dB, int64_t* nnz_out) {
+  const int64_t m = dA.nrows, ncols = dB.ncols;
+  if (m == 0) return;
+  size_t need = align_up(sizeof(int64_t) * cb::kCounters) + align_up(8 * (size_t)m + 8) +
+                align_up(4 * (size_t)m + 4);
+  ensure(ctx, &ctx->ws, &ctx->ws_cap, need);
+  Carver cv{static_cast<char*>(ctx->ws)};
+  int64_t* counters = cv.take<int64_t>(cb::kCounters);
+  int64_t* flops = cv.take<int64_t>(m + 1);
+  int32_t* perm = cv.take<int32_t>(m + 1);
+  CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+  cb::launch_check_sorted(dB, counters, ctx->stream, ctx->sms);
+  cb::launch_classify_sym(dA, dB, flops, nullptr, counters, ctx->stream, ctx->sms);
+  cb::launch_scatter_sym(m, ncols, flops, perm, nnz_out, counters, ctx->stream, ctx->sms);
+  CB_LAUNCHED();
+  ctx->stats.kernels += 3;
+  read_counters(ctx, counters, nullptr, 0);
+  int64_t cnt[cb::kSymTiers], beg[cb::kSymTiers];
+  for (int t = 0; t < cb::kSymTiers; ++t) cnt[t] = ctx->host[cb::kCntSym + t];
+  beg[0] = beg[1] = 0;
+  for (int t = 2; t < cb::kSymTiers; ++t) beg[t] = beg[t - 1] + cnt[t - 1];
+  ctx->stats.flops += ctx->host[cb::kTotalFlops];
+  const int64_t n_heavy = cnt[cb::kSymHeavy];
+  const int64_t spans = (ncols + cb::kSpanCols - 1) / cb::kSpanCols;
+  ensure(ctx, &ctx->ws2, &ctx->ws2_cap, align_up(4 * (size_t)(n_heavy * spans) + 4));
+  int launches = 0;
+  cb::launch_symbolic(dA, dB, perm, beg, cnt, flops, nnz_out, static_cast<int32_t*>(ctx->ws2),
+                      nullptr, cb::num_window_cut(CB_PLUS_TIMES_F64), nullptr, 0, nullptr,
+                      ctx->host[cb::kUnsorted] == 0 ? 1 : 0, counters, ctx->stream, ctx->sms,
+                      &launches);
+  CB_LAUNCHED();
+  ctx->stats.kernels += launches;
+}
+
+// Stream-ordered device buffer released when it goes out of scope.
+struct DevBuf {
+  cb_ctx* ctx;
+  void* p = nullptr;
+  explicit DevBuf(cb_ctx* c) : ctx(c) {}
+  void alloc(size_t bytes) {
+    CB_CUDA(cudaMallocAsync(&p, bytes ? bytes : 1, ctx->stream));
+  }
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, ctx->stream);
+  }
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+// Column-batched SpGEMM (paper Sec. 7.2; batch count from a symbolic step,
+// Sec. 7.4): C is formed in contiguous column ranges whose output
+// (row_ptr + col + val) fits opt.budget_bytes, each handed to on_batch.
+// The batch count comes from the exact symbolic total; ranges are equal in
+// width and a range whose output still exceeds the budget is halved.  When
+// B's rows are sorted each batch reads only its slab of every B row (slab
+// offsets found by search); otherwise batches filter whole rows.
+void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_csr* C,
+                     const cb_opts& opt) {
+  const int64_t m = A->nrows, n = B->nrows, k = B->ncols;
+  const int64_t per = 4 + (int64_t)value_size(sr);
+  const int64_t rp_bytes = 8 * (m + 1);
+  if (opt.budget_bytes < rp_bytes + per)
+    fail(ctx, CB_ERR_BUDGET, "budget smaller than one row-pointer array plus one entry");
+  const int64_t cap = (opt.budget_bytes - rp_bytes) / per;
+  if (opt.validate) run_validation(ctx, A, B);
+  C->nrows = m;
+  C->ncols = k;
+  C->nnz = 0;
+  C->row_ptr = nullptr;
+  C->col = nullptr;
+  C->val = nullptr;
+  ctx->stats.batches = 0;
+  if (m == 0 || k == 0 || A->nnz == 0 || B->nnz == 0) return;
+
+  const DevCSR dA = dev(A), dBfull = dev(B);
+  DevBuf brp(ctx), bcol(ctx), bval(ctx), rownnz(ctx);
+  brp.alloc(sizeof(int64_t) * (size_t)(m + 1));
+  rownnz.alloc(sizeof(int64_t) * (size_t)(m + 1));
+
+  // symbolic step: the exact total nnz(C) sets the batch count
+  count_rows(ctx, dA, dBfull, rownnz.as<int64_t>());
+  const int b_sorted = ctx->host[cb::kUnsorted] == 0 ? 1 : 0;
+  ensure(ctx, &ctx->ws, &ctx->ws_cap, align_up(8 * (size_t)cb::scan_partials(m)));
+  cb::launch_exclusive_scan(rownnz.as<int64_t>(), m, brp.as<int64_t>(), static_cast<int64_t*>(ctx->ws),
+                            ctx->stream);
+  CB_LAUNCHED();
+  CB_CUDA(cudaMemcpyAsync(ctx->host, brp.as<int64_t>() + m, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  CB_CUDA(cudaStreamSynchronize(ctx->stream));
+  const int64_t total = ctx->host[0];
+  const int64_t sym_flops = ctx->stats.flops;
+  int64_t nb = (total + cap - 1) / cap;
+  if (nb < 1) nb = 1;
+  if (nb > k) nb = k;
+
+  bcol.alloc(sizeof(int32_t) * (size_t)cap);
+  bval.alloc((size_t)(per - 4) * (size_t)cap);
+
+  // slab offsets of every boundary (sorted B only)
+  struct Range {
+    int64_t lo, hi;
+    const int64_t* plo;
+    const int64_t* phi;
+  };
+  std::vector<int64_t> bnd((size_t)nb + 1);
+  for (int64_t j = 0; j <= nb; ++j) bnd[(size_t)j] = (int64_t)((__int128)j * k / nb);
+  std::vector<std::unique_ptr<DevBuf>> slab_bufs;
+  auto slabs_for = [&](const std::vector<int64_t>& b) -> const int64_t* {
+    DevBuf* pos = new DevBuf(ctx);
+    slab_bufs.emplace_back(pos);
+    pos->alloc(sizeof(int64_t) * (size_t)n * b.size() + sizeof(int64_t) * b.size());
+    int64_t* dbnd = pos->as<int64_t>() + (size_t)n * b.size();
+    CB_CUDA(cudaMemcpyAsync(dbnd, b.data(), sizeof(int64_t) * b.size(), cudaMemcpyHostToDevice,
+                            ctx->stream));
+    cb::launch_slabs(dBfull, dbnd, (int)b.size(), pos->as<int64_t>(), ctx->stream, ctx->sms);
+    CB_LAUNCHED();
+    ctx->stats.kernels += 1;
+    return pos->as<int64_t>();
+  };
+  std::deque<Range> todo;
+  const int64_t* pos = b_sorted ? slabs_for(bnd) : nullptr;
+  for (int64_t j = 0; j < nb; ++j)
+    todo.push_back(Range{bnd[(size_t)j], bnd[(size_t)j + 1], pos ? pos + (size_t)j * n : nullptr,
+                         pos ? pos + (size_t)(j + 1) * n : nullptr});
+
+  cb_opts inner = opt;
+  inner.validate = 0;
+  inner.budget_bytes = 0;
+  inner.out_capacity = cap;
+  int64_t nnz_sum = 0, batch = 0;
+  int kernels = ctx->stats.kernels;
+  while (!todo.empty()) {
+    const Range r = todo.front();
+    todo.pop_front();
+    DevCSR view = dBfull;
+    view.ncols = r.hi - r.lo;
+    view.col_lo = r.lo;
+    if (b_sorted) {
+      view.rp = r.plo;
+      view.rpe = r.phi;
+    } else {
+      view.filter = 1;
+    }
+    cb_csr Cb{m, k, 0, brp.as<int64_t>(), bcol.as<int32_t>(), bval.p};
+    ctx->stats.kernels = 0;
+    try {
+      spgemm_plain(ctx, sr, A, view, k, &Cb, inner);
+    } catch (const Fail& f) {
+      if (f.code != CB_ERR_CAPACITY) throw;
+      kernels += ctx->stats.kernels;
+      if (r.hi - r.lo <= 1)
+        fail(ctx, CB_ERR_BUDGET, "one output column does not fit the batch budget");
+      const int64_t mid = r.lo + (r.hi - r.lo) / 2;
+      const int64_t* pmid = b_sorted ? slabs_for(std::vector<int64_t>{mid}) : nullptr;
+      todo.push_front(Range{mid, r.hi, pmid, r.phi});
+      todo.push_front(Range{r.lo, mid, r.plo, pmid});
+      continue;
+    }
+    kernels += ctx->stats.kernels;
+    nnz_sum += Cb.nnz;
+    CB_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int stop = opt.on_batch((int)batch, r.lo, r.hi, &Cb, opt.user);
+    ++batch;
+    if (stop) break;
+  }
+  ctx->stats.flops = sym_flops;
+  ctx->stats.nnz = nnz_sum;
+  ctx->stats.batches = (int32_t)batch;
+  ctx->stats.kernels = kernels;
+  C->nnz = nnz_sum;
+}
+
 }  // namespace
 
+namespace cb {
+cudaStream_t ctx_stream(cb_ctx* ctx) { return ctx->stream; }
+int ctx_sms(cb_ctx* ctx) { return ctx->sms; }
+}  // namespace cb
+
 extern "C" {
+
+int cb_row_features(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, float* feat) {
+  if (!ctx) return CB_ERR_ARG;
+  ctx->err.clear();
+  try {
+    if (!A || !B || !feat) fail(ctx, CB_ERR_ARG, "null argument");
+    check_operand(ctx, A, "A");
+    check_operand(ctx, B, "B");
+    if (A->ncols != B->nrows) fail(ctx, CB_ERR_SHAPE, "A.ncols != B.nrows");
+    const int64_t m = A->nrows;
+    if (m == 0) return CB_OK;
+    size_t need = align_up(sizeof(int64_t) * cb::kCounters) + align_up(8 * (size_t)m + 8) +
+                  align_up(4 * (size_t)m + 4);
+    ensure(ctx, &ctx->ws, &ctx->ws_cap, need);
+    Carver cv{static_cast<char*>(ctx->ws)};
+    int64_t* counters = cv.take<int64_t>(cb::kCounters);
+    int64_t* flops = cv.take<int64_t>(m + 1);
+    int32_t* maxb = cv.take<int32_t>(m + 1);
+    CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+    cb::launch_classify_sym(dev(A), dev(B), flops, maxb, counters, ctx->stream, ctx->sms);
+    cb::launch_row_features(dev(A), flops, maxb, feat, ctx->stream, ctx->sms);
+    CB_LAUNCHED();
+    return CB_OK;
+  } catch (const Fail& f) {
+    return f.code;
+  }
+}
 
 void cb_opts_default(cb_opts* opt) {
   if (!opt) return;
@@ -388,8 +597,13 @@ int cb_spgemm_ex(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, 
     if (caller_buf && (!C->row_ptr || !C->col || !C->val))
       fail(ctx, CB_ERR_ARG, "out_capacity > 0 needs C->row_ptr, C->col and C->val");
     if (opt.sizing != CB_SIZING_EXACT) fail(ctx, CB_ERR_ARG, "sizing mode not supported");
-    if (opt.budget_bytes > 0) fail(ctx, CB_ERR_ARG, "column batching not supported");
-    spgemm_plain(ctx, (int)sr, A, B, C, opt);
+    if (opt.budget_bytes > 0) {
+      if (!opt.on_batch) fail(ctx, CB_ERR_ARG, "budget_bytes > 0 needs on_batch");
+      spgemm_colbatch(ctx, (int)sr, A, B, C, opt);
+      return CB_OK;
+    }
+    if (opt.validate) run_validation(ctx, A, B);
+    spgemm_plain(ctx, (int)sr, A, dev(B), B->ncols, C, opt);
     return CB_OK;
   } catch (const Fail& f) {
     if (!caller_buf && C) {
@@ -466,35 +680,7 @@ int cb_row_nnz(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, int64_t* nnz_out) 
     check_operand(ctx, A, "A");
     check_operand(ctx, B, "B");
     if (A->ncols != B->nrows) fail(ctx, CB_ERR_SHAPE, "A.ncols != B.nrows");
-    const int64_t m = A->nrows, ncols = B->ncols;
-    if (m == 0) return CB_OK;
-    size_t need = align_up(sizeof(int64_t) * cb::kCounters) + align_up(8 * (size_t)m + 8) +
-                  align_up(4 * (size_t)m + 4);
-    ensure(ctx, &ctx->ws, &ctx->ws_cap, need);
-    Carver cv{static_cast<char*>(ctx->ws)};
-    int64_t* counters = cv.take<int64_t>(cb::kCounters);
-    int64_t* flops = cv.take<int64_t>(m + 1);
-    int32_t* perm = cv.take<int32_t>(m + 1);
-    const DevCSR dA = dev(A), dB = dev(B);
-    CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
-    cb::launch_check_sorted(dB, counters, ctx->stream, ctx->sms);
-    cb::launch_classify_sym(dA, dB, flops, nullptr, counters, ctx->stream, ctx->sms);
-    cb::launch_scatter_sym(m, ncols, flops, perm, nnz_out, counters, ctx->stream, ctx->sms);
-    CB_LAUNCHED();
-    read_counters(ctx, counters, nullptr, 0);
-    int64_t cnt[cb::kSymTiers], beg[cb::kSymTiers];
-    for (int t = 0; t < cb::kSymTiers; ++t) cnt[t] = ctx->host[cb::kCntSym + t];
-    beg[0] = beg[1] = 0;
-    for (int t = 2; t < cb::kSymTiers; ++t) beg[t] = beg[t - 1] + cnt[t - 1];
-    const int64_t n_heavy = cnt[cb::kSymHeavy];
-    const int64_t spans = (ncols + cb::kSpanCols - 1) / cb::kSpanCols;
-    ensure(ctx, &ctx->ws2, &ctx->ws2_cap, align_up(4 * (size_t)(n_heavy * spans) + 4));
-    int launches = 0;
-    cb::launch_symbolic(dA, dB, perm, beg, cnt, flops, nnz_out, static_cast<int32_t*>(ctx->ws2),
-                        nullptr, cb::num_window_cut(CB_PLUS_TIMES_F64), nullptr, 0, nullptr,
-                        ctx->host[cb::kUnsorted] == 0 ? 1 : 0, counters, ctx->stream, ctx->sms,
-                        &launches);
-    CB_LAUNCHED();
+    count_rows(ctx, dev(A), dev(B), nnz_out);
     return CB_OK;
   } catch (const Fail& f) {
     return f.code;

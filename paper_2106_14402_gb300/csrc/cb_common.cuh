@@ -184,6 +184,16 @@ __device__ __forceinline__ int group_log2(int64_t flops, int64_t nnz_a) {
   return g < lim ? g : lim;
 }
 
+// End offset of row k of a (possibly windowed) operand.
+__device__ __forceinline__ int64_t row_end(const DevCSR& M, int64_t k) {
+  return M.rpe ? M.rpe[k] : M.rp[k + 1];
+}
+
+// Whether column c belongs to B's column window (always true unless filtering).
+__device__ __forceinline__ bool in_window(const DevCSR& B, int c) {
+  return !B.filter || (uint64_t)((int64_t)c - B.col_lo) < (uint64_t)B.ncols;
+}
+
 // Lane layout of a group of G = 2^gl lanes inside a warp (G <= 32).
 struct Group {
   int G, gq, shift;
@@ -221,12 +231,13 @@ __device__ __forceinline__ int64_t group_lower_bound(const int32_t* col, int64_t
 }
 
 // Visit every product A(i,p) * B(p,q) of row i whose column lies in
-// [lo, hi): f(p, q, c) is called by the lane that owns it.  Lanes form
-// groups of 2^gl per stored A entry (a team of TEAM threads, `thread` in
-// [0, TEAM)).  `whole` means [lo, hi) covers every column of B (no filter);
-// `sorted` means B's rows are non-decreasing in column, so each B row's
-// slice in [lo, hi) is located by a group search and walked to its end;
-// otherwise whole B rows are read and filtered.  Uniform per team.
+// [lo, hi) (absolute columns): f(p, q, c) is called by the lane that owns
+// it.  Lanes form groups of 2^gl per stored A entry (a team of TEAM
+// threads, `thread` in [0, TEAM)).  `whole` means every entry of B's rows
+// lies in [lo, hi) (no filter); `sorted` means B's rows are non-decreasing
+// in column, so each B row's slice in [lo, hi) is located by a group search
+// and walked to its end; otherwise whole B rows are read and filtered.
+// Uniform per team.
 template <int TEAM, class F>
 __device__ __forceinline__ void for_row_products(const DevCSR& A, const DevCSR& B, int64_t i,
                                                  int64_t lo, int64_t hi, bool whole, bool sorted,
@@ -238,7 +249,7 @@ __device__ __forceinline__ void for_row_products(const DevCSR& A, const DevCSR& 
   if (whole || !sorted) {
     for (int64_t p = a0 + (thread >> gl); p < a1; p += groups) {
       const int k = A.col[p];
-      const int64_t q1 = B.rp[k + 1];
+      const int64_t q1 = row_end(B, k);
       for (int64_t q = B.rp[k] + g.gq; q < q1; q += g.G) {
         const int c = B.col[q];
         if (whole || (unsigned)((int64_t)c - lo) < width) f(p, q, c);
@@ -248,7 +259,7 @@ __device__ __forceinline__ void for_row_products(const DevCSR& A, const DevCSR& 
   }
   for (int64_t p = a0 + (thread >> gl); p < a1; p += groups) {
     const int k = A.col[p];
-    const int64_t q1 = B.rp[k + 1];
+    const int64_t q1 = row_end(B, k);
     int64_t q = group_lower_bound(B.col, B.rp[k], q1, lo, g);
     while (true) {
       const int64_t qq = q + g.gq;
@@ -296,6 +307,112 @@ __device__ __forceinline__ int team_exclusive_scan(int x, int* scratch /* >= 33 
   const int r = scratch[w] + incl - x;
   __syncthreads();
   return r;
+}
+
+// Exclusive scan of one int64 per thread across a CTA (blockDim.x threads,
+// a multiple of 32, at most 1024).  scratch: >= 33 long longs.
+__device__ __forceinline__ long long cta_exclusive_scan64(long long x, long long* scratch,
+                                                         long long& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  long long incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) scratch[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    long long v = lane < nw ? scratch[lane] : 0;
+    long long vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, vi, o);
+      if (lane >= o) vi += y;
+    }
+    if (lane < nw) scratch[lane] = vi - v;
+    if (lane == nw - 1) scratch[32] = vi;
+  }
+  __syncthreads();
+  total = scratch[32];
+  const long long r = scratch[w] + incl - x;
+  __syncthreads();
+  return r;
+}
+
+// First index in the sorted run col[q0, q1) whose column is >= x (one thread).
+__device__ __forceinline__ int64_t seq_lower_bound(const int32_t* col, int64_t q0, int64_t q1,
+                                                   int64_t x) {
+  while (q0 < q1) {
+    const int64_t mid = q0 + ((q1 - q0) >> 1);
+    if ((int64_t)col[mid] < x) q0 = mid + 1;
+    else q1 = mid;
+  }
+  return q0;
+}
+
+// Shared memory used by for_row_products_balanced: per chunk entry its
+// product offset and its first B index, plus scan scratch.
+struct BalancedSmem {
+  long long* off;  // [blockDim.x]
+  long long* b0;   // [blockDim.x]
+  long long* scan; // [33]
+};
+
+// Load-balanced form of for_row_products for a whole CTA: the row's stored
+// A entries are taken in chunks of blockDim.x; the chunk's product ranges
+// (B row, or the B row's slice in [lo, hi) when `sorted` and not `whole`)
+// are prefix-summed, every warp takes an equal contiguous share of the
+// chunk's products, and its lanes take consecutive products (coalesced B
+// reads).  A product's entry is found by a search over the chunk offsets
+// when a lane crosses into a new B row.  All threads of the CTA must call it.
+template <class F>
+__device__ __forceinline__ void for_row_products_balanced(const DevCSR& A, const DevCSR& B,
+                                                          int64_t i, int64_t lo, int64_t hi,
+                                                          bool whole, bool sorted,
+                                                          const BalancedSmem& sm, F&& f) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthr = blockDim.x, nwarp = nthr >> 5;
+  const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
+  const bool filter = !whole && !sorted;
+  const unsigned width = (unsigned)(hi - lo);
+  for (int64_t c0 = a0; c0 < a1; c0 += nthr) {
+    const int nch = (int)min((int64_t)nthr, a1 - c0);
+    long long len = 0;
+    if (tid < nch) {
+      const int k = A.col[c0 + tid];
+      int64_t q0 = B.rp[k], q1 = row_end(B, k);
+      if (!whole && sorted) {
+        const int64_t s0 = seq_lower_bound(B.col, q0, q1, lo);
+        q1 = seq_lower_bound(B.col, s0, q1, hi);
+        q0 = s0;
+      }
+      len = q1 - q0;
+      sm.b0[tid] = q0;
+    }
+    long long total;
+    const long long off = cta_exclusive_scan64(len, sm.scan, total);
+    if (tid < nch) sm.off[tid] = off;
+    __syncthreads();
+    const long long t_end = total * (warp + 1) / nwarp;
+    int j = -1;
+    for (long long t = total * warp / nwarp + lane; t < t_end; t += 32) {
+      if (j < 0 || (j + 1 < nch && sm.off[j + 1] <= t)) {
+        int l = j < 0 ? 0 : j + 1, r = nch - 1;  // last entry with off <= t
+        while (l < r) {
+          const int mid = (l + r + 1) >> 1;
+          if (sm.off[mid] <= t) l = mid;
+          else r = mid - 1;
+        }
+        j = l;
+      }
+      const int64_t q = sm.b0[j] + (t - sm.off[j]);
+      const int c = B.col[q];
+      if (!filter || (unsigned)((int64_t)c - lo) < width) f(c0 + j, q, c);
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace cb

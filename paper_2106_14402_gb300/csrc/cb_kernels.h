@@ -9,11 +9,19 @@ namespace cb {
 
 struct Window;
 
+// A CSR operand as the kernels see it.  For B it may be a column window:
+// only columns in [col_lo, col_lo + ncols) belong to the view.  Row k spans
+// [rp[k], rpe[k]) (rpe == nullptr: rp[k + 1]).  With filter == 0 every entry
+// of a row lies inside the window (slab offsets); with filter != 0 rows are
+// whole and entries outside the window are skipped.
 struct DevCSR {
   int64_t nrows, ncols;
   const int64_t* rp;
   const int32_t* col;
   const void* val;
+  const int64_t* rpe = nullptr;
+  int64_t col_lo = 0;
+  int filter = 0;
 };
 
 // Counters block in device memory (int64 each).
@@ -48,6 +56,11 @@ int64_t scan_partials(int64_t n);
 void launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* partial,
                            cudaStream_t s);
 
+// Column-batch slab offsets: pos[j * B.nrows + k] = first entry of B row k
+// with column >= bnd[j] (device int64 bnd[nb1]); B's rows must be sorted.
+void launch_slabs(const DevCSR& B, const int64_t* bnd, int nb1, int64_t* pos, cudaStream_t s,
+                  int sms);
+
 // Numeric binning by exact row size.
 void launch_classify_num(int sr, int64_t m, const int64_t* nnz, int32_t* perm,
                          int64_t* counters, cudaStream_t s, int sms);
@@ -77,5 +90,11 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
                     int64_t n_wins, const int32_t* span_counts, int64_t spans,
                     const unsigned* hbits, int b_sorted, const int64_t* Crp, int32_t* Ccol,
                     void* Cval, int64_t* err, cudaStream_t s, int sms, int* launches);
+
+// Learned sizer (k_mlp.cu).
+void launch_row_features(const DevCSR& A, const int64_t* flops, const int32_t* maxb, float* feat,
+                         cudaStream_t s, int sms);
+void launch_mlp_predict(const void* wb, const float* master, const float* norm, const float* feat,
+                        int64_t m, int64_t ncols, float* z, int64_t* pred, cudaStream_t s, int sms);
 
 }  // namespace cb

@@ -65,10 +65,12 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
     for (int64_t p = a0 + (lane >> gl); p < a1; p += groups) {
       const int k = A.col[p];
       const T a = S::kUsesA ? Aval[p] : T();
-      const int64_t b1 = B.rp[k + 1];
+      const int64_t b1 = row_end(B, k);
       for (int64_t q = B.rp[k] + gq; q < b1; q += G) {
+        const int c = B.col[q];
+        if (!in_window(B, c)) continue;
         bool ins;
-        const int slot = probe_insert(keys, mask, shift, B.col[q], ins);
+        const int slot = probe_insert(keys, mask, shift, c, ins);
         if (slot >= 0) S::atomic(&vals[slot], S::mul(a, Bval[q]));
         else flag_error(err, 20);
       }
@@ -156,9 +158,12 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
   constexpr int WPT = kSpanWords / 1024;
   extern __shared__ __align__(16) unsigned char rank_smem[];
   Acc* acc = reinterpret_cast<Acc*>(rank_smem);
-  unsigned* bm = reinterpret_cast<unsigned*>(acc + WCAP);
-  int* pre = reinterpret_cast<int*>(bm + kSpanWords);
+  // word w of the window: .x = its column bits, .y = entries before it
+  uint2* bp = reinterpret_cast<uint2*>(acc + WCAP);
+  long long* bal = reinterpret_cast<long long*>(bp + kSpanWords);
   __shared__ int scratch[33];
+  __shared__ long long scan64[33];
+  const BalancedSmem sm{bal, bal + 1024, scan64};
   __shared__ long long s_base;
   const int tid = threadIdx.x, lane = tid & 31;
   const T* Aval = reinterpret_cast<const T*>(A.val);
@@ -169,17 +174,16 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
     const int i = heavy_rows[wd.h];
     if (nnz[i] <= kNumSmallMax || wd.count <= 0) continue;  // hash tiers own small rows
     const int cnt = wd.count < WCAP ? wd.count : WCAP;
-    const int64_t span_lo = (int64_t)wd.span * kSpanCols;
+    const int64_t span_lo = B.col_lo + (int64_t)wd.span * kSpanCols;
     const int64_t lo = span_lo + 32 * (int64_t)wd.w_lo;
-    const int64_t hi = min(span_lo + 32 * (int64_t)wd.w_hi, B.ncols);
-    const bool whole = lo == 0 && hi == B.ncols;
+    const int64_t hi = min(span_lo + 32 * (int64_t)wd.w_hi, B.col_lo + B.ncols);
+    const bool whole = lo == B.col_lo && hi == B.col_lo + B.ncols && !B.filter;
     const int nw = wd.w_hi - wd.w_lo;
-    const int gl = group_log2<1024>(flops[i], A.rp[i + 1] - A.rp[i]);
     if (hbits) {
       const unsigned* src = hbits + (size_t)((int64_t)wd.h * spans + wd.span) * kSpanWords + wd.w_lo;
-      for (int w = tid; w < nw; w += 1024) bm[w] = src[w];
+      for (int w = tid; w < nw; w += 1024) bp[w].x = src[w];
     } else {
-      for (int w = tid; w < nw; w += 1024) bm[w] = 0u;
+      for (int w = tid; w < nw; w += 1024) bp[w].x = 0u;
     }
     for (int t = tid; t < cnt; t += 1024) acc[t] = S::ident();
     if (tid < 32) {
@@ -192,12 +196,12 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
     __syncthreads();
 
     if (!hbits) {  // pass 1: rebuild the window's columns
-      for_row_products<1024>(A, B, i, lo, hi, whole, b_sorted != 0, gl, tid,
-                             [&](int64_t, int64_t, int c) {
-                               const unsigned off = (unsigned)((int64_t)c - lo);
-                               const unsigned bit = 1u << (off & 31);
-                               if (!(bm[off >> 5] & bit)) atomicOr(&bm[off >> 5], bit);
-                             });
+      for_row_products_balanced(A, B, i, lo, hi, whole, b_sorted != 0, sm,
+                                [&](int64_t, int64_t, int c) {
+                                  const unsigned off = (unsigned)((int64_t)c - lo);
+                                  const unsigned bit = 1u << (off & 31);
+                                  if (!(bp[off >> 5].x & bit)) atomicOr(&bp[off >> 5].x, bit);
+                                });
       __syncthreads();
     }
     // exclusive prefix of word popcounts
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
 #pragma unroll
       for (int j = 0; j < WPT; ++j) {
         const int w = tid * WPT + j;
-        c[j] = w < nw ? __popc(bm[w]) : 0;
+        c[j] = w < nw ? __popc(bp[w].x) : 0;
         mine += c[j];
       }
       int total;
@@ -215,21 +219,21 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
 #pragma unroll
       for (int j = 0; j < WPT; ++j) {
         const int w = tid * WPT + j;
-        if (w < nw) pre[w] = run;
+        if (w < nw) bp[w].y = (unsigned)run;
         run += c[j];
       }
       if (tid == 0 && total != wd.count) flag_error(err, 23);
     }
     __syncthreads();
     // pass 2: accumulate at the rank of each product's column
-    for_row_products<1024>(A, B, i, lo, hi, whole, b_sorted != 0, gl, tid,
-                           [&](int64_t p, int64_t q, int c) {
-                             const unsigned off = (unsigned)((int64_t)c - lo);
-                             const int w = off >> 5;
-                             const int slot = pre[w] + __popc(bm[w] & ((1u << (off & 31)) - 1u));
-                             const T a = S::kUsesA ? Aval[p] : T();
-                             if (slot < cnt) S::atomic(&acc[slot], S::mul(a, Bval[q]));
-                           });
+    for_row_products_balanced(A, B, i, lo, hi, whole, b_sorted != 0, sm,
+                              [&](int64_t p, int64_t q, int c) {
+                                const unsigned off = (unsigned)((int64_t)c - lo);
+                                const uint2 e = bp[off >> 5];
+                                const int slot = (int)e.y + __popc(e.x & ((1u << (off & 31)) - 1u));
+                                const T a = S::kUsesA ? Aval[p] : T();
+                                if (slot < cnt) S::atomic(&acc[slot], S::mul(a, Bval[q]));
+                              });
     __syncthreads();
     // write the window: values by slot (coalesced), columns by word
     const int64_t out = Crp[i] + s_base;
@@ -237,8 +241,8 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
     for (int t = tid; t < cnt; t += 1024)
       if (out + t < row_end) Cval[out + t] = S::out(acc[t]);
     for (int w = tid; w < nw; w += 1024) {
-      unsigned word = bm[w];
-      int64_t o = out + pre[w];
+      unsigned word = bp[w].x;
+      int64_t o = out + bp[w].y;
       while (word) {
         const int b = __ffs(word) - 1;
         word &= word - 1;
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
 
 template <class K>
 void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 inline int capped(int64_t want, int64_t cap) {
@@ -294,7 +298,8 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
     ++*launches;
   }
   if (n_wins) {
-    constexpr size_t smem = NumLimits<SR>::kWcap * sizeof(Acc) + 2 * kSpanWords * sizeof(unsigned);
+    constexpr size_t smem = NumLimits<SR>::kWcap * sizeof(Acc) + 2 * kSpanWords * sizeof(unsigned) +
+                            2 * 1024 * sizeof(long long);
     set_smem(k_num_rank<SR>, smem);
     k_num_rank<SR><<<capped(n_wins, sms), 1024, smem, s>>>(A, B, heavy_rows, wins, n_wins,
                                                            span_counts, spans, hbits, b_sorted,

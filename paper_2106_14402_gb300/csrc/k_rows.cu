@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_classify_sym(DevCSR A, DevCSR B, int64_
     int mx = 0;
     for (int64_t p = a0 + lane; p < a1; p += 32) {
       const int k = A.col[p];
-      const int64_t len = B.rp[k + 1] - B.rp[k];
+      const int64_t len = row_end(B, k) - B.rp[k];
       f += len;
       mx = max(mx, (int)min(len, (int64_t)INT_MAX));
     }
@@ -198,6 +198,24 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int64_t* in, 
   }
 }
 
+// Column-batch slab offsets (paper Sec. 7.2, batched SpGEMM): for every row
+// k of B and every batch boundary bnd[j] (j < nb1), pos[j * n + k] is the
+// first entry of row k whose column is >= bnd[j].  Rows must be
+// non-decreasing.  One warp per row, one cooperative search per boundary.
+__global__ void __launch_bounds__(256) k_slabs(DevCSR B, const int64_t* bnd, int nb1, int64_t* pos) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const Group g(5, lane);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < B.nrows;
+       r += nwarps) {
+    const int64_t q0 = B.rp[r], q1 = B.rp[r + 1];
+    for (int j = 0; j < nb1; ++j) {
+      const int64_t v = group_lower_bound(B.col, q0, q1, bnd[j], g);
+      if (lane == 0) pos[(int64_t)j * B.nrows + r] = v;
+    }
+  }
+}
+
 inline int grid_for(int64_t work, int per_block, int cap) {
   int64_t g = (work + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -235,6 +253,12 @@ void launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* 
   k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial);
   k_scan_partials<<<1, kScanThreads, 0, s>>>(partial, nb, out + n);
   k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial, out);
+}
+
+void launch_slabs(const DevCSR& B, const int64_t* bnd, int nb1, int64_t* pos, cudaStream_t s,
+                  int sms) {
+  if (B.nrows == 0 || nb1 == 0) return;
+  k_slabs<<<grid_for(B.nrows, 8, sms * 8), 256, 0, s>>>(B, bnd, nb1, pos);
 }
 
 void launch_classify_num(int sr, int64_t m, const int64_t* nnz, int32_t* perm, int64_t* counters,

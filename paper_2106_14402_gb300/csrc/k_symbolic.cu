@@ -44,10 +44,12 @@ __global__ void __launch_bounds__(CTA) k_sym_hash(DevCSR A, DevCSR B, const int3
     int cnt = 0;
     for (int64_t p = a0 + (lane >> gl); p < a1; p += groups) {
       const int k = A.col[p];
-      const int64_t b1 = B.rp[k + 1];
+      const int64_t b1 = row_end(B, k);
       for (int64_t q = B.rp[k] + gq; q < b1; q += G) {
+        const int c = B.col[q];
+        if (!in_window(B, c)) continue;
         bool ins;
-        probe_insert(keys, mask, shift, B.col[q], ins);
+        probe_insert(keys, mask, shift, c, ins);
         cnt += ins;
       }
     }
@@ -67,36 +69,39 @@ __global__ void __launch_bounds__(CTA) k_sym_hash(DevCSR A, DevCSR B, const int3
 // covers the span's columns [lo, hi); after counting, the span is cut into
 // rank windows of at most wcut + 31 entries (see cb_common.cuh), appended to
 // `wins` (when non-null) for the numeric phase.
-__global__ void __launch_bounds__(1024) k_sym_bitmap(DevCSR A, DevCSR B, const int32_t* heavy_rows,
+__global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, const int32_t* heavy_rows,
                                                      int64_t n_heavy, int64_t spans,
                                                      const int64_t* flops, int wcut, int64_t* nnz,
                                                      int32_t* span_counts, int2* span_wins,
                                                      Window* wins, int64_t win_cap,
                                                      unsigned* hbits, int b_sorted,
                                                      int64_t* counters) {
-  extern __shared__ unsigned sym_bm[];
+  extern __shared__ __align__(16) unsigned sym_bm[];
   __shared__ int scratch[33];
+  __shared__ long long scan64[33];
   __shared__ int wstart[kMaxWindowsPerSpan];
   __shared__ int wrank[kMaxWindowsPerSpan];
   __shared__ long long wbase;
   constexpr int WPT = kSpanWords / 1024;  // bitmap words per thread in the scan
   const int tid = threadIdx.x;
   const int64_t units = n_heavy * spans;
+  const int bm_words = (int)min((int64_t)kSpanWords, (B.ncols + 31) / 32);
+  long long* bal = reinterpret_cast<long long*>(sym_bm + ((bm_words + 3) & ~3));
+  const BalancedSmem sm{bal, bal + 1024, scan64};
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int64_t h = u / spans, sp = u - h * spans;
     const int i = heavy_rows[h];
-    const int64_t lo = sp * (int64_t)kSpanCols;
-    const int64_t hi = min(lo + (int64_t)kSpanCols, B.ncols);
+    const int64_t lo = B.col_lo + sp * (int64_t)kSpanCols;
+    const int64_t hi = min(lo + (int64_t)kSpanCols, B.col_lo + B.ncols);
     const int nwords = (int)((hi - lo + 31) / 32);
     for (int w = tid; w < nwords; w += 1024) sym_bm[w] = 0u;
     __syncthreads();
-    const int gl = group_log2<1024>(flops[i], A.rp[i + 1] - A.rp[i]);
-    for_row_products<1024>(A, B, i, lo, hi, spans == 1, b_sorted != 0, gl, tid,
-                           [&](int64_t, int64_t, int c) {
-                             const unsigned off = (unsigned)((int64_t)c - lo);
-                             const unsigned bit = 1u << (off & 31);
-                             if (!(sym_bm[off >> 5] & bit)) atomicOr(&sym_bm[off >> 5], bit);
-                           });
+    for_row_products_balanced(A, B, i, lo, hi, spans == 1 && !B.filter, b_sorted != 0, sm,
+                              [&](int64_t, int64_t, int c) {
+                                const unsigned off = (unsigned)((int64_t)c - lo);
+                                const unsigned bit = 1u << (off & 31);
+                                if (!(sym_bm[off >> 5] & bit)) atomicOr(&sym_bm[off >> 5], bit);
+                              });
     __syncthreads();
     if (hbits) {
       unsigned* dst = hbits + (size_t)(h * spans + sp) * kSpanWords;
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(256) k_check_sorted(DevCSR B, int64_t* counter
   int bad = 0;
   for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < B.nrows;
        r += nwarps) {
-    const int64_t q1 = B.rp[r + 1];
+    const int64_t q1 = row_end(B, r);
     for (int64_t q = B.rp[r] + lane; q + 1 < q1; q += 32) bad |= B.col[q + 1] < B.col[q] ? 1 : 0;
   }
   bad = __syncthreads_or(bad);
@@ -191,7 +196,7 @@ __global__ void __launch_bounds__(256) k_check_sorted(DevCSR B, int64_t* counter
 
 template <class K>
 void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 inline int capped(int64_t want, int64_t cap) {
@@ -237,7 +242,8 @@ void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,
   if (seg_count[kSymHeavy]) {
     const int64_t spans = (B.ncols + kSpanCols - 1) / kSpanCols;
     const int64_t width = B.ncols < kSpanCols ? B.ncols : kSpanCols;
-    const size_t smem = (size_t)((width + 31) / 32) * sizeof(unsigned);
+    const size_t bm_words = (size_t)((width + 31) / 32);
+    const size_t smem = ((bm_words + 3) & ~(size_t)3) * sizeof(unsigned) + 2 * 1024 * sizeof(long long);
     set_smem(k_sym_bitmap, smem);
     k_sym_bitmap<<<capped(seg_count[kSymHeavy] * spans, (int64_t)sms * 2), 1024, smem, s>>>(
         A, B, perm + seg_begin[kSymHeavy], seg_count[kSymHeavy], spans, flops, wcut, nnz,

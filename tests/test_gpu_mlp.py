@@ -1,0 +1,120 @@
+"""GPU kernels of the learned row-size predictor (BF16 inputs and weights,
+FP32 accumulation) against the FP64 reference in oracle/mlp.py, evaluated on
+the same bf16-rounded weights and inputs.  The remaining difference comes
+from the kernels rounding the two hidden activations to bf16 (relative
+2^-9 per value), so the bound is a few 1e-2 relative."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_2106_14402_gb300 import gen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_14402_gb300 import cb as _cb
+    _cb.load()
+    return _cb
+
+
+def bf16(a):
+    """Round float64/float32 values to bfloat16 (nearest even), returned as float64."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def flat(p):
+    return np.concatenate([p["W1"].ravel(), p["b1"], p["W2"].ravel(), p["b2"], p["w3"], p["b3"]])
+
+
+def unflat(v):
+    v = np.asarray(v, dtype=np.float64)
+    o = 0
+    out = {}
+    for k, shape in (("W1", (64, 3)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)),
+                     ("w3", (64,)), ("b3", (1,))):
+        n = int(np.prod(shape))
+        out[k] = v[o:o + n].reshape(shape)
+        o += n
+    return out
+
+
+def setup_problem(seed=0):
+    P = gen.rmat(12, 16, *gen.RMAT_ABCD, seed=400 + seed)
+    A = P.with_values(np.ones(P.nnz, np.uint8))
+    flops, maxb = oracle.row_stats(A, A)
+    nnz = np.diff(oracle.spgemm("or_and_bool", A, A)[0])
+    nnza = np.diff(A.row_ptr)
+    F = np.stack([nnza, flops, maxb], 1).astype(np.float64)
+    L = mlp.raw_features(nnza, flops, maxb)
+    norm = np.concatenate([L.mean(0), L.std(0) + 1e-3]).astype(np.float32)
+    p = mlp.init_params(seed)
+    return A, F, nnz, norm, p
+
+
+def reference_inputs(F, norm, p):
+    """bf16-rounded weights and standardized inputs, as the kernels see them."""
+    q = {k: (bf16(v) if k in ("W1", "W2", "w3") else np.asarray(v, np.float32).astype(np.float64))
+         for k, v in p.items()}
+    mu, sg = norm[:3].astype(np.float64), norm[3:].astype(np.float64)
+    X = bf16((np.log2(1.0 + F) - mu) / sg)
+    return q, X
+
+
+def test_row_features_match_row_stats(cb):
+    A, F, nnz, norm, p = setup_problem()
+    dA = cb.DeviceCSR.from_host(A, "or_and_bool")
+    feat = cb.row_features(dA, dA).cpu().numpy()
+    assert np.array_equal(feat.astype(np.int64), F.astype(np.int64))
+
+
+def test_forward_and_sizes(cb):
+    A, F, nnz, norm, p = setup_problem(1)
+    model = cb.MLP(flat(p).astype(np.float32), norm)
+    feat = torch.tensor(F, dtype=torch.float32, device="cuda")
+    z, pred = model.predict(feat, ncols=A.ncols)
+    z = z.cpu().numpy().astype(np.float64)
+    q, X = reference_inputs(F, norm, p)
+    zr, cache = mlp.forward(q, X)
+    scale = np.abs(cache[4]) @ np.abs(q["w3"]) + 1.0
+    assert np.all(np.abs(z - zr) <= 3e-2 * scale), np.max(np.abs(z - zr) / scale)
+    # the integer size rule applied to the kernel's own logits
+    want = mlp.predict_sizes(z, F[:, 1].astype(np.int64), F[:, 2].astype(np.int64), A.ncols)
+    assert np.array_equal(pred.cpu().numpy(), want)
+
+
+def test_gradients_match_fp64_reference(cb):
+    A, F, nnz, norm, p = setup_problem(2)
+    model = cb.MLP(flat(p).astype(np.float32), norm)
+    feat = torch.tensor(F, dtype=torch.float32, device="cuda")
+    g, loss = model.grad(feat, torch.tensor(nnz, dtype=torch.int64, device="cuda"), tau=0.9)
+    g = unflat(g.cpu().numpy())
+    q, X = reference_inputs(F, norm, p)
+    z, cache = mlp.forward(q, X)
+    L, dz = mlp.loss_and_dz(z, F[:, 1], nnz, 0.9)
+    want = mlp.backward(q, cache, dz)
+    assert abs(float(loss.item()) - L) <= 2e-2 * abs(L) + 1e-4
+    for k in want:
+        err = np.linalg.norm(g[k] - want[k]) / (np.linalg.norm(want[k]) + 1e-12)
+        assert err <= 3e-2, (k, err)
+
+
+def test_training_lowers_the_loss(cb):
+    A, F, nnz, norm, p = setup_problem(3)
+    model = cb.MLP(flat(p).astype(np.float32), norm)
+    feat = torch.tensor(F, dtype=torch.float32, device="cuda")
+    lab = torch.tensor(nnz, dtype=torch.int64, device="cuda")
+    _, l0 = model.grad(feat, lab)
+    losses = model.train(feat, lab, epochs=30, batch=1024, lr=3e-3)
+    _, l1 = model.grad(feat, lab)
+    assert losses[-1] < losses[0]
+    assert float(l1.item()) < 0.5 * float(l0.item())
+    params, nrm, step = model.get()
+    assert step > 0 and np.all(np.isfinite(params)) and np.array_equal(nrm, norm)
