@@ -258,7 +258,7 @@ def context(stream: torch.cuda.Stream | None = None) -> Context:
 
 
 def make_opts(sizing="exact", validate=True, out_capacity=0, budget_bytes=0, on_batch=None,
-              margin=0.25, flags=0) -> cb_opts:
+              margin=0.25, flags=0, mlp=None) -> cb_opts:
     lib = load()
     o = cb_opts()
     lib.cb_opts_default(ctypes.byref(o))
@@ -270,6 +270,8 @@ def make_opts(sizing="exact", validate=True, out_capacity=0, budget_bytes=0, on_
         o.on_batch = on_batch
     o.margin = float(margin)
     o.flags = int(flags)
+    if mlp is not None:
+        o.mlp = mlp.handle.value
     return o
 
 
@@ -283,7 +285,7 @@ FLAG_TIMING = 2
 
 def spgemm(semiring: str, A: DeviceCSR, B: DeviceCSR, *, validate: bool = True, check: bool = False,
            ctx: Context | None = None, out: DeviceCSR | None = None, sizing: str = "exact",
-           timing: bool = False) -> DeviceCSR:
+           timing: bool = False, mlp=None, margin: float = 0.25) -> DeviceCSR:
     """C = A (+).(x) B on the GPU (cb_spgemm_ex).
 
     With `out` (a DeviceCSR whose col/val tensors are large enough), C is
@@ -294,7 +296,7 @@ def spgemm(semiring: str, A: DeviceCSR, B: DeviceCSR, *, validate: bool = True, 
     code, dt = SEMIRING[semiring]
     ctx = ctx or context()
     sa, sb = A.as_struct(), B.as_struct()
-    opts = make_opts(sizing=sizing, validate=validate,
+    opts = make_opts(sizing=sizing, validate=validate, mlp=mlp, margin=margin,
                      flags=(FLAG_CHECK if check else 0) | (FLAG_TIMING if timing else 0))
     if out is not None:
         opts.out_capacity = max(1, min(out.col.numel(), out.val.numel()))
@@ -351,7 +353,8 @@ def _view(ptr, n, dtype, device):
 
 def spgemm_column_batches(semiring: str, A: DeviceCSR, B: DeviceCSR, budget_bytes: int, on_batch,
                           *, validate: bool = True, ctx: Context | None = None,
-                          sizing: str = "exact", timing: bool = False) -> dict:
+                          sizing: str = "exact", timing: bool = False, mlp=None,
+                          margin: float = 0.25) -> dict:
     """Column-batched C = A (+).(x) B (cb_spgemm_ex with budget_bytes > 0).
 
     on_batch(batch, col_lo, col_hi, Cb) is called for each batch with a
@@ -377,7 +380,7 @@ def spgemm_column_batches(semiring: str, A: DeviceCSR, B: DeviceCSR, budget_byte
     fn = BATCH_FN(_cb)
     sa, sb = A.as_struct(), B.as_struct()
     opts = make_opts(sizing=sizing, validate=validate, budget_bytes=budget_bytes, on_batch=fn,
-                     flags=FLAG_TIMING if timing else 0)
+                     flags=FLAG_TIMING if timing else 0, mlp=mlp, margin=margin)
     sc = cb_csr()
     ctx.check(ctx.lib.cb_spgemm_ex(ctx.handle, code, ctypes.byref(sa), ctypes.byref(sb),
                                    ctypes.byref(sc), ctypes.byref(opts)))

@@ -96,6 +96,21 @@ void ensure(cb_ctx* ctx, void** buf, size_t* cap, size_t need) {
   *cap = want;
 }
 
+// Stream-ordered device buffer released when it goes out of scope.
+struct DevBuf {
+  cb_ctx* ctx;
+  void* p = nullptr;
+  explicit DevBuf(cb_ctx* c) : ctx(c) {}
+  void alloc(size_t bytes) {
+    CB_CUDA(cudaMallocAsync(&p, bytes ? bytes : 1, ctx->stream));
+  }
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, ctx->stream);
+  }
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
 void check_operand(cb_ctx* ctx, const cb_csr* M, const char* name) {
   if (M->nrows < 0 || M->ncols < 0 || M->nnz < 0)
     fail(ctx, CB_ERR_ARG, std::string(name) + ": negative size");
@@ -161,8 +176,11 @@ void collect_times(cb_ctx* ctx, const cb_opts& opt, bool numeric_ran) {
 // Everything from K1 to the allocation of C and the numeric phase.
 // The plain (unbatched) path on a possibly windowed view dB of B; C gets
 // C->ncols = out_ncols.  Inputs are assumed valid (validation happens first).
+// skip (optional): rows already computed elsewhere; their sizes are preset[i]
+// and the exact phases leave them out.
 void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_t out_ncols,
-                  cb_csr* C, const cb_opts& opt) {
+                  cb_csr* C, const cb_opts& opt, const uint8_t* skip = nullptr,
+                  const int64_t* preset = nullptr) {
   const int64_t m = A->nrows, ncols = dB.ncols;
   const bool caller_buf = opt.out_capacity > 0;
   const size_t vsz = value_size(sr);
@@ -198,8 +216,9 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
   CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
   mark(ctx, opt, 0);
   cb::launch_check_sorted(dB, counters, ctx->stream, ctx->sms);
-  cb::launch_classify_sym(dA, dB, flops, maxb, counters, ctx->stream, ctx->sms);
-  cb::launch_scatter_sym(m, ncols, flops, perm_sym, nnz, counters, ctx->stream, ctx->sms);
+  cb::launch_classify_sym(dA, dB, flops, maxb, counters, ctx->stream, ctx->sms, skip);
+  cb::launch_scatter_sym(m, ncols, flops, perm_sym, nnz, counters, ctx->stream, ctx->sms, skip,
+                         preset);
   CB_LAUNCHED();
   mark(ctx, opt, 1);
   ctx->stats.kernels += 3;
@@ -241,7 +260,7 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
                       wins, win_cap, hbits, b_sorted, counters, ctx->stream, ctx->sms, &launches);
   mark(ctx, opt, 2);
   cb::launch_exclusive_scan(nnz, m, C->row_ptr, partial, ctx->stream);
-  cb::launch_classify_num(sr, m, nnz, perm_num, counters, ctx->stream, ctx->sms);
+  cb::launch_classify_num(sr, m, nnz, perm_num, counters, ctx->stream, ctx->sms, skip);
   CB_LAUNCHED();
   mark(ctx, opt, 3);
   ctx->stats.kernels += launches + 3 + 2;
@@ -303,6 +322,90 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
   }
 }
 
+int64_t total_of(cb_ctx* ctx, const int64_t* in, int64_t n);
+
+// Learned (or upper-bound) sizing (paper Sec. 5: approximate memory
+// estimation in place of the symbolic phase).  Each row's capacity comes
+// from the MLP's predicted size (upper bound: min(flops, ncols)) times
+// (1 + margin); rows whose capacity fits a shared-memory hash table are
+// computed in one pass, without a symbolic phase, into a staging area sized
+// by the capacities.  A row that overflows its capacity is detected on the
+// device and, with the rows too large for the table, goes through the exact
+// two-phase path; the one-pass rows are then copied from staging into C.
+void spgemm_learned(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_t out_ncols,
+                    cb_csr* C, const cb_opts& opt) {
+  const int64_t m = A->nrows, ncols = dB.ncols;
+  const int vsz = (int)value_size(sr);
+  if (m == 0) {
+    spgemm_plain(ctx, sr, A, dB, out_ncols, C, opt);
+    return;
+  }
+  const DevCSR dA = dev(A);
+  DevBuf work(ctx);
+  const size_t nm = (size_t)m + 1;
+  const size_t bytes = align_up(8 * nm) * 5 + align_up(4 * nm) * 2 + align_up(12 * nm) + align_up(nm) +
+                       align_up(8 * (size_t)cb::kCounters) + align_up(8 * (size_t)cb::scan_partials(m));
+  work.alloc(bytes);
+  Carver cv{work.as<char>()};
+  int64_t* flops = cv.take<int64_t>(nm);
+  int64_t* pred = cv.take<int64_t>(nm);
+  int64_t* cap = cv.take<int64_t>(nm);
+  int64_t* stage_rp = cv.take<int64_t>(nm);
+  int64_t* cnt = cv.take<int64_t>(nm);
+  int32_t* maxb = cv.take<int32_t>(nm);
+  int32_t* perm = cv.take<int32_t>(nm);
+  float* feat = cv.take<float>(3 * nm);
+  uint8_t* learned = cv.take<uint8_t>(nm);
+  int64_t* counters = cv.take<int64_t>(cb::kCounters);
+  int64_t* partial = cv.take<int64_t>(cb::scan_partials(m));
+
+  CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+  cb::launch_classify_sym(dA, dB, flops, maxb, counters, ctx->stream, ctx->sms);
+  const bool use_mlp = opt.sizing == CB_SIZING_LEARNED;
+  if (use_mlp) {
+    cb::launch_row_features(dA, flops, maxb, feat, ctx->stream, ctx->sms);
+    cb::launch_mlp_predict(cb::mlp_bf16(opt.mlp), cb::mlp_master(opt.mlp), cb::mlp_norm(opt.mlp),
+                           feat, m, ncols, nullptr, pred, ctx->stream, ctx->sms);
+  }
+  const int64_t hmax = cb::learn_hash_max(sr);
+  cb::launch_learn_caps(m, use_mlp ? pred : nullptr, flops, ncols, use_mlp ? opt.margin : 0.0f, hmax,
+                        cap, learned, ctx->stream, ctx->sms);
+  cb::launch_exclusive_scan(cap, m, stage_rp, partial, ctx->stream);
+  cb::launch_learned_tiers(m, cap, hmax, perm, counters, ctx->stream, ctx->sms);
+  CB_LAUNCHED();
+  int pre_launches = use_mlp ? 9 : 7;
+  read_counters(ctx, counters, stage_rp + m, 1);
+  const int64_t staged = ctx->host[cb::kCounters];
+  int64_t seg_cnt[cb::kNumTiers], seg_beg[cb::kNumTiers];
+  for (int t = 0; t < cb::kNumTiers; ++t) seg_cnt[t] = ctx->host[cb::kCntNum + t];
+  seg_beg[0] = seg_beg[1] = 0;
+  for (int t = 2; t < cb::kNumTiers; ++t) seg_beg[t] = seg_beg[t - 1] + seg_cnt[t - 1];
+
+  DevBuf scol(ctx), sval(ctx);
+  scol.alloc(sizeof(int32_t) * (size_t)staged);
+  sval.alloc((size_t)vsz * (size_t)staged);
+  int launches = 0;
+  cb::launch_learned_numeric(sr, dA, dB, perm, seg_beg, seg_cnt, flops, cap, stage_rp,
+                             scol.as<int32_t>(), sval.p, learned, cnt, counters + cb::kError,
+                             ctx->stream, ctx->sms, &launches);
+  CB_LAUNCHED();
+  // the overflow count is read back with the exact pipeline's first sync
+  CB_CUDA(cudaMemcpyAsync(ctx->host + cb::kCounters + 2, counters + cb::kError, sizeof(int64_t),
+                          cudaMemcpyDeviceToHost, ctx->stream));
+  pre_launches += launches;
+  // rows that stayed on the one-pass path carry their size into the exact
+  // pipeline; the rest (including overflowed rows) are computed exactly
+  spgemm_plain(ctx, sr, A, dB, out_ncols, C, opt, learned, cnt);
+  if (C->nnz > 0) {
+    cb::launch_compact_rows(vsz, m, learned, stage_rp, cnt, scol.as<int32_t>(), sval.p, C->row_ptr,
+                            C->col, C->val, ctx->stream, ctx->sms);
+    CB_LAUNCHED();
+    ctx->stats.kernels += 1;
+  }
+  ctx->stats.kernels += pre_launches;
+  ctx->stats.overflow_rows = ctx->host[cb::kCounters + 2];
+}
+
 // Symbolic counts only: nnz_out[i] = nnz of row i of A.B (view dB).
 void count_rows(cb_ctx* ctx, const DevCSR& dA, const DevCSR& dB, int64_t* nnz_out) {
   const int64_t m = dA.nrows, ncols = dB.ncols;
@@ -338,20 +441,18 @@ void count_rows(cb_ctx* ctx, const DevCSR& dA, const DevCSR& dB, int64_t* nnz_ou
   ctx->stats.kernels += launches;
 }
 
-// Stream-ordered device buffer released when it goes out of scope.
-struct DevBuf {
-  cb_ctx* ctx;
-  void* p = nullptr;
-  explicit DevBuf(cb_ctx* c) : ctx(c) {}
-  void alloc(size_t bytes) {
-    CB_CUDA(cudaMallocAsync(&p, bytes ? bytes : 1, ctx->stream));
-  }
-  ~DevBuf() {
-    if (p) cudaFreeAsync(p, ctx->stream);
-  }
-  template <class T>
-  T* as() const { return static_cast<T*>(p); }
-};
+// Sum of n int64 values on the device (synchronises); uses ctx->ws.
+int64_t total_of(cb_ctx* ctx, const int64_t* in, int64_t n) {
+  DevBuf out(ctx);
+  out.alloc(sizeof(int64_t) * (size_t)(n + 1));
+  ensure(ctx, &ctx->ws2, &ctx->ws2_cap, align_up(8 * (size_t)cb::scan_partials(n)));
+  cb::launch_exclusive_scan(in, n, out.as<int64_t>(), static_cast<int64_t*>(ctx->ws2), ctx->stream);
+  CB_LAUNCHED();
+  CB_CUDA(cudaMemcpyAsync(ctx->host + cb::kCounters + 1, out.as<int64_t>() + n, sizeof(int64_t),
+                          cudaMemcpyDeviceToHost, ctx->stream));
+  CB_CUDA(cudaStreamSynchronize(ctx->stream));
+  return ctx->host[cb::kCounters + 1];
+}
 
 // Column-batched SpGEMM (paper Sec. 7.2; batch count from a symbolic step,
 // Sec. 7.4): C is formed in contiguous column ranges whose output
@@ -383,17 +484,37 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
   brp.alloc(sizeof(int64_t) * (size_t)(m + 1));
   rownnz.alloc(sizeof(int64_t) * (size_t)(m + 1));
 
-  // symbolic step: the exact total nnz(C) sets the batch count
-  count_rows(ctx, dA, dBfull, rownnz.as<int64_t>());
-  const int b_sorted = ctx->host[cb::kUnsorted] == 0 ? 1 : 0;
-  ensure(ctx, &ctx->ws, &ctx->ws_cap, align_up(8 * (size_t)cb::scan_partials(m)));
-  cb::launch_exclusive_scan(rownnz.as<int64_t>(), m, brp.as<int64_t>(), static_cast<int64_t*>(ctx->ws),
-                            ctx->stream);
-  CB_LAUNCHED();
-  CB_CUDA(cudaMemcpyAsync(ctx->host, brp.as<int64_t>() + m, sizeof(int64_t), cudaMemcpyDeviceToHost,
-                          ctx->stream));
-  CB_CUDA(cudaStreamSynchronize(ctx->stream));
-  const int64_t total = ctx->host[0];
+  // The batch count: from the exact symbolic total (paper Sec. 7.4), or,
+  // with learned sizing, from the sum of the predicted row sizes times
+  // (1 + margin), which skips that whole symbolic pass.
+  int b_sorted;
+  int64_t total;
+  if (opt.sizing == CB_SIZING_LEARNED) {
+    ensure(ctx, &ctx->ws, &ctx->ws_cap,
+           align_up(sizeof(int64_t) * cb::kCounters) + align_up(8 * (size_t)(m + 1)) +
+               align_up(4 * (size_t)(m + 1)) + align_up(12 * (size_t)(m + 1)));
+    Carver cv{static_cast<char*>(ctx->ws)};
+    int64_t* counters = cv.take<int64_t>(cb::kCounters);
+    int64_t* flops = cv.take<int64_t>(m + 1);
+    int32_t* maxb = cv.take<int32_t>(m + 1);
+    float* feat = cv.take<float>(3 * (m + 1));
+    CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+    cb::launch_check_sorted(dBfull, counters, ctx->stream, ctx->sms);
+    cb::launch_classify_sym(dA, dBfull, flops, maxb, counters, ctx->stream, ctx->sms);
+    cb::launch_row_features(dA, flops, maxb, feat, ctx->stream, ctx->sms);
+    cb::launch_mlp_predict(cb::mlp_bf16(opt.mlp), cb::mlp_master(opt.mlp), cb::mlp_norm(opt.mlp),
+                           feat, m, k, nullptr, rownnz.as<int64_t>(), ctx->stream, ctx->sms);
+    CB_LAUNCHED();
+    ctx->stats.kernels += 4;
+    total = total_of(ctx, rownnz.as<int64_t>(), m);  // synchronises
+    b_sorted = ctx->host[cb::kUnsorted] == 0 ? 1 : 0;
+    ctx->stats.flops = ctx->host[cb::kTotalFlops];
+    total = (int64_t)((double)total * (1.0 + (double)opt.margin));
+  } else {
+    count_rows(ctx, dA, dBfull, rownnz.as<int64_t>());
+    b_sorted = ctx->host[cb::kUnsorted] == 0 ? 1 : 0;
+    total = total_of(ctx, rownnz.as<int64_t>(), m);
+  }
   const int64_t sym_flops = ctx->stats.flops;
   int64_t nb = (total + cap - 1) / cap;
   if (nb < 1) nb = 1;
@@ -450,7 +571,8 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
     cb_csr Cb{m, k, 0, brp.as<int64_t>(), bcol.as<int32_t>(), bval.p};
     ctx->stats.kernels = 0;
     try {
-      spgemm_plain(ctx, sr, A, view, k, &Cb, inner);
+      if (opt.sizing == CB_SIZING_EXACT) spgemm_plain(ctx, sr, A, view, k, &Cb, inner);
+      else spgemm_learned(ctx, sr, A, view, k, &Cb, inner);
     } catch (const Fail& f) {
       if (f.code != CB_ERR_CAPACITY) throw;
       kernels += ctx->stats.kernels;
@@ -596,14 +718,19 @@ int cb_spgemm_ex(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, 
     if (A->ncols != B->nrows) fail(ctx, CB_ERR_SHAPE, "A.ncols != B.nrows");
     if (caller_buf && (!C->row_ptr || !C->col || !C->val))
       fail(ctx, CB_ERR_ARG, "out_capacity > 0 needs C->row_ptr, C->col and C->val");
-    if (opt.sizing != CB_SIZING_EXACT) fail(ctx, CB_ERR_ARG, "sizing mode not supported");
+    if (opt.sizing != CB_SIZING_EXACT && opt.sizing != CB_SIZING_LEARNED &&
+        opt.sizing != CB_SIZING_UPPER_BOUND)
+      fail(ctx, CB_ERR_ARG, "unknown sizing mode");
+    if (opt.sizing == CB_SIZING_LEARNED && !opt.mlp) fail(ctx, CB_ERR_ARG, "learned sizing needs opt->mlp");
+    if (!(opt.margin >= 0.0f)) fail(ctx, CB_ERR_ARG, "margin must be >= 0");
     if (opt.budget_bytes > 0) {
       if (!opt.on_batch) fail(ctx, CB_ERR_ARG, "budget_bytes > 0 needs on_batch");
       spgemm_colbatch(ctx, (int)sr, A, B, C, opt);
       return CB_OK;
     }
     if (opt.validate) run_validation(ctx, A, B);
-    spgemm_plain(ctx, (int)sr, A, dev(B), B->ncols, C, opt);
+    if (opt.sizing == CB_SIZING_EXACT) spgemm_plain(ctx, (int)sr, A, dev(B), B->ncols, C, opt);
+    else spgemm_learned(ctx, (int)sr, A, dev(B), B->ncols, C, opt);
     return CB_OK;
   } catch (const Fail& f) {
     if (!caller_buf && C) {

@@ -110,6 +110,10 @@ template <int SR> struct NumLimits {
   // window cut: a window starts where the running count crosses a multiple
   // of kWcut, so it holds at most kWcut + 31 <= kWcap entries
   static constexpr int kWcut = kWcap - 32;
+  // learned sizing: rows predicted to hold at most this many entries skip the
+  // symbolic phase and are computed in one pass in a hash table of
+  // 2^ceil(log2(2 cap)) slots (1024-thread team at most)
+  static constexpr int kLearnHashMax = sizeof(typename Sem<SR>::A) == 8 ? 4096 : 8192;
 };
 
 // One rank window of a heavy row: row index h into the heavy-row list, the

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct cb_mlp;
+
 namespace cb {
 
 struct Window;
@@ -46,10 +48,12 @@ void launch_validate(const DevCSR& M, int64_t nnz, int code_base, int64_t* count
 
 // K1: flops_i, maxB_i and the symbolic tier histogram; total flops.
 void launch_classify_sym(const DevCSR& A, const DevCSR& B, int64_t* flops, int32_t* maxb,
-                         int64_t* counters, cudaStream_t s, int sms);
+                         int64_t* counters, cudaStream_t s, int sms,
+                         const uint8_t* skip = nullptr);
 // K2: rows into per-tier segments of perm; heavy rows also get nnz[i] = 0.
 void launch_scatter_sym(int64_t m, int64_t ncols, const int64_t* flops, int32_t* perm,
-                        int64_t* nnz, int64_t* counters, cudaStream_t s, int sms);
+                        int64_t* nnz, int64_t* counters, cudaStream_t s, int sms,
+                        const uint8_t* skip = nullptr, const int64_t* preset = nullptr);
 
 // K4: out[0] = 0, out[i+1] = out[i] + in[i]; partial needs scan_partials(n) int64.
 int64_t scan_partials(int64_t n);
@@ -63,7 +67,26 @@ void launch_slabs(const DevCSR& B, const int64_t* bnd, int nb1, int64_t* pos, cu
 
 // Numeric binning by exact row size.
 void launch_classify_num(int sr, int64_t m, const int64_t* nnz, int32_t* perm,
-                         int64_t* counters, cudaStream_t s, int sms);
+                         int64_t* counters, cudaStream_t s, int sms,
+                         const uint8_t* skip = nullptr);
+
+// Learned sizing (rows whose capacity fits a hash table skip the symbolic
+// phase): capacities + routing, their tiers, the one-pass numeric into
+// staging, and the copy from staging into C.
+void launch_learn_caps(int64_t m, const int64_t* pred, const int64_t* flops, int64_t ncols,
+                       float margin, int64_t hash_max, int64_t* cap, uint8_t* learned,
+                       cudaStream_t s, int sms);
+void launch_learned_tiers(int64_t m, const int64_t* cap, int64_t hash_max, int32_t* perm,
+                          int64_t* counters, cudaStream_t s, int sms);
+int learn_hash_max(int sr);
+void launch_learned_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* perm,
+                            const int64_t* seg_begin, const int64_t* seg_count,
+                            const int64_t* flops, const int64_t* cap, const int64_t* stage_rp,
+                            int32_t* scol, void* sval, uint8_t* learned, int64_t* cnt,
+                            int64_t* overflows, cudaStream_t s, int sms, int* launches);
+void launch_compact_rows(int vsz, int64_t m, const uint8_t* learned, const int64_t* stage_rp,
+                         const int64_t* cnt, const int32_t* scol, const void* sval,
+                         const int64_t* Crp, int32_t* Ccol, void* Cval, cudaStream_t s, int sms);
 
 // K3: symbolic phase, all tiers.  perm holds the tier segments in order;
 // seg_begin[t] / seg_count[t] are host copies of the tier layout.  Heavy
@@ -92,6 +115,9 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
                     void* Cval, int64_t* err, cudaStream_t s, int sms, int* launches);
 
 // Learned sizer (k_mlp.cu).
+const void* mlp_bf16(const cb_mlp* m);
+const float* mlp_master(const cb_mlp* m);
+const float* mlp_norm(const cb_mlp* m);
 void launch_row_features(const DevCSR& A, const int64_t* flops, const int32_t* maxb, float* feat,
                          cudaStream_t s, int sms);
 void launch_mlp_predict(const void* wb, const float* master, const float* norm, const float* feat,

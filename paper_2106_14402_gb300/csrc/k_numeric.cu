@@ -25,12 +25,18 @@ __device__ __forceinline__ void flag_error(int64_t* err, int64_t code) {
   if (err) atomicCAS((unsigned long long*)err, 0ull, (unsigned long long)code);
 }
 
-template <int SR, int CTA, int TEAM, int TABLE_MAX>
+// LEARNED: nnz holds each row's predicted capacity instead of its exact
+// size; the row is written at Crp[i] (its staging slot) only when it fits,
+// its size goes to cnt_out[i]; a row that overflows its capacity (full
+// table or more entries than predicted) is marked learned[i] = 0 and
+// recomputed later by the exact path.
+template <int SR, int CTA, int TEAM, int TABLE_MAX, bool LEARNED = false>
 __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int32_t* rows,
                                                   int64_t nrows_tier, const int64_t* flops,
                                                   const int64_t* nnz, const int64_t* Crp,
                                                   int32_t* Ccol, typename Sem<SR>::T* Cval,
-                                                  int64_t* err) {
+                                                  int64_t* err, uint8_t* learned = nullptr,
+                                                  int64_t* cnt_out = nullptr) {
   typedef Sem<SR> S;
   typedef typename S::A Acc;
   typedef typename S::T T;
@@ -38,6 +44,7 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
   constexpr int PER = TABLE_MAX / TEAM;
   extern __shared__ __align__(16) unsigned char num_smem[];
   __shared__ int scan_scratch[TEAMS][33];
+  __shared__ int overflow[TEAMS];
   const int team = threadIdx.x / TEAM, lane = threadIdx.x % TEAM;
   Acc* vals = reinterpret_cast<Acc*>(num_smem) + team * TABLE_MAX;
   int* keys = reinterpret_cast<int*>(reinterpret_cast<Acc*>(num_smem) + TEAMS * TABLE_MAX) + team * TABLE_MAX;
@@ -56,6 +63,7 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
       keys[s] = kEmptyKey;
       vals[s] = S::ident();
     }
+    if (LEARNED && lane == 0) overflow[team] = 0;
     team_sync<TEAM>();
 
     // accumulate every product of row i
@@ -72,6 +80,7 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
         bool ins;
         const int slot = probe_insert(keys, mask, shift, c, ins);
         if (slot >= 0) S::atomic(&vals[slot], S::mul(a, Bval[q]));
+        else if (LEARNED) overflow[team] = 1;
         else flag_error(err, 20);
       }
     }
@@ -94,6 +103,15 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
     int total;
     int pos = team_exclusive_scan<TEAM>(mc, scan_scratch[team], total);
     team_sync<TEAM>();
+    if (LEARNED && (overflow[team] || total > nz)) {  // uniform over the team
+      if (lane == 0) {
+        learned[i] = 0;
+        cnt_out[i] = 0;
+        if (err) atomicAdd((unsigned long long*)err, 1ull);  // overflow count
+      }
+      team_sync<TEAM>();
+      continue;
+    }
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
       if (mk[j] != kEmptyKey) {
@@ -127,7 +145,8 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
     }
 
     // write the sorted row
-    if (total != nz && lane == 0) flag_error(err, 21);
+    if (!LEARNED && total != nz && lane == 0) flag_error(err, 21);
+    if (LEARNED && lane == 0) cnt_out[i] = total;
     const int nw = total < nz ? total : (int)nz;
     const int64_t off = Crp[i];
     for (int t = lane; t < nw; t += TEAM) {
@@ -308,7 +327,70 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
   }
 }
 
+template <int SR>
+void learned_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int64_t* seg_begin,
+                const int64_t* seg_count, const int64_t* flops, const int64_t* cap,
+                const int64_t* stage_rp, int32_t* scol, void* sval_, uint8_t* learned,
+                int64_t* cnt, int64_t* overflows, cudaStream_t s, int sms, int* launches) {
+  typedef typename Sem<SR>::A Acc;
+  typedef typename Sem<SR>::T T;
+  T* sval = reinterpret_cast<T*>(sval_);
+  constexpr size_t slot = sizeof(Acc) + sizeof(int);
+  if (seg_count[1]) {
+    constexpr int CTA = 256, TEAM = 32, TBL = 2 * kNumWarpMax;
+    k_num_hash<SR, CTA, TEAM, TBL, true><<<capped((seg_count[1] + 7) / 8, sms * 8), CTA,
+                                            (CTA / TEAM) * TBL * slot, s>>>(
+        A, B, perm + seg_begin[1], seg_count[1], flops, cap, stage_rp, scol, sval, overflows,
+        learned, cnt);
+    ++*launches;
+  }
+  if (seg_count[2]) {
+    constexpr int CTA = 256, TEAM = 256, TBL = 2 * kNumSmallMax;
+    k_num_hash<SR, CTA, TEAM, TBL, true><<<capped(seg_count[2], sms * 8), CTA, TBL * slot, s>>>(
+        A, B, perm + seg_begin[2], seg_count[2], flops, cap, stage_rp, scol, sval, overflows,
+        learned, cnt);
+    ++*launches;
+  }
+  if (seg_count[3]) {
+    constexpr int CTA = 1024, TEAM = 1024, TBL = 2 * NumLimits<SR>::kLearnHashMax;
+    const size_t smem = TBL * slot;
+    set_smem(k_num_hash<SR, CTA, TEAM, TBL, true>, smem);
+    k_num_hash<SR, CTA, TEAM, TBL, true><<<capped(seg_count[3], sms), CTA, smem, s>>>(
+        A, B, perm + seg_begin[3], seg_count[3], flops, cap, stage_rp, scol, sval, overflows,
+        learned, cnt);
+    ++*launches;
+  }
+}
+
 }  // namespace
+
+void launch_learned_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* perm,
+                            const int64_t* seg_begin, const int64_t* seg_count,
+                            const int64_t* flops, const int64_t* cap, const int64_t* stage_rp,
+                            int32_t* scol, void* sval, uint8_t* learned, int64_t* cnt,
+                            int64_t* overflows, cudaStream_t s, int sms, int* launches) {
+#define CB_LRN(SRV)                                                                            \
+  learned_sr<SRV>(A, B, perm, seg_begin, seg_count, flops, cap, stage_rp, scol, sval, learned, \
+                  cnt, overflows, s, sms, launches)
+  switch (sr) {
+    case 1: CB_LRN(1); break;
+    case 2: CB_LRN(2); break;
+    case 3: CB_LRN(3); break;
+    case 4: CB_LRN(4); break;
+    case 5: CB_LRN(5); break;
+  }
+#undef CB_LRN
+}
+
+int learn_hash_max(int sr) {
+  switch (sr) {
+    case 1: return NumLimits<1>::kLearnHashMax;
+    case 2: return NumLimits<2>::kLearnHashMax;
+    case 3: return NumLimits<3>::kLearnHashMax;
+    case 4: return NumLimits<4>::kLearnHashMax;
+    default: return NumLimits<5>::kLearnHashMax;
+  }
+}
 
 int num_window_cut(int sr) {
   switch (sr) {

@@ -29,7 +29,8 @@ __global__ void k_validate(DevCSR M, int64_t nnz, int code_base, int64_t* counte
 // K1: one warp per row of A.  flops_i = sum of B row lengths over the row's
 // stored entries (the flops count of Table 1), maxb_i = the longest of them.
 __global__ void __launch_bounds__(256) k_classify_sym(DevCSR A, DevCSR B, int64_t* flops,
-                                                      int32_t* maxb, int64_t* counters) {
+                                                      int32_t* maxb, int64_t* counters,
+                                                      const uint8_t* skip) {
   __shared__ unsigned long long hist[kSymTiers];
   __shared__ unsigned long long total;
   if (threadIdx.x < kSymTiers) hist[threadIdx.x] = 0;
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(256) k_classify_sym(DevCSR A, DevCSR B, int64_
     if (lane == 0) {
       flops[i] = f;
       if (maxb) maxb[i] = mx;
-      atomicAdd(&hist[sym_tier(min((int64_t)f, B.ncols))], 1ull);
+      atomicAdd(&hist[skip && skip[i] ? 0 : sym_tier(min((int64_t)f, B.ncols))], 1ull);
       atomicAdd(&total, (unsigned long long)f);
     }
   }
@@ -69,7 +70,9 @@ __global__ void __launch_bounds__(256) k_classify_sym(DevCSR A, DevCSR B, int64_
 struct TierBySize {
   const int64_t* v;
   int64_t cap, t1, t2, t3;
+  const uint8_t* skip;  // rows with skip[i] != 0 are left out (tier 0)
   __device__ __forceinline__ int operator()(int64_t i) const {
+    if (skip && skip[i]) return 0;
     const int64_t u = min(v[i], cap);
     return u == 0 ? 0 : u <= t1 ? 1 : u <= t2 ? 2 : u <= t3 ? 3 : 4;
   }
@@ -88,11 +91,12 @@ __global__ void __launch_bounds__(256) k_tier_count(int64_t m, TierBySize tier, 
 }
 
 // K2: place row i into the segment of its tier inside perm (tiers 1..4 in
-// order; tier 0 rows are empty and get no slot).  zero_nnz (optional): rows
-// of tier 0 and 4 get nnz = 0 (tier 4 rows are summed slice by slice later).
+// order; tier 0 rows are empty or skipped and get no slot).  zero_nnz
+// (optional): rows of tier 0 and 4 get nnz = 0 (tier 4 rows are summed slice
+// by slice later), except skipped rows, which get preset[i].
 __global__ void __launch_bounds__(256) k_tier_scatter(int64_t m, TierBySize tier, int32_t* perm,
                                                       const int64_t* cnt, int64_t* cur,
-                                                      int64_t* zero_nnz) {
+                                                      int64_t* zero_nnz, const int64_t* preset) {
   __shared__ int local[5];
   __shared__ long long base[5];
   if (threadIdx.x < 5) local[threadIdx.x] = 0;
@@ -101,7 +105,10 @@ __global__ void __launch_bounds__(256) k_tier_scatter(int64_t m, TierBySize tier
   int t = -1, slot = 0;
   if (i < m) {
     t = tier(i);
-    if (zero_nnz && (t == 0 || t == 4)) zero_nnz[i] = 0;
+    if (zero_nnz) {
+      if (tier.skip && tier.skip[i]) zero_nnz[i] = preset ? preset[i] : 0;
+      else if (t == 0 || t == 4) zero_nnz[i] = 0;
+    }
     if (t > 0) slot = atomicAdd(&local[t], 1);
   }
   __syncthreads();
@@ -230,15 +237,16 @@ void launch_validate(const DevCSR& M, int64_t nnz, int code_base, int64_t* count
 }
 
 void launch_classify_sym(const DevCSR& A, const DevCSR& B, int64_t* flops, int32_t* maxb,
-                         int64_t* counters, cudaStream_t s, int sms) {
-  k_classify_sym<<<grid_for(A.nrows, 8, sms * 8), 256, 0, s>>>(A, B, flops, maxb, counters);
+                         int64_t* counters, cudaStream_t s, int sms, const uint8_t* skip) {
+  k_classify_sym<<<grid_for(A.nrows, 8, sms * 8), 256, 0, s>>>(A, B, flops, maxb, counters, skip);
 }
 
 void launch_scatter_sym(int64_t m, int64_t ncols, const int64_t* flops, int32_t* perm,
-                        int64_t* nnz, int64_t* counters, cudaStream_t s, int) {
-  TierBySize t{flops, ncols, kSymWarpMax, kSymSmallMax, kSymHashMax};
+                        int64_t* nnz, int64_t* counters, cudaStream_t s, int,
+                        const uint8_t* skip, const int64_t* preset) {
+  TierBySize t{flops, ncols, kSymWarpMax, kSymSmallMax, kSymHashMax, skip};
   k_tier_scatter<<<grid_for(m, 256, 1 << 30), 256, 0, s>>>(m, t, perm, counters + kCntSym,
-                                                            counters + kCurSym, nnz);
+                                                            counters + kCurSym, nnz, preset);
 }
 
 int64_t scan_partials(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
@@ -262,11 +270,91 @@ void launch_slabs(const DevCSR& B, const int64_t* bnd, int nb1, int64_t* pos, cu
 }
 
 void launch_classify_num(int sr, int64_t m, const int64_t* nnz, int32_t* perm, int64_t* counters,
-                         cudaStream_t s, int sms) {
-  TierBySize t{nnz, INT64_MAX, kNumWarpMax, kNumSmallMax, (int64_t)num_hash_max(sr)};
+                         cudaStream_t s, int sms, const uint8_t* skip) {
+  TierBySize t{nnz, INT64_MAX, kNumWarpMax, kNumSmallMax, (int64_t)num_hash_max(sr), skip};
   k_tier_count<<<grid_for(m, 256, sms * 8), 256, 0, s>>>(m, t, counters + kCntNum);
   k_tier_scatter<<<grid_for(m, 256, 1 << 30), 256, 0, s>>>(m, t, perm, counters + kCntNum,
-                                                            counters + kCurNum, nullptr);
+                                                            counters + kCurNum, nullptr, nullptr);
+}
+
+// Learned sizing: capacity of each row from its predicted size, and whether
+// the row takes the one-pass hash path (cap <= hash_max) or the exact path.
+// cap = min(bound, max(pred, ceil(pred * (1 + margin)))), bound = min(flops, ncols);
+// learned rows also get their tier histogram in cnt[0..4] (by cap).
+__global__ void __launch_bounds__(256) k_learn_caps(int64_t m, const int64_t* pred,
+                                                    const int64_t* flops, int64_t ncols,
+                                                    float margin, int64_t hash_max, int64_t* cap,
+                                                    uint8_t* learned) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = flops[i];
+    const int64_t bound = f < ncols ? f : ncols;
+    int64_t p = pred ? pred[i] : bound;
+    int64_t c = (int64_t)ceil((double)p * (1.0 + (double)margin));
+    if (c < p) c = p;
+    if (c > bound) c = bound;
+    const bool l = f > 0 && c <= hash_max;
+    learned[i] = l ? 1 : 0;
+    cap[i] = l ? c : 0;
+  }
+}
+
+// Copy the rows computed in one pass from their staging slots into C.
+// One warp per row.
+template <class T>
+__global__ void __launch_bounds__(256) k_compact_rows(int64_t m, const uint8_t* learned,
+                                                      const int64_t* stage_rp, const int64_t* cnt,
+                                                      const int32_t* scol, const T* sval,
+                                                      const int64_t* Crp, int32_t* Ccol, T* Cval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += nwarps) {
+    if (!learned[i]) continue;
+    const int64_t src = stage_rp[i], dst = Crp[i], n = cnt[i];
+    for (int64_t t = lane; t < n; t += 32) {
+      Ccol[dst + t] = scol[src + t];
+      Cval[dst + t] = sval[src + t];
+    }
+  }
+}
+
+void launch_learn_caps(int64_t m, const int64_t* pred, const int64_t* flops, int64_t ncols,
+                       float margin, int64_t hash_max, int64_t* cap, uint8_t* learned,
+                       cudaStream_t s, int sms) {
+  if (m == 0) return;
+  k_learn_caps<<<grid_for(m, 256, sms * 8), 256, 0, s>>>(m, pred, flops, ncols, margin, hash_max,
+                                                          cap, learned);
+}
+
+void launch_learned_tiers(int64_t m, const int64_t* cap, int64_t hash_max, int32_t* perm,
+                          int64_t* counters, cudaStream_t s, int sms) {
+  TierBySize t{cap, INT64_MAX, kNumWarpMax, kNumSmallMax, hash_max, nullptr};
+  k_tier_count<<<grid_for(m, 256, sms * 8), 256, 0, s>>>(m, t, counters + kCntNum);
+  k_tier_scatter<<<grid_for(m, 256, 1 << 30), 256, 0, s>>>(m, t, perm, counters + kCntNum,
+                                                            counters + kCurNum, nullptr, nullptr);
+}
+
+void launch_compact_rows(int vsz, int64_t m, const uint8_t* learned, const int64_t* stage_rp,
+                         const int64_t* cnt, const int32_t* scol, const void* sval,
+                         const int64_t* Crp, int32_t* Ccol, void* Cval, cudaStream_t s, int sms) {
+  if (m == 0) return;
+  const int g = grid_for(m, 8, sms * 16);
+  switch (vsz) {
+    case 8:
+      k_compact_rows<uint64_t><<<g, 256, 0, s>>>(m, learned, stage_rp, cnt, scol,
+                                                 static_cast<const uint64_t*>(sval), Crp, Ccol,
+                                                 static_cast<uint64_t*>(Cval));
+      break;
+    case 4:
+      k_compact_rows<uint32_t><<<g, 256, 0, s>>>(m, learned, stage_rp, cnt, scol,
+                                                 static_cast<const uint32_t*>(sval), Crp, Ccol,
+                                                 static_cast<uint32_t*>(Cval));
+      break;
+    default:
+      k_compact_rows<uint8_t><<<g, 256, 0, s>>>(m, learned, stage_rp, cnt, scol,
+                                                static_cast<const uint8_t*>(sval), Crp, Ccol,
+                                                static_cast<uint8_t*>(Cval));
+  }
 }
 
 }  // namespace cb
