@@ -302,6 +302,10 @@ def main_gpu(args):
                 "peak_source": peak_src,
                 "algorithmic_bytes_per_step": num_bytes, "ms_per_step_in_kernel": round(num_ms, 4)}
 
+    legs = {}
+    if not args.no_legs:
+        legs = run_legs(args, cb, ctx, dprob, flush, ms_step, products)
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, cb, ctx, dprob, dev, world, dist, products)
@@ -323,12 +327,84 @@ def main_gpu(args):
                            "parallelism": f"replicas x{world}"},
                 "nnz_per_s": nnz_rate, "per_semiring": per_sr, "phase_ms_per_step":
                     {k: round(v, 4) for k, v in phase_tot.items()},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, **legs,
                 "gpu_launches": launches, "clocks": clocks, "wall_s_timed": round(wall, 3)}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def load_sizer(cb):
+    """The trained predictor checkpoint, or a quickly trained stand-in when absent."""
+    from paper_2106_14402_gb300 import sizer
+    if os.path.exists(sizer.CHECKPOINT):
+        model, meta = sizer.load()
+        return model, {"source": "checkpoint", "train_rows": meta.get("rows"),
+                       "train_matrices": meta.get("matrices")}
+    feats, labels = zip(*(sizer.product_rows(sizer.gen.training_family(i))
+                          for i in list(range(660, 667)) + list(range(667, 700, 4))))
+    model, _ = sizer.train(__import__("torch").cat(feats), __import__("torch").cat(labels),
+                           epochs=20, batch=4096, lr=3e-3)
+    return model, {"source": "trained at start on 16 family matrices"}
+
+
+def timed(fn, steps, flush):
+    import torch
+    times = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return sum(times) / len(times)
+
+
+def run_legs(args, cb, ctx, dprob, flush, plain_ms, products):
+    """Learned sizing and column batching on the same workload, timed like the main loop."""
+    model, src = load_sizer(cb)
+    out = {}
+
+    def learned_step():
+        st = []
+        for sr, A, B, dA, dB, o, nnz in dprob:
+            cb.spgemm(sr, dA, dB, validate=False, out=o, sizing="learned", mlp=model, ctx=ctx)
+            st.append(ctx.stats())
+        return st
+
+    for _ in range(max(1, args.warmup)):
+        st = learned_step()
+    ms = timed(learned_step, args.steps, flush)
+    out["learned"] = {"value": products / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                      "vs_plain_two_phase": plain_ms / ms,
+                      "overflow_rows": [x["overflow_rows"] for x in st], "sizer": src,
+                      "margin": 0.25}
+    # column batching of the 8-byte-value product under a budget of ~1/4 of its output
+    sr, A, B, dA, dB, o, nnz = next((p for p in dprob if VAL_BYTES[p[0]] == 8), dprob[0])
+    per = 4 + VAL_BYTES[sr]
+    budget = 8 * (A.nrows + 1) + (nnz // 4 + 1) * per
+    res = {"semiring": sr, "budget_bytes": budget, "output_bytes": 8 * (A.nrows + 1) + nnz * per}
+    prods = None
+    for mode in ("exact", "learned"):
+        info = {}
+
+        def run():
+            st = cb.spgemm_column_batches(sr, dA, dB, budget, lambda *a: False, validate=False,
+                                          sizing=mode, mlp=model if mode == "learned" else None,
+                                          ctx=ctx)
+            info.update(st)
+
+        run()
+        ms = timed(run, max(1, min(args.steps, 3)), flush)
+        prods = info["flops"]
+        res[mode] = {"ms": ms, "batches": info["batches"], "products_per_s": prods / (ms * 1e-3)}
+    res["learned_vs_exact"] = res["exact"]["ms"] / res["learned"]["ms"]
+    out["column_batched"] = res
+    return out
 
 
 def run_e2e(args, cb, ctx, dprob, dev, world, dist, products):
@@ -395,6 +471,7 @@ def main():
     ap.add_argument("--workload", default="rmat18", choices=("rmat18", "rmat16", "er16k"))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-legs", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -77,6 +77,17 @@ class CSR:
         return np.diff(self.row_ptr)
 
 
+def sorted_unique(keys: np.ndarray) -> np.ndarray:
+    """Sorted distinct values (same result as np.unique, via one sort and a mask)."""
+    s = np.sort(keys)
+    if s.size == 0:
+        return s
+    keep = np.empty(s.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(s[1:], s[:-1], out=keep[1:])
+    return s[keep]
+
+
 def _csr_from_sorted_keys(keys: np.ndarray, nrows: int, ncols: int) -> CSR:
     rows = keys // ncols
     cols = (keys - rows * ncols).astype(np.int32)
@@ -88,7 +99,7 @@ def _csr_from_sorted_keys(keys: np.ndarray, nrows: int, ncols: int) -> CSR:
 
 def csr_from_coo(rows: np.ndarray, cols: np.ndarray, nrows: int, ncols: int) -> CSR:
     """Sorted, de-duplicated CSR pattern from COO coordinates."""
-    keys = np.unique(rows.astype(np.int64) * ncols + cols.astype(np.int64))
+    keys = sorted_unique(rows.astype(np.int64) * ncols + cols.astype(np.int64))
     return _csr_from_sorted_keys(keys, nrows, ncols)
 
 
@@ -124,7 +135,7 @@ def rmat(scale: int, edgefactor: int, a: float, b: float, c: float, seed: int,
         j = perm[j]
     if symmetrize:
         i, j = np.concatenate([i, j]), np.concatenate([j, i])
-    keys = np.unique(i * n + j)
+    keys = sorted_unique(i * n + j)
     del i, j
     return _csr_from_sorted_keys(keys, n, n)
 
