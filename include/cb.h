@@ -107,8 +107,12 @@ typedef struct {
 enum {
   CB_FLAG_CHECK = 1,  /* synchronise at the end and fail (CB_ERR_CUDA) if a kernel's
                          internal consistency word is set (debug)                   */
-  CB_FLAG_TIMING = 2  /* record CUDA events between the phases on ctx's stream and
+  CB_FLAG_TIMING = 2, /* record CUDA events between the phases on ctx's stream and
                          report their durations in cb_stats (synchronises at the end) */
+  CB_FLAG_LEARNED_ROWS = 4 /* batched modes with learned sizing: besides the batch
+                         count, also size each batch's rows from predictions
+                         (default: predictions set the batch count only and each
+                         batch runs the exact two-phase path) */
 };
 
 /* Fill *opt with defaults (exact sizing, validation on, library-allocated C). */
@@ -144,6 +148,27 @@ int cb_spgemm(cb_semiring sr, const cb_csr *A, const cb_csr *B, cb_csr *C);
  * through another stream). */
 int cb_spgemm_ex(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B,
                  cb_csr *C, const cb_opts *opt);
+
+/* Batched SpGEMM: count independent products C_i = A_i (+).(x)_{sr[i]} B_i
+ * (the paper's GPU path picks a library per call by flops and compression,
+ * Sec. 5; here all products of a batch share one launch sequence).
+ * Consecutive products with the same semiring form a group; a group is laid
+ * out as one block-diagonal product (A_i stacked by rows with their columns
+ * shifted to the stacked rows of B_i; B_i stacked by rows with their own
+ * columns) and cut into waves of consecutive products whose output (row
+ * pointers + columns + values) fits opt->budget_bytes (0 = one wave per
+ * group).  Wave sizes come from exact symbolic counts or, with learned
+ * sizing, from predicted sizes times (1 + margin); a wave whose exact output
+ * still exceeds the budget returns CB_ERR_CAPACITY.  Each wave is handed to
+ *   opt->on_batch(wave, first, end, &Cw, opt->user)
+ * where Cw stacks C_first .. C_{end-1} by rows (Cw.row_ptr covers all their
+ * rows, in order; columns are each product's own), valid only during the
+ * call; a nonzero return stops the batch (CB_OK).  opt->on_batch is
+ * required; inputs are device CSR as for cb_spgemm_ex; sizing may be exact
+ * or learned.  The stacked rows of each group must fit int32 indices
+ * (CB_ERR_INDEX otherwise). */
+int cb_spgemm_batched(cb_ctx *ctx, int count, const cb_semiring *sr, const cb_csr *A,
+                      const cb_csr *B, const cb_opts *opt);
 
 /* Release arrays that the library allocated for C; zeroes *C.  Waits for all
  * work on the device to finish first, so it is safe right after an
@@ -237,6 +262,31 @@ int cb_mlp_train(cb_ctx *ctx, cb_mlp *m, const float *feat, const int64_t *nnz, 
  *     order them on one stream or with events.
  *   Returns CB_OK or CB_ERR_CUDA (launch failure). */
 int cb_exclusive_scan_noalloc(const int64_t *in, int64_t n, int64_t *out, void *cuda_stream);
+
+/* ---- tier bounds and autotuning -------------------------------------------
+ * The paper's GPU path picks a library per call by compression factor and
+ * flops (Sec. 5); here one set of kernels covers all rows and the bounds
+ * between its row tiers are chosen per workload:
+ *   sym_hash_max  rows with min(flops_i, ncols) <= this are counted in a
+ *                 shared-memory hash table, the rest with dense bitmaps
+ *                 (512..4096, default 512);
+ *   num_hash_max  rows with nnz(C_i) <= this are computed in a hash table +
+ *                 in-row sort, the rest in rank windows (sym_hash_max..4096 for
+ *                 8-byte values, ..8192 for smaller ones, default 512);
+ *   learn_max     with learned or upper-bound sizing, rows whose capacity is
+ *                 <= this skip the symbolic phase (0..8192, default 512).
+ * cb_ctx_set_tune clamps the values into range (and writes back what it set).
+ * cb_autotune times cb_spgemm_ex-equivalent runs of A.B under a grid of
+ * bounds (learn_max too when opt->sizing is learned), keeps the fastest in
+ * the context and returns it with its time in ms; it allocates and frees its
+ * own output and synchronises the stream. */
+typedef struct {
+  int32_t sym_hash_max, num_hash_max, learn_max;
+} cb_tune;
+int cb_ctx_set_tune(cb_ctx *ctx, cb_tune *tune);
+int cb_ctx_get_tune(const cb_ctx *ctx, cb_tune *tune);
+int cb_autotune(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B, const cb_opts *opt,
+                cb_tune *best, float *best_ms);
 
 /* Statistics of the most recent cb_spgemm_ex on this context (host memory). */
 typedef struct {

@@ -14,8 +14,10 @@ from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
+GSRC = os.path.join(HERE, "csrc_gen")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcb.so")
+GENLIB = os.path.join(OUT, "libcbgen.so")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 
@@ -65,6 +67,13 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
         run([cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
              "-Xlinker", "-rpath,/usr/local/cuda/lib64"])
         os.replace(tmp, LIB)
+    # the device-side input generator is a library of its own
+    gsrc = os.path.join(GSRC, "cbgen.cu")
+    if force or not os.path.exists(GENLIB) or os.path.getmtime(GENLIB) < os.path.getmtime(gsrc):
+        tmp = GENLIB + f".tmp{os.getpid()}"
+        run([cc, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
+             "-o", tmp, gsrc, "-Xlinker", "-rpath,/usr/local/cuda/lib64"])
+        os.replace(tmp, GENLIB)
     return LIB
 
 

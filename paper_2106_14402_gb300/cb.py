@@ -50,6 +50,11 @@ class cb_opts(ctypes.Structure):
                 ("margin", ctypes.c_float), ("flags", ctypes.c_int32)]
 
 
+class cb_tune(ctypes.Structure):
+    _fields_ = [("sym_hash_max", ctypes.c_int32), ("num_hash_max", ctypes.c_int32),
+                ("learn_max", ctypes.c_int32)]
+
+
 class cb_stats(ctypes.Structure):
     _fields_ = [("flops", c_int64), ("nnz", c_int64), ("heavy_rows", c_int64),
                 ("heavy_units", c_int64), ("overflow_rows", c_int64), ("batches", ctypes.c_int32),
@@ -87,6 +92,13 @@ _SIGS = {
     "cb_exclusive_scan": ([c_void_p, c_void_p, c_int64, c_void_p], ctypes.c_int),
     "cb_exclusive_scan_noalloc": ([c_void_p, c_int64, c_void_p, c_void_p], ctypes.c_int),
     "cb_last_stats": ([c_void_p, ctypes.POINTER(cb_stats)], ctypes.c_int),
+    "cb_spgemm_batched": ([c_void_p, ctypes.c_int, c_void_p, c_void_p, c_void_p,
+                           ctypes.POINTER(cb_opts)], ctypes.c_int),
+    "cb_ctx_set_tune": ([c_void_p, ctypes.POINTER(cb_tune)], ctypes.c_int),
+    "cb_ctx_get_tune": ([c_void_p, ctypes.POINTER(cb_tune)], ctypes.c_int),
+    "cb_autotune": ([c_void_p, ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr),
+                     ctypes.POINTER(cb_opts), ctypes.POINTER(cb_tune), ctypes.POINTER(ctypes.c_float)],
+                    ctypes.c_int),
     "cb_mlp_create": ([ctypes.POINTER(c_void_p), c_void_p, c_void_p], ctypes.c_int),
     "cb_mlp_destroy": ([c_void_p], None),
     "cb_mlp_get": ([c_void_p, c_void_p, c_void_p, c_void_p], ctypes.c_int),
@@ -237,6 +249,16 @@ class Context:
     def check(self, rc: int):
         if rc != 0:
             raise CBError(rc, self.error())
+
+    def set_tune(self, sym_hash_max=512, num_hash_max=512, learn_max=512) -> dict:
+        t = cb_tune(sym_hash_max, num_hash_max, learn_max)
+        self.check(self.lib.cb_ctx_set_tune(self.handle, ctypes.byref(t)))
+        return {k: getattr(t, k) for k, _ in cb_tune._fields_}
+
+    def get_tune(self) -> dict:
+        t = cb_tune()
+        self.check(self.lib.cb_ctx_get_tune(self.handle, ctypes.byref(t)))
+        return {k: getattr(t, k) for k, _ in cb_tune._fields_}
 
     def stats(self) -> dict:
         s = cb_stats()
@@ -470,3 +492,58 @@ def row_features(A: DeviceCSR, B: DeviceCSR, ctx: Context | None = None) -> torc
     ctx.check(ctx.lib.cb_row_features(ctx.handle, ctypes.byref(sa), ctypes.byref(sb),
                                       c_void_p(feat.data_ptr())))
     return feat
+
+
+def spgemm_batched(semirings, As, Bs, on_wave, *, budget_bytes: int = 0, validate: bool = True,
+                   sizing: str = "exact", mlp=None, margin: float = 0.25,
+                   ctx: Context | None = None) -> dict:
+    """Batched products C_i = A_i (+).(x) B_i (cb_spgemm_batched).
+
+    on_wave(wave, first, end, Cw) receives a DeviceCSR that stacks
+    C_first..C_{end-1} by rows (each product's own column indices), valid
+    only during the call; return True to stop.  Returns the statistics.
+    """
+    ctx = ctx or context()
+    n = len(As)
+    assert len(Bs) == n and len(semirings) == n
+    codes = (ctypes.c_int * max(n, 1))(*[SEMIRING[s][0] for s in semirings])
+    sa = (cb_csr * max(n, 1))(*[a.as_struct() for a in As])
+    sb = (cb_csr * max(n, 1))(*[b.as_struct() for b in Bs])
+    dev = As[0].row_ptr.device if n else torch.device("cuda")
+    errors = []
+
+    def _cb(wave, first, end, cptr, user):
+        try:
+            c = cptr.contents
+            dt = SEMIRING[semirings[first]][1]
+            view = DeviceCSR(c.nrows, c.ncols, _view(c.row_ptr, c.nrows + 1, torch.int64, dev),
+                             _view(c.col, c.nnz, torch.int32, dev), _view(c.val, c.nnz, dt, dev))
+            return 1 if on_wave(wave, first, end, view) else 0
+        except Exception as e:  # never raise through the C ABI
+            errors.append(e)
+            return 1
+
+    fn = BATCH_FN(_cb)
+    opts = make_opts(sizing=sizing, validate=validate, budget_bytes=budget_bytes, on_batch=fn,
+                     mlp=mlp, margin=margin)
+    ctx.check(ctx.lib.cb_spgemm_batched(ctx.handle, n, ctypes.cast(codes, c_void_p),
+                                        ctypes.cast(sa, c_void_p), ctypes.cast(sb, c_void_p),
+                                        ctypes.byref(opts)))
+    if errors:
+        raise errors[0]
+    return ctx.stats()
+
+
+def autotune(semiring: str, A: DeviceCSR, B: DeviceCSR, *, sizing: str = "exact", mlp=None,
+             margin: float = 0.25, ctx: Context | None = None):
+    """Time A.B under a grid of tier bounds (cb_autotune); the context keeps the
+    fastest.  Returns (bounds dict, milliseconds)."""
+    ctx = ctx or context()
+    code, _ = SEMIRING[semiring]
+    sa, sb = A.as_struct(), B.as_struct()
+    opts = make_opts(sizing=sizing, mlp=mlp, margin=margin)
+    t = cb_tune()
+    ms = ctypes.c_float()
+    ctx.check(ctx.lib.cb_autotune(ctx.handle, code, ctypes.byref(sa), ctypes.byref(sb), ctypes.byref(opts),
+                                  ctypes.byref(t), ctypes.byref(ms)))
+    return {k: getattr(t, k) for k, _ in cb_tune._fields_}, ms.value

@@ -6,6 +6,7 @@
 //   binning + heavy units -> [sync: nnz(C)] -> allocate C -> K5-K7 numeric.
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <deque>
 #include <memory>
 #include <new>
@@ -26,6 +27,7 @@ struct cb_ctx {
   size_t ws2_cap = 0;
   int64_t* host = nullptr;  // pinned read-back buffer
   cudaEvent_t ev[6] = {};   // phase boundaries (CB_FLAG_TIMING)
+  cb::Tune tune;            // tier bounds (cb_ctx_set_tune / cb_autotune)
   std::string err;
   cb_stats stats{};
 };
@@ -216,9 +218,10 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
   CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
   mark(ctx, opt, 0);
   cb::launch_check_sorted(dB, counters, ctx->stream, ctx->sms);
-  cb::launch_classify_sym(dA, dB, flops, maxb, counters, ctx->stream, ctx->sms, skip);
+  cb::launch_classify_sym(dA, dB, flops, maxb, counters, ctx->stream, ctx->sms, skip,
+                          ctx->tune.sym_hash_max);
   cb::launch_scatter_sym(m, ncols, flops, perm_sym, nnz, counters, ctx->stream, ctx->sms, skip,
-                         preset);
+                         preset, ctx->tune.sym_hash_max);
   CB_LAUNCHED();
   mark(ctx, opt, 1);
   ctx->stats.kernels += 3;
@@ -260,7 +263,10 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
                       wins, win_cap, hbits, b_sorted, counters, ctx->stream, ctx->sms, &launches);
   mark(ctx, opt, 2);
   cb::launch_exclusive_scan(nnz, m, C->row_ptr, partial, ctx->stream);
-  cb::launch_classify_num(sr, m, nnz, perm_num, counters, ctx->stream, ctx->sms, skip);
+  // the hash tier's table bounds the row size it can take for this value type
+  const int64_t num_hash_max = std::min<int64_t>(ctx->tune.num_hash_max, cb::num_large_max(sr));
+  cb::launch_classify_num(sr, m, nnz, perm_num, counters, ctx->stream, ctx->sms, skip,
+                          num_hash_max);
   CB_LAUNCHED();
   mark(ctx, opt, 3);
   ctx->stats.kernels += launches + 3 + 2;
@@ -305,7 +311,7 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
   mark(ctx, opt, 4);
   cb::launch_numeric(sr, dA, dB, perm_num, num_beg, num_cnt, flops, nnz, heavy_rows, wins,
                      n_units, span_counts, spans, hbits, b_sorted, C->row_ptr, C->col, C->val,
-                     counters + cb::kError, ctx->stream, ctx->sms, &launches);
+                     counters + cb::kError, ctx->stream, ctx->sms, &launches, num_hash_max);
   CB_LAUNCHED();
   mark(ctx, opt, 5);
   ctx->stats.kernels += launches;
@@ -367,7 +373,7 @@ void spgemm_learned(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int6
     cb::launch_mlp_predict(cb::mlp_bf16(opt.mlp), cb::mlp_master(opt.mlp), cb::mlp_norm(opt.mlp),
                            feat, m, ncols, nullptr, pred, ctx->stream, ctx->sms);
   }
-  const int64_t hmax = cb::learn_hash_max(sr);
+  const int64_t hmax = std::min<int64_t>(ctx->tune.learn_max, cb::learn_hash_max(sr));
   cb::launch_learn_caps(m, use_mlp ? pred : nullptr, flops, ncols, use_mlp ? opt.margin : 0.0f, hmax,
                         cap, learned, ctx->stream, ctx->sms);
   cb::launch_exclusive_scan(cap, m, stage_rp, partial, ctx->stream);
@@ -419,8 +425,10 @@ void count_rows(cb_ctx* ctx, const DevCSR& dA, const DevCSR& dB, int64_t* nnz_ou
   int32_t* perm = cv.take<int32_t>(m + 1);
   CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
   cb::launch_check_sorted(dB, counters, ctx->stream, ctx->sms);
-  cb::launch_classify_sym(dA, dB, flops, nullptr, counters, ctx->stream, ctx->sms);
-  cb::launch_scatter_sym(m, ncols, flops, perm, nnz_out, counters, ctx->stream, ctx->sms);
+  cb::launch_classify_sym(dA, dB, flops, nullptr, counters, ctx->stream, ctx->sms, nullptr,
+                          ctx->tune.sym_hash_max);
+  cb::launch_scatter_sym(m, ncols, flops, perm, nnz_out, counters, ctx->stream, ctx->sms, nullptr,
+                         nullptr, ctx->tune.sym_hash_max);
   CB_LAUNCHED();
   ctx->stats.kernels += 3;
   read_counters(ctx, counters, nullptr, 0);
@@ -571,7 +579,8 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
     cb_csr Cb{m, k, 0, brp.as<int64_t>(), bcol.as<int32_t>(), bval.p};
     ctx->stats.kernels = 0;
     try {
-      if (opt.sizing == CB_SIZING_EXACT) spgemm_plain(ctx, sr, A, view, k, &Cb, inner);
+      if (opt.sizing == CB_SIZING_EXACT || !(opt.flags & CB_FLAG_LEARNED_ROWS))
+        spgemm_plain(ctx, sr, A, view, k, &Cb, inner);
       else spgemm_learned(ctx, sr, A, view, k, &Cb, inner);
     } catch (const Fail& f) {
       if (f.code != CB_ERR_CAPACITY) throw;
@@ -596,6 +605,168 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
   ctx->stats.batches = (int32_t)batch;
   ctx->stats.kernels = kernels;
   C->nnz = nnz_sum;
+}
+
+// Per-row sizes of the product A.B (exact counts, or predictions with
+// learned sizing) summed per group of rows: sums[j] = sum of rows
+// [bounds[j], bounds[j+1]).  bounds is host memory (n + 1 values).
+void row_group_sums(cb_ctx* ctx, const cb_csr* A, const DevCSR& dB, const cb_opts& opt,
+                    const std::vector<int64_t>& bounds, std::vector<int64_t>& sums) {
+  const int64_t m = A->nrows, n = (int64_t)bounds.size() - 1;
+  DevBuf rows(ctx), pre(ctx), idx(ctx), got(ctx);
+  rows.alloc(sizeof(int64_t) * (size_t)(m + 1));
+  pre.alloc(sizeof(int64_t) * (size_t)(m + 1));
+  idx.alloc(sizeof(int64_t) * bounds.size());
+  got.alloc(sizeof(int64_t) * bounds.size());
+  const DevCSR dA = dev(A);
+  if (opt.sizing == CB_SIZING_LEARNED) {
+    ensure(ctx, &ctx->ws, &ctx->ws_cap,
+           align_up(sizeof(int64_t) * cb::kCounters) + align_up(8 * (size_t)(m + 1)) +
+               align_up(4 * (size_t)(m + 1)) + align_up(12 * (size_t)(m + 1)));
+    Carver cv{static_cast<char*>(ctx->ws)};
+    int64_t* counters = cv.take<int64_t>(cb::kCounters);
+    int64_t* flops = cv.take<int64_t>(m + 1);
+    int32_t* maxb = cv.take<int32_t>(m + 1);
+    float* feat = cv.take<float>(3 * (m + 1));
+    CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+    cb::launch_classify_sym(dA, dB, flops, maxb, counters, ctx->stream, ctx->sms);
+    cb::launch_row_features(dA, flops, maxb, feat, ctx->stream, ctx->sms);
+    cb::launch_mlp_predict(cb::mlp_bf16(opt.mlp), cb::mlp_master(opt.mlp), cb::mlp_norm(opt.mlp),
+                           feat, m, dB.ncols, nullptr, rows.as<int64_t>(), ctx->stream, ctx->sms);
+  } else {
+    count_rows(ctx, dA, dB, rows.as<int64_t>());
+  }
+  ensure(ctx, &ctx->ws2, &ctx->ws2_cap, align_up(8 * (size_t)cb::scan_partials(m)));
+  cb::launch_exclusive_scan(rows.as<int64_t>(), m, pre.as<int64_t>(), static_cast<int64_t*>(ctx->ws2),
+                            ctx->stream);
+  CB_CUDA(cudaMemcpyAsync(idx.p, bounds.data(), sizeof(int64_t) * bounds.size(),
+                          cudaMemcpyHostToDevice, ctx->stream));
+  cb::launch_gather(pre.as<int64_t>(), idx.as<int64_t>(), (int64_t)bounds.size(), got.as<int64_t>(),
+                    ctx->stream);
+  CB_LAUNCHED();
+  std::vector<int64_t> h(bounds.size());
+  CB_CUDA(cudaMemcpyAsync(h.data(), got.p, sizeof(int64_t) * h.size(), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  CB_CUDA(cudaStreamSynchronize(ctx->stream));
+  sums.resize((size_t)n);
+  double scale = opt.sizing == CB_SIZING_LEARNED ? 1.0 + (double)opt.margin : 1.0;
+  for (int64_t j = 0; j < n; ++j) sums[(size_t)j] = (int64_t)((double)(h[(size_t)j + 1] - h[(size_t)j]) * scale);
+}
+
+// One run of consecutive products that share a semiring (see cb_spgemm_batched).
+void batched_group(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, int n, int first,
+                   const cb_opts& opt, int& wave, int& kernels, int64_t& nnz_total,
+                   int64_t& flops_total) {
+  const int64_t vsz = (int64_t)value_size(sr), per = 4 + vsz;
+  int64_t rowsA = 0, nnzA = 0, rowsB = 0, nnzB = 0, kmax = 0;
+  std::vector<int64_t> arow(n + 1), brow(n + 1);
+  for (int i = 0; i < n; ++i) {
+    arow[i] = rowsA;
+    brow[i] = rowsB;
+    rowsA += A[i].nrows;
+    nnzA += A[i].nnz;
+    rowsB += B[i].nrows;
+    nnzB += B[i].nnz;
+    kmax = B[i].ncols > kmax ? B[i].ncols : kmax;
+  }
+  arow[n] = rowsA;
+  brow[n] = rowsB;
+  if (rowsA >= INT32_MAX || rowsB > INT32_MAX)
+    fail(ctx, CB_ERR_INDEX, "batch too large to stack (rows beyond int32); split it");
+  // stack the group once
+  DevBuf sArp(ctx), sAcol(ctx), sAval(ctx), sBrp(ctx), sBcol(ctx), sBval(ctx), parts(ctx);
+  sArp.alloc(8 * (size_t)(rowsA + 1));
+  sAcol.alloc(4 * (size_t)nnzA);
+  sAval.alloc((size_t)vsz * (size_t)nnzA);
+  sBrp.alloc(8 * (size_t)(rowsB + 1));
+  sBcol.alloc(4 * (size_t)nnzB);
+  sBval.alloc((size_t)vsz * (size_t)nnzB);
+  const size_t psz = cb::stack_part_size();
+  parts.alloc(2 * (size_t)n * psz);
+  std::vector<unsigned char> hp(2 * (size_t)n * psz);
+  int64_t ao = 0, bo = 0;
+  for (int i = 0; i < n; ++i) {
+    cb::fill_stack_part(&hp[(size_t)i * psz], A[i].row_ptr, A[i].col, A[i].val, A[i].nrows, arow[i], ao,
+                        (int32_t)brow[i]);
+    cb::fill_stack_part(&hp[(size_t)(n + i) * psz], B[i].row_ptr, B[i].col, B[i].val, B[i].nrows,
+                        brow[i], bo, 0);
+    ao += A[i].nnz;
+    bo += B[i].nnz;
+  }
+  CB_CUDA(cudaMemcpyAsync(parts.p, hp.data(), hp.size(), cudaMemcpyHostToDevice, ctx->stream));
+  cb::launch_stack(parts.p, n, (int)vsz, sArp.as<int64_t>(), sAcol.as<int32_t>(), sAval.p, ctx->stream,
+                   ctx->sms);
+  cb::launch_stack(static_cast<char*>(parts.p) + (size_t)n * psz, n, (int)vsz, sBrp.as<int64_t>(),
+                   sBcol.as<int32_t>(), sBval.p, ctx->stream, ctx->sms);
+  CB_LAUNCHED();
+  kernels += 2;
+  const DevCSR dB{rowsB, kmax, sBrp.as<int64_t>(), sBcol.as<int32_t>(), sBval.p};
+  const cb_csr sA{rowsA, rowsB, nnzA, sArp.as<int64_t>(), sAcol.as<int32_t>(), sAval.p};
+
+  // waves: consecutive products whose output fits the budget
+  std::vector<int> cut{0};
+  if (opt.budget_bytes > 0) {
+    std::vector<int64_t> sizes;
+    row_group_sums(ctx, &sA, dB, opt, arow, sizes);
+    int64_t rows = 0, nz = 0;
+    for (int i = 0; i < n; ++i) {
+      if (8 * (A[i].nrows + 1) + sizes[(size_t)i] * per > opt.budget_bytes) {
+        if (opt.sizing == CB_SIZING_EXACT || 8 * (A[i].nrows + 1) + per > opt.budget_bytes)
+          fail(ctx, CB_ERR_BUDGET, "one product's output does not fit the wave budget");
+        // a prediction above the budget: the product gets a wave of its own
+        // (its exact output is checked against the budget when it runs)
+        sizes[(size_t)i] = (opt.budget_bytes - 8 * (A[i].nrows + 1)) / per;
+      }
+      const int64_t r2 = rows + A[i].nrows, z2 = nz + sizes[(size_t)i];
+      if (i > cut.back() && 8 * (r2 + 1) + z2 * per > opt.budget_bytes) {
+        cut.push_back(i);
+        rows = A[i].nrows;
+        nz = sizes[(size_t)i];
+      } else {
+        rows = r2;
+        nz = z2;
+      }
+    }
+  }
+  cut.push_back(n);
+
+  cb_opts inner = opt;
+  inner.validate = 0;
+  inner.budget_bytes = 0;
+  DevBuf orp(ctx), ocol(ctx), oval(ctx);
+  int64_t cap = 0;
+  if (opt.budget_bytes > 0) {
+    int64_t max_rows = 0;
+    for (size_t w = 0; w + 1 < cut.size(); ++w)
+      max_rows = std::max(max_rows, arow[cut[w + 1]] - arow[cut[w]]);
+    cap = (opt.budget_bytes - 8 * (max_rows + 1)) / per;
+    orp.alloc(8 * (size_t)(max_rows + 1));
+    ocol.alloc(4 * (size_t)std::max<int64_t>(cap, 1));
+    oval.alloc((size_t)vsz * (size_t)std::max<int64_t>(cap, 1));
+    inner.out_capacity = std::max<int64_t>(cap, 1);
+  }
+  for (size_t w = 0; w + 1 < cut.size(); ++w) {
+    int w0 = cut[w];
+    const int w1 = cut[w + 1];
+    const cb_csr Aw{arow[w1] - arow[w0], rowsB, 0, sArp.as<int64_t>() + arow[w0], sAcol.as<int32_t>(),
+                    sAval.p};
+    cb_csr Cw{};
+    if (inner.out_capacity > 0) Cw = cb_csr{0, 0, 0, orp.as<int64_t>(), ocol.as<int32_t>(), oval.p};
+    ctx->stats.kernels = 0;
+    if (opt.sizing == CB_SIZING_EXACT || !(opt.flags & CB_FLAG_LEARNED_ROWS))
+      spgemm_plain(ctx, sr, &Aw, dB, kmax, &Cw, inner);
+    else spgemm_learned(ctx, sr, &Aw, dB, kmax, &Cw, inner);
+    kernels += ctx->stats.kernels;
+    nnz_total += Cw.nnz;
+    flops_total += ctx->stats.flops;
+    CB_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int stop = opt.on_batch(wave++, first + w0, first + w1, &Cw, opt.user);
+    if (inner.out_capacity == 0) {
+      for (void* q : {(void*)Cw.row_ptr, (void*)Cw.col, Cw.val})
+        if (q) CB_CUDA(cudaFreeAsync(q, ctx->stream));
+    }
+    if (stop) throw Fail{-1};
+  }
 }
 
 }  // namespace
@@ -824,6 +995,153 @@ int cb_exclusive_scan(cb_ctx* ctx, const int64_t* in, int64_t n, int64_t* out) {
     CB_LAUNCHED();
     return CB_OK;
   } catch (const Fail& f) {
+    return f.code;
+  }
+}
+
+int cb_spgemm_batched(cb_ctx* ctx, int count, const cb_semiring* sr, const cb_csr* A,
+                      const cb_csr* B, const cb_opts* opt_in) {
+  if (!ctx) return CB_ERR_ARG;
+  ctx->err.clear();
+  ctx->stats = cb_stats{};
+  cb_opts opt;
+  if (opt_in) opt = *opt_in;
+  else cb_opts_default(&opt);
+  int wave = 0, kernels = 0;
+  int64_t nnz = 0, flops = 0;
+  try {
+    if (count < 0 || (count > 0 && (!sr || !A || !B))) fail(ctx, CB_ERR_ARG, "bad batch arguments");
+    if (!opt.on_batch) fail(ctx, CB_ERR_ARG, "batched SpGEMM needs on_batch");
+    if (opt.sizing == CB_SIZING_LEARNED && !opt.mlp) fail(ctx, CB_ERR_ARG, "learned sizing needs opt->mlp");
+    if (opt.sizing != CB_SIZING_EXACT && opt.sizing != CB_SIZING_LEARNED)
+      fail(ctx, CB_ERR_ARG, "batched SpGEMM supports exact and learned sizing");
+    for (int i = 0; i < count; ++i) {
+      if (value_size(sr[i]) == 0) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
+      check_operand(ctx, &A[i], "A[i]");
+      check_operand(ctx, &B[i], "B[i]");
+      if (A[i].ncols != B[i].nrows) fail(ctx, CB_ERR_SHAPE, "A[i].ncols != B[i].nrows");
+    }
+    if (opt.validate)
+      for (int i = 0; i < count; ++i) run_validation(ctx, &A[i], &B[i]);
+    for (int g0 = 0; g0 < count;) {
+      int g1 = g0 + 1;
+      while (g1 < count && sr[g1] == sr[g0]) ++g1;
+      batched_group(ctx, (int)sr[g0], A + g0, B + g0, g1 - g0, g0, opt, wave, kernels, nnz, flops);
+      g0 = g1;
+    }
+  } catch (const Fail& f) {
+    if (f.code != -1) return f.code;  // -1: the consumer stopped early
+  }
+  ctx->stats.batches = wave;
+  ctx->stats.kernels = kernels;
+  ctx->stats.nnz = nnz;
+  ctx->stats.flops = flops;
+  return CB_OK;
+}
+
+int cb_ctx_set_tune(cb_ctx* ctx, cb_tune* t) {
+  if (!ctx || !t) return CB_ERR_ARG;
+  auto clamp = [](int v, int lo, int hi) { return v < lo ? lo : v > hi ? hi : v; };
+  cb::Tune u;
+  u.sym_hash_max = clamp(t->sym_hash_max, cb::kSymSmallMax, cb::kSymLargeMax);
+  u.num_hash_max = clamp(t->num_hash_max, u.sym_hash_max, 8192);
+  u.learn_max = clamp(t->learn_max, 0, 8192);
+  ctx->tune = u;
+  t->sym_hash_max = u.sym_hash_max;
+  t->num_hash_max = u.num_hash_max;
+  t->learn_max = u.learn_max;
+  return CB_OK;
+}
+
+int cb_ctx_get_tune(const cb_ctx* ctx, cb_tune* t) {
+  if (!ctx || !t) return CB_ERR_ARG;
+  t->sym_hash_max = ctx->tune.sym_hash_max;
+  t->num_hash_max = ctx->tune.num_hash_max;
+  t->learn_max = ctx->tune.learn_max;
+  return CB_OK;
+}
+
+int cb_autotune(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, const cb_opts* opt_in,
+                cb_tune* best, float* best_ms) {
+  if (!ctx || !best) return CB_ERR_ARG;
+  ctx->err.clear();
+  cb_opts opt;
+  if (opt_in) opt = *opt_in;
+  else cb_opts_default(&opt);
+  opt.budget_bytes = 0;
+  opt.validate = 0;
+  opt.flags = 0;
+  const cb::Tune saved = ctx->tune;
+  cb_csr C{};
+  try {
+    if (!A || !B) fail(ctx, CB_ERR_ARG, "null matrix argument");
+    if (value_size(sr) == 0) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
+    check_operand(ctx, A, "A");
+    check_operand(ctx, B, "B");
+    if (A->ncols != B->nrows) fail(ctx, CB_ERR_SHAPE, "A.ncols != B.nrows");
+    if (opt.sizing == CB_SIZING_LEARNED && !opt.mlp) fail(ctx, CB_ERR_ARG, "learned sizing needs opt->mlp");
+    run_validation(ctx, A, B);
+    // output buffers sized once by an exact run
+    spgemm_plain(ctx, (int)sr, A, dev(B), B->ncols, &C, opt);
+    CB_CUDA(cudaStreamSynchronize(ctx->stream));
+    opt.out_capacity = C.nnz > 0 ? C.nnz : 1;
+    if (C.nnz == 0) {
+      CB_CUDA(cudaMallocAsync((void**)&C.col, 4, ctx->stream));
+      CB_CUDA(cudaMallocAsync(&C.val, 8, ctx->stream));
+    }
+    const int big = cb::num_large_max((int)sr);
+    const int syms[] = {512, 1024, 2048, 4096};
+    const int nums[] = {512, 1024, 2048, 4096, 8192};
+    const int learns[] = {64, 512, 2048};
+    cudaEvent_t e0, e1;
+    CB_CUDA(cudaEventCreate(&e0));
+    CB_CUDA(cudaEventCreate(&e1));
+    float best_t = 1e30f;
+    cb::Tune best_u = saved;
+    auto trial = [&](const cb::Tune& u) {
+      ctx->tune = u;
+      cb_csr Cc{0, 0, 0, C.row_ptr, C.col, C.val};
+      if (opt.sizing == CB_SIZING_EXACT) spgemm_plain(ctx, (int)sr, A, dev(B), B->ncols, &Cc, opt);
+      else spgemm_learned(ctx, (int)sr, A, dev(B), B->ncols, &Cc, opt);  // warm-up
+      CB_CUDA(cudaEventRecord(e0, ctx->stream));
+      if (opt.sizing == CB_SIZING_EXACT) spgemm_plain(ctx, (int)sr, A, dev(B), B->ncols, &Cc, opt);
+      else spgemm_learned(ctx, (int)sr, A, dev(B), B->ncols, &Cc, opt);
+      CB_CUDA(cudaEventRecord(e1, ctx->stream));
+      CB_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CB_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      if (t < best_t) {
+        best_t = t;
+        best_u = u;
+      }
+    };
+    for (int sh : syms)
+      for (int nh : nums) {
+        if (nh < sh || nh > big) continue;
+        cb::Tune u = saved;
+        u.sym_hash_max = sh;
+        u.num_hash_max = nh;
+        if (opt.sizing == CB_SIZING_EXACT) {
+          trial(u);
+        } else {
+          for (int lm : learns) {
+            u.learn_max = lm;
+            trial(u);
+          }
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tune = best_u;
+    best->sym_hash_max = best_u.sym_hash_max;
+    best->num_hash_max = best_u.num_hash_max;
+    best->learn_max = best_u.learn_max;
+    if (best_ms) *best_ms = best_t;
+    cb_csr_free_async(ctx, &C);
+    return CB_OK;
+  } catch (const Fail& f) {
+    ctx->tune = saved;
+    cb_csr_free_async(ctx, &C);
     return f.code;
   }
 }

@@ -96,7 +96,8 @@ constexpr int kEmptyKey = -1;
 
 constexpr int kSymWarpMax = 128;     // warp team, table <= 256 slots
 constexpr int kSymSmallMax = 512;    // 256-thread team, table <= 1024
-constexpr int kSymHashMax = 512;     // above: dense bitmap spans
+constexpr int kSymHashMax = 512;     // default bound of the hash tiers (runtime-tunable)
+constexpr int kSymLargeMax = 4096;   // largest bound the 1024-thread hash tier supports
 constexpr int kSpanCols = 1 << 18;   // columns per bitmap span
 constexpr int kSpanWords = kSpanCols / 32;
 constexpr int kMaxWindowsPerSpan = 64;
@@ -104,7 +105,9 @@ constexpr int kMaxWindowsPerSpan = 64;
 constexpr int kNumWarpMax = 64;      // warp team, table <= 128
 constexpr int kNumSmallMax = 512;    // 256-thread team, table <= 1024
 template <int SR> struct NumLimits {
-  static constexpr int kHashMax = kNumSmallMax;
+  static constexpr int kHashMax = kNumSmallMax;  // default bound of the hash tiers
+  // largest bound the 1024-thread hash tier supports (table of 2x slots)
+  static constexpr int kLargeMax = sizeof(typename Sem<SR>::A) == 8 ? 4096 : 8192;
   // accumulators per rank window
   static constexpr int kWcap = sizeof(typename Sem<SR>::A) == 8 ? 16384 : 32768;
   // window cut: a window starts where the running count crosses a multiple
@@ -113,7 +116,7 @@ template <int SR> struct NumLimits {
   // learned sizing: rows predicted to hold at most this many entries skip the
   // symbolic phase and are computed in one pass in a hash table of
   // 2^ceil(log2(2 cap)) slots (1024-thread team at most)
-  static constexpr int kLearnHashMax = sizeof(typename Sem<SR>::A) == 8 ? 4096 : 8192;
+  static constexpr int kLearnHashMax = kLargeMax;
 };
 
 // One rank window of a heavy row: row index h into the heavy-row list, the
@@ -126,16 +129,11 @@ struct Window {
 enum SymTier { kSymEmpty = 0, kSymWarp = 1, kSymSmall = 2, kSymLarge = 3, kSymHeavy = 4, kSymTiers = 5 };
 enum NumTier { kNumEmpty = 0, kNumWarp = 1, kNumSmall = 2, kNumLarge = 3, kNumHeavy = 4, kNumTiers = 5 };
 
-__device__ __forceinline__ int sym_tier(int64_t u) {
+__device__ __forceinline__ int sym_tier(int64_t u, int64_t hash_max) {
   return u == 0 ? kSymEmpty : u <= kSymWarpMax ? kSymWarp : u <= kSymSmallMax ? kSymSmall
-         : u <= kSymHashMax ? kSymLarge : kSymHeavy;
+         : u <= hash_max ? kSymLarge : kSymHeavy;
 }
 
-template <int SR>
-__device__ __forceinline__ int num_tier(int64_t nz) {
-  return nz == 0 ? kNumEmpty : nz <= kNumWarpMax ? kNumWarp : nz <= kNumSmallMax ? kNumSmall
-         : nz <= NumLimits<SR>::kHashMax ? kNumLarge : kNumHeavy;
-}
 
 // Smallest power of two >= x (x >= 1), as log2.
 __host__ __device__ __forceinline__ int ceil_log2(int64_t x) {
@@ -356,21 +354,27 @@ __device__ __forceinline__ int64_t seq_lower_bound(const int32_t* col, int64_t q
   return q0;
 }
 
-// Shared memory used by for_row_products_balanced: per chunk entry its
-// product offset and its first B index, plus scan scratch.
+// Shared memory used by for_row_products_balanced: per chunk entry with a
+// nonempty product range, its product offset, its first B index and its A
+// index (relative to the chunk), plus scan scratch.
 struct BalancedSmem {
   long long* off;  // [blockDim.x]
   long long* b0;   // [blockDim.x]
+  int* pa;         // [blockDim.x]
   long long* scan; // [33]
+  int* iscan;      // [33]
 };
 
 // Load-balanced form of for_row_products for a whole CTA: the row's stored
-// A entries are taken in chunks of blockDim.x; the chunk's product ranges
-// (B row, or the B row's slice in [lo, hi) when `sorted` and not `whole`)
-// are prefix-summed, every warp takes an equal contiguous share of the
-// chunk's products, and its lanes take consecutive products (coalesced B
-// reads).  A product's entry is found by a search over the chunk offsets
-// when a lane crosses into a new B row.  All threads of the CTA must call it.
+// A entries are taken in chunks of blockDim.x; the chunk's nonempty product
+// ranges (B row, or the B row's slice in [lo, hi) when `sorted` and not
+// `whole`) are compacted and prefix-summed, every warp takes an equal
+// contiguous share of the chunk's products and its lanes take consecutive
+// products (coalesced B reads).  Since ranges are nonempty, the 32 products
+// of one warp step start at most 31 new ranges: each lane reads one range
+// start, the warp ORs together the bits of the starts that fall inside the
+// step, and a lane's range is the step's first range plus the number of
+// starts at or before its product.  All threads of the CTA must call it.
 template <class F>
 __device__ __forceinline__ void for_row_products_balanced(const DevCSR& A, const DevCSR& B,
                                                           int64_t i, int64_t lo, int64_t hi,
@@ -384,36 +388,53 @@ __device__ __forceinline__ void for_row_products_balanced(const DevCSR& A, const
   for (int64_t c0 = a0; c0 < a1; c0 += nthr) {
     const int nch = (int)min((int64_t)nthr, a1 - c0);
     long long len = 0;
+    int64_t q0 = 0;
     if (tid < nch) {
       const int k = A.col[c0 + tid];
-      int64_t q0 = B.rp[k], q1 = row_end(B, k);
+      q0 = B.rp[k];
+      int64_t q1 = row_end(B, k);
       if (!whole && sorted) {
         const int64_t s0 = seq_lower_bound(B.col, q0, q1, lo);
         q1 = seq_lower_bound(B.col, s0, q1, hi);
         q0 = s0;
       }
       len = q1 - q0;
-      sm.b0[tid] = q0;
     }
     long long total;
     const long long off = cta_exclusive_scan64(len, sm.scan, total);
-    if (tid < nch) sm.off[tid] = off;
+    int ne;
+    const int slot = team_exclusive_scan<1024>(len > 0 ? 1 : 0, sm.iscan, ne);
+    if (len > 0) {
+      sm.off[slot] = off;
+      sm.b0[slot] = q0;
+      sm.pa[slot] = tid;
+    }
     __syncthreads();
-    const long long t_end = total * (warp + 1) / nwarp;
-    int j = -1;
-    for (long long t = total * warp / nwarp + lane; t < t_end; t += 32) {
-      if (j < 0 || (j + 1 < nch && sm.off[j + 1] <= t)) {
-        int l = j < 0 ? 0 : j + 1, r = nch - 1;  // last entry with off <= t
-        while (l < r) {
-          const int mid = (l + r + 1) >> 1;
-          if (sm.off[mid] <= t) l = mid;
-          else r = mid - 1;
-        }
-        j = l;
+    const long long t_beg = total * warp / nwarp, t_end = total * (warp + 1) / nwarp;
+    if (t_beg < t_end) {
+      // range holding the warp's first product (the same search in every lane)
+      int l = 0, r = ne - 1;
+      while (l < r) {
+        const int mid = (l + r + 1) >> 1;
+        if (sm.off[mid] <= t_beg) l = mid;
+        else r = mid - 1;
       }
-      const int64_t q = sm.b0[j] + (t - sm.off[j]);
-      const int c = B.col[q];
-      if (!filter || (unsigned)((int64_t)c - lo) < width) f(c0 + j, q, c);
+      int j0 = l;
+      for (long long tb = t_beg; tb < t_end; tb += 32) {
+        const int k = j0 + 1 + lane;
+        const long long st = k < ne ? sm.off[k] : LLONG_MAX;
+        const long long pos = st - tb;  // >= 1 by the choice of j0
+        const unsigned bits = __reduce_or_sync(0xffffffffu, pos < 32 ? 1u << (int)pos : 0u);
+        const int j = j0 + __popc(bits & ((2u << lane) - 1u));
+        const long long t = tb + lane;
+        if (t < t_end) {
+          const int64_t q = sm.b0[j] + (t - sm.off[j]);
+          const int c = B.col[q];
+          if (!filter || (unsigned)((int64_t)c - lo) < width) f(c0 + sm.pa[j], q, c);
+        }
+        j0 += __popc(bits);  // range holding product tb + 32 (ranges are nonempty)
+        if (j0 + 1 < ne && sm.off[j0 + 1] <= tb + 32) ++j0;
+      }
     }
     __syncthreads();
   }

@@ -9,6 +9,17 @@ struct cb_mlp;
 
 namespace cb {
 
+// Tier bounds chosen at run time (autotuned): rows with u = min(flops, ncols)
+// <= sym_hash_max are counted in hash tables (else bitmaps); rows with
+// nnz <= num_hash_max are computed in hash tables (else rank windows;
+// num_hash_max >= sym_hash_max); with learned sizing, rows whose capacity is
+// <= learn_max skip the symbolic phase.
+struct Tune {
+  int sym_hash_max = 512;
+  int num_hash_max = 512;
+  int learn_max = 512;
+};
+
 struct Window;
 
 // A CSR operand as the kernels see it.  For B it may be a column window:
@@ -49,16 +60,21 @@ void launch_validate(const DevCSR& M, int64_t nnz, int code_base, int64_t* count
 // K1: flops_i, maxB_i and the symbolic tier histogram; total flops.
 void launch_classify_sym(const DevCSR& A, const DevCSR& B, int64_t* flops, int32_t* maxb,
                          int64_t* counters, cudaStream_t s, int sms,
-                         const uint8_t* skip = nullptr);
+                         const uint8_t* skip = nullptr, int64_t sym_hash_max = 512);
 // K2: rows into per-tier segments of perm; heavy rows also get nnz[i] = 0.
 void launch_scatter_sym(int64_t m, int64_t ncols, const int64_t* flops, int32_t* perm,
                         int64_t* nnz, int64_t* counters, cudaStream_t s, int sms,
-                        const uint8_t* skip = nullptr, const int64_t* preset = nullptr);
+                        const uint8_t* skip = nullptr, const int64_t* preset = nullptr,
+                        int64_t sym_hash_max = 512);
 
 // K4: out[0] = 0, out[i+1] = out[i] + in[i]; partial needs scan_partials(n) int64.
 int64_t scan_partials(int64_t n);
 void launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* partial,
                            cudaStream_t s);
+
+// out[j] = prefix[idx[j]] for j < n.
+void launch_gather(const int64_t* prefix, const int64_t* idx, int64_t n, int64_t* out,
+                   cudaStream_t s);
 
 // Column-batch slab offsets: pos[j * B.nrows + k] = first entry of B row k
 // with column >= bnd[j] (device int64 bnd[nb1]); B's rows must be sorted.
@@ -68,7 +84,7 @@ void launch_slabs(const DevCSR& B, const int64_t* bnd, int nb1, int64_t* pos, cu
 // Numeric binning by exact row size.
 void launch_classify_num(int sr, int64_t m, const int64_t* nnz, int32_t* perm,
                          int64_t* counters, cudaStream_t s, int sms,
-                         const uint8_t* skip = nullptr);
+                         const uint8_t* skip = nullptr, int64_t num_hash_max = 512);
 
 // Learned sizing (rows whose capacity fits a hash table skip the symbolic
 // phase): capacities + routing, their tiers, the one-pass numeric into
@@ -106,13 +122,21 @@ void launch_check_sorted(const DevCSR& B, int64_t* counters, cudaStream_t s, int
 // K5-K7: numeric phase over the numeric tier segments + rank windows,
 // writing sorted rows of C at Crp.
 int num_window_cut(int sr);
-int num_hash_max(int sr);
+int num_large_max(int sr);
 void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* perm,
                     const int64_t* seg_begin, const int64_t* seg_count, const int64_t* flops,
                     const int64_t* nnz, const int32_t* heavy_rows, const Window* wins,
                     int64_t n_wins, const int32_t* span_counts, int64_t spans,
                     const unsigned* hbits, int b_sorted, const int64_t* Crp, int32_t* Ccol,
-                    void* Cval, int64_t* err, cudaStream_t s, int sms, int* launches);
+                    void* Cval, int64_t* err, cudaStream_t s, int sms, int* launches,
+                    int64_t num_hash_max = 512);
+
+// Batched products (cb_batched.cu): stack parts into one CSR.
+size_t stack_part_size();
+void fill_stack_part(void* dst, const int64_t* rp, const int32_t* col, const void* val, int64_t nrows,
+                     int64_t row_off, int64_t nnz_off, int32_t col_add);
+void launch_stack(const void* parts_dev, int nparts, int vsz, int64_t* rp_out, int32_t* col_out,
+                  void* val_out, cudaStream_t s, int sms);
 
 // Learned sizer (k_mlp.cu).
 const void* mlp_bf16(const cb_mlp* m);

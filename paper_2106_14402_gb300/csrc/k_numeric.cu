@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
                                                       const unsigned* hbits, int b_sorted,
                                                       const int64_t* flops, const int64_t* nnz,
                                                       const int64_t* Crp, int32_t* Ccol,
-                                                      typename Sem<SR>::T* Cval, int64_t* err) {
+                                                      typename Sem<SR>::T* Cval, int64_t* err,
+                                                      int64_t num_hash_max) {
   typedef Sem<SR> S;
   typedef typename S::A Acc;
   typedef typename S::T T;
@@ -182,7 +183,8 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
   long long* bal = reinterpret_cast<long long*>(bp + kSpanWords);
   __shared__ int scratch[33];
   __shared__ long long scan64[33];
-  const BalancedSmem sm{bal, bal + 1024, scan64};
+  __shared__ int iscan[33];
+  const BalancedSmem sm{bal, bal + 1024, reinterpret_cast<int*>(bal + 2048), scan64, iscan};
   __shared__ long long s_base;
   const int tid = threadIdx.x, lane = tid & 31;
   const T* Aval = reinterpret_cast<const T*>(A.val);
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
   for (int64_t u = blockIdx.x; u < n_wins; u += gridDim.x) {
     const Window wd = wins[u];
     const int i = heavy_rows[wd.h];
-    if (nnz[i] <= kNumSmallMax || wd.count <= 0) continue;  // hash tiers own small rows
+    if (nnz[i] <= num_hash_max || wd.count <= 0) continue;  // hash tiers own these rows
     const int cnt = wd.count < WCAP ? wd.count : WCAP;
     const int64_t span_lo = B.col_lo + (int64_t)wd.span * kSpanCols;
     const int64_t lo = span_lo + 32 * (int64_t)wd.w_lo;
@@ -289,7 +291,7 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
                 const int32_t* heavy_rows, const Window* wins, int64_t n_wins,
                 const int32_t* span_counts, int64_t spans, const unsigned* hbits, int b_sorted,
                 const int64_t* Crp, int32_t* Ccol, void* Cval_, int64_t* err, cudaStream_t s,
-                int sms, int* launches) {
+                int sms, int* launches, int64_t num_hash_max) {
   typedef typename Sem<SR>::A Acc;
   typedef typename Sem<SR>::T T;
   T* Cval = reinterpret_cast<T*>(Cval_);
@@ -309,7 +311,7 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
     ++*launches;
   }
   if (seg_count[kNumLarge]) {
-    constexpr int CTA = 1024, TEAM = 1024, TBL = 2 * NumLimits<SR>::kHashMax;
+    constexpr int CTA = 1024, TEAM = 1024, TBL = 2 * NumLimits<SR>::kLargeMax;
     const size_t smem = TBL * slot;
     set_smem(k_num_hash<SR, CTA, TEAM, TBL>, smem);
     k_num_hash<SR, CTA, TEAM, TBL><<<capped(seg_count[kNumLarge], sms), CTA, smem, s>>>(
@@ -318,11 +320,12 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
   }
   if (n_wins) {
     constexpr size_t smem = NumLimits<SR>::kWcap * sizeof(Acc) + 2 * kSpanWords * sizeof(unsigned) +
-                            2 * 1024 * sizeof(long long);
+                            2 * 1024 * sizeof(long long) + 1024 * sizeof(int);
     set_smem(k_num_rank<SR>, smem);
     k_num_rank<SR><<<capped(n_wins, sms), 1024, smem, s>>>(A, B, heavy_rows, wins, n_wins,
                                                            span_counts, spans, hbits, b_sorted,
-                                                           flops, nnz, Crp, Ccol, Cval, err);
+                                                           flops, nnz, Crp, Ccol, Cval, err,
+                                                           num_hash_max);
     ++*launches;
   }
 }
@@ -402,13 +405,13 @@ int num_window_cut(int sr) {
   }
 }
 
-int num_hash_max(int sr) {
+int num_large_max(int sr) {
   switch (sr) {
-    case 1: return NumLimits<1>::kHashMax;
-    case 2: return NumLimits<2>::kHashMax;
-    case 3: return NumLimits<3>::kHashMax;
-    case 4: return NumLimits<4>::kHashMax;
-    default: return NumLimits<5>::kHashMax;
+    case 1: return NumLimits<1>::kLargeMax;
+    case 2: return NumLimits<2>::kLargeMax;
+    case 3: return NumLimits<3>::kLargeMax;
+    case 4: return NumLimits<4>::kLargeMax;
+    default: return NumLimits<5>::kLargeMax;
   }
 }
 
@@ -417,10 +420,12 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
                     const int64_t* nnz, const int32_t* heavy_rows, const Window* wins,
                     int64_t n_wins, const int32_t* span_counts, int64_t spans,
                     const unsigned* hbits, int b_sorted, const int64_t* Crp, int32_t* Ccol,
-                    void* Cval, int64_t* err, cudaStream_t s, int sms, int* launches) {
+                    void* Cval, int64_t* err, cudaStream_t s, int sms, int* launches,
+                    int64_t num_hash_max) {
 #define CB_NUM(SRV)                                                                        \
   numeric_sr<SRV>(A, B, perm, seg_begin, seg_count, flops, nnz, heavy_rows, wins, n_wins,   \
-                  span_counts, spans, hbits, b_sorted, Crp, Ccol, Cval, err, s, sms, launches)
+                  span_counts, spans, hbits, b_sorted, Crp, Ccol, Cval, err, s, sms, launches, \
+                  num_hash_max)
   switch (sr) {
     case 1: CB_NUM(1); break;
     case 2: CB_NUM(2); break;

@@ -30,7 +30,7 @@ __global__ void k_validate(DevCSR M, int64_t nnz, int code_base, int64_t* counte
 // stored entries (the flops count of Table 1), maxb_i = the longest of them.
 __global__ void __launch_bounds__(256) k_classify_sym(DevCSR A, DevCSR B, int64_t* flops,
                                                       int32_t* maxb, int64_t* counters,
-                                                      const uint8_t* skip) {
+                                                      const uint8_t* skip, int64_t sym_hash_max) {
   __shared__ unsigned long long hist[kSymTiers];
   __shared__ unsigned long long total;
   if (threadIdx.x < kSymTiers) hist[threadIdx.x] = 0;
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) k_classify_sym(DevCSR A, DevCSR B, int64_
     if (lane == 0) {
       flops[i] = f;
       if (maxb) maxb[i] = mx;
-      atomicAdd(&hist[skip && skip[i] ? 0 : sym_tier(min((int64_t)f, B.ncols))], 1ull);
+      atomicAdd(&hist[skip && skip[i] ? 0 : sym_tier(min((int64_t)f, B.ncols), sym_hash_max)], 1ull);
       atomicAdd(&total, (unsigned long long)f);
     }
   }
@@ -223,6 +223,13 @@ __global__ void __launch_bounds__(256) k_slabs(DevCSR B, const int64_t* bnd, int
   }
 }
 
+// out[j] = prefix[idx[j]] for j < n (gather of a few prefix values).
+__global__ void k_gather(const int64_t* prefix, const int64_t* idx, int64_t n, int64_t* out) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = prefix[idx[j]];
+}
+
 inline int grid_for(int64_t work, int per_block, int cap) {
   int64_t g = (work + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -237,14 +244,16 @@ void launch_validate(const DevCSR& M, int64_t nnz, int code_base, int64_t* count
 }
 
 void launch_classify_sym(const DevCSR& A, const DevCSR& B, int64_t* flops, int32_t* maxb,
-                         int64_t* counters, cudaStream_t s, int sms, const uint8_t* skip) {
-  k_classify_sym<<<grid_for(A.nrows, 8, sms * 8), 256, 0, s>>>(A, B, flops, maxb, counters, skip);
+                         int64_t* counters, cudaStream_t s, int sms, const uint8_t* skip,
+                         int64_t sym_hash_max) {
+  k_classify_sym<<<grid_for(A.nrows, 8, sms * 8), 256, 0, s>>>(A, B, flops, maxb, counters, skip,
+                                                                sym_hash_max);
 }
 
 void launch_scatter_sym(int64_t m, int64_t ncols, const int64_t* flops, int32_t* perm,
                         int64_t* nnz, int64_t* counters, cudaStream_t s, int,
-                        const uint8_t* skip, const int64_t* preset) {
-  TierBySize t{flops, ncols, kSymWarpMax, kSymSmallMax, kSymHashMax, skip};
+                        const uint8_t* skip, const int64_t* preset, int64_t sym_hash_max) {
+  TierBySize t{flops, ncols, kSymWarpMax, kSymSmallMax, sym_hash_max, skip};
   k_tier_scatter<<<grid_for(m, 256, 1 << 30), 256, 0, s>>>(m, t, perm, counters + kCntSym,
                                                             counters + kCurSym, nnz, preset);
 }
@@ -263,15 +272,20 @@ void launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* 
   k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial, out);
 }
 
+void launch_gather(const int64_t* prefix, const int64_t* idx, int64_t n, int64_t* out,
+                   cudaStream_t s) {
+  if (n > 0) k_gather<<<grid_for(n, 256, 1024), 256, 0, s>>>(prefix, idx, n, out);
+}
+
 void launch_slabs(const DevCSR& B, const int64_t* bnd, int nb1, int64_t* pos, cudaStream_t s,
                   int sms) {
   if (B.nrows == 0 || nb1 == 0) return;
   k_slabs<<<grid_for(B.nrows, 8, sms * 8), 256, 0, s>>>(B, bnd, nb1, pos);
 }
 
-void launch_classify_num(int sr, int64_t m, const int64_t* nnz, int32_t* perm, int64_t* counters,
-                         cudaStream_t s, int sms, const uint8_t* skip) {
-  TierBySize t{nnz, INT64_MAX, kNumWarpMax, kNumSmallMax, (int64_t)num_hash_max(sr), skip};
+void launch_classify_num(int, int64_t m, const int64_t* nnz, int32_t* perm, int64_t* counters,
+                         cudaStream_t s, int sms, const uint8_t* skip, int64_t num_hash_max) {
+  TierBySize t{nnz, INT64_MAX, kNumWarpMax, kNumSmallMax, num_hash_max, skip};
   k_tier_count<<<grid_for(m, 256, sms * 8), 256, 0, s>>>(m, t, counters + kCntNum);
   k_tier_scatter<<<grid_for(m, 256, 1 << 30), 256, 0, s>>>(m, t, perm, counters + kCntNum,
                                                             counters + kCurNum, nullptr, nullptr);

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
   extern __shared__ __align__(16) unsigned sym_bm[];
   __shared__ int scratch[33];
   __shared__ long long scan64[33];
+  __shared__ int iscan[33];
   __shared__ int wstart[kMaxWindowsPerSpan];
   __shared__ int wrank[kMaxWindowsPerSpan];
   __shared__ long long wbase;
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
   const int64_t units = n_heavy * spans;
   const int bm_words = (int)min((int64_t)kSpanWords, (B.ncols + 31) / 32);
   long long* bal = reinterpret_cast<long long*>(sym_bm + ((bm_words + 3) & ~3));
-  const BalancedSmem sm{bal, bal + 1024, scan64};
+  const BalancedSmem sm{bal, bal + 1024, reinterpret_cast<int*>(bal + 2048), scan64, iscan};
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int64_t h = u / spans, sp = u - h * spans;
     const int i = heavy_rows[h];
@@ -232,7 +233,7 @@ void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,
     ++*launches;
   }
   if (seg_count[kSymLarge]) {
-    constexpr int CTA = 1024, TEAM = 1024, TBL = 2 * kSymHashMax;
+    constexpr int CTA = 1024, TEAM = 1024, TBL = 2 * kSymLargeMax;
     const size_t smem = TBL * sizeof(int);
     set_smem(k_sym_hash<CTA, TEAM, TBL>, smem);
     k_sym_hash<CTA, TEAM, TBL><<<capped(seg_count[kSymLarge], sms * 2), CTA, smem, s>>>(
@@ -243,7 +244,8 @@ void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,
     const int64_t spans = (B.ncols + kSpanCols - 1) / kSpanCols;
     const int64_t width = B.ncols < kSpanCols ? B.ncols : kSpanCols;
     const size_t bm_words = (size_t)((width + 31) / 32);
-    const size_t smem = ((bm_words + 3) & ~(size_t)3) * sizeof(unsigned) + 2 * 1024 * sizeof(long long);
+    const size_t smem = ((bm_words + 3) & ~(size_t)3) * sizeof(unsigned) + 2 * 1024 * sizeof(long long) +
+                        1024 * sizeof(int);
     set_smem(k_sym_bitmap, smem);
     k_sym_bitmap<<<capped(seg_count[kSymHeavy] * spans, (int64_t)sms * 2), 1024, smem, s>>>(
         A, B, perm + seg_begin[kSymHeavy], seg_count[kSymHeavy], spans, flops, wcut, nnz,

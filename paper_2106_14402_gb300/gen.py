@@ -300,3 +300,91 @@ def random_csr(nrows: int, ncols: int, density: float, seed: int, semiring: str 
     if semiring is not None:
         out = out.with_values(random_values(semiring, out.nnz, subseed(seed, 7), lo, hi))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Counter-based generator (same definition as csrc_gen/cbgen.cu, which
+# generates the large batched workload on the device):
+#   draw(s, c) = mix(s + 0x9E3779B97F4A7C15 * (c + 1)), mix = splitmix64 output
+#   ER row r: candidates (draw(s, (r << 32) | t) >> 32) * ncols >> 32, first
+#   `deg` distinct in draw order, sorted.
+# ---------------------------------------------------------------------------
+
+_GOLD = 0x9E3779B97F4A7C15
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def counter_draw(seed: int, counters: np.ndarray) -> np.ndarray:
+    c = np.asarray(counters, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _mix64(np.uint64(seed & _M64) + np.uint64(_GOLD) * (c + np.uint64(1)))
+
+
+def er_counter(seed: int, nrows: int, ncols: int, deg: int) -> CSR:
+    """Exact-degree ER pattern from the counter-based draw (matches cbgen_er)."""
+    cols = np.zeros((nrows, deg), dtype=np.int64)
+    for r in range(nrows):
+        got: list[int] = []
+        seen: set[int] = set()
+        t = 0
+        while len(got) < deg:
+            ts = np.arange(t, t + 2 * deg, dtype=np.uint64)
+            x = counter_draw(seed, (np.uint64(r) << np.uint64(32)) | ts)
+            cand = ((x >> np.uint64(32)) * np.uint64(ncols)) >> np.uint64(32)
+            for c in cand.tolist():
+                if c not in seen:
+                    seen.add(c)
+                    got.append(c)
+                    if len(got) == deg:
+                        break
+            t += 2 * deg
+        cols[r] = np.sort(np.array(got, dtype=np.int64))
+    return CSR(nrows, ncols, np.arange(nrows + 1, dtype=np.int64) * deg,
+               cols.reshape(-1).astype(np.int32))
+
+
+def counter_values_u32(seed: int, n: int, lo: int, hi: int) -> np.ndarray:
+    x = counter_draw(seed, np.arange(n, dtype=np.uint64))
+    return (np.uint64(lo) + (((x >> np.uint64(32)) * np.uint64(hi - lo + 1)) >> np.uint64(32))).astype(np.uint32)
+
+
+def counter_values_f64(seed: int, n: int, lo: float, hi: float) -> np.ndarray:
+    x = counter_draw(seed, np.arange(n, dtype=np.uint64))
+    return lo + (hi - lo) * ((x >> np.uint64(11)).astype(np.float64) * 2.0 ** -53)
+
+
+def batched_plan(count: int = 4096, cfg: int = 4):
+    """Shapes of the batched workload: product i has n_i = floor(exp U(ln 256,
+    ln 65536)), ER degree d_i uniform in 4..64, semiring (min,+) u32 in [1,1000]
+    for the first half and (+,x) fp64 U(-1,1) for the second; A_i and B_i
+    are n_i x n_i with independent seeds."""
+    out = []
+    for i in range(count):
+        rng = rng_for(cfg, 200, i)
+        n = int(math.exp(rng.uniform(math.log(256), math.log(65536))))
+        d = int(rng.integers(4, 65))
+        sr = "min_plus_u32" if i < count // 2 else "plus_times_f64"
+        out.append({"i": i, "n": n, "deg": d, "semiring": sr,
+                    "seed_a": subseed(cfg, 201, i), "seed_b": subseed(cfg, 202, i),
+                    "seed_va": subseed(cfg, 203, i), "seed_vb": subseed(cfg, 204, i)})
+    return out
+
+
+def batched_product_host(p: dict):
+    """One product of the batched workload on the host (for the oracle)."""
+    A = er_counter(p["seed_a"], p["n"], p["n"], p["deg"])
+    B = er_counter(p["seed_b"], p["n"], p["n"], p["deg"])
+    if p["semiring"] == "min_plus_u32":
+        A = A.with_values(counter_values_u32(p["seed_va"], A.nnz, 1, 1000))
+        B = B.with_values(counter_values_u32(p["seed_vb"], B.nnz, 1, 1000))
+    else:
+        A = A.with_values(counter_values_f64(p["seed_va"], A.nnz, -1.0, 1.0))
+        B = B.with_values(counter_values_f64(p["seed_vb"], B.nnz, -1.0, 1.0))
+    return A, B

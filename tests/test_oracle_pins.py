@@ -419,3 +419,18 @@ def test_planted_mistakes_are_caught():
     BT = gen.CSR(B.nrows, B.ncols, BT.row_ptr, BT.col, BT.val)
     with pytest.raises(AssertionError):
         assert_same(sr, to_dict(*oracle.spgemm(sr, A, BT)), want)
+
+
+def test_counter_generator_rows_are_exact_degree_and_sorted():
+    A = gen.er_counter(12345, 300, 257, 40)
+    assert np.all(np.diff(A.row_ptr) == 40)
+    for r in range(A.nrows):
+        c = A.col[A.row_ptr[r]:A.row_ptr[r + 1]]
+        assert np.all(np.diff(c.astype(np.int64)) > 0) and c.min() >= 0 and c.max() < 257
+    v = gen.counter_values_u32(7, 1000, 1, 1000)
+    assert v.min() >= 1 and v.max() <= 1000
+    f = gen.counter_values_f64(8, 1000, -1.0, 1.0)
+    assert f.min() >= -1.0 and f.max() < 1.0
+    # the draw is the published splitmix64 output function of seed + golden * (c + 1)
+    x = int(gen.counter_draw(0, np.array([0], np.uint64))[0])
+    assert x == gen.splitmix64(0)
