@@ -271,8 +271,8 @@ int cb_exclusive_scan_noalloc(const int64_t *in, int64_t n, int64_t *out, void *
  *                 shared-memory hash table, the rest with dense bitmaps
  *                 (512..4096, default 512);
  *   num_hash_max  rows with nnz(C_i) <= this are computed in a hash table +
- *                 in-row sort, the rest in rank windows (sym_hash_max..4096 for
- *                 8-byte values, ..8192 for smaller ones, default 512);
+ *                 in-row sort, the rest in rank windows (sym_hash_max..4096,
+ *                 default 512);
  *   learn_max     with learned or upper-bound sizing, rows whose capacity is
  *                 <= this skip the symbolic phase (0..8192, default 512).
  * cb_ctx_set_tune clamps the values into range (and writes back what it set).

@@ -180,9 +180,10 @@ void collect_times(cb_ctx* ctx, const cb_opts& opt, bool numeric_ran) {
 // C->ncols = out_ncols.  Inputs are assumed valid (validation happens first).
 // skip (optional): rows already computed elsewhere; their sizes are preset[i]
 // and the exact phases leave them out.
+// a_rcols (optional): per-row output width of A's rows (stacked batches).
 void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_t out_ncols,
                   cb_csr* C, const cb_opts& opt, const uint8_t* skip = nullptr,
-                  const int64_t* preset = nullptr) {
+                  const int64_t* preset = nullptr, const int32_t* a_rcols = nullptr) {
   const int64_t m = A->nrows, ncols = dB.ncols;
   const bool caller_buf = opt.out_capacity > 0;
   const size_t vsz = value_size(sr);
@@ -214,14 +215,15 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
     return;
   }
 
-  const DevCSR dA = dev(A);
+  DevCSR dA = dev(A);
+  dA.rcols = a_rcols;
   CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
   mark(ctx, opt, 0);
   cb::launch_check_sorted(dB, counters, ctx->stream, ctx->sms);
   cb::launch_classify_sym(dA, dB, flops, maxb, counters, ctx->stream, ctx->sms, skip,
                           ctx->tune.sym_hash_max);
   cb::launch_scatter_sym(m, ncols, flops, perm_sym, nnz, counters, ctx->stream, ctx->sms, skip,
-                         preset, ctx->tune.sym_hash_max);
+                         preset, ctx->tune.sym_hash_max, a_rcols);
   CB_LAUNCHED();
   mark(ctx, opt, 1);
   ctx->stats.kernels += 3;
@@ -339,14 +341,15 @@ int64_t total_of(cb_ctx* ctx, const int64_t* in, int64_t n);
 // device and, with the rows too large for the table, goes through the exact
 // two-phase path; the one-pass rows are then copied from staging into C.
 void spgemm_learned(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_t out_ncols,
-                    cb_csr* C, const cb_opts& opt) {
+                    cb_csr* C, const cb_opts& opt, const int32_t* a_rcols = nullptr) {
   const int64_t m = A->nrows, ncols = dB.ncols;
   const int vsz = (int)value_size(sr);
   if (m == 0) {
     spgemm_plain(ctx, sr, A, dB, out_ncols, C, opt);
     return;
   }
-  const DevCSR dA = dev(A);
+  DevCSR dA = dev(A);
+  dA.rcols = a_rcols;
   DevBuf work(ctx);
   const size_t nm = (size_t)m + 1;
   const size_t bytes = align_up(8 * nm) * 5 + align_up(4 * nm) * 2 + align_up(12 * nm) + align_up(nm) +
@@ -375,7 +378,7 @@ void spgemm_learned(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int6
   }
   const int64_t hmax = std::min<int64_t>(ctx->tune.learn_max, cb::learn_hash_max(sr));
   cb::launch_learn_caps(m, use_mlp ? pred : nullptr, flops, ncols, use_mlp ? opt.margin : 0.0f, hmax,
-                        cap, learned, ctx->stream, ctx->sms);
+                        cap, learned, ctx->stream, ctx->sms, a_rcols);
   cb::launch_exclusive_scan(cap, m, stage_rp, partial, ctx->stream);
   cb::launch_learned_tiers(m, cap, hmax, perm, counters, ctx->stream, ctx->sms);
   CB_LAUNCHED();
@@ -401,7 +404,7 @@ void spgemm_learned(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int6
   pre_launches += launches;
   // rows that stayed on the one-pass path carry their size into the exact
   // pipeline; the rest (including overflowed rows) are computed exactly
-  spgemm_plain(ctx, sr, A, dB, out_ncols, C, opt, learned, cnt);
+  spgemm_plain(ctx, sr, A, dB, out_ncols, C, opt, learned, cnt, a_rcols);
   if (C->nnz > 0) {
     cb::launch_compact_rows(vsz, m, learned, stage_rp, cnt, scol.as<int32_t>(), sval.p, C->row_ptr,
                             C->col, C->val, ctx->stream, ctx->sms);
@@ -428,7 +431,7 @@ void count_rows(cb_ctx* ctx, const DevCSR& dA, const DevCSR& dB, int64_t* nnz_ou
   cb::launch_classify_sym(dA, dB, flops, nullptr, counters, ctx->stream, ctx->sms, nullptr,
                           ctx->tune.sym_hash_max);
   cb::launch_scatter_sym(m, ncols, flops, perm, nnz_out, counters, ctx->stream, ctx->sms, nullptr,
-                         nullptr, ctx->tune.sym_hash_max);
+                         nullptr, ctx->tune.sym_hash_max, dA.rcols);
   CB_LAUNCHED();
   ctx->stats.kernels += 3;
   read_counters(ctx, counters, nullptr, 0);
@@ -611,14 +614,16 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
 // learned sizing) summed per group of rows: sums[j] = sum of rows
 // [bounds[j], bounds[j+1]).  bounds is host memory (n + 1 values).
 void row_group_sums(cb_ctx* ctx, const cb_csr* A, const DevCSR& dB, const cb_opts& opt,
-                    const std::vector<int64_t>& bounds, std::vector<int64_t>& sums) {
+                    const std::vector<int64_t>& bounds, std::vector<int64_t>& sums,
+                    const int32_t* a_rcols = nullptr) {
   const int64_t m = A->nrows, n = (int64_t)bounds.size() - 1;
   DevBuf rows(ctx), pre(ctx), idx(ctx), got(ctx);
   rows.alloc(sizeof(int64_t) * (size_t)(m + 1));
   pre.alloc(sizeof(int64_t) * (size_t)(m + 1));
   idx.alloc(sizeof(int64_t) * bounds.size());
   got.alloc(sizeof(int64_t) * bounds.size());
-  const DevCSR dA = dev(A);
+  DevCSR dA = dev(A);
+  dA.rcols = a_rcols;
   if (opt.sizing == CB_SIZING_LEARNED) {
     ensure(ctx, &ctx->ws, &ctx->ws_cap,
            align_up(sizeof(int64_t) * cb::kCounters) + align_up(8 * (size_t)(m + 1)) +
@@ -674,8 +679,9 @@ void batched_group(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, int n,
   if (rowsA >= INT32_MAX || rowsB > INT32_MAX)
     fail(ctx, CB_ERR_INDEX, "batch too large to stack (rows beyond int32); split it");
   // stack the group once
-  DevBuf sArp(ctx), sAcol(ctx), sAval(ctx), sBrp(ctx), sBcol(ctx), sBval(ctx), parts(ctx);
+  DevBuf sArp(ctx), sAcol(ctx), sAval(ctx), sBrp(ctx), sBcol(ctx), sBval(ctx), parts(ctx), rcols(ctx);
   sArp.alloc(8 * (size_t)(rowsA + 1));
+  rcols.alloc(4 * (size_t)(rowsA + 1));
   sAcol.alloc(4 * (size_t)nnzA);
   sAval.alloc((size_t)vsz * (size_t)nnzA);
   sBrp.alloc(8 * (size_t)(rowsB + 1));
@@ -687,17 +693,17 @@ void batched_group(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, int n,
   int64_t ao = 0, bo = 0;
   for (int i = 0; i < n; ++i) {
     cb::fill_stack_part(&hp[(size_t)i * psz], A[i].row_ptr, A[i].col, A[i].val, A[i].nrows, arow[i], ao,
-                        (int32_t)brow[i]);
+                        (int32_t)brow[i], (int32_t)B[i].ncols);
     cb::fill_stack_part(&hp[(size_t)(n + i) * psz], B[i].row_ptr, B[i].col, B[i].val, B[i].nrows,
-                        brow[i], bo, 0);
+                        brow[i], bo, 0, (int32_t)B[i].ncols);
     ao += A[i].nnz;
     bo += B[i].nnz;
   }
   CB_CUDA(cudaMemcpyAsync(parts.p, hp.data(), hp.size(), cudaMemcpyHostToDevice, ctx->stream));
-  cb::launch_stack(parts.p, n, (int)vsz, sArp.as<int64_t>(), sAcol.as<int32_t>(), sAval.p, ctx->stream,
-                   ctx->sms);
+  cb::launch_stack(parts.p, n, (int)vsz, sArp.as<int64_t>(), sAcol.as<int32_t>(), sAval.p,
+                   rcols.as<int32_t>(), ctx->stream, ctx->sms);
   cb::launch_stack(static_cast<char*>(parts.p) + (size_t)n * psz, n, (int)vsz, sBrp.as<int64_t>(),
-                   sBcol.as<int32_t>(), sBval.p, ctx->stream, ctx->sms);
+                   sBcol.as<int32_t>(), sBval.p, nullptr, ctx->stream, ctx->sms);
   CB_LAUNCHED();
   kernels += 2;
   const DevCSR dB{rowsB, kmax, sBrp.as<int64_t>(), sBcol.as<int32_t>(), sBval.p};
@@ -707,7 +713,7 @@ void batched_group(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, int n,
   std::vector<int> cut{0};
   if (opt.budget_bytes > 0) {
     std::vector<int64_t> sizes;
-    row_group_sums(ctx, &sA, dB, opt, arow, sizes);
+    row_group_sums(ctx, &sA, dB, opt, arow, sizes, rcols.as<int32_t>());
     int64_t rows = 0, nz = 0;
     for (int i = 0; i < n; ++i) {
       if (8 * (A[i].nrows + 1) + sizes[(size_t)i] * per > opt.budget_bytes) {
@@ -753,9 +759,10 @@ void batched_group(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, int n,
     cb_csr Cw{};
     if (inner.out_capacity > 0) Cw = cb_csr{0, 0, 0, orp.as<int64_t>(), ocol.as<int32_t>(), oval.p};
     ctx->stats.kernels = 0;
+    const int32_t* wr = rcols.as<int32_t>() + arow[w0];
     if (opt.sizing == CB_SIZING_EXACT || !(opt.flags & CB_FLAG_LEARNED_ROWS))
-      spgemm_plain(ctx, sr, &Aw, dB, kmax, &Cw, inner);
-    else spgemm_learned(ctx, sr, &Aw, dB, kmax, &Cw, inner);
+      spgemm_plain(ctx, sr, &Aw, dB, kmax, &Cw, inner, nullptr, nullptr, wr);
+    else spgemm_learned(ctx, sr, &Aw, dB, kmax, &Cw, inner, wr);
     kernels += ctx->stats.kernels;
     nnz_total += Cw.nnz;
     flops_total += ctx->stats.flops;
@@ -1044,7 +1051,7 @@ int cb_ctx_set_tune(cb_ctx* ctx, cb_tune* t) {
   auto clamp = [](int v, int lo, int hi) { return v < lo ? lo : v > hi ? hi : v; };
   cb::Tune u;
   u.sym_hash_max = clamp(t->sym_hash_max, cb::kSymSmallMax, cb::kSymLargeMax);
-  u.num_hash_max = clamp(t->num_hash_max, u.sym_hash_max, 8192);
+  u.num_hash_max = clamp(t->num_hash_max, u.sym_hash_max, 4096);
   u.learn_max = clamp(t->learn_max, 0, 8192);
   ctx->tune = u;
   t->sym_hash_max = u.sym_hash_max;
@@ -1091,7 +1098,7 @@ int cb_autotune(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, c
     }
     const int big = cb::num_large_max((int)sr);
     const int syms[] = {512, 1024, 2048, 4096};
-    const int nums[] = {512, 1024, 2048, 4096, 8192};
+    const int nums[] = {512, 1024, 2048, 4096};
     const int learns[] = {64, 512, 2048};
     cudaEvent_t e0, e1;
     CB_CUDA(cudaEventCreate(&e0));

@@ -17,18 +17,22 @@ struct StackPart {
   const void* val;     // source values
   int64_t nrows, row_off, nnz_off;
   int32_t col_add;     // added to every column (row offset of B_i in the stacked B for A)
+  int32_t width;       // output width of the part's rows (k_i)
 };
 
 // blockIdx.y = part; x-blocks stride over the part's rows and entries.  The
 // last part also writes the closing row pointer.
 template <class T>
 __global__ void __launch_bounds__(256) k_stack(const StackPart* parts, int nparts, int64_t* rp_out,
-                                               int32_t* col_out, T* val_out) {
+                                               int32_t* col_out, T* val_out, int32_t* rcols_out) {
   const StackPart pt = parts[blockIdx.y];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t base = pt.rp[0];
-  for (int64_t r = t0; r < pt.nrows; r += stride) rp_out[pt.row_off + r] = pt.nnz_off + pt.rp[r] - base;
+  for (int64_t r = t0; r < pt.nrows; r += stride) {
+    rp_out[pt.row_off + r] = pt.nnz_off + pt.rp[r] - base;
+    if (rcols_out) rcols_out[pt.row_off + r] = pt.width;
+  }
   const int64_t nnz = pt.rp[pt.nrows] - base;
   if (t0 == 0 && (int)blockIdx.y == nparts - 1) rp_out[pt.row_off + pt.nrows] = pt.nnz_off + nnz;
   const T* src = static_cast<const T*>(pt.val) + base;
@@ -41,21 +45,21 @@ __global__ void __launch_bounds__(256) k_stack(const StackPart* parts, int npart
 }  // namespace
 
 void launch_stack(const void* parts_dev, int nparts, int vsz, int64_t* rp_out, int32_t* col_out,
-                  void* val_out, cudaStream_t s, int sms) {
+                  void* val_out, int32_t* rcols_out, cudaStream_t s, int sms) {
   if (nparts <= 0) return;
   dim3 grid((unsigned)(nparts < 64 ? sms * 4 : 8), (unsigned)nparts);
   const StackPart* pp = static_cast<const StackPart*>(parts_dev);
   switch (vsz) {
-    case 8: k_stack<uint64_t><<<grid, 256, 0, s>>>(pp, nparts, rp_out, col_out, static_cast<uint64_t*>(val_out)); break;
-    case 4: k_stack<uint32_t><<<grid, 256, 0, s>>>(pp, nparts, rp_out, col_out, static_cast<uint32_t*>(val_out)); break;
-    default: k_stack<uint8_t><<<grid, 256, 0, s>>>(pp, nparts, rp_out, col_out, static_cast<uint8_t*>(val_out));
+    case 8: k_stack<uint64_t><<<grid, 256, 0, s>>>(pp, nparts, rp_out, col_out, static_cast<uint64_t*>(val_out), rcols_out); break;
+    case 4: k_stack<uint32_t><<<grid, 256, 0, s>>>(pp, nparts, rp_out, col_out, static_cast<uint32_t*>(val_out), rcols_out); break;
+    default: k_stack<uint8_t><<<grid, 256, 0, s>>>(pp, nparts, rp_out, col_out, static_cast<uint8_t*>(val_out), rcols_out);
   }
 }
 
 size_t stack_part_size() { return sizeof(StackPart); }
 
 void fill_stack_part(void* dst, const int64_t* rp, const int32_t* col, const void* val, int64_t nrows,
-                     int64_t row_off, int64_t nnz_off, int32_t col_add) {
+                     int64_t row_off, int64_t nnz_off, int32_t col_add, int32_t width) {
   StackPart* p = static_cast<StackPart*>(dst);
   p->rp = rp;
   p->col = col;
@@ -64,6 +68,7 @@ void fill_stack_part(void* dst, const int64_t* rp, const int32_t* col, const voi
   p->row_off = row_off;
   p->nnz_off = nnz_off;
   p->col_add = col_add;
+  p->width = width;
 }
 
 }  // namespace cb

@@ -106,8 +106,8 @@ constexpr int kNumWarpMax = 64;      // warp team, table <= 128
 constexpr int kNumSmallMax = 512;    // 256-thread team, table <= 1024
 template <int SR> struct NumLimits {
   static constexpr int kHashMax = kNumSmallMax;  // default bound of the hash tiers
-  // largest bound the 1024-thread hash tier supports (table of 2x slots)
-  static constexpr int kLargeMax = sizeof(typename Sem<SR>::A) == 8 ? 4096 : 8192;
+  // largest bound the large hash tier supports (512-thread team, table of 2x slots)
+  static constexpr int kLargeMax = 4096;
   // accumulators per rank window
   static constexpr int kWcap = sizeof(typename Sem<SR>::A) == 8 ? 16384 : 32768;
   // window cut: a window starts where the running count crosses a multiple
@@ -189,6 +189,12 @@ __device__ __forceinline__ int group_log2(int64_t flops, int64_t nnz_a) {
 // End offset of row k of a (possibly windowed) operand.
 __device__ __forceinline__ int64_t row_end(const DevCSR& M, int64_t k) {
   return M.rpe ? M.rpe[k] : M.rp[k + 1];
+}
+
+// Output width of row i of A.B: A.rcols[i] when set (stacked batches, where
+// each product keeps its own columns), else the width of B's view.
+__device__ __forceinline__ int64_t row_width(const DevCSR& A, const DevCSR& B, int64_t i) {
+  return A.rcols ? (int64_t)A.rcols[i] : B.ncols;
 }
 
 // Whether column c belongs to B's column window (always true unless filtering).
@@ -400,12 +406,16 @@ __device__ __forceinline__ void for_row_products_balanced(const DevCSR& A, const
       }
       len = q1 - q0;
     }
-    long long total;
-    const long long off = cta_exclusive_scan64(len, sm.scan, total);
-    int ne;
-    const int slot = team_exclusive_scan<1024>(len > 0 ? 1 : 0, sm.iscan, ne);
+    // one scan gives both the product offsets (high bits) and the slots of
+    // the nonempty ranges (low 11 bits; at most 1024 of them)
+    long long packed_total;
+    const long long packed =
+        cta_exclusive_scan64((len << 11) | (len > 0 ? 1 : 0), sm.scan, packed_total);
+    const long long total = packed_total >> 11;
+    const int ne = (int)(packed_total & 2047);
     if (len > 0) {
-      sm.off[slot] = off;
+      const int slot = (int)(packed & 2047);
+      sm.off[slot] = packed >> 11;
       sm.b0[slot] = q0;
       sm.pa[slot] = tid;
     }
@@ -421,18 +431,23 @@ __device__ __forceinline__ void for_row_products_balanced(const DevCSR& A, const
       }
       int j0 = l;
       for (long long tb = t_beg; tb < t_end; tb += 32) {
-        const int k = j0 + 1 + lane;
-        const long long st = k < ne ? sm.off[k] : LLONG_MAX;
-        const long long pos = st - tb;  // >= 1 by the choice of j0
-        const unsigned bits = __reduce_or_sync(0xffffffffu, pos < 32 ? 1u << (int)pos : 0u);
-        const int j = j0 + __popc(bits & ((2u << lane) - 1u));
+        const long long nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;
+        int j = j0;
+        if (nxt <= tb + 31) {  // the step crosses range starts (uniform over the warp)
+          const int k = j0 + 1 + lane;
+          const long long st = k < ne ? sm.off[k] : LLONG_MAX;
+          const long long pos = st - tb;  // >= 1 by the choice of j0
+          const unsigned bits = __reduce_or_sync(0xffffffffu, pos < 32 ? 1u << (int)pos : 0u);
+          j = j0 + __popc(bits & ((2u << lane) - 1u));
+          j0 += __popc(bits);
+        }
         const long long t = tb + lane;
         if (t < t_end) {
           const int64_t q = sm.b0[j] + (t - sm.off[j]);
           const int c = B.col[q];
           if (!filter || (unsigned)((int64_t)c - lo) < width) f(c0 + sm.pa[j], q, c);
         }
-        j0 += __popc(bits);  // range holding product tb + 32 (ranges are nonempty)
+        // range holding product tb + 32 (ranges are nonempty, so at most one more start)
         if (j0 + 1 < ne && sm.off[j0 + 1] <= tb + 32) ++j0;
       }
     }

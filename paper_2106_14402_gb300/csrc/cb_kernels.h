@@ -35,6 +35,9 @@ struct DevCSR {
   const int64_t* rpe = nullptr;
   int64_t col_lo = 0;
   int filter = 0;
+  // A only: per-row output width (columns of row i lie in [0, rcols[i]));
+  // nullptr = the width of B's view
+  const int32_t* rcols = nullptr;
 };
 
 // Counters block in device memory (int64 each).
@@ -65,7 +68,7 @@ void launch_classify_sym(const DevCSR& A, const DevCSR& B, int64_t* flops, int32
 void launch_scatter_sym(int64_t m, int64_t ncols, const int64_t* flops, int32_t* perm,
                         int64_t* nnz, int64_t* counters, cudaStream_t s, int sms,
                         const uint8_t* skip = nullptr, const int64_t* preset = nullptr,
-                        int64_t sym_hash_max = 512);
+                        int64_t sym_hash_max = 512, const int32_t* rcols = nullptr);
 
 // K4: out[0] = 0, out[i+1] = out[i] + in[i]; partial needs scan_partials(n) int64.
 int64_t scan_partials(int64_t n);
@@ -91,7 +94,7 @@ void launch_classify_num(int sr, int64_t m, const int64_t* nnz, int32_t* perm,
 // staging, and the copy from staging into C.
 void launch_learn_caps(int64_t m, const int64_t* pred, const int64_t* flops, int64_t ncols,
                        float margin, int64_t hash_max, int64_t* cap, uint8_t* learned,
-                       cudaStream_t s, int sms);
+                       cudaStream_t s, int sms, const int32_t* rcols = nullptr);
 void launch_learned_tiers(int64_t m, const int64_t* cap, int64_t hash_max, int32_t* perm,
                           int64_t* counters, cudaStream_t s, int sms);
 int learn_hash_max(int sr);
@@ -134,9 +137,10 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
 // Batched products (cb_batched.cu): stack parts into one CSR.
 size_t stack_part_size();
 void fill_stack_part(void* dst, const int64_t* rp, const int32_t* col, const void* val, int64_t nrows,
-                     int64_t row_off, int64_t nnz_off, int32_t col_add);
+                     int64_t row_off, int64_t nnz_off, int32_t col_add, int32_t width);
+// rcols_out (optional): every stacked row gets its part's width
 void launch_stack(const void* parts_dev, int nparts, int vsz, int64_t* rp_out, int32_t* col_out,
-                  void* val_out, cudaStream_t s, int sms);
+                  void* val_out, int32_t* rcols_out, cudaStream_t s, int sms);
 
 // Learned sizer (k_mlp.cu).
 const void* mlp_bf16(const cb_mlp* m);

@@ -197,8 +197,9 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
     const int cnt = wd.count < WCAP ? wd.count : WCAP;
     const int64_t span_lo = B.col_lo + (int64_t)wd.span * kSpanCols;
     const int64_t lo = span_lo + 32 * (int64_t)wd.w_lo;
-    const int64_t hi = min(span_lo + 32 * (int64_t)wd.w_hi, B.col_lo + B.ncols);
-    const bool whole = lo == B.col_lo && hi == B.col_lo + B.ncols && !B.filter;
+    const int64_t rw = row_width(A, B, i);
+    const int64_t hi = min(span_lo + 32 * (int64_t)wd.w_hi, B.col_lo + rw);
+    const bool whole = lo == B.col_lo && hi == B.col_lo + rw && !B.filter;
     const int nw = wd.w_hi - wd.w_lo;
     if (hbits) {
       const unsigned* src = hbits + (size_t)((int64_t)wd.h * spans + wd.span) * kSpanWords + wd.w_lo;
@@ -311,10 +312,10 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
     ++*launches;
   }
   if (seg_count[kNumLarge]) {
-    constexpr int CTA = 1024, TEAM = 1024, TBL = 2 * NumLimits<SR>::kLargeMax;
+    constexpr int CTA = 512, TEAM = 512, TBL = 2 * NumLimits<SR>::kLargeMax;
     const size_t smem = TBL * slot;
     set_smem(k_num_hash<SR, CTA, TEAM, TBL>, smem);
-    k_num_hash<SR, CTA, TEAM, TBL><<<capped(seg_count[kNumLarge], sms), CTA, smem, s>>>(
+    k_num_hash<SR, CTA, TEAM, TBL><<<capped(seg_count[kNumLarge], sms * 4), CTA, smem, s>>>(
         A, B, perm + seg_begin[kNumLarge], seg_count[kNumLarge], flops, nnz, Crp, Ccol, Cval, err);
     ++*launches;
   }
@@ -355,10 +356,10 @@ void learned_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
     ++*launches;
   }
   if (seg_count[3]) {
-    constexpr int CTA = 1024, TEAM = 1024, TBL = 2 * NumLimits<SR>::kLearnHashMax;
+    constexpr int CTA = 512, TEAM = 512, TBL = 2 * NumLimits<SR>::kLearnHashMax;
     const size_t smem = TBL * slot;
     set_smem(k_num_hash<SR, CTA, TEAM, TBL, true>, smem);
-    k_num_hash<SR, CTA, TEAM, TBL, true><<<capped(seg_count[3], sms), CTA, smem, s>>>(
+    k_num_hash<SR, CTA, TEAM, TBL, true><<<capped(seg_count[3], sms * 4), CTA, smem, s>>>(
         A, B, perm + seg_begin[3], seg_count[3], flops, cap, stage_rp, scol, sval, overflows,
         learned, cnt);
     ++*launches;

@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(256) k_classify_sym(DevCSR A, DevCSR B, int64_
     if (lane == 0) {
       flops[i] = f;
       if (maxb) maxb[i] = mx;
-      atomicAdd(&hist[skip && skip[i] ? 0 : sym_tier(min((int64_t)f, B.ncols), sym_hash_max)], 1ull);
+      atomicAdd(&hist[skip && skip[i] ? 0 : sym_tier(min((int64_t)f, row_width(A, B, i)), sym_hash_max)],
+                1ull);
       atomicAdd(&total, (unsigned long long)f);
     }
   }
@@ -70,10 +71,11 @@ __global__ void __launch_bounds__(256) k_classify_sym(DevCSR A, DevCSR B, int64_
 struct TierBySize {
   const int64_t* v;
   int64_t cap, t1, t2, t3;
-  const uint8_t* skip;  // rows with skip[i] != 0 are left out (tier 0)
+  const uint8_t* skip;         // rows with skip[i] != 0 are left out (tier 0)
+  const int32_t* rcap = nullptr;  // per-row cap (replaces cap when set)
   __device__ __forceinline__ int operator()(int64_t i) const {
     if (skip && skip[i]) return 0;
-    const int64_t u = min(v[i], cap);
+    const int64_t u = min(v[i], rcap ? (int64_t)rcap[i] : cap);
     return u == 0 ? 0 : u <= t1 ? 1 : u <= t2 ? 2 : u <= t3 ? 3 : 4;
   }
 };
@@ -252,8 +254,9 @@ void launch_classify_sym(const DevCSR& A, const DevCSR& B, int64_t* flops, int32
 
 void launch_scatter_sym(int64_t m, int64_t ncols, const int64_t* flops, int32_t* perm,
                         int64_t* nnz, int64_t* counters, cudaStream_t s, int,
-                        const uint8_t* skip, const int64_t* preset, int64_t sym_hash_max) {
-  TierBySize t{flops, ncols, kSymWarpMax, kSymSmallMax, sym_hash_max, skip};
+                        const uint8_t* skip, const int64_t* preset, int64_t sym_hash_max,
+                        const int32_t* rcols) {
+  TierBySize t{flops, ncols, kSymWarpMax, kSymSmallMax, sym_hash_max, skip, rcols};
   k_tier_scatter<<<grid_for(m, 256, 1 << 30), 256, 0, s>>>(m, t, perm, counters + kCntSym,
                                                             counters + kCurSym, nnz, preset);
 }
@@ -298,11 +301,12 @@ void launch_classify_num(int, int64_t m, const int64_t* nnz, int32_t* perm, int6
 __global__ void __launch_bounds__(256) k_learn_caps(int64_t m, const int64_t* pred,
                                                     const int64_t* flops, int64_t ncols,
                                                     float margin, int64_t hash_max, int64_t* cap,
-                                                    uint8_t* learned) {
+                                                    uint8_t* learned, const int32_t* rcols) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t f = flops[i];
-    const int64_t bound = f < ncols ? f : ncols;
+    const int64_t w = rcols ? (int64_t)rcols[i] : ncols;
+    const int64_t bound = f < w ? f : w;
     int64_t p = pred ? pred[i] : bound;
     int64_t c = (int64_t)ceil((double)p * (1.0 + (double)margin));
     if (c < p) c = p;
@@ -334,10 +338,10 @@ __global__ void __launch_bounds__(256) k_compact_rows(int64_t m, const uint8_t* 
 
 void launch_learn_caps(int64_t m, const int64_t* pred, const int64_t* flops, int64_t ncols,
                        float margin, int64_t hash_max, int64_t* cap, uint8_t* learned,
-                       cudaStream_t s, int sms) {
+                       cudaStream_t s, int sms, const int32_t* rcols) {
   if (m == 0) return;
   k_learn_caps<<<grid_for(m, 256, sms * 8), 256, 0, s>>>(m, pred, flops, ncols, margin, hash_max,
-                                                          cap, learned);
+                                                          cap, learned, rcols);
 }
 
 void launch_learned_tiers(int64_t m, const int64_t* cap, int64_t hash_max, int32_t* perm,

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(CTA) k_sym_hash(DevCSR A, DevCSR B, const int3
        r += (int64_t)gridDim.x * TEAMS) {
     const int i = rows[r];
     const int64_t f = flops[i];
-    const int64_t u = min(f, B.ncols);
+    const int64_t u = min(f, row_width(A, B, i));
     const int bits = max(ceil_log2(2 * u), 5);
     const int tsize = 1 << bits;
     const uint32_t mask = (uint32_t)tsize - 1;
@@ -93,7 +93,14 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
     const int64_t h = u / spans, sp = u - h * spans;
     const int i = heavy_rows[h];
     const int64_t lo = B.col_lo + sp * (int64_t)kSpanCols;
-    const int64_t hi = min(lo + (int64_t)kSpanCols, B.col_lo + B.ncols);
+    const int64_t hi = min(lo + (int64_t)kSpanCols, B.col_lo + row_width(A, B, i));
+    if (hi <= lo) {  // this row's columns end before the span: nothing to count
+      if (tid == 0) {
+        span_counts[h * spans + sp] = 0;
+        if (span_wins) span_wins[h * spans + sp] = make_int2(0, 0);
+      }
+      continue;
+    }
     const int nwords = (int)((hi - lo + 31) / 32);
     for (int w = tid; w < nwords; w += 1024) sym_bm[w] = 0u;
     __syncthreads();
@@ -233,10 +240,10 @@ void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,
     ++*launches;
   }
   if (seg_count[kSymLarge]) {
-    constexpr int CTA = 1024, TEAM = 1024, TBL = 2 * kSymLargeMax;
+    constexpr int CTA = 512, TEAM = 512, TBL = 2 * kSymLargeMax;
     const size_t smem = TBL * sizeof(int);
     set_smem(k_sym_hash<CTA, TEAM, TBL>, smem);
-    k_sym_hash<CTA, TEAM, TBL><<<capped(seg_count[kSymLarge], sms * 2), CTA, smem, s>>>(
+    k_sym_hash<CTA, TEAM, TBL><<<capped(seg_count[kSymLarge], sms * 4), CTA, smem, s>>>(
         A, B, perm + seg_begin[kSymLarge], seg_count[kSymLarge], flops, nnz);
     ++*launches;
   }
