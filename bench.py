@@ -298,13 +298,14 @@ def main_gpu(args):
     achieved = num_bytes / (num_ms * 1e-3) / 1e9 if num_ms > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "numeric phase (K5-K7: hash tiers + dense heavy slices), per SpGEMM",
+                "kernel": "numeric phase (hash tiers + rank windows of heavy rows), per SpGEMM",
                 "peak_source": peak_src,
                 "algorithmic_bytes_per_step": num_bytes, "ms_per_step_in_kernel": round(num_ms, 4)}
 
     legs = {}
     if not args.no_legs:
         legs = run_legs(args, cb, ctx, dprob, flush, ms_step, products)
+        legs["one_launch_er16k"] = run_one_launch(args, cb, ctx, flush, dev, peak, peak_src)
 
     e2e = None
     if not args.no_e2e:
@@ -407,6 +408,55 @@ def run_legs(args, cb, ctx, dprob, flush, plain_ms, products):
     if not args.no_multi:
         out["multi_spgemm"] = run_multi(args, cb, ctx, model)
     return out
+
+
+def run_one_launch(args, cb, ctx, flush, dev, peak, peak_src):
+    """ER n=16384, 8 distinct columns per row, C = A.A over (+,x) int64:
+    the one-launch kernel for small rows (cb_spgemm_fused) timed alone, next
+    to the same product on the two-phase path and through cb_spgemm_ex's
+    automatic branch (flop count + host sync + the one launch)."""
+    import torch
+    from paper_2106_14402_gb300 import gen
+    (sr, A, _), = gen.er_square()
+    dA = cb.DeviceCSR.from_host(A, sr, dev)
+    lanes, flops = cb.fused_lanes(dA, dA, ctx=ctx)
+    dt = cb.SEMIRING[sr][1]
+    out = cb.DeviceCSR(A.nrows, A.ncols, torch.empty(A.nrows + 1, dtype=torch.int64, device=dev),
+                       torch.empty(flops, dtype=torch.int32, device=dev),
+                       torch.empty(flops, dtype=dt, device=dev))
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def fused():
+        cb.spgemm_fused(sr, dA, dA, out, status, lanes=lanes, ctx=ctx)
+
+    steps = max(args.steps, 20)
+    for _ in range(max(args.warmup, 3)):
+        fused()
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0, "one-launch SpGEMM reported an error"
+    ms = timed(fused, steps, flush)
+    nnz = int(out.row_ptr[-1].item())
+    two = lambda: cb.spgemm(sr, dA, dA, validate=False, out=out, fused=False, ctx=ctx)  # noqa: E731
+    auto = lambda: cb.spgemm(sr, dA, dA, validate=False, out=out, ctx=ctx)  # noqa: E731
+    for f in (two, auto):
+        f()
+    ms_two = timed(two, steps, flush)
+    ms_auto = timed(auto, steps, flush)
+    nbytes = compulsory_bytes(sr, A, A, nnz, A.nrows)
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    return {"workload": "ER n=16384, 8 distinct cols/row, (+,x) int64 U{1..10}; C=A.A",
+            "lanes": lanes, "products": flops, "nnz_c": nnz,
+            "us_per_call": round(ms * 1e3, 3), "products_per_s": flops / (ms * 1e-3),
+            "nnz_per_s": nnz / (ms * 1e-3),
+            "two_phase_us": round(ms_two * 1e3, 3), "auto_branch_us": round(ms_auto * 1e3, 3),
+            "one_launch_vs_two_phase": ms_two / ms,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "kernel": "k_fused (one launch, 8 lanes per row)",
+                         "peak_source": peak_src, "algorithmic_bytes": nbytes,
+                         "note": "bytes = A + B rows touched + C; B is A here, so A's "
+                                 "bytes are counted twice"},
+            "l2": "flushed before every timed call", "steps": steps}
 
 
 def run_multi(args, cb, ctx, model):

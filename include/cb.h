@@ -109,10 +109,15 @@ enum {
                          internal consistency word is set (debug)                   */
   CB_FLAG_TIMING = 2, /* record CUDA events between the phases on ctx's stream and
                          report their durations in cb_stats (synchronises at the end) */
-  CB_FLAG_LEARNED_ROWS = 4 /* batched modes with learned sizing: besides the batch
+  CB_FLAG_LEARNED_ROWS = 4, /* batched modes with learned sizing: besides the batch
                          count, also size each batch's rows from predictions
                          (default: predictions set the batch count only and each
                          batch runs the exact two-phase path) */
+  CB_FLAG_NO_FUSED = 8 /* exact sizing: always run the two-phase path.  By default
+                         a product whose rows all meet the bounds of
+                         cb_spgemm_fused (below) is formed by that one launch
+                         after the flop count, with a library-allocated C sized
+                         by flops (an upper bound of nnz(C)) */
 };
 
 /* Fill *opt with defaults (exact sizing, validation on, library-allocated C). */
@@ -288,12 +293,48 @@ int cb_ctx_get_tune(const cb_ctx *ctx, cb_tune *tune);
 int cb_autotune(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B, const cb_opts *opt,
                 cb_tune *best, float *best_ms);
 
+/* ---- one-launch SpGEMM for small rows -----------------------------------
+ * The row-wise SpGEMM of Sec. 4.1 with its symbolic and numeric phases fused
+ * into one kernel launch, for products whose rows are all small:
+ *   - every row of A holds at most `lanes` entries (lanes = 8, 16 or 32),
+ *   - every row of C has at most 8 * lanes products (flops_i),
+ *   - B->ncols <= cb_fused_max_cols(lanes) (2^26 - 1 for 8 lanes).
+ * Each row is formed by `lanes` threads (products in registers, sorted by a
+ * register bitonic network, equal columns merged), and each CTA finds its
+ * output offset from the earlier CTAs' row totals, so C comes out compact
+ * and sorted without a host synchronisation.
+ *   C->row_ptr (A->nrows + 1 int64), C->col (int32) and C->val (the
+ *   semiring's type) are caller-provided device buffers, col/val holding
+ *   `capacity` entries; C->nrows/ncols are set, C->nnz to -1 (nnz(C) is
+ *   C->row_ptr[nrows] on the device).
+ *   `status` is a device int that the kernel ORs CB_FUSED_* bits into (the
+ *   caller zeroes it); any bit set means C is not valid.
+ * Inputs are not validated (see cb_spgemm_ex).  Nothing is synchronised; the
+ * first call on a context, or one with more rows than any earlier call,
+ * allocates the context's tile-status array (so call once before capturing
+ * the launch into a CUDA graph); later calls allocate nothing.  Calls on one
+ * context must be ordered on its stream.  Returns CB_ERR_ARG for bad
+ * arguments or lanes, else CB_OK / CB_ERR_CUDA. */
+enum {
+  CB_FUSED_CAPACITY = 1,      /* nnz(C) > capacity: nothing past capacity written */
+  CB_FUSED_ROW_TOO_LARGE = 2, /* a row beyond the lanes' bounds (left empty)      */
+  CB_FUSED_STALLED = 4        /* a CTA gave up waiting for an earlier CTA's total  */
+};
+int cb_spgemm_fused(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B, cb_csr *C,
+                    int64_t capacity, int lanes, int *status);
+/* Largest column count cb_spgemm_fused takes with `lanes` lanes per row. */
+int64_t cb_fused_max_cols(int lanes);
+/* Smallest lanes (8, 16, 32) whose bounds every row of A.B meets, or 0 if
+ * none; *flops (optional) receives the total product count, an upper bound
+ * of nnz(C).  Synchronises ctx's stream. */
+int cb_fused_lanes(cb_ctx *ctx, const cb_csr *A, const cb_csr *B, int *lanes, int64_t *flops);
+
 /* Statistics of the most recent cb_spgemm_ex on this context (host memory). */
 typedef struct {
   int64_t flops;        /* number of (x)-products                              */
   int64_t nnz;          /* nnz(C)                                              */
-  int64_t heavy_rows;   /* rows computed with the dense column-slice path      */
-  int64_t heavy_units;  /* (row, column slice) units launched for heavy rows   */
+  int64_t heavy_rows;   /* rows computed in rank windows                       */
+  int64_t heavy_units;  /* rank windows launched for heavy rows                */
   int64_t overflow_rows;/* rows recomputed exactly after a sizing overflow     */
   int32_t batches;      /* column batches (1 when not batched)                 */
   int32_t kernels;      /* kernel launches issued by the call                  */

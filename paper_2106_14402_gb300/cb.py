@@ -99,6 +99,11 @@ _SIGS = {
     "cb_autotune": ([c_void_p, ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr),
                      ctypes.POINTER(cb_opts), ctypes.POINTER(cb_tune), ctypes.POINTER(ctypes.c_float)],
                     ctypes.c_int),
+    "cb_spgemm_fused": ([c_void_p, ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr),
+                         ctypes.POINTER(cb_csr), c_int64, ctypes.c_int, c_void_p], ctypes.c_int),
+    "cb_fused_max_cols": ([ctypes.c_int], c_int64),
+    "cb_fused_lanes": ([c_void_p, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr),
+                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(c_int64)], ctypes.c_int),
     "cb_mlp_create": ([ctypes.POINTER(c_void_p), c_void_p, c_void_p], ctypes.c_int),
     "cb_mlp_destroy": ([c_void_p], None),
     "cb_mlp_get": ([c_void_p, c_void_p, c_void_p, c_void_p], ctypes.c_int),
@@ -303,23 +308,33 @@ def make_opts(sizing="exact", validate=True, out_capacity=0, budget_bytes=0, on_
 
 FLAG_CHECK = 1
 FLAG_TIMING = 2
+FLAG_LEARNED_ROWS = 4
+FLAG_NO_FUSED = 8
+
+# device status bits of cb_spgemm_fused
+FUSED_CAPACITY = 1
+FUSED_ROW_TOO_LARGE = 2
+FUSED_STALLED = 4
 
 
 def spgemm(semiring: str, A: DeviceCSR, B: DeviceCSR, *, validate: bool = True, check: bool = False,
            ctx: Context | None = None, out: DeviceCSR | None = None, sizing: str = "exact",
-           timing: bool = False, mlp=None, margin: float = 0.25) -> DeviceCSR:
+           timing: bool = False, mlp=None, margin: float = 0.25, fused: bool = True) -> DeviceCSR:
     """C = A (+).(x) B on the GPU (cb_spgemm_ex).
 
     With `out` (a DeviceCSR whose col/val tensors are large enough), C is
     written into those buffers and a DeviceCSR viewing the first nnz(C)
     entries is returned; otherwise the library allocates C.
     `check` adds a synchronising self-consistency check of the kernels.
+    `fused=False` keeps products whose rows are all small on the two-phase
+    path instead of the one-launch kernel.
     """
     code, dt = SEMIRING[semiring]
     ctx = ctx or context()
     sa, sb = A.as_struct(), B.as_struct()
     opts = make_opts(sizing=sizing, validate=validate, mlp=mlp, margin=margin,
-                     flags=(FLAG_CHECK if check else 0) | (FLAG_TIMING if timing else 0))
+                     flags=(FLAG_CHECK if check else 0) | (FLAG_TIMING if timing else 0) |
+                     (0 if fused else FLAG_NO_FUSED))
     if out is not None:
         opts.out_capacity = max(1, min(out.col.numel(), out.val.numel()))
         sc = cb_csr(0, 0, 0, out.row_ptr.data_ptr(), out.col.data_ptr(), out.val.data_ptr())
@@ -335,6 +350,42 @@ def spgemm(semiring: str, A: DeviceCSR, B: DeviceCSR, *, validate: bool = True, 
     return DeviceCSR(sc.nrows, sc.ncols, _wrap(sc.row_ptr, sc.nrows + 1, torch.int64, owner, dev),
                      _wrap(sc.col, sc.nnz, torch.int32, owner, dev),
                      _wrap(sc.val, sc.nnz, dt, owner, dev), owner)
+
+
+def fused_lanes(A: DeviceCSR, B: DeviceCSR, ctx: Context | None = None):
+    """(lanes, flops): the smallest lanes per row (8, 16, 32) whose bounds
+    every row of A.B meets (0 if none) and the total product count
+    (cb_fused_lanes; synchronises)."""
+    ctx = ctx or context()
+    sa, sb = A.as_struct(), B.as_struct()
+    lanes, flops = ctypes.c_int(0), c_int64(0)
+    ctx.check(ctx.lib.cb_fused_lanes(ctx.handle, ctypes.byref(sa), ctypes.byref(sb),
+                                     ctypes.byref(lanes), ctypes.byref(flops)))
+    return lanes.value, flops.value
+
+
+def fused_max_cols(lanes: int) -> int:
+    return int(load().cb_fused_max_cols(int(lanes)))
+
+
+def spgemm_fused(semiring: str, A: DeviceCSR, B: DeviceCSR, out: DeviceCSR, status: torch.Tensor,
+                 lanes: int = 8, ctx: Context | None = None) -> None:
+    """One-launch C = A (+).(x) B into `out` (cb_spgemm_fused): out.row_ptr
+    gets nrows + 1 entries, out.col / out.val hold the capacity; `status`
+    (int32 device tensor, zeroed by the caller) receives FUSED_* bits.
+    Nothing is synchronised: nnz(C) is out.row_ptr[nrows] on the device."""
+    code, dt = SEMIRING[semiring]
+    ctx = ctx or context()
+    if status.dtype != torch.int32 or not status.is_cuda:
+        raise ValueError("status must be an int32 CUDA tensor")
+    if out.val.dtype != dt:
+        raise ValueError("out.val has the wrong dtype for this semiring")
+    sa, sb = A.as_struct(), B.as_struct()
+    cap = min(out.col.numel(), out.val.numel())
+    sc = cb_csr(0, 0, 0, out.row_ptr.data_ptr(), out.col.data_ptr() if cap else None,
+                out.val.data_ptr() if cap else None)
+    ctx.check(ctx.lib.cb_spgemm_fused(ctx.handle, code, ctypes.byref(sa), ctypes.byref(sb),
+                                      ctypes.byref(sc), cap, int(lanes), status.data_ptr()))
 
 
 def row_stats(A: DeviceCSR, B: DeviceCSR, ctx: Context | None = None):

@@ -28,6 +28,9 @@ struct cb_ctx {
   int64_t* host = nullptr;  // pinned read-back buffer
   cudaEvent_t ev[6] = {};   // phase boundaries (CB_FLAG_TIMING)
   cb::Tune tune;            // tier bounds (cb_ctx_set_tune / cb_autotune)
+  unsigned long long* fstat = nullptr;  // tile status words of the one-launch path
+  int64_t fstat_cap = 0;
+  unsigned* fsync = nullptr;  // [0] launch epoch, [1] finished CTAs, [4] status word
   std::string err;
   cb_stats stats{};
 };
@@ -175,6 +178,51 @@ void collect_times(cb_ctx* ctx, const cb_opts& opt, bool numeric_ran) {
   }
 }
 
+// Scratch of the one-launch path: tile status words (zeroed once; launch
+// epochs keep them valid across calls) and the epoch / finished-CTA words.
+void ensure_fused(cb_ctx* ctx, int64_t tiles) {
+  if (!ctx->fsync) {
+    CB_CUDA(cudaMalloc((void**)&ctx->fsync, 64));
+    CB_CUDA(cudaMemsetAsync(ctx->fsync, 0, 64, ctx->stream));
+  }
+  if (tiles <= ctx->fstat_cap) return;
+  const int64_t want = std::max<int64_t>(tiles + tiles / 4, 4096);
+  if (ctx->fstat) {
+    CB_CUDA(cudaStreamSynchronize(ctx->stream));
+    CB_CUDA(cudaFree(ctx->fstat));
+    ctx->fstat = nullptr;
+    ctx->fstat_cap = 0;
+  }
+  CB_CUDA(cudaMalloc((void**)&ctx->fstat, sizeof(unsigned long long) * (size_t)want));
+  CB_CUDA(cudaMemsetAsync(ctx->fstat, 0, sizeof(unsigned long long) * (size_t)want, ctx->stream));
+  ctx->fstat_cap = want;
+}
+
+// Smallest lane count whose bounds hold for every row, 0 if none.
+int fused_fit(int64_t max_arow, int64_t max_flops, int64_t ncols) {
+  for (int lanes : {8, 16, 32})
+    if (max_arow <= lanes && max_flops <= 8 * lanes && ncols <= cb::fused_max_cols(lanes))
+      return lanes;
+  return 0;
+}
+
+void run_fused(cb_ctx* ctx, int sr, int lanes, const DevCSR& dA, const DevCSR& dB, int64_t* rp,
+               int32_t* col, void* val, int64_t cap, int* status) {
+  if (dA.nrows == 0) {
+    CB_CUDA(cudaMemsetAsync(rp, 0, sizeof(int64_t), ctx->stream));
+    return;
+  }
+  ensure_fused(ctx, cb::fused_tiles(lanes, dA.nrows));
+  const cudaError_t e = cb::launch_fused(sr, lanes, dA, dB, rp, col, val, cap, ctx->fstat,
+                                         ctx->fstat_cap, ctx->fsync, status, ctx->stream, ctx->sms);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("fused launch: ") + cudaGetErrorString(e);
+    throw Fail{CB_ERR_CUDA};
+  }
+  CB_LAUNCHED();
+  ctx->stats.kernels += 1;
+}
+
 // Everything from K1 to the allocation of C and the numeric phase.
 // The plain (unbatched) path on a possibly windowed view dB of B; C gets
 // C->ncols = out_ncols.  Inputs are assumed valid (validation happens first).
@@ -236,6 +284,46 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
   sym_beg[1] = 0;
   for (int t = 2; t < cb::kSymTiers; ++t) sym_beg[t] = sym_beg[t - 1] + sym_cnt[t - 1];
   ctx->stats.flops = ctx->host[cb::kTotalFlops];
+
+  // Every row small: one launch forms, sorts and places all rows (k_fused),
+  // into C sized by flops (an upper bound of nnz(C)).
+  const int lanes = fused_fit(ctx->host[cb::kMaxArow], ctx->host[cb::kMaxFlops], ncols);
+  if (lanes && !(opt.flags & CB_FLAG_NO_FUSED) && !skip && !preset && !a_rcols && !dB.rpe &&
+      !dB.filter && dB.col_lo == 0) {
+    const int64_t cap = caller_buf ? opt.out_capacity : ctx->stats.flops;
+    if (!caller_buf && cap > 0) {
+      CB_CUDA(cudaMallocAsync((void**)&C->col, sizeof(int32_t) * (size_t)cap, ctx->stream));
+      CB_CUDA(cudaMallocAsync(&C->val, vsz * (size_t)cap, ctx->stream));
+    }
+    ensure_fused(ctx, 0);
+    int* st = reinterpret_cast<int*>(ctx->fsync + 4);
+    CB_CUDA(cudaMemsetAsync(st, 0, sizeof(int), ctx->stream));
+    mark(ctx, opt, 2);
+    mark(ctx, opt, 3);
+    mark(ctx, opt, 4);
+    run_fused(ctx, sr, lanes, dA, dB, C->row_ptr, C->col, C->val, cap, st);
+    mark(ctx, opt, 5);
+    CB_CUDA(cudaMemcpyAsync(ctx->host, C->row_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    CB_CUDA(cudaMemcpyAsync(ctx->host + 1, st, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CB_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int64_t total = ctx->host[0];
+    const int bits = (int)(ctx->host[1] & 0xFFFFFFFF);
+    C->nnz = total;
+    ctx->stats.nnz = total;
+    if (bits & CB_FUSED_STALLED) fail(ctx, CB_ERR_TIMEOUT, "fused SpGEMM: a tile wait expired");
+    if (bits & CB_FUSED_ROW_TOO_LARGE) fail(ctx, CB_ERR_CUDA, "fused SpGEMM: row bound violated");
+    if (bits & CB_FUSED_CAPACITY) {
+      char msg[128];
+      std::snprintf(msg, sizeof msg, "output needs %lld entries, capacity %lld", (long long)total,
+                    (long long)cap);
+      ctx->err = msg;
+      throw Fail{CB_ERR_CAPACITY};
+    }
+    collect_times(ctx, opt, true);
+    return;
+  }
+
   const int64_t n_heavy = sym_cnt[cb::kSymHeavy];
   const int64_t spans = (ncols + cb::kSpanCols - 1) / cb::kSpanCols;
   const int wcut = cb::num_window_cut(sr);
@@ -842,6 +930,9 @@ void cb_ctx_destroy(cb_ctx* ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->ws2) cudaFree(ctx->ws2);
   if (ctx->host) cudaFreeHost(ctx->host);
+  if (ctx->fstat || ctx->fsync) cudaStreamSynchronize(ctx->stream);
+  if (ctx->fstat) cudaFree(ctx->fstat);
+  if (ctx->fsync) cudaFree(ctx->fsync);
   for (cudaEvent_t e : ctx->ev)
     if (e) cudaEventDestroy(e);
   delete ctx;
@@ -918,6 +1009,63 @@ int cb_spgemm_ex(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, 
       cudaStreamSynchronize(ctx->stream);
       std::memset(C, 0, sizeof *C);
     }
+    return f.code;
+  }
+}
+
+int cb_spgemm_fused(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, cb_csr* C,
+                    int64_t capacity, int lanes, int* status) {
+  if (!ctx) return CB_ERR_ARG;
+  ctx->err.clear();
+  ctx->stats = cb_stats{};
+  ctx->stats.batches = 1;
+  try {
+    if (!A || !B || !C || !status) fail(ctx, CB_ERR_ARG, "null argument");
+    if (value_size(sr) == 0) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
+    check_operand(ctx, A, "A");
+    check_operand(ctx, B, "B");
+    if (A->ncols != B->nrows) fail(ctx, CB_ERR_SHAPE, "A.ncols != B.nrows");
+    if (lanes != 8 && lanes != 16 && lanes != 32) fail(ctx, CB_ERR_ARG, "lanes must be 8, 16 or 32");
+    if (B->ncols > cb::fused_max_cols(lanes))
+      fail(ctx, CB_ERR_ARG, "B.ncols beyond the fused path's column bound for these lanes");
+    if (capacity < 0 || !C->row_ptr || (capacity > 0 && (!C->col || !C->val)))
+      fail(ctx, CB_ERR_ARG, "C needs row_ptr, and col/val for capacity > 0");
+    C->nrows = A->nrows;
+    C->ncols = B->ncols;
+    C->nnz = -1;
+    run_fused(ctx, (int)sr, lanes, dev(A), dev(B), C->row_ptr, C->col, C->val, capacity, status);
+    return CB_OK;
+  } catch (const Fail& f) {
+    return f.code;
+  }
+}
+
+int64_t cb_fused_max_cols(int lanes) {
+  return (lanes == 8 || lanes == 16 || lanes == 32) ? cb::fused_max_cols(lanes) : 0;
+}
+
+int cb_fused_lanes(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, int* lanes, int64_t* flops) {
+  if (!ctx) return CB_ERR_ARG;
+  ctx->err.clear();
+  try {
+    if (!A || !B || !lanes) fail(ctx, CB_ERR_ARG, "null argument");
+    check_operand(ctx, A, "A");
+    check_operand(ctx, B, "B");
+    if (A->ncols != B->nrows) fail(ctx, CB_ERR_SHAPE, "A.ncols != B.nrows");
+    const int64_t m = A->nrows;
+    size_t need = align_up(sizeof(int64_t) * cb::kCounters) + align_up(8 * (size_t)m + 8);
+    ensure(ctx, &ctx->ws, &ctx->ws_cap, need);
+    Carver cv{static_cast<char*>(ctx->ws)};
+    int64_t* counters = cv.take<int64_t>(cb::kCounters);
+    int64_t* f = cv.take<int64_t>(m + 1);
+    CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+    if (m > 0) cb::launch_classify_sym(dev(A), dev(B), f, nullptr, counters, ctx->stream, ctx->sms);
+    CB_LAUNCHED();
+    read_counters(ctx, counters, nullptr, 0);
+    *lanes = fused_fit(ctx->host[cb::kMaxArow], ctx->host[cb::kMaxFlops], B->ncols);
+    if (flops) *flops = ctx->host[cb::kTotalFlops];
+    return CB_OK;
+  } catch (const Fail& f) {
     return f.code;
   }
 }

@@ -51,6 +51,8 @@ enum Counter {
   kError = 22,          // validation / overflow error word
   kErrDetail = 23,
   kUnsorted = 24,       // > 0 when some row of B is not non-decreasing
+  kMaxFlops = 25,       // largest flops_i (k_classify_sym)
+  kMaxArow = 26,        // longest row of A (k_classify_sym)
   kCounters = 32
 };
 
@@ -150,5 +152,16 @@ void launch_row_features(const DevCSR& A, const int64_t* flops, const int32_t* m
                          cudaStream_t s, int sms);
 void launch_mlp_predict(const void* wb, const float* master, const float* norm, const float* feat,
                         int64_t m, int64_t ncols, float* z, int64_t* pred, cudaStream_t s, int sms);
+
+// One-launch SpGEMM for products whose rows are all small (k_fused.cu):
+// every row of A holds at most `lanes` entries and every output row at most
+// 8 * lanes products (lanes = 8, 16 or 32), columns below fused_max_cols.
+// tstat holds at least fused_tiles(lanes, A.nrows) words and sync two words,
+// all zero when first used; they must not be shared by launches in flight.
+int64_t fused_tiles(int lanes, int64_t nrows);
+int64_t fused_max_cols(int lanes);
+cudaError_t launch_fused(int sr, int lanes, const DevCSR& A, const DevCSR& B, int64_t* Crp,
+                         int32_t* Ccol, void* Cval, int64_t cap, unsigned long long* tstat,
+                         int64_t tstat_cap, unsigned* sync, int* status, cudaStream_t s, int sms);
 
 }  // namespace cb

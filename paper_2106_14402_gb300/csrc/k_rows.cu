@@ -33,8 +33,13 @@ __global__ void __launch_bounds__(256) k_classify_sym(DevCSR A, DevCSR B, int64_
                                                       const uint8_t* skip, int64_t sym_hash_max) {
   __shared__ unsigned long long hist[kSymTiers];
   __shared__ unsigned long long total;
+  __shared__ long long max_f, max_a;
   if (threadIdx.x < kSymTiers) hist[threadIdx.x] = 0;
-  if (threadIdx.x == 0) total = 0;
+  if (threadIdx.x == 0) {
+    total = 0;
+    max_f = 0;
+    max_a = 0;
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -60,12 +65,18 @@ __global__ void __launch_bounds__(256) k_classify_sym(DevCSR A, DevCSR B, int64_
       atomicAdd(&hist[skip && skip[i] ? 0 : sym_tier(min((int64_t)f, row_width(A, B, i)), sym_hash_max)],
                 1ull);
       atomicAdd(&total, (unsigned long long)f);
+      atomicMax(&max_f, f);
+      atomicMax(&max_a, (long long)(a1 - a0));
     }
   }
   __syncthreads();
   if (threadIdx.x < kSymTiers && hist[threadIdx.x])
     atomicAdd((unsigned long long*)&counters[kCntSym + threadIdx.x], hist[threadIdx.x]);
-  if (threadIdx.x == 0 && total) atomicAdd((unsigned long long*)&counters[kTotalFlops], total);
+  if (threadIdx.x == 0) {
+    if (total) atomicAdd((unsigned long long*)&counters[kTotalFlops], total);
+    if (max_f) atomicMax((long long*)&counters[kMaxFlops], max_f);
+    if (max_a) atomicMax((long long*)&counters[kMaxArow], max_a);
+  }
 }
 
 struct TierBySize {

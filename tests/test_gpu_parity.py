@@ -1,7 +1,8 @@
 """Parity of the CUDA SpGEMM (called through the C ABI) with the CPU oracle.
 
-Covers every tier of the path (warp / 256-thread / 1024-thread hash teams,
-dense heavy-row slices), all five semirings, the adversarial inputs the ABI
+Covers every tier of the path (the one-launch kernel for small rows, warp /
+256-thread / 512-thread hash teams, rank windows of heavy rows), all five
+semirings, the adversarial inputs the ABI
 accepts (unsorted and duplicate columns, empty and full rows, rectangular
 shapes, explicit zeros, saturation), the edge cases (no rows, no entries,
 one column, the largest column index), the two workloads at full size, and
@@ -29,16 +30,16 @@ def cb():
     return _cb
 
 
-def run_pair(cb, sr, A, B, check=True):
+def run_pair(cb, sr, A, B, check=True, fused=True):
     dA = cb.DeviceCSR.from_host(A, sr)
     dB = dA if B is A else cb.DeviceCSR.from_host(B, sr)
-    C = cb.spgemm(sr, dA, dB, check=check)
+    C = cb.spgemm(sr, dA, dB, check=check, fused=fused)
     torch.cuda.synchronize()
     return C.to_host()
 
 
-def assert_parity(cb, sr, A, B, rows=None):
-    got = run_pair(cb, sr, A, B)
+def assert_parity(cb, sr, A, B, rows=None, fused=True):
+    got = run_pair(cb, sr, A, B, fused=fused)
     check_structure(got[0], got[1], B.ncols)
     want = oracle.spgemm(sr, A, B, rows=rows)
     return compare_rows(sr, got, want, rows=rows)
@@ -48,25 +49,27 @@ def assert_parity(cb, sr, A, B, rows=None):
 # small adversarial inputs
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("sr", SR)
 @pytest.mark.parametrize("shape", [(1, 1, 1, 1.0), (7, 5, 9, 0.5), (40, 33, 50, 0.2),
                                    (200, 150, 300, 0.05), (64, 1, 64, 0.9), (3, 100, 1, 0.3)])
-def test_small_random(cb, sr, shape):
+def test_small_random(cb, sr, shape, fused):
     m, n, k, d = shape
     A = gen.random_csr(m, n, d, seed=m * 7 + n, semiring=sr, empty_rows=0.15, full_rows=0.05)
     B = gen.random_csr(n, k, d, seed=k * 11 + n, semiring=sr, empty_rows=0.15, full_rows=0.05)
-    assert_parity(cb, sr, A, B)
+    assert_parity(cb, sr, A, B, fused=fused)
 
 
+@pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("sr", SR)
-def test_duplicates_unsorted_and_zeros(cb, sr):
+def test_duplicates_unsorted_and_zeros(cb, sr, fused):
     lo, hi = {"plus_times_i64": (-3, 3), "plus_times_f64": (-1.0, 1.0), "min_plus_u32": (0, 5),
               "or_and_bool": (0, 1), "sel2nd_min_i32": (-4, 4)}[sr]
     A = gen.random_csr(120, 90, 0.08, seed=5, semiring=sr, duplicates=True, shuffle=True,
                        empty_rows=0.1, lo=lo, hi=hi)
     B = gen.random_csr(90, 140, 0.08, seed=6, semiring=sr, duplicates=True, shuffle=True,
                        empty_rows=0.1, lo=lo, hi=hi)
-    assert_parity(cb, sr, A, B)
+    assert_parity(cb, sr, A, B, fused=fused)
 
 
 def test_wrap_and_saturation(cb):
@@ -176,9 +179,12 @@ def test_largest_column_index(cb):
 # workloads at full size
 # ---------------------------------------------------------------------------
 
-def test_er_square_bit_exact(cb):
+@pytest.mark.parametrize("fused", [True, False])
+def test_er_square_bit_exact(cb, fused):
     (sr, A, B), = gen.er_square()
-    assert_parity(cb, sr, A, B)
+    assert_parity(cb, sr, A, B, fused=fused)
+    if fused:  # validation (2) + sortedness, flops, binning (3) + the one-launch kernel
+        assert cb.context().stats()["kernels"] == 6
 
 
 @pytest.fixture(scope="module")
