@@ -6,10 +6,11 @@
 //   1. a group of G lanes takes one row; lane g loads A entry g and the
 //      bounds of B row A.col[g]; a scan over the group numbers the row's
 //      products t = 0..F-1;
-//   2. lane g forms products t = r*G + g (r = 0..7) -- the owning A entry is
-//      found by a binary search over the group's scan with shuffles -- and
-//      keeps the key (column << log2(8G)) | t in a register, the product in
-//      shared memory;
+//   2. the group's lanes read the B rows with coalesced loads and form up to
+//      8 products each (product t's A entry is t / 8 when every such B row
+//      has at most 8 entries, else a binary search over the group's scan
+//      finds it); keys (column << log2(8G)) | t and products are staged in
+//      shared memory and each lane takes 8 consecutive keys;
 //   3. the 8G keys are sorted in registers (bitonic network: in-lane stages
 //      on registers, cross-lane stages on shuffles); equal columns are then
 //      adjacent and are merged into one output entry (in t order, so FP64
@@ -65,8 +66,63 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
   return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
+// Ascending sort of the G*8 keys of a lane group, element e = g*8 + r, by a
+// bitonic network in the form where every comparator puts the minimum at the
+// lower index: each merge of two sorted halves of size k/2 starts with a
+// "flip" stage (e against e ^ (k-1)) and continues with half-cleaners
+// (e against e ^ j, j = k/4 .. 1).  Partners within a lane are registers
+// (compile-time indices), partners across lanes come by shuffle.  KSTART =
+// 2*8 skips the merges inside a lane when every lane's 8 keys are already
+// ascending.
+template <int G, int KSTART>
+__device__ __forceinline__ void bitonic_sort(unsigned (&key)[kFE], int g) {
+  constexpr int F = G * kFE;
+#pragma unroll
+  for (int k = KSTART; k <= F; k <<= 1) {
+    if (k <= kFE) {
+#pragma unroll
+      for (int r = 0; r < kFE; ++r)
+        if ((r & (k >> 1)) == 0) {
+          const int r2 = r ^ (k - 1);
+          const unsigned lo = min(key[r], key[r2]), hi = max(key[r], key[r2]);
+          key[r] = lo;
+          key[r2] = hi;
+        }
+    } else {
+      const int lm = k / kFE - 1;
+      const bool lower = (g & (k / (2 * kFE))) == 0;
+      unsigned y[kFE];
+#pragma unroll
+      for (int r = 0; r < kFE; ++r) y[r] = __shfl_xor_sync(kFull, key[kFE - 1 - r], lm);
+#pragma unroll
+      for (int r = 0; r < kFE; ++r) key[r] = lower ? min(key[r], y[r]) : max(key[r], y[r]);
+    }
+#pragma unroll
+    for (int j = k >> 2; j >= 1; j >>= 1) {
+      if (j < kFE) {
+#pragma unroll
+        for (int r = 0; r < kFE; ++r)
+          if ((r & j) == 0) {
+            const int r2 = r | j;
+            const unsigned lo = min(key[r], key[r2]), hi = max(key[r], key[r2]);
+            key[r] = lo;
+            key[r2] = hi;
+          }
+      } else {
+        const int lm = j / kFE;
+        const bool lower = (g & lm) == 0;
+#pragma unroll
+        for (int r = 0; r < kFE; ++r) {
+          const unsigned y = __shfl_xor_sync(kFull, key[r], lm);
+          key[r] = lower ? min(key[r], y) : max(key[r], y);
+        }
+      }
+    }
+  }
+}
+
 template <int SR, int G>
-__global__ void __launch_bounds__(kFThreads) k_fused(DevCSR A, DevCSR B, int64_t* __restrict__ Crp,
+__global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int64_t* __restrict__ Crp,
                                                      int32_t* __restrict__ Ccol,
                                                      typename Sem<SR>::T* __restrict__ Cval,
                                                      int64_t cap, unsigned long long* tstat,
@@ -93,9 +149,17 @@ __global__ void __launch_bounds__(kFThreads) k_fused(DevCSR A, DevCSR B, int64_t
   const T* __restrict__ Bval = reinterpret_cast<const T*>(B.val);
   Acc* sv = &sval[warp][grp * F];
   unsigned* sk = &skey[warp][grp * F];
-  if (threadIdx.x == 0) s_epoch = *reinterpret_cast<volatile unsigned*>(sync) & kEpochMask;
-  __syncthreads();
-  const unsigned long long ep = (unsigned long long)s_epoch << kEpochShift;
+  // Bank swizzles of a row's shared arrays: entry t lives at t ^ h, h < 8,
+  // chosen so that the 32 lanes of a warp storing entry 8b + r of their own
+  // block b (or reading 32 consecutive entries of one row) spread over all
+  // banks: 8-byte values over 16 bank pairs twice, 4-byte keys over 32 banks.
+  const auto pv = [grp](int t) { return t ^ (((t >> 4) | grp * (G / 2)) & 7); };
+  const auto pk = [grp](int t) { return t ^ (((t >> 5) | grp * (G / 4)) & 7); };
+  // the launch epoch is read now and shared at the first tile's publication,
+  // off the critical path of the first loads
+  unsigned epoch0 = 0;
+  if (threadIdx.x == 0) epoch0 = *reinterpret_cast<volatile unsigned*>(sync) & kEpochMask;
+  unsigned long long ep = 0;
   const int64_t ntiles = (A.nrows + TR - 1) / TR;
 
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -103,8 +167,8 @@ __global__ void __launch_bounds__(kFThreads) k_fused(DevCSR A, DevCSR B, int64_t
     const int64_t i = tile * TR + warp * RPW + grp;
     int64_t a0 = 0, a1 = 0;
     if (i < A.nrows) {
-      a0 = A.rp[i];
-      a1 = A.rp[i + 1];
+      a0 = __ldg(A.rp + i);
+      a1 = __ldg(A.rp + i + 1);
     }
     const int64_t nA = a1 - a0;
     int64_t b0 = 0;
@@ -113,10 +177,10 @@ __global__ void __launch_bounds__(kFThreads) k_fused(DevCSR A, DevCSR B, int64_t
     bool bad = nA > G;
     if (!bad && g < nA) {
       const int64_t p = a0 + g;
-      const int k = A.col[p];
-      if (S::kUsesA) av = Aval[p];
-      b0 = B.rp[k];
-      const int64_t bl = B.rp[k + 1] - b0;
+      const int k = __ldg(A.col + p);
+      if (S::kUsesA) av = __ldg(Aval + p);
+      b0 = __ldg(B.rp + k);
+      const int64_t bl = __ldg(B.rp + k + 1) - b0;
       len = bl > F ? F + 1 : (int)bl;
     }
     int incl = len;
@@ -130,60 +194,62 @@ __global__ void __launch_bounds__(kFThreads) k_fused(DevCSR A, DevCSR B, int64_t
     bad = bad || Fr > F;
     if (bad) Fr = 0;
 
-    // ---- 2. products: lane g takes t = r*G + g
-    unsigned key[kFE];
+    // ---- 2. products, numbered t < 8G and formed by lanes that read B rows
+    // with coalesced loads (lane g, register r takes slot r*G + g).  Fast form
+    // (every entry's B row holds <= 8 entries): t = entry*8 + element, so the
+    // slot needs no search.  General form: t is the product's rank in the row
+    // and a binary search over the group's scan finds its A entry.  Keys
+    // (column << log2(8G) | t) and products go to shared memory; lane g then
+    // takes keys g*8 .. g*8+7 (entry g's B row in the fast form, already
+    // ascending when B's rows are sorted).
+    const bool fast = __all_sync(kFull, bad || len <= kFE);
 #pragma unroll
     for (int r = 0; r < kFE; ++r) {
       const int t = r * G + g;
-      int m = 0;  // largest lane with o_m <= t: the entry that owns product t
+      int m, first;
+      bool valid;
+      if (fast) {
+        m = t >> 3;
+        first = t & ~7;
+        const int lm = __shfl_sync(kFull, len, m, G);  // every lane shuffles
+        valid = !bad && (t & 7) < lm;
+      } else {
+        m = 0;  // largest lane with o_m <= t: the entry that owns product t
 #pragma unroll
-      for (int s = G / 2; s >= 1; s >>= 1) {
-        const int om = __shfl_sync(kFull, o, m + s, G);
-        if (om <= t) m += s;
+        for (int s2 = G / 2; s2 >= 1; s2 >>= 1) {
+          const int om = __shfl_sync(kFull, o, m + s2, G);
+          if (om <= t) m += s2;
+        }
+        first = __shfl_sync(kFull, o, m, G);
+        valid = t < Fr;
       }
-      const int om = __shfl_sync(kFull, o, m, G);
       const int64_t bq = __shfl_sync(kFull, b0, m, G);
       const T a = S::kUsesA ? shfl_idx(av, m, G) : T();
-      key[r] = kFPad;
-      if (t < Fr) {
-        const int64_t q = bq + (t - om);
-        key[r] = ((unsigned)B.col[q] << LOGF) | (unsigned)t;
-        sv[t] = S::mul(a, Bval[q]);
+      unsigned kt = kFPad;
+      if (valid) {
+        const int64_t q = bq + (t - first);
+        kt = ((unsigned)__ldg(B.col + q) << LOGF) | (unsigned)t;
+        sv[pv(t)] = S::mul(a, __ldg(Bval + q));
       }
+      sk[pk(t)] = kt;
     }
+    __syncwarp();
+    unsigned key[kFE];
+#pragma unroll
+    for (int r = 0; r < kFE; ++r) key[r] = sk[pk(g * kFE + r)];
 
-    // ---- 3. sort the row's keys: element e = g*8 + r of a bitonic network
+    // ---- 3. sort the row's keys (lanes whose 8 keys are already ascending --
+    // sorted B rows in the fast form -- skip the in-lane merges)
+    bool run_sorted = true;
 #pragma unroll
-    for (int k = 2; k <= F; k <<= 1) {
-#pragma unroll
-      for (int j = k >> 1; j >= 1; j >>= 1) {
-        if (j >= kFE) {
-          const int lm = j / kFE;
-          const bool asc = ((g * kFE) & k) == 0;
-          const bool keep_min = ((g & lm) == 0) == asc;
-#pragma unroll
-          for (int r = 0; r < kFE; ++r) {
-            const unsigned y = __shfl_xor_sync(kFull, key[r], lm);
-            key[r] = keep_min ? min(key[r], y) : max(key[r], y);
-          }
-        } else {
-#pragma unroll
-          for (int r = 0; r < kFE; ++r) {
-            if ((r & j) == 0) {
-              const int r2 = r | j;
-              const bool asc = k >= kFE ? ((g * kFE) & k) == 0 : (r & k) == 0;
-              const unsigned lo = min(key[r], key[r2]), hi = max(key[r], key[r2]);
-              key[r] = asc ? lo : hi;
-              key[r2] = asc ? hi : lo;
-            }
-          }
-        }
-      }
-    }
+    for (int r = 0; r + 1 < kFE; ++r) run_sorted = run_sorted && key[r] <= key[r + 1];
+    if (__all_sync(kFull, run_sorted)) bitonic_sort<G, 2 * kFE>(key, g);
+    else bitonic_sort<G, 2>(key, g);
 
     // merge equal columns: a head is the first key of its column
-    reinterpret_cast<uint4*>(sk)[g * 2] = make_uint4(key[0], key[1], key[2], key[3]);
-    reinterpret_cast<uint4*>(sk)[g * 2 + 1] = make_uint4(key[4], key[5], key[6], key[7]);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < kFE; ++r) sk[pk(g * kFE + r)] = key[r];
     const unsigned prev_last = __shfl_up_sync(kFull, key[kFE - 1], 1, G);
     const unsigned next_first = __shfl_down_sync(kFull, key[0], 1, G);
     __syncwarp();
@@ -209,13 +275,13 @@ __global__ void __launch_bounds__(kFThreads) k_fused(DevCSR A, DevCSR B, int64_t
       hv[r] = S::ident();
       if (heads & (1u << r)) {
         const unsigned c = key[r] >> LOGF;
-        Acc v = sv[key[r] & (F - 1)];
+        Acc v = sv[pv(key[r] & (F - 1))];
         const unsigned nc = (r + 1 < kFE ? key[r + 1 < kFE ? r + 1 : r] : next_first) >> LOGF;
         if (nc == c && (r + 1 < kFE || g + 1 < G)) {  // a run of equal columns: walk it
           for (int e2 = g * kFE + r + 1; e2 < F; ++e2) {
-            const unsigned k2 = sk[e2];
+            const unsigned k2 = sk[pk(e2)];
             if ((k2 >> LOGF) != c) break;
-            v = S::add(v, sv[k2 & (F - 1)]);
+            v = S::add(v, sv[pv(k2 & (F - 1))]);
           }
         }
         hv[r] = v;
@@ -227,15 +293,17 @@ __global__ void __launch_bounds__(kFThreads) k_fused(DevCSR A, DevCSR B, int64_t
 #pragma unroll
       for (int r = 0; r < kFE; ++r) {
         if (heads & (1u << r)) {
-          sk[p] = key[r] >> LOGF;
-          sv[p] = hv[r];
+          sk[pk(p)] = key[r] >> LOGF;
+          sv[pv(p)] = hv[r];
           ++p;
         }
       }
     }
     if (g == 0) snz[warp * RPW + grp] = bad ? 0 : nz;
     if (bad && g == 0 && i < A.nrows) atomicOr(status, CB_FUSED_ROW_TOO_LARGE);
+    if (threadIdx.x == 0 && tile == blockIdx.x) s_epoch = epoch0;
     __syncthreads();
+    ep = (unsigned long long)s_epoch << kEpochShift;
 
     // ---- 4. tile offsets, publish, look back
     if (warp == 0) {
@@ -271,6 +339,7 @@ __global__ void __launch_bounds__(kFThreads) k_fused(DevCSR A, DevCSR B, int64_t
             w = ep | kKindInc;
             break;
           }
+          __nanosleep(40);  // leave issue slots to the CTAs still computing
         }
         inc_here = (w & kKindMask) == kKindInc;
         val = (long long)(w & kValMask);
@@ -317,8 +386,8 @@ __global__ void __launch_bounds__(kFThreads) k_fused(DevCSR A, DevCSR B, int64_t
         const unsigned* rk = &skey[warp][rr * F];
         const Acc* rv = &sval[warp][rr * F];
         for (int t = lane; t < n; t += 32) {
-          Ccol[off + t] = (int32_t)rk[t];
-          Cval[off + t] = S::out(rv[t]);
+          Ccol[off + t] = (int32_t)rk[t ^ (((t >> 5) | rr * (G / 4)) & 7)];
+          Cval[off + t] = S::out(rv[t ^ (((t >> 4) | rr * (G / 2)) & 7)]);
         }
       }
     }
