@@ -304,7 +304,7 @@ def main_gpu(args):
 
     legs = {}
     if not args.no_legs:
-        legs = run_legs(args, cb, ctx, dprob, flush, ms_step, products)
+        legs = run_legs(args, cb, ctx, dprob, flush, ms_step, products, dev, peak, peak_src)
         legs["one_launch_er16k"] = run_one_launch(args, cb, ctx, flush, dev, peak, peak_src)
 
     e2e = None
@@ -365,7 +365,7 @@ def timed(fn, steps, flush):
     return sum(times) / len(times)
 
 
-def run_legs(args, cb, ctx, dprob, flush, plain_ms, products):
+def run_legs(args, cb, ctx, dprob, flush, plain_ms, products, dev, peak, peak_src):
     """Learned sizing and column batching on the same workload, timed like the main loop."""
     model, src = load_sizer(cb)
     out = {}
@@ -407,6 +407,8 @@ def run_legs(args, cb, ctx, dprob, flush, plain_ms, products):
     out["column_batched"] = res
     if not args.no_multi:
         out["multi_spgemm"] = run_multi(args, cb, ctx, model)
+    if not args.no_full:
+        out["memory_constrained"] = run_full_configs(args, cb, ctx, flush, model, dev, peak, peak_src)
     return out
 
 
@@ -444,6 +446,31 @@ def run_one_launch(args, cb, ctx, flush, dev, peak, peak_src):
     ms_auto = timed(auto, steps, flush)
     nbytes = compulsory_bytes(sr, A, A, nnz, A.nrows)
     achieved = nbytes / (ms * 1e-3) / 1e9
+
+    # warm: inputs and output L2-resident, 100 launches per CUDA graph replay
+    gctx = cb.Context(torch.cuda.Stream(device=dev))
+    with torch.cuda.stream(gctx.stream):
+        fused_g = lambda: cb.spgemm_fused(sr, dA, dA, out, status, lanes=lanes, ctx=gctx)  # noqa: E731
+        fused_g()
+        gctx.stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        per_graph = 100
+        with torch.cuda.graph(graph, stream=gctx.stream):
+            for _ in range(per_graph):
+                fused_g()
+        graph.replay()
+        gctx.stream.synchronize()
+        reps = 10
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(gctx.stream)
+        for _ in range(reps):
+            graph.replay()
+        e1.record(gctx.stream)
+        e1.synchronize()
+        ms_warm = e0.elapsed_time(e1) / (reps * per_graph)
+    assert int(status.item()) == 0, "one-launch SpGEMM reported an error in graph replay"
+    achieved_warm = nbytes / (ms_warm * 1e-3) / 1e9
     return {"workload": "ER n=16384, 8 distinct cols/row, (+,x) int64 U{1..10}; C=A.A",
             "lanes": lanes, "products": flops, "nnz_c": nnz,
             "us_per_call": round(ms * 1e3, 3), "products_per_s": flops / (ms * 1e-3),
@@ -456,7 +483,73 @@ def run_one_launch(args, cb, ctx, flush, dev, peak, peak_src):
                          "peak_source": peak_src, "algorithmic_bytes": nbytes,
                          "note": "bytes = A + B rows touched + C; B is A here, so A's "
                                  "bytes are counted twice"},
+            "warm_graph": {"us_per_call": round(ms_warm * 1e3, 3), "launches": reps * per_graph,
+                           "achieved_gbs": round(achieved_warm, 1),
+                           "frac": round(achieved_warm / peak, 4),
+                           "l2": "inputs and output L2-resident (no flush), 100 launches per "
+                                 "CUDA graph replay"},
             "l2": "flushed before every timed call", "steps": steps}
+
+
+def run_full_configs(args, cb, ctx, flush, model, dev, peak, peak_src):
+    """The two memory-constrained workloads, formed in column batches under a
+    24 GB output budget with exact and with learned sizing (batch count and
+    per-batch sizing), plus the sizing step alone on the held-out product."""
+    import torch
+    from paper_2106_14402_gb300 import gen, sizer
+    budget = 24 * 10**9
+    out = {}
+    for name, make in (("rmat21_fp64_colbatch", gen.rmat_column_batched),
+                       ("rmat20_ef32_sel2nd_held_out", gen.rmat_held_out)):
+        (sr, A, B), = make()
+        dA = cb.DeviceCSR.from_host(A, sr, dev)
+        dB = dA if B is A else cb.DeviceCSR.from_host(B, sr, dev)
+        res = {"semiring": sr, "nrows": A.nrows, "nnz_a": A.nnz, "budget_bytes": budget}
+        for mode in ("exact", "learned"):
+            info = {}
+
+            def run():
+                info.update(cb.spgemm_column_batches(
+                    sr, dA, dB, budget, lambda *a: False, validate=False, sizing=mode,
+                    mlp=model if mode == "learned" else None, ctx=ctx))
+
+            run()
+            ms = timed(run, max(1, min(args.steps, 2)), flush)
+            b = info["batches"]
+            v = VAL_BYTES[sr]
+            a_bytes = 8 * (A.nrows + 1) + A.nnz * (4 + v)
+            b_bytes = 8 * (B.nrows + 1) + B.nnz * (4 + v)
+            c_bytes = 8 * (A.nrows + 1) * b + info["nnz_total"] * (4 + v)
+            nbytes = b * a_bytes + b_bytes + c_bytes
+            res[mode] = {"ms": ms, "batches": b, "products": info["flops"], "nnz_c": info["nnz_total"],
+                         "products_per_s": info["flops"] / (ms * 1e-3),
+                         "nnz_per_s": info["nnz_total"] / (ms * 1e-3),
+                         "roofline_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
+                         "algorithmic_bytes": nbytes}
+        res["learned_vs_exact"] = res["exact"]["ms"] / res["learned"]["ms"]
+        res["peak_gbs"] = peak
+        res["peak_source"] = peak_src
+        if name.startswith("rmat20"):
+            def sizing_learned():
+                model.predict(cb.row_features(dA, dB, ctx=ctx), B.ncols, ctx=ctx)
+
+            def sizing_exact():
+                cb.row_nnz(dA, dB, ctx=ctx)
+
+            sizing_learned()
+            sizing_exact()
+            ms_l = timed(sizing_learned, 3, flush)
+            ms_e = timed(sizing_exact, 3, flush)
+            feat = cb.row_features(dA, dB, ctx=ctx)
+            lab = cb.row_nnz(dA, dB, ctx=ctx)
+            keep = lab > 0
+            res["sizing_step"] = {"features_plus_mlp_ms": ms_l, "exact_symbolic_ms": ms_e,
+                                  "speedup": ms_e / ms_l,
+                                  "prediction": sizer.evaluate(model, feat[keep], lab[keep], B.ncols)}
+        out[name] = res
+        del dA, dB
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_multi(args, cb, ctx, model):
@@ -586,6 +679,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-legs", action="store_true")
     ap.add_argument("--no-multi", action="store_true")
+    ap.add_argument("--no-full", action="store_true", help="skip the memory-constrained R-MAT workloads")
     ap.add_argument("--multi-count", type=int, default=4096)
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     args = ap.parse_args()

@@ -204,10 +204,14 @@ int cb_exclusive_scan(cb_ctx *ctx, const int64_t *in, int64_t n, int64_t *out);
  * Paper Sec. 5 (optimizations): the GPU path estimates the output's memory
  * needs with approximate algorithms instead of an exact symbolic pass; Sec.
  * 7.4 sizes batched SpGEMM from such a step.  Here the estimate is a small
- * MLP over three row features f_i = (nnz(A_i), flops_i, max_p nnz(B_p)):
- *   x = bf16((log2(1 + f) - mu) / sigma); h1 = bf16(relu(W1 x + b1));
+ * MLP over three row features f_i = (nnz(A_i), flops_i, max_p nnz(B_p)),
+ * the last two taken relative to the row's output width w_i (B's column
+ * count), which lets one network serve products of any size:
+ *   l = (log2(1 + f_0), log2(1 + f_1) - log2 w_i, log2(1 + f_2) - log2 w_i);
+ *   x = bf16((l - mu) / sigma); h1 = bf16(relu(W1 x + b1));
  *   h2 = bf16(relu(W2 h1 + b2)); z = w3 . h2 + b3;
- *   pred_i = clamp(ceil(sigmoid(z) * flops_i), maxB_i, min(flops_i, ncols)).
+ *   pred_i = clamp(ceil(sigmoid(z) * flops_i), maxB_i, min(flops_i, w_i)).
+ * A feature row is CB_MLP_NFEAT floats: nnz(A_i), flops_i, maxB_i, w_i.
  * Weights are used as bf16 copies of fp32 master weights, products are
  * accumulated in fp32.  Parameters are one fp32 vector of CB_MLP_NPARAM
  * values laid out W1[64][3], b1[64], W2[64][64], b2[64], w3[64], b3[1];
@@ -215,17 +219,19 @@ int cb_exclusive_scan(cb_ctx *ctx, const int64_t *in, int64_t n, int64_t *out);
  * was current when it was created. */
 #define CB_MLP_HIDDEN 64
 #define CB_MLP_NPARAM 4481
+#define CB_MLP_NFEAT 4
 /* Create from host parameters and normalisation (copied); CB_ERR_OOM/CUDA. */
 int cb_mlp_create(cb_mlp **out, const float *params, const float *norm);
 void cb_mlp_destroy(cb_mlp *m);
 /* Copy the fp32 master parameters, the normalisation and the Adam step
  * count back to host memory (checkpointing); any output may be NULL. */
 int cb_mlp_get(const cb_mlp *m, float *params, float *norm, int64_t *step);
-/* Raw features of every row of A.B: feat[3*i + 0..2] = (nnz(A_i), flops_i,
- * maxB_i) as floats (device float[3*m]). */
+/* Raw features of every row of A.B: feat[4*i + 0..3] = (nnz(A_i), flops_i,
+ * maxB_i, B->ncols) as floats (device float[4*m]). */
 int cb_row_features(cb_ctx *ctx, const cb_csr *A, const cb_csr *B, float *feat);
 /* K8: logits z[i] and sizes pred[i] for nrows feature rows (device; either
- * output may be NULL); ncols is the width that caps the sizes. */
+ * output may be NULL); ncols > 0 caps the sizes further (0: only each row's
+ * own width). */
 int cb_mlp_predict(cb_ctx *ctx, const cb_mlp *m, const float *feat, int64_t nrows, int64_t ncols,
                    float *z, int64_t *pred);
 /* K9: mean pinball-loss gradient (quantile tau) over rows with flops > 0

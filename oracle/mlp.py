@@ -8,11 +8,14 @@ SpGEMM strong-scaling figure).  The predictor here is that approximate estimator
 fixes none of its details; this file is the plain statement of the reading
 used (every step written out in numpy float64):
 
-  features  f_i = (nnz(A(i,:)), flops_i, max_p nnz(B(p,:)))
-  inputs    x_i = (log2(1 + f_i) - mu) / sigma
+  features  f_i = (nnz(A(i,:)), flops_i, max_p nnz(B(p,:))), w_i = ncols(B)
+  inputs    l_i = (log2(1 + f_i0), log2(1 + f_i1) - log2 w_i, log2(1 + f_i2) - log2 w_i)
+            x_i = (l_i - mu) / sigma
+            (the last two features relative to the output width, so that one
+            network serves products of any size)
   network   h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), z = w3 . h2 + b3
   ratio     rho_i = sigmoid(z_i)             (predicted nnz(C_i) / flops_i)
-  size      pred_i = clamp(ceil(rho_i * flops_i), maxB_i, min(flops_i, ncols))
+  size      pred_i = clamp(ceil(rho_i * flops_i), maxB_i, min(flops_i, w_i))
   loss      e_i = log2(nnz_i / flops_i) - log2(rho_i)
             L = mean_i  tau * e_i          if e_i >= 0   (under-prediction)
                         (tau - 1) * e_i    otherwise     (over-prediction)
@@ -42,10 +45,12 @@ def init_params(seed: int = 0, hidden: int = HIDDEN) -> dict:
     }
 
 
-def raw_features(nnz_a, flops, maxb) -> np.ndarray:
+def raw_features(nnz_a, flops, maxb, width) -> np.ndarray:
+    """The network's inputs before standardisation (one row per output row)."""
+    lw = np.log2(np.maximum(np.asarray(width, dtype=np.float64), 1.0))
     return np.stack([np.log2(1.0 + np.asarray(nnz_a, dtype=np.float64)),
-                     np.log2(1.0 + np.asarray(flops, dtype=np.float64)),
-                     np.log2(1.0 + np.asarray(maxb, dtype=np.float64))], axis=1)
+                     np.log2(1.0 + np.asarray(flops, dtype=np.float64)) - lw,
+                     np.log2(1.0 + np.asarray(maxb, dtype=np.float64)) - lw], axis=1)
 
 
 def standardise(F: np.ndarray, mu: np.ndarray, sigma: np.ndarray) -> np.ndarray:
@@ -101,8 +106,9 @@ def backward(p: dict, cache, dz: np.ndarray) -> dict:
     return g
 
 
-def predict_sizes(z: np.ndarray, flops, maxb, ncols: int) -> np.ndarray:
-    """Integer per-row size: ceil(sigmoid(z) * flops) clamped to [maxB, min(flops, ncols)]."""
+def predict_sizes(z: np.ndarray, flops, maxb, ncols) -> np.ndarray:
+    """Integer per-row size: ceil(sigmoid(z) * flops) clamped to [maxB, min(flops, ncols)]
+    (ncols: the output width, one value or one per row)."""
     flops = np.asarray(flops, dtype=np.int64)
     maxb = np.asarray(maxb, dtype=np.int64)
     est = np.ceil(sigmoid(z) * flops.astype(np.float64)).astype(np.int64)

@@ -469,6 +469,7 @@ def spgemm_column_batches(semiring: str, A: DeviceCSR, B: DeviceCSR, budget_byte
 # ---------------------------------------------------------------------------
 
 MLP_NPARAM = 4481
+MLP_NFEAT = 4
 
 
 def _ptr_or_none(t):
@@ -505,7 +506,14 @@ class MLP:
             raise CBError(rc, "cb_mlp_get failed")
         return p, nrm, step.value
 
+    @staticmethod
+    def _check_feat(feat):
+        if feat.dim() != 2 or feat.shape[1] != MLP_NFEAT or feat.dtype != torch.float32 \
+                or not feat.is_contiguous():
+            raise ValueError(f"features must be a contiguous float32 [m, {MLP_NFEAT}] tensor")
+
     def predict(self, feat: torch.Tensor, ncols: int, ctx: Context | None = None):
+        self._check_feat(feat)
         ctx = ctx or context()
         m = feat.shape[0]
         z = torch.empty(m, dtype=torch.float32, device=feat.device)
@@ -517,6 +525,7 @@ class MLP:
 
     def grad(self, feat: torch.Tensor, nnz: torch.Tensor, tau: float = 0.9,
              ctx: Context | None = None):
+        self._check_feat(feat)
         ctx = ctx or context()
         g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=feat.device)
         loss = torch.empty(1, dtype=torch.float32, device=feat.device)
@@ -527,6 +536,7 @@ class MLP:
 
     def train(self, feat: torch.Tensor, nnz: torch.Tensor, epochs: int, batch: int, lr: float,
               tau: float = 0.9, ctx: Context | None = None):
+        self._check_feat(feat)
         ctx = ctx or context()
         losses = np.zeros(max(epochs, 1), np.float32)
         ctx.check(self.lib.cb_mlp_train(ctx.handle, self.handle, c_void_p(feat.data_ptr()),
@@ -536,9 +546,10 @@ class MLP:
 
 
 def row_features(A: DeviceCSR, B: DeviceCSR, ctx: Context | None = None) -> torch.Tensor:
-    """Raw per-row features (nnz(A_i), flops_i, maxB_i) as a float32 [m, 3] device tensor."""
+    """Raw per-row features (nnz(A_i), flops_i, maxB_i, output width) as a
+    float32 [m, 4] device tensor."""
     ctx = ctx or context()
-    feat = torch.empty((A.nrows, 3), dtype=torch.float32, device=A.row_ptr.device)
+    feat = torch.empty((A.nrows, 4), dtype=torch.float32, device=A.row_ptr.device)
     sa, sb = A.as_struct(), B.as_struct()
     ctx.check(ctx.lib.cb_row_features(ctx.handle, ctypes.byref(sa), ctypes.byref(sb),
                                       c_void_p(feat.data_ptr())))

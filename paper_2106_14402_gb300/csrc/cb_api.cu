@@ -440,7 +440,7 @@ void spgemm_learned(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int6
   dA.rcols = a_rcols;
   DevBuf work(ctx);
   const size_t nm = (size_t)m + 1;
-  const size_t bytes = align_up(8 * nm) * 5 + align_up(4 * nm) * 2 + align_up(12 * nm) + align_up(nm) +
+  const size_t bytes = align_up(8 * nm) * 5 + align_up(4 * nm) * 2 + align_up(16 * nm) + align_up(nm) +
                        align_up(8 * (size_t)cb::kCounters) + align_up(8 * (size_t)cb::scan_partials(m));
   work.alloc(bytes);
   Carver cv{work.as<char>()};
@@ -451,7 +451,7 @@ void spgemm_learned(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int6
   int64_t* cnt = cv.take<int64_t>(nm);
   int32_t* maxb = cv.take<int32_t>(nm);
   int32_t* perm = cv.take<int32_t>(nm);
-  float* feat = cv.take<float>(3 * nm);
+  float* feat = cv.take<float>(CB_MLP_NFEAT * nm);
   uint8_t* learned = cv.take<uint8_t>(nm);
   int64_t* counters = cv.take<int64_t>(cb::kCounters);
   int64_t* partial = cv.take<int64_t>(cb::scan_partials(m));
@@ -460,7 +460,7 @@ void spgemm_learned(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int6
   cb::launch_classify_sym(dA, dB, flops, maxb, counters, ctx->stream, ctx->sms);
   const bool use_mlp = opt.sizing == CB_SIZING_LEARNED;
   if (use_mlp) {
-    cb::launch_row_features(dA, flops, maxb, feat, ctx->stream, ctx->sms);
+    cb::launch_row_features(dA, flops, maxb, ncols, feat, ctx->stream, ctx->sms);
     cb::launch_mlp_predict(cb::mlp_bf16(opt.mlp), cb::mlp_master(opt.mlp), cb::mlp_norm(opt.mlp),
                            feat, m, ncols, nullptr, pred, ctx->stream, ctx->sms);
   }
@@ -556,8 +556,10 @@ int64_t total_of(cb_ctx* ctx, const int64_t* in, int64_t n) {
 // Column-batched SpGEMM (paper Sec. 7.2; batch count from a symbolic step,
 // Sec. 7.4): C is formed in contiguous column ranges whose output
 // (row_ptr + col + val) fits opt.budget_bytes, each handed to on_batch.
-// The batch count comes from the exact symbolic total; ranges are equal in
-// width and a range whose output still exceeds the budget is halved.  When
+// With exact sizing the batch count comes from the exact symbolic total and
+// ranges are equal in width; with learned sizing the predicted total sets
+// the first range and the density seen so far the later ones.  A range whose
+// output still exceeds the budget is halved.  When
 // B's rows are sorted each batch reads only its slab of every B row (slab
 // offsets found by search); otherwise batches filter whole rows.
 void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_csr* C,
@@ -591,23 +593,24 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
   if (opt.sizing == CB_SIZING_LEARNED) {
     ensure(ctx, &ctx->ws, &ctx->ws_cap,
            align_up(sizeof(int64_t) * cb::kCounters) + align_up(8 * (size_t)(m + 1)) +
-               align_up(4 * (size_t)(m + 1)) + align_up(12 * (size_t)(m + 1)));
+               align_up(4 * (size_t)(m + 1)) + align_up(16 * (size_t)(m + 1)));
     Carver cv{static_cast<char*>(ctx->ws)};
     int64_t* counters = cv.take<int64_t>(cb::kCounters);
     int64_t* flops = cv.take<int64_t>(m + 1);
     int32_t* maxb = cv.take<int32_t>(m + 1);
-    float* feat = cv.take<float>(3 * (m + 1));
+    float* feat = cv.take<float>(CB_MLP_NFEAT * (m + 1));
     CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
     cb::launch_check_sorted(dBfull, counters, ctx->stream, ctx->sms);
     cb::launch_classify_sym(dA, dBfull, flops, maxb, counters, ctx->stream, ctx->sms);
-    cb::launch_row_features(dA, flops, maxb, feat, ctx->stream, ctx->sms);
+    cb::launch_row_features(dA, flops, maxb, k, feat, ctx->stream, ctx->sms);
     cb::launch_mlp_predict(cb::mlp_bf16(opt.mlp), cb::mlp_master(opt.mlp), cb::mlp_norm(opt.mlp),
                            feat, m, k, nullptr, rownnz.as<int64_t>(), ctx->stream, ctx->sms);
     CB_LAUNCHED();
     ctx->stats.kernels += 4;
-    total = total_of(ctx, rownnz.as<int64_t>(), m);  // synchronises
+    read_counters(ctx, counters, nullptr, 0);  // synchronises
     b_sorted = ctx->host[cb::kUnsorted] == 0 ? 1 : 0;
     ctx->stats.flops = ctx->host[cb::kTotalFlops];
+    total = total_of(ctx, rownnz.as<int64_t>(), m);  // synchronises
     total = (int64_t)((double)total * (1.0 + (double)opt.margin));
   } else {
     count_rows(ctx, dA, dBfull, rownnz.as<int64_t>());
@@ -643,11 +646,28 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
     ctx->stats.kernels += 1;
     return pos->as<int64_t>();
   };
+  // Exact sizing: nb equal ranges up front.  Learned sizing: ranges are cut
+  // as the batches go, the first from the predicted total, every later one
+  // from the output density (entries per column) the finished batches
+  // showed, aiming at kFill of the budget, so that the predictor's bias
+  // costs neither extra batches nor overflowing ones.
+  constexpr double kFill = 0.9;
+  const bool adaptive = opt.sizing == CB_SIZING_LEARNED;
   std::deque<Range> todo;
-  const int64_t* pos = b_sorted ? slabs_for(bnd) : nullptr;
-  for (int64_t j = 0; j < nb; ++j)
-    todo.push_back(Range{bnd[(size_t)j], bnd[(size_t)j + 1], pos ? pos + (size_t)j * n : nullptr,
-                         pos ? pos + (size_t)(j + 1) * n : nullptr});
+  int64_t next_lo = k;
+  const int64_t* next_plo = nullptr;
+  double width = 0.0;
+  if (!adaptive) {
+    const int64_t* pos = b_sorted ? slabs_for(bnd) : nullptr;
+    for (int64_t j = 0; j < nb; ++j)
+      todo.push_back(Range{bnd[(size_t)j], bnd[(size_t)j + 1], pos ? pos + (size_t)j * n : nullptr,
+                           pos ? pos + (size_t)(j + 1) * n : nullptr});
+  } else {
+    next_lo = 0;
+    next_plo = b_sorted ? slabs_for(std::vector<int64_t>{0}) : nullptr;
+    width = (double)k * kFill * (double)cap / (double)std::max<int64_t>(total, 1);
+  }
+  int64_t done_cols = 0, done_nnz = 0;
 
   cb_opts inner = opt;
   inner.validate = 0;
@@ -655,7 +675,16 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
   inner.out_capacity = cap;
   int64_t nnz_sum = 0, batch = 0;
   int kernels = ctx->stats.kernels;
-  while (!todo.empty()) {
+  for (;;) {
+    if (todo.empty()) {
+      if (next_lo >= k) break;
+      const int64_t w = std::max<int64_t>(1, (int64_t)std::min(width, (double)k));
+      const int64_t hi = std::min<int64_t>(k, next_lo + w);
+      const int64_t* phi = b_sorted ? slabs_for(std::vector<int64_t>{hi}) : nullptr;
+      todo.push_back(Range{next_lo, hi, next_plo, phi});
+      next_lo = hi;
+      next_plo = phi;
+    }
     const Range r = todo.front();
     todo.pop_front();
     DevCSR view = dBfull;
@@ -686,6 +715,10 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
     }
     kernels += ctx->stats.kernels;
     nnz_sum += Cb.nnz;
+    done_cols += r.hi - r.lo;
+    done_nnz += Cb.nnz;
+    if (adaptive)
+      width = done_nnz > 0 ? kFill * (double)cap * (double)done_cols / (double)done_nnz : (double)k;
     CB_CUDA(cudaStreamSynchronize(ctx->stream));
     const int stop = opt.on_batch((int)batch, r.lo, r.hi, &Cb, opt.user);
     ++batch;
@@ -715,15 +748,15 @@ void row_group_sums(cb_ctx* ctx, const cb_csr* A, const DevCSR& dB, const cb_opt
   if (opt.sizing == CB_SIZING_LEARNED) {
     ensure(ctx, &ctx->ws, &ctx->ws_cap,
            align_up(sizeof(int64_t) * cb::kCounters) + align_up(8 * (size_t)(m + 1)) +
-               align_up(4 * (size_t)(m + 1)) + align_up(12 * (size_t)(m + 1)));
+               align_up(4 * (size_t)(m + 1)) + align_up(16 * (size_t)(m + 1)));
     Carver cv{static_cast<char*>(ctx->ws)};
     int64_t* counters = cv.take<int64_t>(cb::kCounters);
     int64_t* flops = cv.take<int64_t>(m + 1);
     int32_t* maxb = cv.take<int32_t>(m + 1);
-    float* feat = cv.take<float>(3 * (m + 1));
+    float* feat = cv.take<float>(CB_MLP_NFEAT * (m + 1));
     CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
     cb::launch_classify_sym(dA, dB, flops, maxb, counters, ctx->stream, ctx->sms);
-    cb::launch_row_features(dA, flops, maxb, feat, ctx->stream, ctx->sms);
+    cb::launch_row_features(dA, flops, maxb, dB.ncols, feat, ctx->stream, ctx->sms);
     cb::launch_mlp_predict(cb::mlp_bf16(opt.mlp), cb::mlp_master(opt.mlp), cb::mlp_norm(opt.mlp),
                            feat, m, dB.ncols, nullptr, rows.as<int64_t>(), ctx->stream, ctx->sms);
   } else {
@@ -884,7 +917,7 @@ int cb_row_features(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, float* feat) 
     const int64_t m = A->nrows;
     if (m == 0) return CB_OK;
     size_t need = align_up(sizeof(int64_t) * cb::kCounters) + align_up(8 * (size_t)m + 8) +
-                  align_up(4 * (size_t)m + 4);
+                  align_up(4 * (size_t)m + 4);  // feat is the caller's
     ensure(ctx, &ctx->ws, &ctx->ws_cap, need);
     Carver cv{static_cast<char*>(ctx->ws)};
     int64_t* counters = cv.take<int64_t>(cb::kCounters);
@@ -892,7 +925,7 @@ int cb_row_features(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, float* feat) 
     int32_t* maxb = cv.take<int32_t>(m + 1);
     CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
     cb::launch_classify_sym(dev(A), dev(B), flops, maxb, counters, ctx->stream, ctx->sms);
-    cb::launch_row_features(dev(A), flops, maxb, feat, ctx->stream, ctx->sms);
+    cb::launch_row_features(dev(A), flops, maxb, B->ncols, feat, ctx->stream, ctx->sms);
     CB_LAUNCHED();
     return CB_OK;
   } catch (const Fail& f) {

@@ -148,8 +148,8 @@ void launch_stack(const void* parts_dev, int nparts, int vsz, int64_t* rp_out, i
 const void* mlp_bf16(const cb_mlp* m);
 const float* mlp_master(const cb_mlp* m);
 const float* mlp_norm(const cb_mlp* m);
-void launch_row_features(const DevCSR& A, const int64_t* flops, const int32_t* maxb, float* feat,
-                         cudaStream_t s, int sms);
+void launch_row_features(const DevCSR& A, const int64_t* flops, const int32_t* maxb, int64_t ncols,
+                         float* feat, cudaStream_t s, int sms);
 void launch_mlp_predict(const void* wb, const float* master, const float* norm, const float* feat,
                         int64_t m, int64_t ncols, float* z, int64_t* pred, cudaStream_t s, int sms);
 

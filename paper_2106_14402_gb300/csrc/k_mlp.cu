@@ -3,12 +3,16 @@
 // symbolic pass; Sec. 7.4: the batch count of batched SpGEMM comes from
 // such an estimate).
 //
-// Model: 3 -> 64 -> 64 -> 1 MLP over the row features (nnz(A_i), flops_i,
-// max_p nnz(B_p)):
-//   x  = bf16((log2(1 + f) - mu) / sigma)
+// Model: 3 -> 64 -> 64 -> 1 MLP over the row features f = (nnz(A_i), flops_i,
+// max_p nnz(B_p)), the last two taken relative to the row's output width w_i
+// (the column count of B), so that the same network serves products of any
+// size:
+//   l  = (log2(1 + f_0), log2(1 + f_1) - log2(w_i), log2(1 + f_2) - log2(w_i))
+//   x  = bf16((l - mu) / sigma)
 //   h1 = bf16(relu(W1 x + b1)),  h2 = bf16(relu(W2 h1 + b2)),  z = w3 . h2 + b3
 //   rho = sigmoid(z) ~ nnz(C_i) / flops_i,
-//   pred = clamp(ceil(rho * flops_i), maxB_i, min(flops_i, ncols))
+//   pred = clamp(ceil(rho * flops_i), maxB_i, min(flops_i, w_i))
+// Feature rows are float32 [4]: nnz(A_i), flops_i, maxB_i, w_i.
 // Weights are used as bf16 copies of fp32 master weights; every product is
 // accumulated in fp32.  Training minimises the pinball loss (tau) on
 // e = log2(nnz/flops) - log2(rho) with Adam on the fp32 master weights.
@@ -58,9 +62,13 @@ __device__ __forceinline__ void stage_weights(SmemWeights& w, const __nv_bfloat1
   }
 }
 
+constexpr int kNF = CB_MLP_NFEAT;  // floats per feature row
+
 __device__ __forceinline__ void features(const SmemWeights& w, const float* f, float x[3]) {
+  const float lw = log2f(fmaxf(f[3], 1.0f));
+  float l[3] = {log2f(1.0f + f[0]), log2f(1.0f + f[1]) - lw, log2f(1.0f + f[2]) - lw};
 #pragma unroll
-  for (int d = 0; d < 3; ++d) x[d] = bf16r((log2f(1.0f + f[d]) - w.mu[d]) / w.sg[d]);
+  for (int d = 0; d < 3; ++d) x[d] = bf16r((l[d] - w.mu[d]) / w.sg[d]);
 }
 
 // Forward pass of one row; h1/h2 receive the bf16-rounded activations.
@@ -87,11 +95,12 @@ __device__ __forceinline__ float forward_row(const SmemWeights& w, const float x
 }
 
 __device__ __forceinline__ int64_t size_from_logit(float z, int64_t flops, int64_t maxb,
-                                                   int64_t ncols) {
+                                                   int64_t width, int64_t ncols) {
   if (flops <= 0) return 0;
   const double rho = 1.0 / (1.0 + exp(-(double)z));
   int64_t est = (int64_t)ceil(rho * (double)flops);
-  const int64_t hi = flops < ncols ? flops : ncols;
+  int64_t hi = flops < width ? flops : width;
+  if (ncols > 0 && ncols < hi) hi = ncols;
   if (est < maxb) est = maxb;
   if (est > hi) est = hi;
   return est;
@@ -112,11 +121,11 @@ __global__ void __launch_bounds__(kFwdThreads) k_mlp_predict(const __nv_bfloat16
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m;
        r += (int64_t)gridDim.x * blockDim.x) {
     float x[3];
-    features(w, feat + 3 * r, x);
+    const float* f = feat + kNF * r;
+    features(w, f, x);
     const float z = forward_row(w, x, h1, h2);
     if (z_out) z_out[r] = z;
-    if (pred_out)
-      pred_out[r] = size_from_logit(z, (int64_t)feat[3 * r + 1], (int64_t)feat[3 * r + 2], ncols);
+    if (pred_out) pred_out[r] = size_from_logit(z, (int64_t)f[1], (int64_t)f[2], (int64_t)f[3], ncols);
   }
 }
 
@@ -150,12 +159,12 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_grad(const __nv_bfloat16* w
   float* my2 = h2 + t * kPad;
   if (r < r0 + n) {
     float x[3];
-    features(w, feat + 3 * r, x);
+    features(w, feat + kNF * r, x);
     xs[t * 3 + 0] = x[0];
     xs[t * 3 + 1] = x[1];
     xs[t * 3 + 2] = x[2];
     const float z = forward_row(w, x, my1, my2);
-    const float fl = feat[3 * r + 1];
+    const float fl = feat[kNF * r + 1];
     if (fl > 0.0f) {
       live = 1;
       const float ls = -(fmaxf(-z, 0.0f) + log1pf(expf(-fabsf(z))));  // log sigmoid(z)
@@ -273,12 +282,14 @@ __global__ void k_mlp_round(const float* master, __nv_bfloat16* wb) {
 }
 
 // raw features (nnz(A_i), flops_i, maxB_i) as floats
-__global__ void k_row_features(DevCSR A, const int64_t* flops, const int32_t* maxb, float* feat) {
+__global__ void k_row_features(DevCSR A, const int64_t* flops, const int32_t* maxb, int64_t ncols,
+                               float* feat) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.nrows;
        i += (int64_t)gridDim.x * blockDim.x) {
-    feat[3 * i + 0] = (float)(A.rp[i + 1] - A.rp[i]);
-    feat[3 * i + 1] = (float)flops[i];
-    feat[3 * i + 2] = (float)maxb[i];
+    feat[kNF * i + 0] = (float)(A.rp[i + 1] - A.rp[i]);
+    feat[kNF * i + 1] = (float)flops[i];
+    feat[kNF * i + 2] = (float)maxb[i];
+    feat[kNF * i + 3] = (float)(A.rcols ? (int64_t)A.rcols[i] : ncols);
   }
 }
 
@@ -286,11 +297,11 @@ constexpr size_t kGradSmem = (size_t)kBwdThreads * (4 * kPad + 4) * sizeof(float
 
 }  // namespace
 
-void launch_row_features(const DevCSR& A, const int64_t* flops, const int32_t* maxb, float* feat,
-                         cudaStream_t s, int sms) {
+void launch_row_features(const DevCSR& A, const int64_t* flops, const int32_t* maxb, int64_t ncols,
+                         float* feat, cudaStream_t s, int sms) {
   if (A.nrows == 0) return;
   int64_t g = (A.nrows + 255) / 256;
-  k_row_features<<<(int)(g < sms * 8 ? g : sms * 8), 256, 0, s>>>(A, flops, maxb, feat);
+  k_row_features<<<(int)(g < sms * 8 ? g : sms * 8), 256, 0, s>>>(A, flops, maxb, ncols, feat);
 }
 
 void launch_mlp_predict(const void* wb, const float* master, const float* norm, const float* feat,

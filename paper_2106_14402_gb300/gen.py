@@ -238,6 +238,20 @@ def rmat_square(scale: int = 18, edgefactor: int = 16, cfg: int = 2,
     return out
 
 
+def rmat_column_batched(scale: int = 21, edgefactor: int = 16, cfg: int = 3):
+    """Memory-constrained workload: C = A.A over (+,x) fp64 U(0,1) on a
+    symmetrised R-MAT of scale 21, edgefactor 16 (formed in column batches
+    under a 24 GB output budget)."""
+    return rmat_square(scale, edgefactor, cfg=cfg, semirings=("plus_times_f64",))
+
+
+def rmat_held_out(scale: int = 20, edgefactor: int = 32, cfg: int = 5):
+    """Held-out product of the learned sizer: (select2nd,min) int32 on a
+    symmetrised R-MAT of scale 20, edgefactor 32 (A's values 1, B's values
+    uniform in [0, 2^30))."""
+    return rmat_square(scale, edgefactor, cfg=cfg, semirings=("sel2nd_min_i32",))
+
+
 def training_family(index: int, cfg: int = 5) -> CSR:
     """Matrix `index` of the learned-sizer training mix (R-MAT / ER / banded, 2000 in all).
 

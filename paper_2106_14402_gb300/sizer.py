@@ -1,7 +1,8 @@
 """Training and checkpointing of the learned row-size predictor.
 
 The predictor estimates nnz(C_i) for every row of a product from three
-features (nnz(A_i), flops_i, max_p nnz(B_p)) so that the SpGEMM can size its
+features (nnz(A_i), flops_i, max_p nnz(B_p)), the last two relative to the
+output width, so that the SpGEMM can size its
 hash tables and its column-batch count without the symbolic phase (paper
 Sec. 5, approximate memory estimation; Sec. 7.4, batch count of batched
 SpGEMM).  Training data are squares C = A.A of the generated matrix
@@ -35,7 +36,7 @@ def init_params(seed: int = 0) -> np.ndarray:
 
 
 def product_rows(A_host, device="cuda"):
-    """(features [m,3], exact row sizes [m]) of A.A on the device, live rows only."""
+    """(features [m,4], exact row sizes [m]) of A.A on the device, live rows only."""
     dA = cb.DeviceCSR.from_host(A_host.with_values(np.ones(A_host.nnz, np.uint8)), "or_and_bool",
                                 device)
     feat = cb.row_features(dA, dA)
@@ -53,8 +54,16 @@ def dataset(indices, device="cuda", cfg: int = 5):
     return torch.cat(feats), torch.cat(labels)
 
 
+def inputs(feat: torch.Tensor) -> torch.Tensor:
+    """The network's inputs before standardisation (the library's transform)."""
+    f = feat.double()
+    lw = torch.log2(torch.clamp(f[:, 3], min=1.0))
+    return torch.stack([torch.log2(1.0 + f[:, 0]), torch.log2(1.0 + f[:, 1]) - lw,
+                        torch.log2(1.0 + f[:, 2]) - lw], 1)
+
+
 def normalisation(feat: torch.Tensor) -> np.ndarray:
-    L = torch.log2(1.0 + feat.double())
+    L = inputs(feat)
     return np.concatenate([L.mean(0).cpu().numpy(), L.std(0).cpu().numpy() + 1e-3]).astype(np.float32)
 
 

@@ -121,19 +121,72 @@ def test_learned_column_batches(cb, trained):
     compare_rows(sr, (rp, np.concatenate(cols), np.concatenate(vals)), want)
 
 
+def _column_batched(cb, sr, dA, dB, budget, sizing, mlp):
+    parts = []
+
+    def on_batch(b, lo, hi, Cb):
+        parts.append((lo, hi) + Cb.to_host())
+
+    st = cb.spgemm_column_batches(sr, dA, dB, budget, on_batch, sizing=sizing, mlp=mlp)
+    assert st["batches"] == len(parts)
+    parts.sort(key=lambda p: p[0])
+    m = dA.nrows
+    rp = np.zeros(m + 1, np.int64)
+    cols, vals = [], []
+    for i in range(m):
+        n = 0
+        for lo, hi, prp, pcol, pval in parts:
+            cols.append(pcol[prp[i]:prp[i + 1]])
+            vals.append(pval[prp[i]:prp[i + 1]])
+            n += prp[i + 1] - prp[i]
+        rp[i + 1] = rp[i] + n
+    return (rp, np.concatenate(cols), np.concatenate(vals)), st
+
+
+def test_learned_column_batches_unsorted_after_sorted(cb, trained):
+    """Whether B's rows are sorted is decided per call: a call on a B with
+    unsorted rows right after one on sorted rows must not reuse the slab
+    offsets of sorted rows."""
+    sr = "min_plus_u32"
+    A, B = held_out(sr, seed=650)
+    rng = np.random.default_rng(651)
+    col, val = B.col.copy(), B.val.copy()
+    for r in range(B.nrows):
+        s0, e0 = B.row_ptr[r], B.row_ptr[r + 1]
+        perm = rng.permutation(e0 - s0) + s0
+        col[s0:e0], val[s0:e0] = col[perm], val[perm]
+    Bu = gen.CSR(B.nrows, B.ncols, B.row_ptr, col, val)
+    want = oracle.spgemm(sr, A, B)
+    budget = 8 * (A.nrows + 1) + (int(want[0][-1]) // 5) * 8
+    dA = cb.DeviceCSR.from_host(A, sr)
+    for Bx in (B, Bu):
+        got, st = _column_batched(cb, sr, dA, cb.DeviceCSR.from_host(Bx, sr), budget, "learned", trained)
+        assert st["batches"] >= 4 and st["flops"] == int(oracle.row_stats(A, B)[0].sum())
+        compare_rows(sr, got, want)
+
+
 def test_what_the_trained_network_gains(cb, trained):
-    """On a held-out product, the trained sizer's capacities stay within a
-    small factor of the exact sizes with few overflows, while the untrained
-    network and the flops upper bound over-allocate by far more."""
+    """On a held-out product, the trained sizer (a 0.9-quantile estimate of
+    each row's size) overflows on few rows while allocating clearly less
+    than the flop bound min(flops_i, ncols), is closer to the exact sizes
+    than that bound row by row, and scores a lower held-out training
+    objective than the same network untrained."""
     from paper_2106_14402_gb300 import sizer
     A, _ = held_out("or_and_bool", seed=640)
     feat, y = sizer.product_rows(A)
+    untrained = cb.MLP(sizer.init_params(1), sizer.normalisation(feat))
     good = sizer.evaluate(trained, feat, y, A.ncols)
-    raw = sizer.evaluate(cb.MLP(sizer.init_params(1), sizer.normalisation(feat)), feat, y, A.ncols)
+    raw = sizer.evaluate(untrained, feat, y, A.ncols)
     assert good["sum_cap_over_sum_true"] < 2.0
     assert good["overflow_rows"] < 0.05
     assert good["sum_bound_over_sum_true"] > 1.8
-    assert good["sum_cap_over_sum_true"] < 0.75 * good["sum_bound_over_sum_true"]
-    # per row, the trained sizes are closer to the exact ones and overflow less
-    assert good["median_abs_log2_err"] < raw["median_abs_log2_err"]
+    assert good["sum_cap_over_sum_true"] < 0.9 * good["sum_bound_over_sum_true"]
+    live = feat[:, 1] > 0
+    bound = torch.clamp(feat[live][:, 1].double(), max=A.ncols)
+    yl = y[live].double()
+    assert good["median_abs_log2_err"] < float(torch.median(torch.abs(torch.log2(bound) - torch.log2(yl))))
+    # the pinball objective on the held-out rows, and the overflow rate
+    _, loss_good = trained.grad(feat, y, tau=sizer.TAU)
+    _, loss_raw = untrained.grad(feat, y, tau=sizer.TAU)
+    assert float(loss_good.item()) < float(loss_raw.item())
     assert good["overflow_rows"] <= raw["overflow_rows"]

@@ -52,8 +52,9 @@ def setup_problem(seed=0):
     flops, maxb = oracle.row_stats(A, A)
     nnz = np.diff(oracle.spgemm("or_and_bool", A, A)[0])
     nnza = np.diff(A.row_ptr)
-    F = np.stack([nnza, flops, maxb], 1).astype(np.float64)
-    L = mlp.raw_features(nnza, flops, maxb)
+    width = np.full(A.nrows, A.ncols)
+    F = np.stack([nnza, flops, maxb, width], 1).astype(np.float64)
+    L = mlp.raw_features(nnza, flops, maxb, width)
     norm = np.concatenate([L.mean(0), L.std(0) + 1e-3]).astype(np.float32)
     p = mlp.init_params(seed)
     return A, F, nnz, norm, p
@@ -64,7 +65,7 @@ def reference_inputs(F, norm, p):
     q = {k: (bf16(v) if k in ("W1", "W2", "w3") else np.asarray(v, np.float32).astype(np.float64))
          for k, v in p.items()}
     mu, sg = norm[:3].astype(np.float64), norm[3:].astype(np.float64)
-    X = bf16((np.log2(1.0 + F) - mu) / sg)
+    X = bf16((mlp.raw_features(F[:, 0], F[:, 1], F[:, 2], F[:, 3]) - mu) / sg)
     return q, X
 
 
