@@ -430,8 +430,10 @@ __device__ __forceinline__ void for_row_products_balanced(const DevCSR& A, const
         else r = mid - 1;
       }
       int j0 = l;
+      long long nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;  // start of the next range
+      int jc = -1;          // the lane's current range, its B offset and A entry
+      int64_t qb = 0, pc = 0;
       for (long long tb = t_beg; tb < t_end; tb += 32) {
-        const long long nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;
         int j = j0;
         if (nxt <= tb + 31) {  // the step crosses range starts (uniform over the warp)
           const int k = j0 + 1 + lane;
@@ -440,15 +442,24 @@ __device__ __forceinline__ void for_row_products_balanced(const DevCSR& A, const
           const unsigned bits = __reduce_or_sync(0xffffffffu, pos < 32 ? 1u << (int)pos : 0u);
           j = j0 + __popc(bits & ((2u << lane) - 1u));
           j0 += __popc(bits);
+          nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;
         }
         const long long t = tb + lane;
         if (t < t_end) {
-          const int64_t q = sm.b0[j] + (t - sm.off[j]);
+          if (j != jc) {
+            jc = j;
+            qb = sm.b0[j] - sm.off[j];
+            pc = c0 + sm.pa[j];
+          }
+          const int64_t q = qb + t;
           const int c = B.col[q];
-          if (!filter || (unsigned)((int64_t)c - lo) < width) f(c0 + sm.pa[j], q, c);
+          if (!filter || (unsigned)((int64_t)c - lo) < width) f(pc, q, c);
         }
         // range holding product tb + 32 (ranges are nonempty, so at most one more start)
-        if (j0 + 1 < ne && sm.off[j0 + 1] <= tb + 32) ++j0;
+        if (nxt <= tb + 32) {
+          ++j0;
+          nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;
+        }
       }
     }
     __syncthreads();

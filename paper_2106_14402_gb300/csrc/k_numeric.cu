@@ -248,13 +248,18 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
     }
     __syncthreads();
     // pass 2: accumulate at the rank of each product's column
+    int64_t p_last = -1;  // the lane's last A entry and its value
+    T a_last = T();
     for_row_products_balanced(A, B, i, lo, hi, whole, b_sorted != 0, sm,
                               [&](int64_t p, int64_t q, int c) {
                                 const unsigned off = (unsigned)((int64_t)c - lo);
                                 const uint2 e = bp[off >> 5];
                                 const int slot = (int)e.y + __popc(e.x & ((1u << (off & 31)) - 1u));
-                                const T a = S::kUsesA ? Aval[p] : T();
-                                if (slot < cnt) S::atomic(&acc[slot], S::mul(a, Bval[q]));
+                                if (S::kUsesA && p != p_last) {
+                                  p_last = p;
+                                  a_last = Aval[p];
+                                }
+                                if (slot < cnt) S::atomic(&acc[slot], S::mul(a_last, Bval[q]));
                               });
     __syncthreads();
     // write the window: values by slot (coalesced), columns by word
