@@ -337,15 +337,18 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
   size_t free_b = 0, total_b = 0;
   CB_CUDA(cudaMemGetInfo(&free_b, &total_b));
   const bool keep_bits = n_heavy > 0 && bits_bytes <= free_b / 4 && bits_bytes <= (32ull << 30);
+  const size_t racc_bytes = n_heavy > 0 ? cb::rank_scratch_bytes(sr, ctx->sms) : 0;
   size_t need2 = align_up(4 * (size_t)(n_heavy * spans) + 4) +
                  align_up(8 * (size_t)(n_heavy * spans) + 8) +
-                 align_up(sizeof(cb::Window) * (size_t)win_cap) + (keep_bits ? align_up(bits_bytes) : 0);
+                 align_up(sizeof(cb::Window) * (size_t)win_cap) + (keep_bits ? align_up(bits_bytes) : 0) +
+                 align_up(racc_bytes);
   ensure(ctx, &ctx->ws2, &ctx->ws2_cap, need2);
   Carver cv2{static_cast<char*>(ctx->ws2)};
   int32_t* span_counts = cv2.take<int32_t>(n_heavy * spans + 1);
   int2* span_wins = cv2.take<int2>(n_heavy * spans + 1);
   cb::Window* wins = cv2.take<cb::Window>(win_cap);
   unsigned* hbits = keep_bits ? cv2.take<unsigned>((size_t)(n_heavy * spans) * cb::kSpanWords) : nullptr;
+  void* racc = racc_bytes ? cv2.take<char>(racc_bytes) : nullptr;
   const int32_t* heavy_rows = perm_sym + sym_beg[cb::kSymHeavy];
 
   int launches = 0;
@@ -401,7 +404,7 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
   mark(ctx, opt, 4);
   cb::launch_numeric(sr, dA, dB, perm_num, num_beg, num_cnt, flops, nnz, heavy_rows, wins,
                      n_units, span_counts, spans, hbits, b_sorted, C->row_ptr, C->col, C->val,
-                     counters + cb::kError, ctx->stream, ctx->sms, &launches, num_hash_max);
+                     counters + cb::kError, ctx->stream, ctx->sms, &launches, num_hash_max, racc);
   CB_LAUNCHED();
   mark(ctx, opt, 5);
   ctx->stats.kernels += launches;

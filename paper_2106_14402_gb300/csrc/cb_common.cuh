@@ -117,6 +117,9 @@ template <int SR> struct NumLimits {
   // symbolic phase and are computed in one pass in a hash table of
   // 2^ceil(log2(2 cap)) slots (1024-thread team at most)
   static constexpr int kLearnHashMax = kLargeMax;
+  // rank windows accumulate in L2 (reductions into a per-CTA global slice)
+  // instead of shared memory: FP64 only
+  static constexpr bool kL2Acc = SR == 2;
 };
 
 // One rank window of a heavy row: row index h into the heavy-row list, the
@@ -381,11 +384,12 @@ struct BalancedSmem {
 // start, the warp ORs together the bits of the starts that fall inside the
 // step, and a lane's range is the step's first range plus the number of
 // starts at or before its product.  All threads of the CTA must call it.
-template <class F>
-__device__ __forceinline__ void for_row_products_balanced(const DevCSR& A, const DevCSR& B,
-                                                          int64_t i, int64_t lo, int64_t hi,
-                                                          bool whole, bool sorted,
-                                                          const BalancedSmem& sm, F&& f) {
+template <int U, class LD, class F>
+__device__ __forceinline__ void for_row_products_balanced_u(const DevCSR& A, const DevCSR& B,
+                                                            int64_t i, int64_t lo, int64_t hi,
+                                                            bool whole, bool sorted,
+                                                            const BalancedSmem& sm, LD&& ld, F&& f) {
+  typedef decltype(ld(int64_t(0))) V;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nthr = blockDim.x, nwarp = nthr >> 5;
   const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
@@ -433,37 +437,64 @@ __device__ __forceinline__ void for_row_products_balanced(const DevCSR& A, const
       long long nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;  // start of the next range
       int jc = -1;          // the lane's current range, its B offset and A entry
       int64_t qb = 0, pc = 0;
-      for (long long tb = t_beg; tb < t_end; tb += 32) {
-        int j = j0;
-        if (nxt <= tb + 31) {  // the step crosses range starts (uniform over the warp)
-          const int k = j0 + 1 + lane;
-          const long long st = k < ne ? sm.off[k] : LLONG_MAX;
-          const long long pos = st - tb;  // >= 1 by the choice of j0
-          const unsigned bits = __reduce_or_sync(0xffffffffu, pos < 32 ? 1u << (int)pos : 0u);
-          j = j0 + __popc(bits & ((2u << lane) - 1u));
-          j0 += __popc(bits);
-          nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;
-        }
-        const long long t = tb + lane;
-        if (t < t_end) {
-          if (j != jc) {
+      // U warp steps per iteration: positions first, then all loads, then
+      // the callbacks, so that U independent loads are in flight per lane
+      for (long long tb = t_beg; tb < t_end; tb += 32 * U) {
+        int64_t qu[U], pu[U];
+        bool vu[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const long long ts = tb + 32 * u;
+          int j = j0;
+          if (nxt <= ts + 31) {  // the step crosses range starts (uniform over the warp)
+            const int k = j0 + 1 + lane;
+            const long long st = k < ne ? sm.off[k] : LLONG_MAX;
+            const long long pos = st - ts;  // >= 1 by the choice of j0
+            const unsigned bits = __reduce_or_sync(0xffffffffu, pos < 32 ? 1u << (int)pos : 0u);
+            j = j0 + __popc(bits & ((2u << lane) - 1u));
+            j0 += __popc(bits);
+            nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;
+          }
+          const long long t = ts + lane;
+          vu[u] = t < t_end;
+          if (vu[u] && j != jc) {
             jc = j;
             qb = sm.b0[j] - sm.off[j];
             pc = c0 + sm.pa[j];
           }
-          const int64_t q = qb + t;
-          const int c = B.col[q];
-          if (!filter || (unsigned)((int64_t)c - lo) < width) f(pc, q, c);
+          qu[u] = qb + t;
+          pu[u] = pc;
+          // range holding product ts + 32 (ranges are nonempty, so at most one more start)
+          if (nxt <= ts + 32) {
+            ++j0;
+            nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;
+          }
         }
-        // range holding product tb + 32 (ranges are nonempty, so at most one more start)
-        if (nxt <= tb + 32) {
-          ++j0;
-          nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;
+        int cu[U];
+        V vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          cu[u] = vu[u] ? __ldg(B.col + qu[u]) : 0;
+          vv[u] = vu[u] ? ld(qu[u]) : V();
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (vu[u] && (!filter || (unsigned)((int64_t)cu[u] - lo) < width)) f(pu[u], qu[u], cu[u], vv[u]);
       }
     }
     __syncthreads();
   }
+}
+
+// The loop above with one warp step per iteration and no value loads.
+template <class F>
+__device__ __forceinline__ void for_row_products_balanced(const DevCSR& A, const DevCSR& B,
+                                                          int64_t i, int64_t lo, int64_t hi,
+                                                          bool whole, bool sorted,
+                                                          const BalancedSmem& sm, F&& f) {
+  for_row_products_balanced_u<1>(A, B, i, lo, hi, whole, sorted, sm,
+                                 [](int64_t) { return 0; },
+                                 [&](int64_t p, int64_t q, int c, int) { f(p, q, c); });
 }
 
 }  // namespace cb

@@ -134,7 +134,7 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
                     int64_t n_wins, const int32_t* span_counts, int64_t spans,
                     const unsigned* hbits, int b_sorted, const int64_t* Crp, int32_t* Ccol,
                     void* Cval, int64_t* err, cudaStream_t s, int sms, int* launches,
-                    int64_t num_hash_max = 512);
+                    int64_t num_hash_max = 512, void* racc = nullptr);
 
 // Batched products (cb_batched.cu): stack parts into one CSR.
 size_t stack_part_size();
@@ -158,6 +158,9 @@ void launch_mlp_predict(const void* wb, const float* master, const float* norm, 
 // 8 * lanes products (lanes = 8, 16 or 32), columns below fused_max_cols.
 // tstat holds at least fused_tiles(lanes, A.nrows) words and sync two words,
 // all zero when first used; they must not be shared by launches in flight.
+// Bytes of the global accumulator slices of the rank-window numeric kernel
+// (semirings whose windows accumulate in L2; 0 otherwise).
+size_t rank_scratch_bytes(int sr, int sms);
 int64_t fused_tiles(int lanes, int64_t nrows);
 int64_t fused_max_cols(int lanes);
 cudaError_t launch_fused(int sr, int lanes, const DevCSR& A, const DevCSR& B, int64_t* Crp,

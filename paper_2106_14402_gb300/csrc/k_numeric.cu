@@ -170,16 +170,21 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
                                                       const int64_t* flops, const int64_t* nnz,
                                                       const int64_t* Crp, int32_t* Ccol,
                                                       typename Sem<SR>::T* Cval, int64_t* err,
-                                                      int64_t num_hash_max) {
+                                                      int64_t num_hash_max,
+                                                      typename Sem<SR>::A* racc) {
   typedef Sem<SR> S;
   typedef typename S::A Acc;
   typedef typename S::T T;
   constexpr int WCAP = NumLimits<SR>::kWcap;
+  // FP64 windows accumulate with reductions in L2 (a per-CTA slice of racc):
+  // shared-memory fp64 atomic addition costs far more than an L2 reduction.
+  constexpr bool kL2 = NumLimits<SR>::kL2Acc;
   constexpr int WPT = kSpanWords / 1024;
   extern __shared__ __align__(16) unsigned char rank_smem[];
+  // shared layout: [accumulators (shared-memory windows only)] [bp] [iterator scratch]
   Acc* acc = reinterpret_cast<Acc*>(rank_smem);
   // word w of the window: .x = its column bits, .y = entries before it
-  uint2* bp = reinterpret_cast<uint2*>(acc + WCAP);
+  uint2* bp = reinterpret_cast<uint2*>(rank_smem + (kL2 ? 0 : (size_t)WCAP * sizeof(Acc)));
   long long* bal = reinterpret_cast<long long*>(bp + kSpanWords);
   __shared__ int scratch[33];
   __shared__ long long scan64[33];
@@ -207,7 +212,8 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
     } else {
       for (int w = tid; w < nw; w += 1024) bp[w].x = 0u;
     }
-    for (int t = tid; t < cnt; t += 1024) acc[t] = S::ident();
+    Acc* wacc = kL2 ? racc + (size_t)blockIdx.x * WCAP : acc;
+    for (int t = tid; t < cnt; t += 1024) wacc[t] = S::ident();
     if (tid < 32) {
       long long o = 0;
       for (int64_t t = lane; t < wd.span; t += 32) o += span_counts[(int64_t)wd.h * spans + t];
@@ -247,26 +253,31 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
       if (tid == 0 && total != wd.count) flag_error(err, 23);
     }
     __syncthreads();
-    // pass 2: accumulate at the rank of each product's column
+    // pass 2: accumulate at the rank of each product's column (two warp
+    // steps per iteration, B columns and values loaded before the atomics)
     int64_t p_last = -1;  // the lane's last A entry and its value
     T a_last = T();
-    for_row_products_balanced(A, B, i, lo, hi, whole, b_sorted != 0, sm,
-                              [&](int64_t p, int64_t q, int c) {
-                                const unsigned off = (unsigned)((int64_t)c - lo);
-                                const uint2 e = bp[off >> 5];
-                                const int slot = (int)e.y + __popc(e.x & ((1u << (off & 31)) - 1u));
-                                if (S::kUsesA && p != p_last) {
-                                  p_last = p;
-                                  a_last = Aval[p];
-                                }
-                                if (slot < cnt) S::atomic(&acc[slot], S::mul(a_last, Bval[q]));
-                              });
+    for_row_products_balanced_u<2>(A, B, i, lo, hi, whole, b_sorted != 0, sm,
+                                   [&](int64_t q) { return __ldg(Bval + q); },
+                                   [&](int64_t p, int64_t, int c, T bv) {
+                                     const unsigned off = (unsigned)((int64_t)c - lo);
+                                     const uint2 e = bp[off >> 5];
+                                     const int slot = (int)e.y + __popc(e.x & ((1u << (off & 31)) - 1u));
+                                     if (S::kUsesA && p != p_last) {
+                                       p_last = p;
+                                       a_last = __ldg(Aval + p);
+                                     }
+                                     if (slot < cnt) {
+                                       if (kL2) atomicAdd(&wacc[slot], S::mul(a_last, bv));
+                                       else S::atomic(&wacc[slot], S::mul(a_last, bv));
+                                     }
+                                   });
     __syncthreads();
     // write the window: values by slot (coalesced), columns by word
     const int64_t out = Crp[i] + s_base;
     const int64_t row_end = Crp[i + 1];
     for (int t = tid; t < cnt; t += 1024)
-      if (out + t < row_end) Cval[out + t] = S::out(acc[t]);
+      if (out + t < row_end) Cval[out + t] = S::out(kL2 ? __ldcg(wacc + t) : wacc[t]);
     for (int w = tid; w < nw; w += 1024) {
       unsigned word = bp[w].x;
       int64_t o = out + bp[w].y;
@@ -297,7 +308,7 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
                 const int32_t* heavy_rows, const Window* wins, int64_t n_wins,
                 const int32_t* span_counts, int64_t spans, const unsigned* hbits, int b_sorted,
                 const int64_t* Crp, int32_t* Ccol, void* Cval_, int64_t* err, cudaStream_t s,
-                int sms, int* launches, int64_t num_hash_max) {
+                int sms, int* launches, int64_t num_hash_max, void* racc) {
   typedef typename Sem<SR>::A Acc;
   typedef typename Sem<SR>::T T;
   T* Cval = reinterpret_cast<T*>(Cval_);
@@ -325,13 +336,14 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
     ++*launches;
   }
   if (n_wins) {
-    constexpr size_t smem = NumLimits<SR>::kWcap * sizeof(Acc) + 2 * kSpanWords * sizeof(unsigned) +
-                            2 * 1024 * sizeof(long long) + 1024 * sizeof(int);
+    constexpr size_t smem = (NumLimits<SR>::kL2Acc ? 0 : NumLimits<SR>::kWcap * sizeof(Acc)) +
+                            2 * kSpanWords * sizeof(unsigned) + 2 * 1024 * sizeof(long long) +
+                            1024 * sizeof(int);
     set_smem(k_num_rank<SR>, smem);
     k_num_rank<SR><<<capped(n_wins, sms), 1024, smem, s>>>(A, B, heavy_rows, wins, n_wins,
                                                            span_counts, spans, hbits, b_sorted,
                                                            flops, nnz, Crp, Ccol, Cval, err,
-                                                           num_hash_max);
+                                                           num_hash_max, static_cast<Acc*>(racc));
     ++*launches;
   }
 }
@@ -427,11 +439,11 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
                     int64_t n_wins, const int32_t* span_counts, int64_t spans,
                     const unsigned* hbits, int b_sorted, const int64_t* Crp, int32_t* Ccol,
                     void* Cval, int64_t* err, cudaStream_t s, int sms, int* launches,
-                    int64_t num_hash_max) {
+                    int64_t num_hash_max, void* racc) {
 #define CB_NUM(SRV)                                                                        \
   numeric_sr<SRV>(A, B, perm, seg_begin, seg_count, flops, nnz, heavy_rows, wins, n_wins,   \
                   span_counts, spans, hbits, b_sorted, Crp, Ccol, Cval, err, s, sms, launches, \
-                  num_hash_max)
+                  num_hash_max, racc)
   switch (sr) {
     case 1: CB_NUM(1); break;
     case 2: CB_NUM(2); break;
@@ -440,6 +452,14 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
     case 5: CB_NUM(5); break;
   }
 #undef CB_NUM
+}
+
+size_t rank_scratch_bytes(int sr, int sms) {
+  switch (sr) {
+    case 1: return NumLimits<1>::kL2Acc ? (size_t)sms * NumLimits<1>::kWcap * sizeof(unsigned long long) : 0;
+    case 2: return NumLimits<2>::kL2Acc ? (size_t)sms * NumLimits<2>::kWcap * sizeof(double) : 0;
+  }
+  return 0;
 }
 
 }  // namespace cb

@@ -104,12 +104,13 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
     const int nwords = (int)((hi - lo + 31) / 32);
     for (int w = tid; w < nwords; w += 1024) sym_bm[w] = 0u;
     __syncthreads();
-    for_row_products_balanced(A, B, i, lo, hi, spans == 1 && !B.filter, b_sorted != 0, sm,
-                              [&](int64_t, int64_t, int c) {
-                                const unsigned off = (unsigned)((int64_t)c - lo);
-                                const unsigned bit = 1u << (off & 31);
-                                if (!(sym_bm[off >> 5] & bit)) atomicOr(&sym_bm[off >> 5], bit);
-                              });
+    for_row_products_balanced_u<2>(A, B, i, lo, hi, spans == 1 && !B.filter, b_sorted != 0, sm,
+                                   [](int64_t) { return 0; },
+                                   [&](int64_t, int64_t, int c, int) {
+                                     const unsigned off = (unsigned)((int64_t)c - lo);
+                                     const unsigned bit = 1u << (off & 31);
+                                     if (!(sym_bm[off >> 5] & bit)) atomicOr(&sym_bm[off >> 5], bit);
+                                   });
     __syncthreads();
     if (hbits) {
       unsigned* dst = hbits + (size_t)(h * spans + sp) * kSpanWords;
