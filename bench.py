@@ -59,6 +59,18 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def fp64_traffic_per_product():
+    """DRAM bytes per product of the fp64 numeric phase from the committed ncu summary."""
+    path = os.path.join(ROOT, "profiles", "k_num_rank_k_sym_bitmap_rmat_s16.md")
+    try:
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_product_fp64_numeric:"):
+                return float(line.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
 def compulsory_bytes(sr, A, B, nnz_c, m):
     """bytes(A) + bytes(B rows touched, once) + bytes(C): row_ptr 8 B/row, col 4 B, val by type."""
     v = VAL_BYTES[sr]
@@ -296,11 +308,29 @@ def main_gpu(args):
     else:
         peak, peak_src = 6800.0, "fallback"
     achieved = num_bytes / (num_ms * 1e-3) / 1e9 if num_ms > 0 else 0.0
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "numeric phase (hash tiers + rank windows of heavy rows), per SpGEMM",
-                "peak_source": peak_src,
-                "algorithmic_bytes_per_step": num_bytes, "ms_per_step_in_kernel": round(num_ms, 4)}
+    all_sr = {"achieved": round(achieved, 1), "frac": round(achieved / peak, 4),
+              "algorithmic_bytes_per_step": num_bytes, "ms_per_step_in_kernel": round(num_ms, 4)}
+    if "plus_times_f64" in per_sr:
+        # the dominant kernel: the numeric phase of the (+,x) fp64 product
+        f = per_sr["plus_times_f64"]
+        a64 = f["compulsory_bytes"] / (f["ms_numeric"] * 1e-3) / 1e9 if f["ms_numeric"] > 0 else 0.0
+        tpp = fp64_traffic_per_product()
+        roofline = {"bound": "hbm", "achieved": round(a64, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(a64 / peak, 4),
+                    "traffic": round(tpp * f["products"]) if tpp else None,
+                    "kernel": "numeric phase of the (+,x) f64 product (k_num_rank<2> + k_num_hash<2,...>), "
+                              "per SpGEMM",
+                    "algorithmic_bytes": f["compulsory_bytes"], "ms_in_kernel": f["ms_numeric"],
+                    "traffic_source": "ncu dram bytes per product of the same kernels on R-MAT s16 "
+                                      "(profiles/k_num_rank_k_sym_bitmap_rmat_s16.md) x this product's "
+                                      "products" if tpp else None,
+                    "peak_source": peak_src, "all_semirings": all_sr}
+    else:
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "kernel": "numeric phase (hash tiers + rank windows of heavy rows, or the one-launch "
+                              "kernel), per SpGEMM",
+                    "peak_source": peak_src, **all_sr}
 
     legs = {}
     if not args.no_legs:
