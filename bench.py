@@ -59,6 +59,23 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks of the process group (x itself without one):
+    a multi-GPU step takes as long as its slowest rank."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each process units_per_rank
+    units in `seconds` (the max over ranks): weak scaling."""
+    return world * units_per_rank / seconds
+
+
 def fp64_traffic_per_product():
     """DRAM bytes per product of the fp64 numeric phase from the committed ncu summary."""
     path = os.path.join(ROOT, "profiles", "k_num_rank_k_sym_bitmap_rmat_s16.md")
@@ -272,17 +289,14 @@ def main_gpu(args):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
-    ms_step = sum(times) / len(times)
+    ms_step = max_over_ranks(sum(times) / len(times), dist, dev)
     if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
         dist.barrier()
 
     products = sum(st[0]["flops"] for st in stats.values())
     nnz_c = sum(st[0]["nnz"] for st in stats.values())
-    value = world * products / (ms_step * 1e-3)
-    nnz_rate = world * nnz_c / (ms_step * 1e-3)
+    value = whole_job_rate(products, world, ms_step * 1e-3)
+    nnz_rate = whole_job_rate(nnz_c, world, ms_step * 1e-3)
 
     # per-semiring breakdown and the numeric-phase roofline
     per_sr = {}
@@ -688,12 +702,8 @@ def run_e2e(args, cb, ctx, dprob, dev, world, dist, products):
     t0 = time.perf_counter()
     for _ in range(steps):
         one(True)
-    el = (time.perf_counter() - t0) / steps
-    if dist:
-        t = torch.tensor([el], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
-    return {"value": world * products / el, "unit": UNIT,
+    el = max_over_ranks((time.perf_counter() - t0) / steps, dist, dev)
+    return {"value": whole_job_rate(products, world, el), "unit": UNIT,
             "h2d_bytes_per_step": moved["h2d"] // steps, "d2h_bytes_per_step": moved["d2h"] // steps,
             "ms_per_step": el * 1e3, "steps": steps, "timing": "host wall clock, synchronised"}
 
