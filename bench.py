@@ -453,6 +453,7 @@ def run_legs(args, cb, ctx, dprob, flush, plain_ms, products, dev, peak, peak_sr
         out["multi_spgemm"] = run_multi(args, cb, ctx, model)
     if not args.no_full:
         out["memory_constrained"] = run_full_configs(args, cb, ctx, flush, model, dev, peak, peak_src)
+    out["high_compression"] = run_high_compression(args, cb, ctx, flush, model, dev, peak, peak_src)
     return out
 
 
@@ -594,6 +595,58 @@ def run_full_configs(args, cb, ctx, flush, model, dev, peak, peak_src):
         del dA, dB
         torch.cuda.empty_cache()
     return out
+
+
+def run_high_compression(args, cb, ctx, flush, model, dev, peak, peak_src):
+    """A high-compression product (block-clustered matrix, compression ratio
+    ~36, shaped like the paper's protein-similarity networks): plain exact
+    path with the default tier bounds and with autotuned ones, and learned
+    per-row sizing."""
+    import torch
+    from paper_2106_14402_gb300 import gen
+    (sr, A, _), = gen.high_compression()
+    dA = cb.DeviceCSR.from_host(A, sr, dev)
+    C = cb.spgemm(sr, dA, dA, validate=False, ctx=ctx)
+    nnz = C.nnz
+    del C
+    out = cb.DeviceCSR(A.nrows, A.ncols, torch.empty(A.nrows + 1, dtype=torch.int64, device=dev),
+                       torch.empty(nnz, dtype=torch.int32, device=dev),
+                       torch.empty(nnz, dtype=cb.SEMIRING[sr][1], device=dev))
+    steps = max(1, min(args.steps, 3))
+    res = {"workload": "block-clustered n=131072, clusters of 256, density 0.5, ~1 inter-cluster edge "
+                       "per vertex, symmetrised+permuted; C=A.A over (+,x) f64",
+           "nnz_a": A.nnz, "nnz_c": nnz}
+    saved = ctx.get_tune()
+    info = {}
+
+    def plain():
+        cb.spgemm(sr, dA, dA, validate=False, out=out, ctx=ctx, timing=True)
+        info.update(ctx.stats())
+
+    def learned():
+        cb.spgemm(sr, dA, dA, validate=False, out=out, ctx=ctx, sizing="learned", mlp=model)
+
+    plain()
+    ms = timed(plain, steps, flush)
+    prods = info["flops"]
+    res["products"] = prods
+    res["compression_ratio"] = prods / max(nnz, 1)
+    nbytes = compulsory_bytes(sr, A, A, nnz, A.nrows)
+    res["default"] = {"ms": ms, "products_per_s": prods / (ms * 1e-3), "nnz_per_s": nnz / (ms * 1e-3),
+                      "ms_symbolic": info["ms_symbolic"], "ms_numeric": info["ms_numeric"],
+                      "roofline_frac_numeric": round(nbytes / (info["ms_numeric"] * 1e-3) / 1e9 / peak, 4)}
+    best, _ = cb.autotune(sr, dA, dA, ctx=ctx)
+    plain()
+    ms_t = timed(plain, steps, flush)
+    res["autotuned"] = {"bounds": best, "ms": ms_t, "products_per_s": prods / (ms_t * 1e-3),
+                        "vs_default": ms / ms_t}
+    learned()
+    ms_l = timed(learned, steps, flush)
+    res["learned"] = {"ms": ms_l, "vs_autotuned_plain": ms_t / ms_l}
+    ctx.set_tune(**saved)
+    res["peak_gbs"] = peak
+    res["peak_source"] = peak_src
+    return res
 
 
 def run_multi(args, cb, ctx, model):

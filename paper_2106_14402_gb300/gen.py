@@ -140,6 +140,45 @@ def rmat(scale: int, edgefactor: int, a: float, b: float, c: float, seed: int,
     return _csr_from_sorted_keys(keys, n, n)
 
 
+def block_clustered(n: int, cluster: int, density: float, inter: float, seed: int) -> CSR:
+    """High-compression pattern shaped like the paper's protein-similarity
+    networks (dense groups of similar sequences, few links between groups):
+    the n vertices form clusters of `cluster` consecutive vertices; every
+    ordered pair inside a cluster is an edge with probability `density`, and
+    each vertex gets Poisson(`inter`) edges to uniformly random vertices.
+    Symmetrised, vertices relabelled by one seeded permutation, duplicates
+    dropped, self-loops kept.  Squaring it gives compression ratios of
+    order density^2 * cluster."""
+    rng = rng_for(seed, 7)
+    nc = n // cluster
+    # intra-cluster pairs: per cluster a Bernoulli(density) cluster x cluster block
+    blocks = rng.random((nc, cluster, cluster)) < density
+    cb, ib, jb = np.nonzero(blocks)
+    del blocks
+    i = cb.astype(np.int64) * cluster + ib
+    j = cb.astype(np.int64) * cluster + jb
+    del cb, ib, jb
+    k = rng.poisson(inter, nc * cluster)
+    src = np.repeat(np.arange(nc * cluster, dtype=np.int64), k)
+    dst = rng.integers(0, n, src.size, dtype=np.int64)
+    i = np.concatenate([i, src])
+    j = np.concatenate([j, dst])
+    perm = rng_for(seed, 8).permutation(n).astype(np.int64)
+    i, j = perm[i], perm[j]
+    i, j = np.concatenate([i, j]), np.concatenate([j, i])
+    keys = sorted_unique(i * n + j)
+    del i, j
+    return _csr_from_sorted_keys(keys, n, n)
+
+
+def high_compression(n: int = 1 << 17, cluster: int = 256, density: float = 0.5, inter: float = 1.0,
+                     cfg: int = 6, semiring: str = "plus_times_f64"):
+    """C = A.A on a block-clustered matrix (compression ratio ~40)."""
+    P = block_clustered(n, cluster, density, inter, seed=subseed(cfg, 0))
+    A = P.with_values(random_values(semiring, P.nnz, subseed(cfg, 1)))
+    return [(semiring, A, A)]
+
+
 def er_exact(nrows: int, ncols: int, deg: int, seed: int) -> CSR:
     """Each row gets exactly min(deg, ncols) distinct uniformly random columns."""
     d = min(deg, ncols)

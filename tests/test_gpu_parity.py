@@ -315,3 +315,27 @@ def test_drop_result_without_sync(cb):
     got = cb.spgemm(sr, dA, dA).to_host()
     rows = np.arange(0, A.nrows, 97)
     compare_rows(sr, got, oracle.spgemm(sr, A, A, rows=rows), rows=rows)
+
+
+# ---------------------------------------------------------------------------
+# high compression (block-clustered, shaped like protein-similarity networks)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bounds", [(512, 512), (4096, 4096)])
+@pytest.mark.parametrize("sr", SR)
+def test_high_compression_block_clustered(cb, sr, bounds):
+    P = gen.block_clustered(1 << 13, 256, 0.5, 1.0, seed=31)
+    vals = gen.random_values(sr, P.nnz, 32)
+    A = P.with_values(vals if sr != "sel2nd_min_i32" else np.ones(P.nnz, np.int32))
+    B = P.with_values(vals)
+    flops, _ = oracle.row_stats(A, B)
+    ctx = cb.context()
+    ctx.set_tune(bounds[0], bounds[1], 512)
+    try:
+        got = run_pair(cb, sr, A, B)
+    finally:
+        ctx.set_tune(512, 512, 512)
+    check_structure(got[0], got[1], B.ncols)
+    want = oracle.spgemm(sr, A, B)
+    assert flops.sum() > 20 * int(want[0][-1])      # compression ratio above 20
+    compare_rows(sr, got, want)
