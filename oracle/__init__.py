@@ -9,7 +9,8 @@ the CUDA path).
 output row (paper Sec. 4.1), over the five semirings named below.
 `row_stats` gives flops_i and max_p nnz(B(p,:)) per row (Sec. 4.1, phase (1);
 Table 1 defines flops).  `mlp` holds the FP64 reference of the learned row
-size predictor.
+size predictor.  `merge` is the semiring sum of k partial results (Sec. 3.2),
+stated directly in numpy.
 """
 from __future__ import annotations
 
@@ -131,3 +132,6 @@ def spgemm(semiring: str, A, B, rows=None, threads: int = 0):
         for p in (o_rp, o_col, o_val, o_abs):
             lib.orc_free(p)
     return rp, col, val, absum
+
+
+from .merge import merge  # noqa: E402,F401
