@@ -454,6 +454,7 @@ def run_legs(args, cb, ctx, dprob, flush, plain_ms, products, dev, peak, peak_sr
     if not args.no_full:
         out["memory_constrained"] = run_full_configs(args, cb, ctx, flush, model, dev, peak, peak_src)
     out["high_compression"] = run_high_compression(args, cb, ctx, flush, model, dev, peak, peak_src)
+    out["merge"] = run_merge_leg(args, cb, ctx, flush, dev, peak, peak_src)
     return out
 
 
@@ -647,6 +648,62 @@ def run_high_compression(args, cb, ctx, flush, model, dev, peak, peak_src):
     res["peak_gbs"] = peak
     res["peak_source"] = peak_src
     return res
+
+
+def _inner_blocks(A, k):
+    """The k (column block of A, row block of A) pairs of a split of the inner dimension."""
+    cuts = np.linspace(0, A.ncols, k + 1).astype(np.int64)
+    rows = np.repeat(np.arange(A.nrows), np.diff(A.row_ptr))
+    out = []
+    from paper_2106_14402_gb300 import gen
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        keep = (A.col >= lo) & (A.col < hi)
+        rp = np.zeros(A.nrows + 1, np.int64)
+        np.add.at(rp, rows[keep] + 1, 1)
+        L = gen.CSR(A.nrows, A.ncols, np.cumsum(rp), A.col[keep], A.val[keep])
+        lens = np.diff(A.row_ptr).copy()
+        lens[:lo] = 0
+        lens[hi:] = 0
+        rp2 = np.zeros(A.nrows + 1, np.int64)
+        rp2[1:] = np.cumsum(lens)
+        s0, e0 = A.row_ptr[lo], A.row_ptr[hi]
+        R = gen.CSR(A.nrows, A.ncols, rp2, A.col[s0:e0], A.val[s0:e0])
+        out.append((L, R))
+    return out
+
+
+def run_merge_leg(args, cb, ctx, flush, dev, peak, peak_src):
+    """The merge of k partial results (Sec. 3.2): R-MAT s16 ef16 (+,x) f64,
+    the inner dimension split into k = 8 blocks as in a SUMMA stage; the 8
+    partial products are formed first (untimed), then merged (timed)."""
+    import torch
+    from paper_2106_14402_gb300 import gen
+    (sr, A, _), = gen.rmat_square(16, 16, cfg=2, semirings=("plus_times_f64",))
+    k = 8
+    parts = []
+    for L, R in _inner_blocks(A, k):
+        parts.append(cb.spgemm(sr, cb.DeviceCSR.from_host(L, sr, dev), cb.DeviceCSR.from_host(R, sr, dev),
+                               validate=False, ctx=ctx))
+    torch.cuda.synchronize()
+    nnz_parts = sum(p.nnz for p in parts)
+    info = {}
+
+    def run():
+        C = cb.merge(sr, parts, validate=False, ctx=ctx)
+        info["nnz"] = C.nnz
+        info["kernels"] = ctx.stats()["kernels"]
+
+    run()
+    ms = timed(run, max(1, min(args.steps, 3)), flush)
+    v = VAL_BYTES[sr]
+    nbytes = k * 8 * (A.nrows + 1) + nnz_parts * (4 + v) + 8 * (A.nrows + 1) + info["nnz"] * (4 + v)
+    ach = nbytes / (ms * 1e-3) / 1e9
+    return {"workload": "R-MAT s16 ef16 (+,x) f64, inner dimension in 8 blocks; merge of the 8 partial "
+                        "products", "k": k, "nnz_parts": nnz_parts, "nnz_c": info["nnz"], "ms": ms,
+            "entries_in_per_s": nnz_parts / (ms * 1e-3), "kernels": info["kernels"],
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(ach / peak, 4), "algorithmic_bytes": nbytes,
+                         "peak_source": peak_src}}
 
 
 def run_multi(args, cb, ctx, model):

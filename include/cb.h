@@ -299,6 +299,20 @@ int cb_ctx_get_tune(const cb_ctx *ctx, cb_tune *tune);
 int cb_autotune(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B, const cb_opts *opt,
                 cb_tune *best, float *best_ms);
 
+/* ---- semiring merge of k partial results ---------------------------------
+ * C = P_0 (+) P_1 (+) ... (+) P_{k-1}, entry by entry over the union of the
+ * patterns: the combination of the partial products of a SUMMA stage or of
+ * the layers of the communication-avoiding SpGEMM (Sec. 3.2).  All parts are
+ * device CSR of one shape (rows may be unsorted and hold duplicates, which
+ * combine the same way); C has sorted, unique columns.  It runs as the
+ * SpGEMM (selector) (+).(x) [P_0; ...; P_{k-1}], whose selector row i holds
+ * the multiplicative identity at column l*m + i of every part l, so every
+ * tier of the SpGEMM (and its one-launch kernel for small rows) serves it.
+ * opt: validate, out_capacity (caller buffers as for cb_spgemm_ex), flags;
+ * exact sizing only, no budget.  Returns CB_ERR_SHAPE if the parts differ
+ * in shape, CB_ERR_INDEX if k * nrows reaches INT32_MAX. */
+int cb_merge(cb_ctx *ctx, cb_semiring sr, int k, const cb_csr *parts, cb_csr *C, const cb_opts *opt);
+
 /* ---- one-launch SpGEMM for small rows -----------------------------------
  * The row-wise SpGEMM of Sec. 4.1 with its symbolic and numeric phases fused
  * into one kernel launch, for products whose rows are all small:

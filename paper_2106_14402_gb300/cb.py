@@ -99,6 +99,8 @@ _SIGS = {
     "cb_autotune": ([c_void_p, ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr),
                      ctypes.POINTER(cb_opts), ctypes.POINTER(cb_tune), ctypes.POINTER(ctypes.c_float)],
                     ctypes.c_int),
+    "cb_merge": ([c_void_p, ctypes.c_int, ctypes.c_int, c_void_p, ctypes.POINTER(cb_csr),
+                  ctypes.POINTER(cb_opts)], ctypes.c_int),
     "cb_spgemm_fused": ([c_void_p, ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr),
                          ctypes.POINTER(cb_csr), c_int64, ctypes.c_int, c_void_p], ctypes.c_int),
     "cb_fused_max_cols": ([ctypes.c_int], c_int64),
@@ -347,6 +349,25 @@ def spgemm(semiring: str, A: DeviceCSR, B: DeviceCSR, *, validate: bool = True, 
                                    ctypes.byref(sc), ctypes.byref(opts)))
     owner = _Owner(ctx, cb_csr(sc.nrows, sc.ncols, sc.nnz, sc.row_ptr, sc.col, sc.val))
     dev = A.row_ptr.device
+    return DeviceCSR(sc.nrows, sc.ncols, _wrap(sc.row_ptr, sc.nrows + 1, torch.int64, owner, dev),
+                     _wrap(sc.col, sc.nnz, torch.int32, owner, dev),
+                     _wrap(sc.val, sc.nnz, dt, owner, dev), owner)
+
+
+def merge(semiring: str, parts, *, validate: bool = True, ctx: Context | None = None,
+          timing: bool = False, fused: bool = True) -> DeviceCSR:
+    """C = parts[0] (+) ... (+) parts[k-1] on the GPU (cb_merge); the parts are
+    DeviceCSR of one shape.  The library allocates C."""
+    code, dt = SEMIRING[semiring]
+    ctx = ctx or context()
+    arr = (cb_csr * len(parts))(*[p.as_struct() for p in parts])
+    opts = make_opts(validate=validate,
+                     flags=(FLAG_TIMING if timing else 0) | (0 if fused else FLAG_NO_FUSED))
+    sc = cb_csr()
+    ctx.check(ctx.lib.cb_merge(ctx.handle, code, len(parts), ctypes.cast(arr, c_void_p),
+                               ctypes.byref(sc), ctypes.byref(opts)))
+    owner = _Owner(ctx, cb_csr(sc.nrows, sc.ncols, sc.nnz, sc.row_ptr, sc.col, sc.val))
+    dev = parts[0].row_ptr.device
     return DeviceCSR(sc.nrows, sc.ncols, _wrap(sc.row_ptr, sc.nrows + 1, torch.int64, owner, dev),
                      _wrap(sc.col, sc.nnz, torch.int32, owner, dev),
                      _wrap(sc.val, sc.nnz, dt, owner, dev), owner)

@@ -1190,6 +1190,91 @@ int cb_exclusive_scan(cb_ctx* ctx, const int64_t* in, int64_t n, int64_t* out) {
   }
 }
 
+int cb_merge(cb_ctx* ctx, cb_semiring sr, int k, const cb_csr* parts, cb_csr* C, const cb_opts* opt_in) {
+  if (!ctx) return CB_ERR_ARG;
+  ctx->err.clear();
+  ctx->stats = cb_stats{};
+  ctx->stats.batches = 1;
+  cb_opts opt;
+  if (opt_in) opt = *opt_in;
+  else cb_opts_default(&opt);
+  const bool caller_buf = opt.out_capacity > 0;
+  cb_csr saved{};
+  if (C) saved = *C;
+  try {
+    if (!parts || !C || k < 1) fail(ctx, CB_ERR_ARG, "cb_merge needs k >= 1 parts and an output");
+    if (value_size(sr) == 0) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
+    if (opt.budget_bytes > 0 || opt.sizing != CB_SIZING_EXACT)
+      fail(ctx, CB_ERR_ARG, "cb_merge takes exact sizing and no budget");
+    if (caller_buf && (!C->row_ptr || !C->col || !C->val))
+      fail(ctx, CB_ERR_ARG, "out_capacity > 0 needs C->row_ptr, C->col and C->val");
+    const int64_t m = parts[0].nrows, n = parts[0].ncols;
+    int64_t total = 0;
+    for (int l = 0; l < k; ++l) {
+      check_operand(ctx, &parts[l], "part");
+      if (parts[l].nrows != m || parts[l].ncols != n) fail(ctx, CB_ERR_SHAPE, "parts differ in shape");
+      total += parts[l].nnz;
+    }
+    if ((int64_t)k * m >= INT32_MAX) fail(ctx, CB_ERR_INDEX, "k * nrows beyond int32 indices");
+    if (opt.validate) {
+      ensure(ctx, &ctx->ws, &ctx->ws_cap, align_up(sizeof(int64_t) * cb::kCounters));
+      int64_t* counters = static_cast<int64_t*>(ctx->ws);
+      CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+      for (int l = 0; l < k; ++l) cb::launch_validate(dev(&parts[l]), parts[l].nnz, 0, counters, ctx->stream, ctx->sms);
+      CB_LAUNCHED();
+      read_counters(ctx, counters, nullptr, 0);
+      if (ctx->host[cb::kError]) fail(ctx, CB_ERR_INDEX, "a part has invalid CSR index data");
+    }
+    const size_t vsz = value_size(sr);
+    // B = [P_0; ...; P_{k-1}] stacked by rows; A = the selector (k entries per row)
+    DevBuf sBrp(ctx), sBcol(ctx), sBval(ctx), hparts(ctx), aRp(ctx), aCol(ctx), aVal(ctx);
+    sBrp.alloc(8 * (size_t)(k * m + 1));
+    sBcol.alloc(4 * (size_t)total);
+    sBval.alloc(vsz * (size_t)total);
+    const size_t psz = cb::stack_part_size();
+    hparts.alloc((size_t)k * psz);
+    std::vector<unsigned char> hp((size_t)k * psz);
+    int64_t off = 0;
+    for (int l = 0; l < k; ++l) {
+      cb::fill_stack_part(&hp[(size_t)l * psz], parts[l].row_ptr, parts[l].col, parts[l].val, m, l * m, off,
+                          0, (int32_t)n);
+      off += parts[l].nnz;
+    }
+    CB_CUDA(cudaMemcpyAsync(hparts.p, hp.data(), hp.size(), cudaMemcpyHostToDevice, ctx->stream));
+    if (m > 0) cb::launch_stack(hparts.p, k, (int)vsz, sBrp.as<int64_t>(), sBcol.as<int32_t>(), sBval.p,
+                                nullptr, ctx->stream, ctx->sms);
+    aRp.alloc(8 * (size_t)(m + 1));
+    aCol.alloc(4 * (size_t)(k * m));
+    aVal.alloc(vsz * (size_t)(k * m));
+    uint64_t one = 1;  // multiplicative identity: 1, 1.0, 0 (min,+), true
+    if (sr == CB_PLUS_TIMES_F64) {
+      const double d = 1.0;
+      std::memcpy(&one, &d, sizeof d);
+    } else if (sr == CB_MIN_PLUS_U32) {
+      one = 0;
+    }
+    cb::launch_merge_selector(m, k, (int)vsz, one, aRp.as<int64_t>(), aCol.as<int32_t>(), aVal.p,
+                              ctx->stream, ctx->sms);
+    if (m == 0) CB_CUDA(cudaMemsetAsync(aRp.p, 0, sizeof(int64_t), ctx->stream));
+    CB_LAUNCHED();
+    const cb_csr sel{m, k * m, k * m, aRp.as<int64_t>(), aCol.as<int32_t>(), aVal.p};
+    const DevCSR dB{k * m, n, sBrp.as<int64_t>(), sBcol.as<int32_t>(), sBval.p};
+    opt.validate = 0;
+    spgemm_plain(ctx, (int)sr, &sel, dB, n, C, opt);
+    ctx->stats.kernels += 2;
+    return CB_OK;
+  } catch (const Fail& f) {
+    if (!caller_buf && C) {
+      if (C->row_ptr && C->row_ptr != saved.row_ptr) cudaFreeAsync(C->row_ptr, ctx->stream);
+      if (C->col && C->col != saved.col) cudaFreeAsync(C->col, ctx->stream);
+      if (C->val && C->val != saved.val) cudaFreeAsync(C->val, ctx->stream);
+      cudaStreamSynchronize(ctx->stream);
+      std::memset(C, 0, sizeof *C);
+    }
+    return f.code;
+  }
+}
+
 int cb_spgemm_batched(cb_ctx* ctx, int count, const cb_semiring* sr, const cb_csr* A,
                       const cb_csr* B, const cb_opts* opt_in) {
   if (!ctx) return CB_ERR_ARG;

@@ -42,7 +42,36 @@ __global__ void __launch_bounds__(256) k_stack(const StackPart* parts, int npart
   }
 }
 
+// Selector of the merge: row i holds k entries, at columns l*m + i
+// (l = 0..k-1) with the semiring's multiplicative identity, so that
+// (selector (+).(x) [P_0; ...; P_{k-1}]) = P_0 (+) ... (+) P_{k-1}.
+template <class T>
+__global__ void __launch_bounds__(256) k_merge_selector(int64_t m, int k, int64_t* rp, int32_t* col,
+                                                        T* val, T one) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    rp[i] = i * k;
+    for (int l = 0; l < k; ++l) {
+      col[i * k + l] = (int32_t)(l * m + i);
+      val[i * k + l] = one;
+    }
+    if (i == m - 1) rp[m] = m * k;
+  }
+}
+
 }  // namespace
+
+void launch_merge_selector(int64_t m, int k, int vsz, uint64_t one_bits, int64_t* rp, int32_t* col,
+                           void* val, cudaStream_t s, int sms) {
+  if (m <= 0) return;
+  const int64_t g = (m + 255) / 256;
+  const unsigned grid = (unsigned)(g < sms * 8 ? g : sms * 8);
+  switch (vsz) {
+    case 8: k_merge_selector<uint64_t><<<grid, 256, 0, s>>>(m, k, rp, col, static_cast<uint64_t*>(val), one_bits); break;
+    case 4: k_merge_selector<uint32_t><<<grid, 256, 0, s>>>(m, k, rp, col, static_cast<uint32_t*>(val), (uint32_t)one_bits); break;
+    default: k_merge_selector<uint8_t><<<grid, 256, 0, s>>>(m, k, rp, col, static_cast<uint8_t*>(val), (uint8_t)one_bits);
+  }
+}
 
 void launch_stack(const void* parts_dev, int nparts, int vsz, int64_t* rp_out, int32_t* col_out,
                   void* val_out, int32_t* rcols_out, cudaStream_t s, int sms) {

@@ -141,6 +141,10 @@ size_t stack_part_size();
 void fill_stack_part(void* dst, const int64_t* rp, const int32_t* col, const void* val, int64_t nrows,
                      int64_t row_off, int64_t nnz_off, int32_t col_add, int32_t width);
 // rcols_out (optional): every stacked row gets its part's width
+// Selector matrix of the k-way merge (m rows, k entries each at columns
+// l*m + i, values = one_bits of the value size vsz).
+void launch_merge_selector(int64_t m, int k, int vsz, uint64_t one_bits, int64_t* rp, int32_t* col,
+                           void* val, cudaStream_t s, int sms);
 void launch_stack(const void* parts_dev, int nparts, int vsz, int64_t* rp_out, int32_t* col_out,
                   void* val_out, int32_t* rcols_out, cudaStream_t s, int sms);
 
