@@ -10,7 +10,8 @@ output row (paper Sec. 4.1), over the five semirings named below.
 `row_stats` gives flops_i and max_p nnz(B(p,:)) per row (Sec. 4.1, phase (1);
 Table 1 defines flops).  `mlp` holds the FP64 reference of the learned row
 size predictor.  `merge` is the semiring sum of k partial results (Sec. 3.2),
-stated directly in numpy.
+stated directly in numpy; `spmspv` the sparse-vector x sparse-matrix
+product (Sec. 4.3), likewise.
 """
 from __future__ import annotations
 
@@ -135,3 +136,4 @@ def spgemm(semiring: str, A, B, rows=None, threads: int = 0):
 
 
 from .merge import merge  # noqa: E402,F401
+from .spmspv import spmspv  # noqa: E402,F401
