@@ -455,6 +455,7 @@ def run_legs(args, cb, ctx, dprob, flush, plain_ms, products, dev, peak, peak_sr
         out["memory_constrained"] = run_full_configs(args, cb, ctx, flush, model, dev, peak, peak_src)
     out["high_compression"] = run_high_compression(args, cb, ctx, flush, model, dev, peak, peak_src)
     out["merge"] = run_merge_leg(args, cb, ctx, flush, dev, peak, peak_src)
+    out["spmspv"] = run_spmspv_leg(args, cb, ctx, flush, dev, dprob, peak, peak_src)
     return out
 
 
@@ -704,6 +705,54 @@ def run_merge_leg(args, cb, ctx, flush, dev, peak, peak_src):
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(ach / peak, 4), "algorithmic_bytes": nbytes,
                          "peak_source": peak_src}}
+
+
+def run_spmspv_leg(args, cb, ctx, flush, dev, dprob, peak, peak_src):
+    """SpMSpV y^T = x^T A (Sec. 4.3) on the workload's R-MAT matrix: random
+    frontiers of 1K, 16K and 128K vertices, (or,and) and (min,+); next to the
+    same product as a one-row SpGEMM."""
+    import torch
+    from paper_2106_14402_gb300 import gen
+    out = {"workload": "R-MAT s18 ef16 (the step's matrix); x = seeded random distinct vertices",
+           "legs": []}
+    for sr, A, B, dA, dB, o, nnz in dprob:
+        if sr not in ("or_and_bool", "min_plus_u32"):
+            continue
+        rng = np.random.default_rng(7)
+        v = VAL_BYTES[sr]
+        for f in (1 << 10, 1 << 14, 1 << 17):
+            idx = np.sort(rng.choice(A.nrows, f, replace=False)).astype(np.int32)
+            val = gen.random_values(sr, f, 8)
+            xi = torch.from_numpy(idx).to(dev)
+            xv = torch.from_numpy(val.view(np.int32) if val.dtype == np.uint32 else val).to(dev)
+            if cb.SEMIRING[sr][1] == torch.uint32:
+                xv = xv.view(torch.uint32)
+            res = {}
+
+            def run():
+                yi, _ = cb.spmspv(sr, dA, xi, xv, validate=False, ctx=ctx)
+                res["nnz"] = yi.numel()
+
+            run()
+            ms = timed(run, max(3, args.steps), flush)
+            X = cb.DeviceCSR(1, A.nrows, torch.tensor([0, f], dtype=torch.int64, device=dev), xi, xv)
+
+            def as_spgemm():
+                cb.spgemm(sr, X, dA, validate=False, ctx=ctx)
+
+            as_spgemm()
+            ms_g = timed(as_spgemm, max(3, args.steps), flush)
+            lens = np.diff(A.row_ptr)[idx]
+            prods = int(lens.sum())
+            nbytes = f * (4 + v) + 16 * f + prods * (4 + v) + res["nnz"] * (4 + v)
+            out["legs"].append({"semiring": sr, "nnz_x": f, "products": prods, "nnz_y": res["nnz"],
+                                "us": round(ms * 1e3, 2), "products_per_s": prods / (ms * 1e-3),
+                                "roofline_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
+                                "one_row_spgemm_us": round(ms_g * 1e3, 2),
+                                "vs_one_row_spgemm": ms_g / ms})
+    out["peak_gbs"] = peak
+    out["peak_source"] = peak_src
+    return out
 
 
 def run_multi(args, cb, ctx, model):

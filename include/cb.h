@@ -299,6 +299,33 @@ int cb_ctx_get_tune(const cb_ctx *ctx, cb_tune *tune);
 int cb_autotune(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B, const cb_opts *opt,
                 cb_tune *best, float *best_ms);
 
+/* ---- semiring SpMSpV ----------------------------------------------------------
+ * y^T = x^T A over a semiring: y_c = (+) over stored x entries (i, x_i) and
+ * stored A(i, c) of x_i (x) A(i, c) (Sec. 4.3, SpMSpV; the row form suits
+ * CSR: for y = A x pass A's transpose in CSR, i.e. A in CSC).  x is a sparse
+ * vector of length A->nrows (indices in any order, duplicates contribute
+ * separately); y gets length A->ncols, indices strictly increasing, the
+ * pattern structural.  (x) takes x's value on the left: with (select2nd,
+ * min), y_c = min of A(i, c) over the x entries i.
+ * The product is pushed into a dense accumulator kept in the context (one
+ * value per column of A plus a bitmap); it is initialised once per width
+ * and semiring and reset sparsely after each call.  The stream is
+ * synchronised once (to learn nnz(y)); y->idx / y->val are allocated by the
+ * library (free with cb_spvec_free_async) unless opt->out_capacity > 0, in
+ * which case they are the caller's (CB_ERR_CAPACITY with y->nnz = needed if
+ * too small).  opt->validate checks A (row pointers and columns); x's
+ * indices are always checked on the device (CB_ERR_INDEX). */
+typedef struct {
+  int64_t n;    /* length                                    */
+  int64_t nnz;  /* stored entries                            */
+  int32_t *idx; /* device, nnz indices                       */
+  void *val;    /* device, nnz values of the semiring's type */
+} cb_spvec;
+int cb_spmspv(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_spvec *x, cb_spvec *y,
+              const cb_opts *opt);
+/* Stream-ordered release of a library-allocated y; zeroes *y. */
+int cb_spvec_free_async(cb_ctx *ctx, cb_spvec *y);
+
 /* ---- semiring merge of k partial results ---------------------------------
  * C = P_0 (+) P_1 (+) ... (+) P_{k-1}, entry by entry over the union of the
  * patterns: the combination of the partial products of a SUMMA stage or of

@@ -63,6 +63,10 @@ class cb_stats(ctypes.Structure):
                 ("ms_numeric", ctypes.c_float)]
 
 
+class cb_spvec(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("nnz", c_int64), ("idx", c_void_p), ("val", c_void_p)]
+
+
 class CBError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -99,6 +103,9 @@ _SIGS = {
     "cb_autotune": ([c_void_p, ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr),
                      ctypes.POINTER(cb_opts), ctypes.POINTER(cb_tune), ctypes.POINTER(ctypes.c_float)],
                     ctypes.c_int),
+    "cb_spmspv": ([c_void_p, ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_spvec),
+                   ctypes.POINTER(cb_spvec), ctypes.POINTER(cb_opts)], ctypes.c_int),
+    "cb_spvec_free_async": ([c_void_p, ctypes.POINTER(cb_spvec)], ctypes.c_int),
     "cb_merge": ([c_void_p, ctypes.c_int, ctypes.c_int, c_void_p, ctypes.POINTER(cb_csr),
                   ctypes.POINTER(cb_opts)], ctypes.c_int),
     "cb_spgemm_fused": ([c_void_p, ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr),
@@ -352,6 +359,41 @@ def spgemm(semiring: str, A: DeviceCSR, B: DeviceCSR, *, validate: bool = True, 
     return DeviceCSR(sc.nrows, sc.ncols, _wrap(sc.row_ptr, sc.nrows + 1, torch.int64, owner, dev),
                      _wrap(sc.col, sc.nnz, torch.int32, owner, dev),
                      _wrap(sc.val, sc.nnz, dt, owner, dev), owner)
+
+
+class _SpvOwner:
+    """Frees a library-allocated sparse vector in stream order on the context's stream."""
+
+    def __init__(self, ctx, v: cb_spvec):
+        self.ctx = ctx
+        self.v = v
+
+    def __del__(self):
+        try:
+            self.ctx.lib.cb_spvec_free_async(self.ctx.handle, ctypes.byref(self.v))
+        except Exception:
+            pass
+
+
+def spmspv(semiring: str, A: DeviceCSR, x_idx: torch.Tensor, x_val: torch.Tensor, *,
+           validate: bool = True, ctx: Context | None = None):
+    """y^T = x^T A over the semiring (cb_spmspv): x is a sparse vector of length
+    A.nrows given by int32 indices and values of the semiring's type.  Returns
+    (y_idx int32, y_val) device tensors, indices strictly increasing."""
+    code, dt = SEMIRING[semiring]
+    ctx = ctx or context()
+    if x_idx.dtype != torch.int32 or x_val.dtype != dt or x_idx.numel() != x_val.numel():
+        raise ValueError("x needs int32 indices and values of the semiring's dtype, equally many")
+    sa = A.as_struct()
+    nx = x_idx.numel()
+    sx = cb_spvec(A.nrows, nx, x_idx.data_ptr() if nx else None, x_val.data_ptr() if nx else None)
+    sy = cb_spvec()
+    opts = make_opts(validate=validate)
+    ctx.check(ctx.lib.cb_spmspv(ctx.handle, code, ctypes.byref(sa), ctypes.byref(sx), ctypes.byref(sy),
+                                ctypes.byref(opts)))
+    owner = _SpvOwner(ctx, cb_spvec(sy.n, sy.nnz, sy.idx, sy.val))
+    dev = A.row_ptr.device
+    return (_wrap(sy.idx, sy.nnz, torch.int32, owner, dev), _wrap(sy.val, sy.nnz, dt, owner, dev))
 
 
 def merge(semiring: str, parts, *, validate: bool = True, ctx: Context | None = None,

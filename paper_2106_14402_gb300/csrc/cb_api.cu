@@ -31,6 +31,10 @@ struct cb_ctx {
   unsigned long long* fstat = nullptr;  // tile status words of the one-launch path
   int64_t fstat_cap = 0;
   unsigned* fsync = nullptr;  // [0] launch epoch, [1] finished CTAs, [4] status word
+  void* spa = nullptr;        // SpMSpV dense accumulator (spa_n values of spa_sr's type)
+  unsigned* spa_bits = nullptr;  // its touched bitmap, all zero between calls
+  int64_t spa_n = 0;
+  int spa_sr = 0;
   std::string err;
   cb_stats stats{};
 };
@@ -969,6 +973,9 @@ void cb_ctx_destroy(cb_ctx* ctx) {
   if (ctx->fstat || ctx->fsync) cudaStreamSynchronize(ctx->stream);
   if (ctx->fstat) cudaFree(ctx->fstat);
   if (ctx->fsync) cudaFree(ctx->fsync);
+  if (ctx->spa || ctx->spa_bits) cudaStreamSynchronize(ctx->stream);
+  if (ctx->spa) cudaFree(ctx->spa);
+  if (ctx->spa_bits) cudaFree(ctx->spa_bits);
   for (cudaEvent_t e : ctx->ev)
     if (e) cudaEventDestroy(e);
   delete ctx;
@@ -1188,6 +1195,144 @@ int cb_exclusive_scan(cb_ctx* ctx, const int64_t* in, int64_t n, int64_t* out) {
   } catch (const Fail& f) {
     return f.code;
   }
+}
+
+int cb_spmspv(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_spvec* x, cb_spvec* y,
+              const cb_opts* opt_in) {
+  if (!ctx) return CB_ERR_ARG;
+  ctx->err.clear();
+  ctx->stats = cb_stats{};
+  ctx->stats.batches = 1;
+  cb_opts opt;
+  if (opt_in) opt = *opt_in;
+  else cb_opts_default(&opt);
+  const bool caller_buf = opt.out_capacity > 0;
+  cb_spvec saved{};
+  if (y) saved = *y;
+  try {
+    if (!A || !x || !y) fail(ctx, CB_ERR_ARG, "null argument");
+    if (value_size(sr) == 0) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
+    check_operand(ctx, A, "A");
+    if (x->n != A->nrows) fail(ctx, CB_ERR_SHAPE, "x's length differs from A.nrows");
+    if (x->nnz < 0 || (x->nnz > 0 && (!x->idx || !x->val))) fail(ctx, CB_ERR_ARG, "bad x");
+    if (caller_buf && (!y->idx || !y->val)) fail(ctx, CB_ERR_ARG, "out_capacity > 0 needs y->idx and y->val");
+    const int64_t n = A->ncols, nx = x->nnz, nw = (n + 31) / 32;
+    const size_t vsz = value_size(sr);
+    y->n = n;
+    y->nnz = 0;
+    if (!caller_buf) {
+      y->idx = nullptr;
+      y->val = nullptr;
+    }
+    if (opt.validate) {
+      ensure(ctx, &ctx->ws, &ctx->ws_cap, align_up(sizeof(int64_t) * cb::kCounters));
+      int64_t* counters = static_cast<int64_t*>(ctx->ws);
+      CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+      cb::launch_validate(dev(A), A->nnz, 0, counters, ctx->stream, ctx->sms);
+      CB_LAUNCHED();
+      read_counters(ctx, counters, nullptr, 0);
+      if (ctx->host[cb::kError]) fail(ctx, CB_ERR_INDEX, "A has invalid CSR index data");
+    }
+    if (n == 0 || nx == 0) return CB_OK;
+    // the dense accumulator: (re)allocated for a wider A, re-initialised for another semiring
+    const size_t avs = cb::spa_value_size((int)sr);
+    if (ctx->spa_n < n) {
+      CB_CUDA(cudaStreamSynchronize(ctx->stream));
+      if (ctx->spa) cudaFree(ctx->spa);
+      if (ctx->spa_bits) cudaFree(ctx->spa_bits);
+      ctx->spa = nullptr;
+      ctx->spa_bits = nullptr;
+      ctx->spa_n = 0;
+      ctx->spa_sr = 0;
+      CB_CUDA(cudaMalloc(&ctx->spa, 8 * (size_t)n));
+      CB_CUDA(cudaMalloc((void**)&ctx->spa_bits, 4 * (size_t)nw));
+      CB_CUDA(cudaMemsetAsync(ctx->spa_bits, 0, 4 * (size_t)nw, ctx->stream));
+      ctx->spa_n = n;
+    }
+    const DevCSR dA = dev(A);
+    if (ctx->spa_sr != (int)sr) {
+      cb::launch_spmspv_step((int)sr, 0, dA, nullptr, nullptr, 0, nullptr, nullptr, ctx->spa, nullptr,
+                             ctx->spa_n, nullptr, nullptr, nullptr, nullptr, 0, nullptr, ctx->stream,
+                             ctx->sms);
+      ctx->spa_sr = (int)sr;
+      ctx->stats.kernels += 1;
+    }
+    (void)avs;
+    const int64_t big = std::max(nx, nw);
+    ensure(ctx, &ctx->ws, &ctx->ws_cap,
+           align_up(sizeof(int64_t) * cb::kCounters) + 2 * align_up(8 * (size_t)(nx + 1)) +
+               2 * align_up(8 * (size_t)(nw + 1)) + align_up(8 * (size_t)cb::scan_partials(big)));
+    Carver cv{static_cast<char*>(ctx->ws)};
+    int64_t* counters = cv.take<int64_t>(cb::kCounters);
+    int64_t* chunks = cv.take<int64_t>(nx + 1);
+    int64_t* cpre = cv.take<int64_t>(nx + 1);
+    int64_t* wcnt = cv.take<int64_t>(nw + 1);
+    int64_t* wpre = cv.take<int64_t>(nw + 1);
+    int64_t* partial = cv.take<int64_t>(cb::scan_partials(big));
+    CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+    mark(ctx, opt, 0);
+    cb::launch_spmspv_step((int)sr, 1, dA, x->idx, x->val, nx, chunks, nullptr, nullptr, nullptr, n,
+                           nullptr, nullptr, nullptr, nullptr, 0, counters + cb::kError, ctx->stream,
+                           ctx->sms);
+    cb::launch_exclusive_scan(chunks, nx, cpre, partial, ctx->stream);
+    cb::launch_spmspv_step((int)sr, 2, dA, x->idx, x->val, nx, nullptr, cpre, ctx->spa, ctx->spa_bits, n,
+                           nullptr, nullptr, nullptr, nullptr, 0, nullptr, ctx->stream, ctx->sms);
+    cb::launch_spmspv_step((int)sr, 3, dA, nullptr, nullptr, 0, nullptr, nullptr, nullptr, ctx->spa_bits,
+                           n, wcnt, nullptr, nullptr, nullptr, 0, nullptr, ctx->stream, ctx->sms);
+    cb::launch_exclusive_scan(wcnt, nw, wpre, partial, ctx->stream);
+    CB_LAUNCHED();
+    ctx->stats.kernels += 6;
+    mark(ctx, opt, 1);
+    read_counters(ctx, counters, wpre + nw, 1);
+    const int64_t total = ctx->host[cb::kCounters];
+    const bool bad_x = ctx->host[cb::kError] != 0;
+    int64_t cap = caller_buf ? opt.out_capacity : total;
+    if (!caller_buf && total > 0) {
+      CB_CUDA(cudaMallocAsync((void**)&y->idx, 4 * (size_t)total, ctx->stream));
+      CB_CUDA(cudaMallocAsync(&y->val, vsz * (size_t)total, ctx->stream));
+    }
+    // compaction always runs: it also resets the accumulator for the next call
+    cb::launch_spmspv_step((int)sr, 4, dA, nullptr, nullptr, 0, nullptr, nullptr, ctx->spa,
+                           ctx->spa_bits, n, nullptr, wpre, y->idx, y->val, std::min(cap, total),
+                           nullptr, ctx->stream, ctx->sms);
+    CB_LAUNCHED();
+    ctx->stats.kernels += 1;
+    mark(ctx, opt, 2);
+    mark(ctx, opt, 3);
+    mark(ctx, opt, 4);
+    mark(ctx, opt, 5);
+    y->nnz = total;
+    ctx->stats.nnz = total;
+    if (bad_x) fail(ctx, CB_ERR_INDEX, "an index of x is outside [0, A.nrows)");
+    if (caller_buf && total > opt.out_capacity) {
+      char msg[128];
+      std::snprintf(msg, sizeof msg, "y needs %lld entries, capacity %lld", (long long)total,
+                    (long long)opt.out_capacity);
+      ctx->err = msg;
+      throw Fail{CB_ERR_CAPACITY};
+    }
+    collect_times(ctx, opt, true);
+    return CB_OK;
+  } catch (const Fail& f) {
+    if (!caller_buf && y) {
+      if (y->idx && y->idx != saved.idx) cudaFreeAsync(y->idx, ctx->stream);
+      if (y->val && y->val != saved.val) cudaFreeAsync(y->val, ctx->stream);
+      cudaStreamSynchronize(ctx->stream);
+      const int64_t need = y->nnz;
+      std::memset(y, 0, sizeof *y);
+      y->nnz = need;
+    }
+    return f.code;
+  }
+}
+
+int cb_spvec_free_async(cb_ctx* ctx, cb_spvec* y) {
+  if (!ctx || !y) return CB_ERR_ARG;
+  int rc = CB_OK;
+  for (void* p : {(void*)y->idx, y->val})
+    if (p && cudaFreeAsync(p, ctx->stream) != cudaSuccess) rc = CB_ERR_CUDA;
+  std::memset(y, 0, sizeof *y);
+  return rc;
 }
 
 int cb_merge(cb_ctx* ctx, cb_semiring sr, int k, const cb_csr* parts, cb_csr* C, const cb_opts* opt_in) {

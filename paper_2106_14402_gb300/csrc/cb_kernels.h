@@ -162,6 +162,16 @@ void launch_mlp_predict(const void* wb, const float* master, const float* norm, 
 // 8 * lanes products (lanes = 8, 16 or 32), columns below fused_max_cols.
 // tstat holds at least fused_tiles(lanes, A.nrows) words and sync two words,
 // all zero when first used; they must not be shared by launches in flight.
+// SpMSpV steps (k_spmspv.cu): 0 SPA init over n, 1 chunk counts of the x
+// entries (bad indices set *err), 2 push into the SPA (cpre = scanned chunk
+// counts, cpre[nx] = total), 3 popcounts of the touched bitmap, 4 compaction
+// into y (wpre = scanned popcounts; nothing past cap) resetting SPA and bitmap.
+size_t spa_value_size(int sr);
+void launch_spmspv_step(int sr, int step, const DevCSR& A, const int32_t* x_idx, const void* x_val,
+                        int64_t nx, int64_t* chunks, const int64_t* cpre, void* spa,
+                        unsigned* touched, int64_t n, int64_t* wcnt, const int64_t* wpre,
+                        int32_t* y_idx, void* y_val, int64_t cap, int64_t* err, cudaStream_t s,
+                        int sms);
 // Bytes of the global accumulator slices of the rank-window numeric kernel
 // (semirings whose windows accumulate in L2; 0 otherwise).
 size_t rank_scratch_bytes(int sr, int sms);
