@@ -117,9 +117,10 @@ template <int SR> struct NumLimits {
   // symbolic phase and are computed in one pass in a hash table of
   // 2^ceil(log2(2 cap)) slots (1024-thread team at most)
   static constexpr int kLearnHashMax = kLargeMax;
-  // rank windows accumulate in L2 (reductions into a per-CTA global slice)
-  // instead of shared memory: FP64 only
-  static constexpr bool kL2Acc = SR == 2;
+  // rank windows of 8-byte accumulators reduce into a per-CTA slice in L2
+  // instead of shared memory (measured faster for int64 and fp64; slower for
+  // the 4-byte ones, whose shared-memory atomics are cheap)
+  static constexpr bool kL2Acc = sizeof(typename Sem<SR>::A) == 8;
 };
 
 // One rank window of a heavy row: row index h into the heavy-row list, the

@@ -162,8 +162,8 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
 // row's products), prefix-count its words, then accumulate every product
 // into the dense accumulator at its column's rank and write the window's
 // slice of the row in column order.
-template <int SR>
-__global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const int32_t* heavy_rows,
+template <int SR, int CTA>
+__global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B, const int32_t* heavy_rows,
                                                       const Window* wins, int64_t n_wins,
                                                       const int32_t* span_counts, int64_t spans,
                                                       const unsigned* hbits, int b_sorted,
@@ -176,10 +176,11 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
   typedef typename S::A Acc;
   typedef typename S::T T;
   constexpr int WCAP = NumLimits<SR>::kWcap;
-  // FP64 windows accumulate with reductions in L2 (a per-CTA slice of racc):
-  // shared-memory fp64 atomic addition costs far more than an L2 reduction.
+  // 8-byte accumulators reduce in L2 (a per-CTA slice of racc): shared-memory
+  // 64-bit atomics cost more than L2 reductions, and without shared
+  // accumulators two 512-thread CTAs share an SM.
   constexpr bool kL2 = NumLimits<SR>::kL2Acc;
-  constexpr int WPT = kSpanWords / 1024;
+  constexpr int WPT = kSpanWords / CTA;
   extern __shared__ __align__(16) unsigned char rank_smem[];
   // shared layout: [accumulators (shared-memory windows only)] [bp] [iterator scratch]
   Acc* acc = reinterpret_cast<Acc*>(rank_smem);
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
   __shared__ int scratch[33];
   __shared__ long long scan64[33];
   __shared__ int iscan[33];
-  const BalancedSmem sm{bal, bal + 1024, reinterpret_cast<int*>(bal + 2048), scan64, iscan};
+  const BalancedSmem sm{bal, bal + CTA, reinterpret_cast<int*>(bal + 2 * CTA), scan64, iscan};
   __shared__ long long s_base;
   const int tid = threadIdx.x, lane = tid & 31;
   const T* Aval = reinterpret_cast<const T*>(A.val);
@@ -208,12 +209,12 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
     const int nw = wd.w_hi - wd.w_lo;
     if (hbits) {
       const unsigned* src = hbits + (size_t)((int64_t)wd.h * spans + wd.span) * kSpanWords + wd.w_lo;
-      for (int w = tid; w < nw; w += 1024) bp[w].x = src[w];
+      for (int w = tid; w < nw; w += CTA) bp[w].x = src[w];
     } else {
-      for (int w = tid; w < nw; w += 1024) bp[w].x = 0u;
+      for (int w = tid; w < nw; w += CTA) bp[w].x = 0u;
     }
     Acc* wacc = kL2 ? racc + (size_t)blockIdx.x * WCAP : acc;
-    for (int t = tid; t < cnt; t += 1024) wacc[t] = S::ident();
+    for (int t = tid; t < cnt; t += CTA) wacc[t] = S::ident();
     if (tid < 32) {
       long long o = 0;
       for (int64_t t = lane; t < wd.span; t += 32) o += span_counts[(int64_t)wd.h * spans + t];
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
         mine += c[j];
       }
       int total;
-      int run = team_exclusive_scan<1024>(mine, scratch, total);
+      int run = team_exclusive_scan<CTA>(mine, scratch, total);
 #pragma unroll
       for (int j = 0; j < WPT; ++j) {
         const int w = tid * WPT + j;
@@ -267,18 +268,15 @@ __global__ void __launch_bounds__(1024, 1) k_num_rank(DevCSR A, DevCSR B, const 
                                        p_last = p;
                                        a_last = __ldg(Aval + p);
                                      }
-                                     if (slot < cnt) {
-                                       if (kL2) atomicAdd(&wacc[slot], S::mul(a_last, bv));
-                                       else S::atomic(&wacc[slot], S::mul(a_last, bv));
-                                     }
+                                     if (slot < cnt) S::atomic(&wacc[slot], S::mul(a_last, bv));
                                    });
     __syncthreads();
     // write the window: values by slot (coalesced), columns by word
     const int64_t out = Crp[i] + s_base;
     const int64_t row_end = Crp[i + 1];
-    for (int t = tid; t < cnt; t += 1024)
+    for (int t = tid; t < cnt; t += CTA)
       if (out + t < row_end) Cval[out + t] = S::out(kL2 ? __ldcg(wacc + t) : wacc[t]);
-    for (int w = tid; w < nw; w += 1024) {
+    for (int w = tid; w < nw; w += CTA) {
       unsigned word = bp[w].x;
       int64_t o = out + bp[w].y;
       while (word) {
@@ -336,14 +334,17 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
     ++*launches;
   }
   if (n_wins) {
+    // windows accumulating in L2 need no shared accumulators: two 512-thread
+    // CTAs per SM then work on two windows at once
+    constexpr int CTA = NumLimits<SR>::kL2Acc ? 512 : 1024;
+    constexpr int PER_SM = 1024 / CTA;
     constexpr size_t smem = (NumLimits<SR>::kL2Acc ? 0 : NumLimits<SR>::kWcap * sizeof(Acc)) +
-                            2 * kSpanWords * sizeof(unsigned) + 2 * 1024 * sizeof(long long) +
-                            1024 * sizeof(int);
-    set_smem(k_num_rank<SR>, smem);
-    k_num_rank<SR><<<capped(n_wins, sms), 1024, smem, s>>>(A, B, heavy_rows, wins, n_wins,
-                                                           span_counts, spans, hbits, b_sorted,
-                                                           flops, nnz, Crp, Ccol, Cval, err,
-                                                           num_hash_max, static_cast<Acc*>(racc));
+                            2 * kSpanWords * sizeof(unsigned) + 2 * CTA * sizeof(long long) +
+                            CTA * sizeof(int);
+    set_smem(k_num_rank<SR, CTA>, smem);
+    k_num_rank<SR, CTA><<<capped(n_wins, (int64_t)sms * PER_SM), CTA, smem, s>>>(
+        A, B, heavy_rows, wins, n_wins, span_counts, spans, hbits, b_sorted, flops, nnz, Crp, Ccol,
+        Cval, err, num_hash_max, static_cast<Acc*>(racc));
     ++*launches;
   }
 }
@@ -454,10 +455,21 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
 #undef CB_NUM
 }
 
+template <int SR>
+size_t rank_scratch_bytes_sr(int sms) {
+  // one slice of kWcap accumulators per resident CTA (two 512-thread CTAs per SM)
+  return NumLimits<SR>::kL2Acc
+             ? 2 * (size_t)sms * NumLimits<SR>::kWcap * sizeof(typename Sem<SR>::A)
+             : 0;
+}
+
 size_t rank_scratch_bytes(int sr, int sms) {
   switch (sr) {
-    case 1: return NumLimits<1>::kL2Acc ? (size_t)sms * NumLimits<1>::kWcap * sizeof(unsigned long long) : 0;
-    case 2: return NumLimits<2>::kL2Acc ? (size_t)sms * NumLimits<2>::kWcap * sizeof(double) : 0;
+    case 1: return rank_scratch_bytes_sr<1>(sms);
+    case 2: return rank_scratch_bytes_sr<2>(sms);
+    case 3: return rank_scratch_bytes_sr<3>(sms);
+    case 4: return rank_scratch_bytes_sr<4>(sms);
+    case 5: return rank_scratch_bytes_sr<5>(sms);
   }
   return 0;
 }
