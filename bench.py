@@ -795,6 +795,23 @@ def run_multi(args, cb, ctx, model):
                                   "products_per_s": info["flops"] / sec,
                                   "nnz_per_s": info["nnz"] / sec}
     flops = info["flops"]
+    # every wave captured into one CUDA graph (exact, waves cut by the flop bound)
+    ginfo = {}
+
+    def graph():
+        ginfo.update(cb.spgemm_batched(srs, As, Bs, lambda *a: None, budget_bytes=budget,
+                                       validate=False, ctx=ctx, mode="graph"))
+        torch.cuda.synchronize()
+
+    graph()
+    t0 = time.perf_counter()
+    graph()
+    sec_g = time.perf_counter() - t0
+    res["batched_graph"] = {"seconds": sec_g, "waves": ginfo["batches"],
+                            "products_per_s": ginfo["flops"] / sec_g,
+                            "nnz_per_s": ginfo["nnz"] / sec_g,
+                            "note": "one CUDA graph per semiring group (capture + instantiate + launch "
+                                    "inside the timed call)"}
 
     def plain():
         for sr, A, B in zip(srs, As, Bs):
@@ -809,6 +826,7 @@ def run_multi(args, cb, ctx, model):
     res["plain_per_product"] = {"seconds": sec, "products_per_s": flops / sec}
     res["batched_vs_plain"] = sec / res["batched_exact"]["seconds"]
     res["learned_batched_vs_plain"] = sec / res["batched_learned"]["seconds"]
+    res["graph_batched_vs_plain"] = sec / res["batched_graph"]["seconds"]
     res["timing"] = "host wall clock with device synchronisation, inputs resident"
     ctx.set_tune()
     del As, Bs

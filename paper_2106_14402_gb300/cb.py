@@ -319,6 +319,8 @@ FLAG_CHECK = 1
 FLAG_TIMING = 2
 FLAG_LEARNED_ROWS = 4
 FLAG_NO_FUSED = 8
+FLAG_GRAPH = 16
+FLAG_SYNC_FREE = 32
 
 # device status bits of cb_spgemm_fused
 FUSED_CAPACITY = 1
@@ -621,13 +623,20 @@ def row_features(A: DeviceCSR, B: DeviceCSR, ctx: Context | None = None) -> torc
 
 def spgemm_batched(semirings, As, Bs, on_wave, *, budget_bytes: int = 0, validate: bool = True,
                    sizing: str = "exact", mlp=None, margin: float = 0.25,
-                   ctx: Context | None = None) -> dict:
+                   ctx: Context | None = None, mode: str = "host") -> dict:
     """Batched products C_i = A_i (+).(x) B_i (cb_spgemm_batched).
 
     on_wave(wave, first, end, Cw) receives a DeviceCSR that stacks
     C_first..C_{end-1} by rows (each product's own column indices), valid
     only during the call; return True to stop.  Returns the statistics.
+    mode "sync_free" runs each wave without host synchronisation inside it;
+    mode "graph" also captures all waves into one CUDA graph, and on_wave is
+    then called as on_wave(wave, first, end, nrows, nnz) from a graph host
+    node (no tensors: CUDA may not be used there; the return value is
+    ignored).  Both need every row to have at most 4096 products, else the
+    call runs as mode "host".
     """
+    flags = {"host": 0, "sync_free": FLAG_SYNC_FREE, "graph": FLAG_GRAPH}[mode]
     ctx = ctx or context()
     n = len(As)
     assert len(Bs) == n and len(semirings) == n
@@ -640,6 +649,9 @@ def spgemm_batched(semirings, As, Bs, on_wave, *, budget_bytes: int = 0, validat
     def _cb(wave, first, end, cptr, user):
         try:
             c = cptr.contents
+            if mode == "graph":
+                on_wave(wave, first, end, c.nrows, c.nnz)
+                return 0
             dt = SEMIRING[semirings[first]][1]
             view = DeviceCSR(c.nrows, c.ncols, _view(c.row_ptr, c.nrows + 1, torch.int64, dev),
                              _view(c.col, c.nnz, torch.int32, dev), _view(c.val, c.nnz, dt, dev))
@@ -650,7 +662,7 @@ def spgemm_batched(semirings, As, Bs, on_wave, *, budget_bytes: int = 0, validat
 
     fn = BATCH_FN(_cb)
     opts = make_opts(sizing=sizing, validate=validate, budget_bytes=budget_bytes, on_batch=fn,
-                     mlp=mlp, margin=margin)
+                     mlp=mlp, margin=margin, flags=flags)
     ctx.check(ctx.lib.cb_spgemm_batched(ctx.handle, n, ctypes.cast(codes, c_void_p),
                                         ctypes.cast(sa, c_void_p), ctypes.cast(sb, c_void_p),
                                         ctypes.byref(opts)))

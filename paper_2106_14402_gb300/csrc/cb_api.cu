@@ -786,6 +786,219 @@ void row_group_sums(cb_ctx* ctx, const cb_csr* A, const DevCSR& dB, const cb_opt
   for (int64_t j = 0; j < n; ++j) sums[(size_t)j] = (int64_t)((double)(h[(size_t)j + 1] - h[(size_t)j]) * scale);
 }
 
+// Per-product sums of flops_i (an upper bound of nnz(C_i)) over the stacked
+// rows [bounds[j], bounds[j+1]), and the largest flops_i of any row.
+void group_flops(cb_ctx* ctx, const cb_csr* A, const DevCSR& dB, const std::vector<int64_t>& bounds,
+                 const int32_t* a_rcols, std::vector<int64_t>& sums, int64_t& max_flops) {
+  const int64_t m = A->nrows, n = (int64_t)bounds.size() - 1;
+  DevBuf flops(ctx), pre(ctx), idx(ctx), got(ctx), counters(ctx);
+  flops.alloc(sizeof(int64_t) * (size_t)(m + 1));
+  pre.alloc(sizeof(int64_t) * (size_t)(m + 1));
+  idx.alloc(sizeof(int64_t) * bounds.size());
+  got.alloc(sizeof(int64_t) * bounds.size());
+  counters.alloc(sizeof(int64_t) * cb::kCounters);
+  DevCSR dA = dev(A);
+  dA.rcols = a_rcols;
+  CB_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+  cb::launch_classify_sym(dA, dB, flops.as<int64_t>(), nullptr, counters.as<int64_t>(), ctx->stream,
+                          ctx->sms);
+  ensure(ctx, &ctx->ws2, &ctx->ws2_cap, align_up(8 * (size_t)cb::scan_partials(m)));
+  cb::launch_exclusive_scan(flops.as<int64_t>(), m, pre.as<int64_t>(), static_cast<int64_t*>(ctx->ws2),
+                            ctx->stream);
+  CB_CUDA(cudaMemcpyAsync(idx.p, bounds.data(), sizeof(int64_t) * bounds.size(),
+                          cudaMemcpyHostToDevice, ctx->stream));
+  cb::launch_gather(pre.as<int64_t>(), idx.as<int64_t>(), (int64_t)bounds.size(), got.as<int64_t>(),
+                    ctx->stream);
+  CB_LAUNCHED();
+  std::vector<int64_t> h(bounds.size());
+  CB_CUDA(cudaMemcpyAsync(h.data(), got.p, sizeof(int64_t) * h.size(), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  read_counters(ctx, counters.as<int64_t>(), nullptr, 0);  // synchronises
+  max_flops = ctx->host[cb::kMaxFlops];
+  sums.resize((size_t)n);
+  for (int64_t j = 0; j < n; ++j) sums[(size_t)j] = h[(size_t)j + 1] - h[(size_t)j];
+}
+
+// What a CUDA-graph host node hands to the wave callback.
+struct GraphWave {
+  const cb_opts* opt;
+  int wave, first, end;
+  cb_csr C;
+  const int64_t* nnz;  // pinned host word written by the graph before the node
+};
+
+void CUDART_CB graph_wave_host(void* p) {
+  GraphWave* g = static_cast<GraphWave*>(p);
+  g->C.nnz = *g->nnz;
+  g->opt->on_batch(g->wave, g->first, g->end, &g->C, g->opt->user);
+}
+
+// Graph mode of a group: every row of every product fits the hash tiers
+// (flops_i <= 4096), so each wave runs a launch sequence without host
+// synchronisation -- tier sizes stay on the device, C is sized by the wave's
+// flop total -- and all waves are captured into one CUDA graph, launched once.
+// Returns false (nothing done) when a row is too large for the hash tiers or
+// a product's flop bound alone exceeds the budget.
+bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB, const int32_t* rcols,
+                         const std::vector<int64_t>& arow, int n, int first, int64_t kmax,
+                         const cb_opts& opt, int& wave, int& kernels, int64_t& nnz_total,
+                         int64_t& flops_total, bool capture) {
+  const int64_t vsz = (int64_t)value_size(sr), per = 4 + vsz;
+  std::vector<int64_t> sizes;
+  int64_t max_flops = 0;
+  group_flops(ctx, &sA, dB, arow, rcols, sizes, max_flops);
+  kernels += 3 + 3 + 1;
+  if (max_flops > cb::kSymLargeMax) return false;
+  const int64_t hash_max = cb::kSymLargeMax;  // every row in a hash tier, symbolic and numeric
+  // waves by the flop bound
+  std::vector<int> cut{0};
+  int64_t rows = 0, nz = 0;
+  const int64_t budget = opt.budget_bytes > 0 ? opt.budget_bytes : INT64_MAX;
+  for (int i = 0; i < n; ++i) {
+    const int64_t ri = arow[i + 1] - arow[i];
+    if (8 * (ri + 1) + sizes[(size_t)i] * per > budget) return false;  // host path sizes it exactly
+    if (i > cut.back() && 8 * (rows + ri + 1) + (nz + sizes[(size_t)i]) * per > budget) {
+      cut.push_back(i);
+      rows = ri;
+      nz = sizes[(size_t)i];
+    } else {
+      rows += ri;
+      nz += sizes[(size_t)i];
+    }
+  }
+  cut.push_back(n);
+  const int nw = (int)cut.size() - 1;
+  int64_t max_rows = 0, max_cap = 1;
+  for (int w = 0; w < nw; ++w) {
+    max_rows = std::max(max_rows, arow[cut[w + 1]] - arow[cut[w]]);
+    int64_t f = 0;
+    for (int i = cut[w]; i < cut[w + 1]; ++i) f += sizes[(size_t)i];
+    max_cap = std::max(max_cap, f);
+  }
+  // everything the graph touches is allocated before the capture
+  DevBuf orp(ctx), ocol(ctx), oval(ctx), wsb(ctx), errw(ctx);
+  orp.alloc(8 * (size_t)(max_rows + 1));
+  ocol.alloc(4 * (size_t)max_cap);
+  oval.alloc((size_t)vsz * (size_t)max_cap);
+  const size_t mr = (size_t)max_rows + 1;
+  const size_t wsz = align_up(8 * (size_t)cb::kCounters) + 2 * align_up(8 * mr) + 2 * align_up(4 * mr) +
+                     align_up(8 * (size_t)cb::scan_partials(max_rows));
+  wsb.alloc(wsz);
+  errw.alloc(sizeof(int64_t));
+  Carver cv{wsb.as<char>()};
+  int64_t* counters = cv.take<int64_t>(cb::kCounters);
+  int64_t* flops = cv.take<int64_t>(mr);
+  int64_t* nnz = cv.take<int64_t>(mr);
+  int32_t* perm_sym = cv.take<int32_t>(mr);
+  int32_t* perm_num = cv.take<int32_t>(mr);
+  int64_t* partial = cv.take<int64_t>(cb::scan_partials(max_rows));
+  int64_t* hnnz = nullptr;
+  CB_CUDA(cudaMallocHost((void**)&hnnz, sizeof(int64_t) * (size_t)nw));
+  struct HostFree {
+    int64_t* p;
+    ~HostFree() { if (p) cudaFreeHost(p); }
+  } hfree{hnnz};
+  std::vector<GraphWave> gw((size_t)nw);
+  CB_CUDA(cudaMemsetAsync(errw.p, 0, sizeof(int64_t), ctx->stream));
+  cb::prepare_dev_launchers(sr);  // kernel attributes are set outside the capture
+  CB_CUDA(cudaStreamSynchronize(ctx->stream));
+
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // the legacy default stream cannot be captured: capture on a private
+  // stream then (the context's stream is idle here, synchronised above)
+  struct StreamSwap {
+    cb_ctx* ctx;
+    cudaStream_t saved, own = nullptr;
+    ~StreamSwap() {
+      ctx->stream = saved;
+      if (own) {
+        cudaStreamSynchronize(own);
+        cudaStreamDestroy(own);
+      }
+    }
+  } swap{ctx, ctx->stream};
+  if (capture && (ctx->stream == nullptr || ctx->stream == cudaStreamLegacy ||
+                  ctx->stream == cudaStreamPerThread)) {
+    CB_CUDA(cudaStreamCreateWithFlags(&swap.own, cudaStreamNonBlocking));
+    ctx->stream = swap.own;
+  }
+  if (capture) CB_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t cap_err = cudaSuccess;
+  for (int w = 0; w < nw && cap_err == cudaSuccess; ++w) {
+    const int64_t r0 = arow[cut[w]], m = arow[cut[w + 1]] - r0;
+    const cb_csr Aw{m, sA.ncols, 0, sA.row_ptr + r0, sA.col, sA.val};
+    DevCSR dA = dev(&Aw);
+    dA.rcols = rcols + r0;
+    cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream);
+    cb::launch_classify_sym(dA, dB, flops, nullptr, counters, ctx->stream, ctx->sms, nullptr, hash_max);
+    cb::launch_scatter_sym(m, kmax, flops, perm_sym, nnz, counters, ctx->stream, ctx->sms, nullptr,
+                           nullptr, hash_max, dA.rcols);
+    cb::launch_symbolic_dev(dA, dB, perm_sym, counters, flops, nnz, ctx->stream, ctx->sms);
+    cb::launch_exclusive_scan(nnz, m, orp.as<int64_t>(), partial, ctx->stream);
+    cb::launch_classify_num(sr, m, nnz, perm_num, counters, ctx->stream, ctx->sms, nullptr, hash_max);
+    cb::launch_numeric_dev(sr, dA, dB, perm_num, counters, flops, nnz, orp.as<int64_t>(),
+                           ocol.as<int32_t>(), oval.p, errw.as<int64_t>(), ctx->stream, ctx->sms);
+    cudaMemcpyAsync(hnnz + w, orp.as<int64_t>() + m, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                    ctx->stream);
+    gw[(size_t)w] = GraphWave{&opt, wave + w, first + cut[w], first + cut[w + 1],
+                              cb_csr{m, kmax, 0, orp.as<int64_t>(), ocol.as<int32_t>(), oval.p},
+                              hnnz + w};
+    kernels += 2 + 2 + 3 + 3 + 2 + 3;
+    if (capture) {
+      cudaLaunchHostFunc(ctx->stream, graph_wave_host, &gw[(size_t)w]);
+      cap_err = cudaGetLastError();
+    } else {
+      // the same launch sequence without the capture: the callback runs on this
+      // thread after the wave (and may use CUDA)
+      CB_LAUNCHED();
+      CB_CUDA(cudaStreamSynchronize(ctx->stream));
+      gw[(size_t)w].C.nnz = hnnz[w];
+      const int stop = opt.on_batch(gw[(size_t)w].wave, gw[(size_t)w].first, gw[(size_t)w].end,
+                                    &gw[(size_t)w].C, opt.user);
+      if (stop) {
+        for (int v = 0; v <= w; ++v) nnz_total += hnnz[v];
+        wave += w + 1;
+        throw Fail{-1};
+      }
+    }
+  }
+  if (!capture) {
+    int64_t err_word = 0;
+    CB_CUDA(cudaMemcpy(&err_word, errw.p, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (err_word) fail(ctx, CB_ERR_CUDA, "sync-free wave: internal consistency check failed");
+    for (int w = 0; w < nw; ++w) nnz_total += hnnz[w];
+    for (int i = 0; i < n; ++i) flops_total += sizes[(size_t)i];
+    wave += nw;
+    return true;
+  }
+  const cudaError_t end_err = cudaStreamEndCapture(ctx->stream, &graph);
+  if (cap_err != cudaSuccess || end_err != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    ctx->err = std::string("graph capture: ") +
+               cudaGetErrorString(cap_err != cudaSuccess ? cap_err : end_err);
+    throw Fail{CB_ERR_CUDA};
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    ctx->err = std::string("graph instantiate: ") + cudaGetErrorString(ie);
+    throw Fail{CB_ERR_CUDA};
+  }
+  const cudaError_t le = cudaGraphLaunch(exec, ctx->stream);
+  const cudaError_t se = cudaStreamSynchronize(ctx->stream);
+  cudaGraphExecDestroy(exec);
+  CB_CUDA(le);
+  CB_CUDA(se);
+  int64_t err_word = 0;
+  CB_CUDA(cudaMemcpy(&err_word, errw.p, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  if (err_word) fail(ctx, CB_ERR_CUDA, "graph wave: internal consistency check failed");
+  for (int w = 0; w < nw; ++w) nnz_total += hnnz[w];
+  for (int i = 0; i < n; ++i) flops_total += sizes[(size_t)i];
+  wave += nw;
+  return true;
+}
+
 // One run of consecutive products that share a semiring (see cb_spgemm_batched).
 void batched_group(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, int n, int first,
                    const cb_opts& opt, int& wave, int& kernels, int64_t& nnz_total,
@@ -836,6 +1049,10 @@ void batched_group(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, int n,
   kernels += 2;
   const DevCSR dB{rowsB, kmax, sBrp.as<int64_t>(), sBcol.as<int32_t>(), sBval.p};
   const cb_csr sA{rowsA, rowsB, nnzA, sArp.as<int64_t>(), sAcol.as<int32_t>(), sAval.p};
+  if ((opt.flags & (CB_FLAG_GRAPH | CB_FLAG_SYNC_FREE)) &&
+      batched_group_graph(ctx, sr, sA, dB, rcols.as<int32_t>(), arow, n, first, kmax, opt, wave,
+                          kernels, nnz_total, flops_total, (opt.flags & CB_FLAG_GRAPH) != 0))
+    return;
 
   // waves: consecutive products whose output fits the budget
   std::vector<int> cut{0};

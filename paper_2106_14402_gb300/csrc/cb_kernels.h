@@ -172,6 +172,19 @@ void launch_spmspv_step(int sr, int step, const DevCSR& A, const int32_t* x_idx,
                         unsigned* touched, int64_t n, int64_t* wcnt, const int64_t* wpre,
                         int32_t* y_idx, void* y_val, int64_t cap, int64_t* err, cudaStream_t s,
                         int sms);
+// Hash-tier symbolic and numeric passes whose tier sizes are read on the
+// device (counters from launch_classify_sym / launch_classify_num): no host
+// synchronisation, so the sequence can be captured into a CUDA graph.  Every
+// row must be in a hash tier (u_i <= sym_hash_max, nnz_i <= num_hash_max).
+void prepare_symbolic_dev();
+void prepare_dev_launchers(int sr);  // sets the shared-memory attributes of both (not capturable)
+void launch_symbolic_dev(const DevCSR& A, const DevCSR& B, const int32_t* perm,
+                         const int64_t* counters, const int64_t* flops, int64_t* nnz,
+                         cudaStream_t s, int sms);
+void launch_numeric_dev(int sr, const DevCSR& A, const DevCSR& B, const int32_t* perm,
+                        const int64_t* counters, const int64_t* flops, const int64_t* nnz,
+                        const int64_t* Crp, int32_t* Ccol, void* Cval, int64_t* err, cudaStream_t s,
+                        int sms);
 // Bytes of the global accumulator slices of the rank-window numeric kernel
 // (semirings whose windows accumulate in L2; 0 otherwise).
 size_t rank_scratch_bytes(int sr, int sms);

@@ -36,12 +36,19 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
                                                   const int64_t* nnz, const int64_t* Crp,
                                                   int32_t* Ccol, typename Sem<SR>::T* Cval,
                                                   int64_t* err, uint8_t* learned = nullptr,
-                                                  int64_t* cnt_out = nullptr) {
+                                                  int64_t* cnt_out = nullptr,
+                                                  const int64_t* dcnt = nullptr, int tier = 0) {
   typedef Sem<SR> S;
   typedef typename S::A Acc;
   typedef typename S::T T;
   constexpr int TEAMS = CTA / TEAM;
   constexpr int PER = TABLE_MAX / TEAM;
+  if (dcnt) {  // tier sizes on the device (launch sequences without host synchronisation)
+    int64_t beg = 0;
+    for (int t = 1; t < tier; ++t) beg += dcnt[t];
+    rows += beg;
+    nrows_tier = dcnt[tier];
+  }
   extern __shared__ __align__(16) unsigned char num_smem[];
   __shared__ int scan_scratch[TEAMS][33];
   __shared__ int overflow[TEAMS];
@@ -349,6 +356,36 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
   }
 }
 
+// Hash tiers only, tier sizes read on the device (counters[kCntNum..]): the
+// grids are sized for the worst case and the kernels stride over their tier.
+template <int SR>
+void numeric_dev_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int64_t* counters,
+                    const int64_t* flops, const int64_t* nnz, const int64_t* Crp, int32_t* Ccol,
+                    void* Cval_, int64_t* err, cudaStream_t s, int sms, int64_t m) {
+  typedef typename Sem<SR>::A Acc;
+  typedef typename Sem<SR>::T T;
+  T* Cval = reinterpret_cast<T*>(Cval_);
+  constexpr size_t slot = sizeof(Acc) + sizeof(int);
+  const int64_t* dc = counters + kCntNum;
+  {
+    constexpr int CTA = 256, TEAM = 32, TBL = 2 * kNumWarpMax;
+    const size_t smem = (CTA / TEAM) * TBL * slot;
+    k_num_hash<SR, CTA, TEAM, TBL><<<capped((m + 7) / 8, sms * 8), CTA, smem, s>>>(
+        A, B, perm, 0, flops, nnz, Crp, Ccol, Cval, err, nullptr, nullptr, dc, kNumWarp);
+  }
+  {
+    constexpr int CTA = 256, TEAM = 256, TBL = 2 * kNumSmallMax;
+    k_num_hash<SR, CTA, TEAM, TBL><<<capped(m, sms * 8), CTA, TBL * slot, s>>>(
+        A, B, perm, 0, flops, nnz, Crp, Ccol, Cval, err, nullptr, nullptr, dc, kNumSmall);
+  }
+  {  // shared-memory attribute set by prepare_dev_launchers
+    constexpr int CTA = 512, TEAM = 512, TBL = 2 * NumLimits<SR>::kLargeMax;
+    const size_t smem = TBL * slot;
+    k_num_hash<SR, CTA, TEAM, TBL><<<capped(m, sms * 4), CTA, smem, s>>>(
+        A, B, perm, 0, flops, nnz, Crp, Ccol, Cval, err, nullptr, nullptr, dc, kNumLarge);
+  }
+}
+
 template <int SR>
 void learned_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int64_t* seg_begin,
                 const int64_t* seg_count, const int64_t* flops, const int64_t* cap,
@@ -461,6 +498,38 @@ size_t rank_scratch_bytes_sr(int sms) {
   return NumLimits<SR>::kL2Acc
              ? 2 * (size_t)sms * NumLimits<SR>::kWcap * sizeof(typename Sem<SR>::A)
              : 0;
+}
+
+template <int SR>
+void prepare_numeric_dev_sr() {
+  constexpr int CTA = 512, TEAM = 512, TBL = 2 * NumLimits<SR>::kLargeMax;
+  set_smem(k_num_hash<SR, CTA, TEAM, TBL>, TBL * (sizeof(typename Sem<SR>::A) + sizeof(int)));
+}
+
+void prepare_dev_launchers(int sr) {
+  prepare_symbolic_dev();
+  switch (sr) {
+    case 1: prepare_numeric_dev_sr<1>(); break;
+    case 2: prepare_numeric_dev_sr<2>(); break;
+    case 3: prepare_numeric_dev_sr<3>(); break;
+    case 4: prepare_numeric_dev_sr<4>(); break;
+    case 5: prepare_numeric_dev_sr<5>(); break;
+  }
+}
+
+void launch_numeric_dev(int sr, const DevCSR& A, const DevCSR& B, const int32_t* perm,
+                        const int64_t* counters, const int64_t* flops, const int64_t* nnz,
+                        const int64_t* Crp, int32_t* Ccol, void* Cval, int64_t* err, cudaStream_t s,
+                        int sms) {
+  const int64_t m = A.nrows;
+  if (m == 0) return;
+  switch (sr) {
+    case 1: numeric_dev_sr<1>(A, B, perm, counters, flops, nnz, Crp, Ccol, Cval, err, s, sms, m); break;
+    case 2: numeric_dev_sr<2>(A, B, perm, counters, flops, nnz, Crp, Ccol, Cval, err, s, sms, m); break;
+    case 3: numeric_dev_sr<3>(A, B, perm, counters, flops, nnz, Crp, Ccol, Cval, err, s, sms, m); break;
+    case 4: numeric_dev_sr<4>(A, B, perm, counters, flops, nnz, Crp, Ccol, Cval, err, s, sms, m); break;
+    case 5: numeric_dev_sr<5>(A, B, perm, counters, flops, nnz, Crp, Ccol, Cval, err, s, sms, m); break;
+  }
 }
 
 size_t rank_scratch_bytes(int sr, int sms) {

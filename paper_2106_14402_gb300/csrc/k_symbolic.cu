@@ -20,9 +20,16 @@ namespace {
 template <int CTA, int TEAM, int TABLE_MAX>
 __global__ void __launch_bounds__(CTA) k_sym_hash(DevCSR A, DevCSR B, const int32_t* rows,
                                                   int64_t nrows_tier, const int64_t* flops,
-                                                  int64_t* nnz) {
+                                                  int64_t* nnz, const int64_t* dcnt = nullptr,
+                                                  int tier = 0) {
   extern __shared__ int sym_keys[];
   __shared__ int block_count;
+  if (dcnt) {  // tier sizes on the device (launch sequences without host synchronisation)
+    int64_t beg = 0;
+    for (int t = 1; t < tier; ++t) beg += dcnt[t];
+    rows += beg;
+    nrows_tier = dcnt[tier];
+  }
   constexpr int TEAMS = CTA / TEAM;
   const int team = threadIdx.x / TEAM, lane = threadIdx.x % TEAM;
   int* keys = sym_keys + team * TABLE_MAX;
@@ -219,6 +226,36 @@ void launch_check_sorted(const DevCSR& B, int64_t* counters, cudaStream_t s, int
   if (B.nrows == 0) return;
   int64_t g = (B.nrows + 7) / 8;
   k_check_sorted<<<(int)(g < sms * 8 ? g : sms * 8), 256, 0, s>>>(B, counters);
+}
+
+void prepare_symbolic_dev() {
+  constexpr int CTA = 512, TEAM = 512, TBL = 2 * kSymLargeMax;
+  set_smem(k_sym_hash<CTA, TEAM, TBL>, TBL * sizeof(int));
+}
+
+void launch_symbolic_dev(const DevCSR& A, const DevCSR& B, const int32_t* perm,
+                         const int64_t* counters, const int64_t* flops, int64_t* nnz,
+                         cudaStream_t s, int sms) {
+  const int64_t m = A.nrows;
+  if (m == 0) return;
+  const int64_t* dc = counters + kCntSym;
+  {
+    constexpr int CTA = 256, TEAM = 32, TBL = 2 * kSymWarpMax;
+    const size_t smem = (CTA / TEAM) * TBL * sizeof(int);
+    k_sym_hash<CTA, TEAM, TBL><<<capped((m + 7) / 8, sms * 8), CTA, smem, s>>>(A, B, perm, 0, flops,
+                                                                              nnz, dc, kSymWarp);
+  }
+  {
+    constexpr int CTA = 256, TEAM = 256, TBL = 2 * kSymSmallMax;
+    k_sym_hash<CTA, TEAM, TBL><<<capped(m, sms * 8), CTA, TBL * sizeof(int), s>>>(A, B, perm, 0, flops,
+                                                                                 nnz, dc, kSymSmall);
+  }
+  {  // shared-memory attribute set by prepare_symbolic_dev
+    constexpr int CTA = 512, TEAM = 512, TBL = 2 * kSymLargeMax;
+    const size_t smem = TBL * sizeof(int);
+    k_sym_hash<CTA, TEAM, TBL><<<capped(m, sms * 4), CTA, smem, s>>>(A, B, perm, 0, flops, nnz, dc,
+                                                                    kSymLarge);
+  }
 }
 
 void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,

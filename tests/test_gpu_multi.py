@@ -40,7 +40,7 @@ def test_device_generator_matches_host_definition(cb):
         assert np.array_equal(val, A.val)
 
 
-def run(cb, plan, budget, sizing="exact", mlp=None):
+def run(cb, plan, budget, sizing="exact", mlp=None, mode="host"):
     from paper_2106_14402_gb300 import gen_device
     As, Bs, host = [], [], []
     for p in plan:
@@ -59,7 +59,7 @@ def run(cb, plan, budget, sizing="exact", mlp=None):
         assert r0 == Cw.nrows
 
     st = cb.spgemm_batched([p["semiring"] for p in plan], As, Bs, on_wave, budget_bytes=budget,
-                           sizing=sizing, mlp=mlp)
+                           sizing=sizing, mlp=mlp, mode=mode)
     return got, st
 
 
@@ -114,3 +114,76 @@ def test_batched_stops_early_and_rejects_tiny_budget(cb):
     with pytest.raises(cb.CBError) as e:
         cb.spgemm_batched([p["semiring"] for p in plan], As, Bs, lambda *a: False, budget_bytes=4096)
     assert e.value.code == 6
+
+
+def bound_bytes(p):
+    A, B = gen.batched_product_host(p)
+    vsz = 4 if p["semiring"] == "min_plus_u32" else 8
+    return 8 * (p["n"] + 1) + int(oracle.row_stats(A, B)[0].sum()) * (4 + vsz)
+
+
+def flop_waves(plan, budget):
+    """Waves when each run of same-semiring products is packed by its flop
+    bound: a wave holds one row-pointer array and the flops of its products."""
+    waves, rows, flops, sr = 0, 0, 0, None
+    for p in plan:
+        A, B = gen.batched_product_host(p)
+        f = int(oracle.row_stats(A, B)[0].sum())
+        per = 4 + (4 if p["semiring"] == "min_plus_u32" else 8)
+        if p["semiring"] != sr or 8 * (rows + p["n"] + 1) + (flops + f) * per > budget:
+            waves, rows, flops, sr = waves + 1, p["n"], f, p["semiring"]
+        else:
+            rows, flops = rows + p["n"], flops + f
+    return waves
+
+
+@pytest.mark.parametrize("waves", [False, True])
+def test_sync_free_waves_match_oracle(cb, waves):
+    """The launch sequence without host synchronisation (tier sizes on the
+    device, C sized by the wave's flop bound) gives the exact products."""
+    plan = small_plan()
+    want = reference(plan)
+    budget = int(1.3 * max(bound_bytes(p) for p in plan)) if waves else 0
+    got, st = run(cb, plan, budget, mode="sync_free")
+    assert len(got) == len(plan)
+    if waves:
+        assert st["batches"] == flop_waves(plan, budget) > 3   # cut by the flop bound
+    for i, p in enumerate(plan):
+        compare_rows(p["semiring"], got[i], want[i])
+
+
+def test_graph_waves(cb):
+    """All waves captured into one CUDA graph: the same waves, and every
+    wave's nnz equal to the oracle's, as the sync-free run reports them."""
+    from paper_2106_14402_gb300 import gen_device
+    plan = small_plan()
+    want = reference(plan)
+    budget = int(1.3 * max(bound_bytes(p) for p in plan))
+    As = [gen_device.er(p["seed_a"], p["n"], p["deg"], p["semiring"], p["seed_va"]) for p in plan]
+    Bs = [gen_device.er(p["seed_b"], p["n"], p["deg"], p["semiring"], p["seed_vb"]) for p in plan]
+    srs = [p["semiring"] for p in plan]
+    waves = []
+    st = cb.spgemm_batched(srs, As, Bs, lambda w, f, e, nr, nz: waves.append((w, f, e, nr, nz)),
+                           budget_bytes=budget, mode="graph")
+    free = []
+    cb.spgemm_batched(srs, As, Bs, lambda w, f, e, C: free.append((w, f, e, C.nrows, C.nnz)),
+                      budget_bytes=budget, mode="sync_free")
+    assert waves == free and st["batches"] == len(waves) == flop_waves(plan, budget) > 3
+    for w, f, e, nr, nz in waves:
+        assert nr == sum(plan[i]["n"] for i in range(f, e))
+        assert nz == sum(int(want[i][0][-1]) for i in range(f, e))
+    assert st["nnz"] == sum(int(x[0][-1]) for x in want)
+
+
+def test_graph_mode_falls_back_for_large_rows(cb):
+    """A product with rows above 4096 products runs on the host-synchronised
+    path; results stay exact."""
+    sr = "min_plus_u32"
+    P = gen.rmat(11, 16, *gen.RMAT_ABCD, seed=300)
+    A = P.with_values(gen.random_values(sr, P.nnz, 301))
+    flops, _ = oracle.row_stats(A, A)
+    assert flops.max() > 4096
+    dA = cb.DeviceCSR.from_host(A, sr)
+    seen = []
+    st = cb.spgemm_batched([sr, sr], [dA, dA], [dA, dA], lambda *a: seen.append(a), mode="graph")
+    assert st["nnz"] == 2 * int(oracle.spgemm(sr, A, A)[0][-1]) and len(seen) == 1
