@@ -113,15 +113,15 @@ enum {
                          count, also size each batch's rows from predictions
                          (default: predictions set the batch count only and each
                          batch runs the exact two-phase path) */
-  CB_FLAG_GRAPH = 16,  /* cb_spgemm_batched: when every row of every product has at
-                         most 4096 products and every product's flop bound (row
-                         pointers + flops entries) fits the budget, run each wave as a
-                         launch sequence without
-                         host synchronisation (tier sizes kept on the device, C sized by
-                         the wave's flop total, waves cut by that bound) and capture all
-                         waves of a group into one CUDA graph, launched once; on_batch
-                         then runs as a graph host node, must not call CUDA, and its
-                         return value is ignored.  Otherwise the flag has no effect. */
+  CB_FLAG_GRAPH = 16,  /* cb_spgemm_batched, exact sizing: cut waves by the flop bound
+                         (row pointers + flops entries per product within the budget),
+                         run each wave as a launch sequence without host synchronisation
+                         (tier sizes, heavy-row and window counts kept on the device; C
+                         sized by the wave's flop total) and capture all waves of a group
+                         into one CUDA graph, launched once; on_batch then runs as a graph
+                         host node, must not call CUDA, and its return value is ignored.
+                         A group with a product whose flop bound alone exceeds the budget
+                         runs as without the flag. */
   CB_FLAG_SYNC_FREE = 32, /* cb_spgemm_batched: the launch sequence of CB_FLAG_GRAPH
                          without the capture; on_batch runs on the calling thread after
                          each wave (and may use CUDA) */

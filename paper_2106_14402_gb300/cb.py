@@ -633,8 +633,8 @@ def spgemm_batched(semirings, As, Bs, on_wave, *, budget_bytes: int = 0, validat
     mode "graph" also captures all waves into one CUDA graph, and on_wave is
     then called as on_wave(wave, first, end, nrows, nnz) from a graph host
     node (no tensors: CUDA may not be used there; the return value is
-    ignored).  Both need every row to have at most 4096 products, else the
-    call runs as mode "host".
+    ignored).  Both cut waves by the flop bound; a group with a product whose
+    bound alone exceeds the budget runs as mode "host".
     """
     flags = {"host": 0, "sync_free": FLAG_SYNC_FREE, "graph": FLAG_GRAPH}[mode]
     ctx = ctx or context()

@@ -833,12 +833,11 @@ void CUDART_CB graph_wave_host(void* p) {
   g->opt->on_batch(g->wave, g->first, g->end, &g->C, g->opt->user);
 }
 
-// Graph mode of a group: every row of every product fits the hash tiers
-// (flops_i <= 4096), so each wave runs a launch sequence without host
-// synchronisation -- tier sizes stay on the device, C is sized by the wave's
-// flop total -- and all waves are captured into one CUDA graph, launched once.
-// Returns false (nothing done) when a row is too large for the hash tiers or
-// a product's flop bound alone exceeds the budget.
+// Graph mode of a group: each wave runs a launch sequence without host
+// synchronisation -- tier sizes, heavy-row and window counts stay on the
+// device, C is sized by the wave's flop total, workspaces by upper bounds --
+// and all waves are captured into one CUDA graph, launched once.  Returns
+// false (nothing done) when a product's flop bound alone exceeds the budget.
 bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB, const int32_t* rcols,
                          const std::vector<int64_t>& arow, int n, int first, int64_t kmax,
                          const cb_opts& opt, int& wave, int& kernels, int64_t& nnz_total,
@@ -848,8 +847,10 @@ bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB
   int64_t max_flops = 0;
   group_flops(ctx, &sA, dB, arow, rcols, sizes, max_flops);
   kernels += 3 + 3 + 1;
-  if (max_flops > cb::kSymLargeMax) return false;
-  const int64_t hash_max = cb::kSymLargeMax;  // every row in a hash tier, symbolic and numeric
+  const int64_t sym_max = ctx->tune.sym_hash_max;
+  const int64_t num_max = std::min<int64_t>(ctx->tune.num_hash_max, cb::num_large_max(sr));
+  const int64_t spans = (kmax + cb::kSpanCols - 1) / cb::kSpanCols;
+  const int wcut = cb::num_window_cut(sr);
   // waves by the flop bound
   std::vector<int> cut{0};
   int64_t rows = 0, nz = 0;
@@ -868,12 +869,15 @@ bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB
   }
   cut.push_back(n);
   const int nw = (int)cut.size() - 1;
-  int64_t max_rows = 0, max_cap = 1;
+  int64_t max_rows = 0, max_cap = 1, max_wins = 1;
   for (int w = 0; w < nw; ++w) {
-    max_rows = std::max(max_rows, arow[cut[w + 1]] - arow[cut[w]]);
+    const int64_t r = arow[cut[w + 1]] - arow[cut[w]];
+    max_rows = std::max(max_rows, r);
     int64_t f = 0;
     for (int i = cut[w]; i < cut[w + 1]; ++i) f += sizes[(size_t)i];
     max_cap = std::max(max_cap, f);
+    // every (row, span) yields at most count / wcut + 1 windows; counts sum to <= flops
+    max_wins = std::max(max_wins, r * spans + f / wcut + 1);
   }
   // everything the graph touches is allocated before the capture
   DevBuf orp(ctx), ocol(ctx), oval(ctx), wsb(ctx), errw(ctx);
@@ -881,8 +885,12 @@ bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB
   ocol.alloc(4 * (size_t)max_cap);
   oval.alloc((size_t)vsz * (size_t)max_cap);
   const size_t mr = (size_t)max_rows + 1;
+  const size_t units = (size_t)max_rows * (size_t)spans + 1;
+  const size_t racc_bytes = cb::rank_scratch_bytes(sr, ctx->sms);
   const size_t wsz = align_up(8 * (size_t)cb::kCounters) + 2 * align_up(8 * mr) + 2 * align_up(4 * mr) +
-                     align_up(8 * (size_t)cb::scan_partials(max_rows));
+                     align_up(8 * (size_t)cb::scan_partials(max_rows)) + align_up(4 * units) +
+                     align_up(8 * units) + align_up(sizeof(cb::Window) * (size_t)max_wins) +
+                     align_up(racc_bytes);
   wsb.alloc(wsz);
   errw.alloc(sizeof(int64_t));
   Carver cv{wsb.as<char>()};
@@ -892,6 +900,10 @@ bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB
   int32_t* perm_sym = cv.take<int32_t>(mr);
   int32_t* perm_num = cv.take<int32_t>(mr);
   int64_t* partial = cv.take<int64_t>(cb::scan_partials(max_rows));
+  int32_t* span_counts = cv.take<int32_t>(units);
+  int2* span_wins = cv.take<int2>(units);
+  cb::Window* wins = cv.take<cb::Window>((size_t)max_wins);
+  void* racc = racc_bytes ? cv.take<char>(racc_bytes) : nullptr;
   int64_t* hnnz = nullptr;
   CB_CUDA(cudaMallocHost((void**)&hnnz, sizeof(int64_t) * (size_t)nw));
   struct HostFree {
@@ -931,14 +943,19 @@ bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB
     DevCSR dA = dev(&Aw);
     dA.rcols = rcols + r0;
     cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream);
-    cb::launch_classify_sym(dA, dB, flops, nullptr, counters, ctx->stream, ctx->sms, nullptr, hash_max);
+    cb::launch_check_sorted(dB, counters, ctx->stream, ctx->sms);
+    cb::launch_classify_sym(dA, dB, flops, nullptr, counters, ctx->stream, ctx->sms, nullptr, sym_max);
     cb::launch_scatter_sym(m, kmax, flops, perm_sym, nnz, counters, ctx->stream, ctx->sms, nullptr,
-                           nullptr, hash_max, dA.rcols);
-    cb::launch_symbolic_dev(dA, dB, perm_sym, counters, flops, nnz, ctx->stream, ctx->sms);
+                           nullptr, sym_max, dA.rcols);
+    cb::launch_symbolic_dev(dA, dB, perm_sym, counters, flops, nnz, span_counts, span_wins, wcut, wins,
+                            max_wins, ctx->stream, ctx->sms);
     cb::launch_exclusive_scan(nnz, m, orp.as<int64_t>(), partial, ctx->stream);
-    cb::launch_classify_num(sr, m, nnz, perm_num, counters, ctx->stream, ctx->sms, nullptr, hash_max);
+    cb::launch_classify_num(sr, m, nnz, perm_num, counters, ctx->stream, ctx->sms, nullptr, num_max);
     cb::launch_numeric_dev(sr, dA, dB, perm_num, counters, flops, nnz, orp.as<int64_t>(),
-                           ocol.as<int32_t>(), oval.p, errw.as<int64_t>(), ctx->stream, ctx->sms);
+                           ocol.as<int32_t>(), oval.p, errw.as<int64_t>(), ctx->stream, ctx->sms,
+                           perm_sym, wins, span_counts, spans, racc, num_max);
+    // the symbolic phase's consistency word (window capacity, span cut) joins the error word
+    cb::launch_merge_error(counters + cb::kError, errw.as<int64_t>(), ctx->stream);
     cudaMemcpyAsync(hnnz + w, orp.as<int64_t>() + m, sizeof(int64_t), cudaMemcpyDeviceToHost,
                     ctx->stream);
     gw[(size_t)w] = GraphWave{&opt, wave + w, first + cut[w], first + cut[w + 1],

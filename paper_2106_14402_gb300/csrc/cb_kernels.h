@@ -166,25 +166,30 @@ void launch_mlp_predict(const void* wb, const float* master, const float* norm, 
 // entries (bad indices set *err), 2 push into the SPA (cpre = scanned chunk
 // counts, cpre[nx] = total), 3 popcounts of the touched bitmap, 4 compaction
 // into y (wpre = scanned popcounts; nothing past cap) resetting SPA and bitmap.
+// dst = max(dst, src) on the device (error words kept across launch sequences).
+void launch_merge_error(const int64_t* src, int64_t* dst, cudaStream_t s);
 size_t spa_value_size(int sr);
 void launch_spmspv_step(int sr, int step, const DevCSR& A, const int32_t* x_idx, const void* x_val,
                         int64_t nx, int64_t* chunks, const int64_t* cpre, void* spa,
                         unsigned* touched, int64_t n, int64_t* wcnt, const int64_t* wpre,
                         int32_t* y_idx, void* y_val, int64_t cap, int64_t* err, cudaStream_t s,
                         int sms);
-// Hash-tier symbolic and numeric passes whose tier sizes are read on the
-// device (counters from launch_classify_sym / launch_classify_num): no host
-// synchronisation, so the sequence can be captured into a CUDA graph.  Every
-// row must be in a hash tier (u_i <= sym_hash_max, nnz_i <= num_hash_max).
+// Symbolic and numeric passes whose tier sizes, heavy-row count, window
+// count and B's sortedness are read on the device (counters from
+// launch_check_sorted / launch_classify_sym / launch_classify_num): no host
+// synchronisation, so the sequence can be captured into a CUDA graph.  The
+// caller sizes span_counts / span_wins (rows x spans) and wins (win_cap, an
+// upper bound) in advance; heavy-row bitmaps are rebuilt, not stored.
 void prepare_symbolic_dev();
 void prepare_dev_launchers(int sr);  // sets the shared-memory attributes of both (not capturable)
-void launch_symbolic_dev(const DevCSR& A, const DevCSR& B, const int32_t* perm,
-                         const int64_t* counters, const int64_t* flops, int64_t* nnz,
-                         cudaStream_t s, int sms);
+void launch_symbolic_dev(const DevCSR& A, const DevCSR& B, const int32_t* perm, int64_t* counters,
+                         const int64_t* flops, int64_t* nnz, int32_t* span_counts, int2* span_wins,
+                         int wcut, Window* wins, int64_t win_cap, cudaStream_t s, int sms);
 void launch_numeric_dev(int sr, const DevCSR& A, const DevCSR& B, const int32_t* perm,
                         const int64_t* counters, const int64_t* flops, const int64_t* nnz,
                         const int64_t* Crp, int32_t* Ccol, void* Cval, int64_t* err, cudaStream_t s,
-                        int sms);
+                        int sms, const int32_t* perm_sym, const Window* wins,
+                        const int32_t* span_counts, int64_t spans, void* racc, int64_t num_hash_max);
 // Bytes of the global accumulator slices of the rank-window numeric kernel
 // (semirings whose windows accumulate in L2; 0 otherwise).
 size_t rank_scratch_bytes(int sr, int sms);

@@ -178,11 +178,19 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
                                                       const int64_t* Crp, int32_t* Ccol,
                                                       typename Sem<SR>::T* Cval, int64_t* err,
                                                       int64_t num_hash_max,
-                                                      typename Sem<SR>::A* racc) {
+                                                      typename Sem<SR>::A* racc,
+                                                      const int64_t* dcounters = nullptr) {
   typedef Sem<SR> S;
   typedef typename S::A Acc;
   typedef typename S::T T;
   constexpr int WCAP = NumLimits<SR>::kWcap;
+  if (dcounters) {  // sizes on the device: heavy segment of the symbolic order, windows, sortedness
+    heavy_rows += dcounters[kCntSym + 1] + dcounters[kCntSym + 2] + dcounters[kCntSym + 3];
+    // a symbolic-phase error (e.g. window capacity) leaves the window list
+    // unusable: do nothing then (the caller reads the error word)
+    n_wins = dcounters[kError] ? 0 : dcounters[kUnits];
+    b_sorted = dcounters[kUnsorted] == 0 ? 1 : 0;
+  }
   // 8-byte accumulators reduce in L2 (a per-CTA slice of racc): shared-memory
   // 64-bit atomics cost more than L2 reductions, and without shared
   // accumulators two 512-thread CTAs share an SM.
@@ -361,7 +369,9 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
 template <int SR>
 void numeric_dev_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int64_t* counters,
                     const int64_t* flops, const int64_t* nnz, const int64_t* Crp, int32_t* Ccol,
-                    void* Cval_, int64_t* err, cudaStream_t s, int sms, int64_t m) {
+                    void* Cval_, int64_t* err, cudaStream_t s, int sms, int64_t m,
+                    const int32_t* perm_sym, const Window* wins, const int32_t* span_counts,
+                    int64_t spans, void* racc, int64_t num_hash_max) {
   typedef typename Sem<SR>::A Acc;
   typedef typename Sem<SR>::T T;
   T* Cval = reinterpret_cast<T*>(Cval_);
@@ -383,6 +393,16 @@ void numeric_dev_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const
     const size_t smem = TBL * slot;
     k_num_hash<SR, CTA, TEAM, TBL><<<capped(m, sms * 4), CTA, smem, s>>>(
         A, B, perm, 0, flops, nnz, Crp, Ccol, Cval, err, nullptr, nullptr, dc, kNumLarge);
+  }
+  {  // rank windows of the heavy rows (window count read on the device)
+    constexpr int CTA = NumLimits<SR>::kL2Acc ? 512 : 1024;
+    constexpr int PER_SM = 1024 / CTA;
+    constexpr size_t smem = (NumLimits<SR>::kL2Acc ? 0 : NumLimits<SR>::kWcap * sizeof(Acc)) +
+                            2 * kSpanWords * sizeof(unsigned) + 2 * CTA * sizeof(long long) +
+                            CTA * sizeof(int);
+    k_num_rank<SR, CTA><<<sms * PER_SM, CTA, smem, s>>>(
+        A, B, perm_sym, wins, 0, span_counts, spans, nullptr, 0, flops, nnz, Crp, Ccol, Cval, err,
+        num_hash_max, static_cast<Acc*>(racc), counters);
   }
 }
 
@@ -502,8 +522,14 @@ size_t rank_scratch_bytes_sr(int sms) {
 
 template <int SR>
 void prepare_numeric_dev_sr() {
+  typedef typename Sem<SR>::A Acc;
   constexpr int CTA = 512, TEAM = 512, TBL = 2 * NumLimits<SR>::kLargeMax;
-  set_smem(k_num_hash<SR, CTA, TEAM, TBL>, TBL * (sizeof(typename Sem<SR>::A) + sizeof(int)));
+  set_smem(k_num_hash<SR, CTA, TEAM, TBL>, TBL * (sizeof(Acc) + sizeof(int)));
+  constexpr int RCTA = NumLimits<SR>::kL2Acc ? 512 : 1024;
+  constexpr size_t rsmem = (NumLimits<SR>::kL2Acc ? 0 : NumLimits<SR>::kWcap * sizeof(Acc)) +
+                           2 * kSpanWords * sizeof(unsigned) + 2 * RCTA * sizeof(long long) +
+                           RCTA * sizeof(int);
+  set_smem(k_num_rank<SR, RCTA>, rsmem);
 }
 
 void prepare_dev_launchers(int sr) {
@@ -520,16 +546,21 @@ void prepare_dev_launchers(int sr) {
 void launch_numeric_dev(int sr, const DevCSR& A, const DevCSR& B, const int32_t* perm,
                         const int64_t* counters, const int64_t* flops, const int64_t* nnz,
                         const int64_t* Crp, int32_t* Ccol, void* Cval, int64_t* err, cudaStream_t s,
-                        int sms) {
+                        int sms, const int32_t* perm_sym, const Window* wins,
+                        const int32_t* span_counts, int64_t spans, void* racc, int64_t num_hash_max) {
   const int64_t m = A.nrows;
   if (m == 0) return;
+#define CB_NDEV(SRV)                                                                            \
+  numeric_dev_sr<SRV>(A, B, perm, counters, flops, nnz, Crp, Ccol, Cval, err, s, sms, m, perm_sym, \
+                      wins, span_counts, spans, racc, num_hash_max)
   switch (sr) {
-    case 1: numeric_dev_sr<1>(A, B, perm, counters, flops, nnz, Crp, Ccol, Cval, err, s, sms, m); break;
-    case 2: numeric_dev_sr<2>(A, B, perm, counters, flops, nnz, Crp, Ccol, Cval, err, s, sms, m); break;
-    case 3: numeric_dev_sr<3>(A, B, perm, counters, flops, nnz, Crp, Ccol, Cval, err, s, sms, m); break;
-    case 4: numeric_dev_sr<4>(A, B, perm, counters, flops, nnz, Crp, Ccol, Cval, err, s, sms, m); break;
-    case 5: numeric_dev_sr<5>(A, B, perm, counters, flops, nnz, Crp, Ccol, Cval, err, s, sms, m); break;
+    case 1: CB_NDEV(1); break;
+    case 2: CB_NDEV(2); break;
+    case 3: CB_NDEV(3); break;
+    case 4: CB_NDEV(4); break;
+    case 5: CB_NDEV(5); break;
   }
+#undef CB_NDEV
 }
 
 size_t rank_scratch_bytes(int sr, int sms) {

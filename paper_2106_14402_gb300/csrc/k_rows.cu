@@ -272,6 +272,16 @@ void launch_scatter_sym(int64_t m, int64_t ncols, const int64_t* flops, int32_t*
                                                             counters + kCurSym, nnz, preset);
 }
 
+namespace {
+__global__ void k_merge_error(const int64_t* src, int64_t* dst) {
+  if (threadIdx.x == 0 && *src) atomicMax(reinterpret_cast<long long*>(dst), (long long)*src);
+}
+}  // namespace
+
+void launch_merge_error(const int64_t* src, int64_t* dst, cudaStream_t s) {
+  k_merge_error<<<1, 32, 0, s>>>(src, dst);
+}
+
 int64_t scan_partials(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
 void launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* partial,

@@ -92,6 +92,11 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
   __shared__ long long wbase;
   constexpr int WPT = kSpanWords / 1024;  // bitmap words per thread in the scan
   const int tid = threadIdx.x;
+  if (b_sorted < 0) {  // sizes on the device: heavy segment of perm, count, B's sortedness
+    heavy_rows += counters[kCntSym + 1] + counters[kCntSym + 2] + counters[kCntSym + 3];
+    n_heavy = counters[kCntSym + kSymHeavy];
+    b_sorted = counters[kUnsorted] == 0 ? 1 : 0;
+  }
   const int64_t units = n_heavy * spans;
   const int bm_words = (int)min((int64_t)kSpanWords, (B.ncols + 31) / 32);
   long long* bal = reinterpret_cast<long long*>(sym_bm + ((bm_words + 3) & ~3));
@@ -231,13 +236,24 @@ void launch_check_sorted(const DevCSR& B, int64_t* counters, cudaStream_t s, int
 void prepare_symbolic_dev() {
   constexpr int CTA = 512, TEAM = 512, TBL = 2 * kSymLargeMax;
   set_smem(k_sym_hash<CTA, TEAM, TBL>, TBL * sizeof(int));
+  set_smem(k_sym_bitmap, (size_t)kSpanWords * sizeof(unsigned) + 2 * 1024 * sizeof(long long) +
+                             1024 * sizeof(int));
 }
 
-void launch_symbolic_dev(const DevCSR& A, const DevCSR& B, const int32_t* perm,
-                         const int64_t* counters, const int64_t* flops, int64_t* nnz,
-                         cudaStream_t s, int sms) {
+void launch_symbolic_dev(const DevCSR& A, const DevCSR& B, const int32_t* perm, int64_t* counters,
+                         const int64_t* flops, int64_t* nnz, int32_t* span_counts, int2* span_wins,
+                         int wcut, Window* wins, int64_t win_cap, cudaStream_t s, int sms) {
   const int64_t m = A.nrows;
   if (m == 0) return;
+  {  // heavy rows (bitmaps, rank windows), count and B's sortedness read on the device
+    const int64_t spans = (B.ncols + kSpanCols - 1) / kSpanCols;
+    const int64_t width = B.ncols < kSpanCols ? B.ncols : kSpanCols;
+    const size_t bm_words = (size_t)((width + 31) / 32);
+    const size_t smem = ((bm_words + 3) & ~(size_t)3) * sizeof(unsigned) + 2 * 1024 * sizeof(long long) +
+                        1024 * sizeof(int);
+    k_sym_bitmap<<<sms * 2, 1024, smem, s>>>(A, B, perm, 0, spans, flops, wcut, nnz, span_counts,
+                                             span_wins, wins, win_cap, nullptr, -1, counters);
+  }
   const int64_t* dc = counters + kCntSym;
   {
     constexpr int CTA = 256, TEAM = 32, TBL = 2 * kSymWarpMax;

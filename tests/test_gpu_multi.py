@@ -175,15 +175,27 @@ def test_graph_waves(cb):
     assert st["nnz"] == sum(int(x[0][-1]) for x in want)
 
 
-def test_graph_mode_falls_back_for_large_rows(cb):
-    """A product with rows above 4096 products runs on the host-synchronised
-    path; results stay exact."""
-    sr = "min_plus_u32"
-    P = gen.rmat(11, 16, *gen.RMAT_ABCD, seed=300)
+@pytest.mark.parametrize("sr", ("min_plus_u32", "plus_times_f64"))
+def test_sync_free_heavy_rows(cb, sr):
+    """Products with heavy rows (bitmap symbolic, rank-window numeric) in the
+    launch sequence without host synchronisation: sortedness, heavy-row and
+    window counts read on the device; exact results."""
+    P = gen.rmat(13, 16, *gen.RMAT_ABCD, seed=300)
     A = P.with_values(gen.random_values(sr, P.nnz, 301))
-    flops, _ = oracle.row_stats(A, A)
+    B = P.with_values(gen.random_values(sr, P.nnz, 302))
+    flops, _ = oracle.row_stats(A, B)
     assert flops.max() > 4096
-    dA = cb.DeviceCSR.from_host(A, sr)
+    dA, dB = cb.DeviceCSR.from_host(A, sr), cb.DeviceCSR.from_host(B, sr)
+    got = []
+    st = cb.spgemm_batched([sr, sr], [dA, dA], [dB, dB], lambda w, f, e, C: got.append(C.to_host()),
+                           mode="sync_free")
+    want = oracle.spgemm(sr, A, B)
+    assert len(got) == 1 and st["nnz"] == 2 * int(want[0][-1])
+    rp, col, val = got[0]
+    m, n = A.nrows, int(want[0][-1])
+    for k in range(2):
+        sub = (rp[k * m:(k + 1) * m + 1] - rp[k * m], col[rp[k * m]:rp[k * m] + n], val[rp[k * m]:rp[k * m] + n])
+        compare_rows(sr, sub, want)
     seen = []
-    st = cb.spgemm_batched([sr, sr], [dA, dA], [dA, dA], lambda *a: seen.append(a), mode="graph")
-    assert st["nnz"] == 2 * int(oracle.spgemm(sr, A, A)[0][-1]) and len(seen) == 1
+    st = cb.spgemm_batched([sr, sr], [dA, dA], [dB, dB], lambda *a: seen.append(a), mode="graph")
+    assert st["nnz"] == 2 * n and len(seen) == 1 and seen[0][4] == 2 * n
