@@ -6,7 +6,8 @@ and this package imports nothing from the library (it shares no code with
 the CUDA path).
 
 `spgemm` wraps oracle.cpp: a plain Gustavson SpGEMM with one ordered map per
-output row (paper Sec. 4.1), over the five semirings named below.
+output row (paper Sec. 4.1), over the six semirings named below (five with
+one value type, one heterogeneous: Sec. 1).
 `row_stats` gives flops_i and max_p nnz(B(p,:)) per row (Sec. 4.1, phase (1);
 Table 1 defines flops).  `mlp` holds the FP64 reference of the learned row
 size predictor.  `merge` is the semiring sum of k partial results (Sec. 3.2),
@@ -26,15 +27,21 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-# Semiring names -> this file's own codes (oracle.cpp's enum) and value dtypes.
+# (weight, label) pairs of the heterogeneous semiring, as oracle.cpp lays them out.
+WLABEL = np.dtype([("w", "<f4"), ("label", "<i4")])
+
+# Semiring names -> this file's own codes (oracle.cpp's enum) and the value
+# dtypes of A, B and C.
 _CODES = {
-    "plus_times_i64": (1, np.int64),
-    "plus_times_f64": (2, np.float64),
-    "min_plus_u32": (3, np.uint32),
-    "or_and_bool": (4, np.uint8),
-    "sel2nd_min_i32": (5, np.int32),
+    "plus_times_i64": (1, np.int64, np.int64, np.int64),
+    "plus_times_f64": (2, np.float64, np.float64, np.float64),
+    "min_plus_u32": (3, np.uint32, np.uint32, np.uint32),
+    "or_and_bool": (4, np.uint8, np.uint8, np.uint8),
+    "sel2nd_min_i32": (5, np.int32, np.int32, np.int32),
+    "maxw_label": (6, np.float32, np.int32, WLABEL),
 }
-SEMIRINGS = tuple(_CODES)
+SEMIRINGS = tuple(s for s in _CODES if s != "maxw_label")   # one value type each
+HETERO_SEMIRINGS = ("maxw_label",)
 
 _lock = threading.Lock()
 _lib = None
@@ -98,18 +105,20 @@ def spgemm(semiring: str, A, B, rows=None, threads: int = 0):
     val arrays.  `rows` (optional int64 array) restricts the output to those
     rows of C, in that order.  Returns (row_ptr, col, val, absum): a CSR over
     the selected rows with sorted unique columns, and for fp64 the sum of
-    |products| of every entry (zeros for the other semirings).
+    |products| of every entry (zeros for the other semirings).  A's and B's
+    values are taken in the semiring's A and B types (maxw_label: float32
+    weights and int32 labels); its C values come back as WLABEL records.
     """
-    code, dt = _CODES[semiring]
+    code, adt, bdt, dt = _CODES[semiring]
     if A.ncols != B.nrows:
         raise ValueError("shape mismatch: A.ncols != B.nrows")
     lib = _load()
     arp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
     acol = np.ascontiguousarray(A.col, dtype=np.int32)
-    aval = np.ascontiguousarray(A.val, dtype=dt)
+    aval = np.ascontiguousarray(A.val, dtype=adt)
     brp = np.ascontiguousarray(B.row_ptr, dtype=np.int64)
     bcol = np.ascontiguousarray(B.col, dtype=np.int32)
-    bval = np.ascontiguousarray(B.val, dtype=dt)
+    bval = np.ascontiguousarray(B.val, dtype=bdt)
     if rows is None:
         nsel, rp_rows = A.nrows, None
     else:

@@ -11,7 +11,10 @@ order, is (+)-combined into its coordinate; coordinates come out sorted.
 Duplicate coordinates inside one part combine the same way.
 
 Semirings as in oracle.cpp: (+) is wrapping int64 add, IEEE fp64 add, uint32
-min, boolean or (uint8, nonzero = true, output 0/1), int32 min.  For fp64 the
+min, boolean or (uint8, nonzero = true, output 0/1), int32 min, and for the
+heterogeneous maxw_label (parts hold (weight, label) records) the record
+with the larger weight in IEEE 754 totalOrder, the smaller label on ties
+(the rank of a weight in that order is spmspv.total_order_rank).  For fp64 the
 sum of |values| per entry is returned for the tolerance test (the order of
 an fp64 sum changes it by far less than that tolerance).
 """
@@ -32,6 +35,8 @@ def merge(semiring: str, parts):
     for P in parts:
         if (P.nrows, P.ncols) != (m, n):
             raise ValueError("all parts must have the same shape")
+    if semiring == "maxw_label":
+        return _merge_maxw_label(parts, m)
     dt = _DT[semiring]
     rows, cols, vals, order = [], [], [], []
     base = 0
@@ -74,3 +79,27 @@ def merge(semiring: str, parts):
     rp = np.cumsum(rp)
     return rp, c[starts].astype(np.int32), out.astype(dt), ab
 
+
+
+def _merge_maxw_label(parts, m):
+    from .spmspv import WLABEL, total_order_rank
+    rows, cols, vals = [], [], []
+    for P in parts:
+        rp = np.asarray(P.row_ptr, dtype=np.int64)
+        nnz = int(rp[-1])
+        rows.append(np.repeat(np.arange(m, dtype=np.int64), np.diff(rp)))
+        cols.append(np.asarray(P.col[:nnz], dtype=np.int64))
+        vals.append(np.asarray(P.val[:nnz]).view(WLABEL))
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    v = np.concatenate(vals) if vals else np.zeros(0, WLABEL)
+    if r.size == 0:
+        return np.zeros(m + 1, np.int64), np.zeros(0, np.int32), np.zeros(0, WLABEL), np.zeros(0)
+    # per coordinate: heaviest weight first, then the smaller label; keep the first
+    idx = np.lexsort((v["label"].astype(np.int64), -total_order_rank(v["w"]), c, r))
+    r, c, v = r[idx], c[idx], v[idx]
+    head = np.ones(r.size, dtype=bool)
+    head[1:] = (r[1:] != r[:-1]) | (c[1:] != c[:-1])
+    rp = np.zeros(m + 1, np.int64)
+    np.add.at(rp, r[head] + 1, 1)
+    return np.cumsum(rp), c[head].astype(np.int32), v[head].copy(), np.zeros(int(head.sum()))

@@ -23,7 +23,7 @@
 //   * flops (Table 1: the count of arithmetic operations on nonzeros) is the
 //     number of (x)-products, flops_i = sum over A(i,p) of nnz(B(p,:)).
 //
-// Semirings (the paper allows any; these five are the ones exercised):
+// Semirings (the paper allows any; these six are the ones exercised):
 //   1 (+,x)   over int64: wrapping two's-complement multiply and add.
 //   2 (+,x)   over fp64 : IEEE multiply (no contraction into FMA), and the
 //                          products of one entry summed with Neumaier's
@@ -34,6 +34,10 @@
 //                          (+) = min.
 //   4 (or,and) over bool : stored as uint8; nonzero = true; output 0/1.
 //   5 (select2nd,min) over int32: (x)(a,b) = b, (+) = signed min.
+//   6 heterogeneous (Sec. 1: two input types and one output type): A holds
+//     float32 weights, B int32 labels, C (weight, label) pairs; (x)(w, l) =
+//     (w, l); (+) keeps the pair whose weight is larger in IEEE 754
+//     totalOrder, and of equal weights the one with the smaller label.
 //
 // Build: g++ -O2 -std=c++17 -fopenmp -ffp-contract=off -shared -fPIC
 #include <cmath>
@@ -46,10 +50,11 @@
 
 namespace {
 
-enum { S_I64 = 1, S_F64 = 2, S_U32 = 3, S_BOOL = 4, S_S2M = 5 };
+enum { S_I64 = 1, S_F64 = 2, S_U32 = 3, S_BOOL = 4, S_S2M = 5, S_WL = 6 };
 
 struct AccI64 {
   typedef int64_t T;
+  typedef T TA, TB, TC;
   uint64_t s;
   void first(T a, T b) { s = (uint64_t)a * (uint64_t)b; }
   void next(T a, T b) { s += (uint64_t)a * (uint64_t)b; }
@@ -59,6 +64,7 @@ struct AccI64 {
 
 struct AccF64 {
   typedef double T;
+  typedef T TA, TB, TC;
   double s, c, abs_s;
   void first(T a, T b) {
     double p = a * b;
@@ -78,6 +84,7 @@ struct AccF64 {
 
 struct AccU32 {
   typedef uint32_t T;
+  typedef T TA, TB, TC;
   uint32_t s;
   static uint32_t mul(T a, T b) {
     uint64_t w = (uint64_t)a + (uint64_t)b;
@@ -91,6 +98,7 @@ struct AccU32 {
 
 struct AccBool {
   typedef uint8_t T;
+  typedef T TA, TB, TC;
   bool s;
   void first(T a, T b) { s = (a != 0) && (b != 0); }
   void next(T a, T b) { s = s || ((a != 0) && (b != 0)); }
@@ -100,10 +108,45 @@ struct AccBool {
 
 struct AccS2M {
   typedef int32_t T;
+  typedef T TA, TB, TC;
   int32_t s;
   void first(T, T b) { s = b; }
   void next(T, T b) { if (b < s) s = b; }
   T value() const { return s; }
+  double absum() const { return 0.0; }
+};
+
+// IEEE 754 totalOrder, strict: x before y.  Negative-signed values (-NaN,
+// -inf, ..., -0) come before positive-signed ones; among negative-signed
+// values a larger magnitude encoding comes first, among positive-signed ones
+// a smaller one (the binary encodings order magnitudes, NaNs above inf).
+bool total_order_before(float x, float y) {
+  uint32_t bx, by;
+  std::memcpy(&bx, &x, sizeof bx);
+  std::memcpy(&by, &y, sizeof by);
+  const bool nx = (bx >> 31) != 0, ny = (by >> 31) != 0;
+  if (nx != ny) return nx;
+  const uint32_t mx = bx & 0x7FFFFFFFu, my = by & 0x7FFFFFFFu;
+  return nx ? mx > my : mx < my;
+}
+
+struct WLabel {
+  float w;
+  int32_t label;
+};
+
+struct AccWL {
+  typedef float TA;
+  typedef int32_t TB;
+  typedef WLabel TC;
+  WLabel s;
+  void first(TA a, TB b) { s = WLabel{a, b}; }
+  void next(TA a, TB b) {
+    const bool heavier = total_order_before(s.w, a);
+    const bool same = !total_order_before(s.w, a) && !total_order_before(a, s.w);
+    if (heavier || (same && b < s.label)) s = WLabel{a, b};
+  }
+  TC value() const { return s; }
   double absum() const { return 0.0; }
 };
 
@@ -112,9 +155,11 @@ int run(int64_t m, const int64_t* Arp, const int32_t* Acol, const void* Aval_,
         const int64_t* Brp, const int32_t* Bcol, const void* Bval_,
         int64_t nsel, const int64_t* rows, int threads,
         int64_t** out_rp, int32_t** out_col, void** out_val, double** out_abs) {
-  typedef typename Acc::T T;
-  const T* Aval = (const T*)Aval_;
-  const T* Bval = (const T*)Bval_;
+  typedef typename Acc::TA TA;
+  typedef typename Acc::TB TB;
+  typedef typename Acc::TC TC;
+  const TA* Aval = (const TA*)Aval_;
+  const TB* Bval = (const TB*)Bval_;
   std::vector<std::vector<std::pair<int32_t, Acc>>> res((size_t)nsel);
   if (threads <= 0) threads = omp_get_max_threads();
 #pragma omp parallel for schedule(dynamic, 16) num_threads(threads)
@@ -123,7 +168,7 @@ int run(int64_t m, const int64_t* Arp, const int32_t* Acol, const void* Aval_,
     std::map<int32_t, Acc> acc;
     for (int64_t p = Arp[i]; p < Arp[i + 1]; ++p) {
       int32_t kk = Acol[p];
-      T a = Aval[p];
+      TA a = Aval[p];
       for (int64_t q = Brp[kk]; q < Brp[kk + 1]; ++q) {
         int32_t j = Bcol[q];
         auto it = acc.find(j);
@@ -144,7 +189,7 @@ int run(int64_t m, const int64_t* Arp, const int32_t* Acol, const void* Aval_,
   for (int64_t r = 0; r < nsel; ++r) rp[r + 1] = rp[r] + (int64_t)res[r].size();
   int64_t nnz = rp[nsel];
   int32_t* col = (int32_t*)std::malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
-  T* val = (T*)std::malloc(sizeof(T) * (size_t)(nnz > 0 ? nnz : 1));
+  TC* val = (TC*)std::malloc(sizeof(TC) * (size_t)(nnz > 0 ? nnz : 1));
   double* ab = (double*)std::malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
   if (!col || !val || !ab) return 2;
 #pragma omp parallel for schedule(dynamic, 64) num_threads(threads)
@@ -202,6 +247,7 @@ int orc_spgemm(int semiring, int64_t m, const int64_t* Arp, const int32_t* Acol,
     case S_U32: return run<AccU32>(m, Arp, Acol, Aval, Brp, Bcol, Bval, nsel, rows, threads, out_rp, out_col, out_val, out_abs);
     case S_BOOL: return run<AccBool>(m, Arp, Acol, Aval, Brp, Bcol, Bval, nsel, rows, threads, out_rp, out_col, out_val, out_abs);
     case S_S2M: return run<AccS2M>(m, Arp, Acol, Aval, Brp, Bcol, Bval, nsel, rows, threads, out_rp, out_col, out_val, out_abs);
+    case S_WL: return run<AccWL>(m, Arp, Acol, Aval, Brp, Bcol, Bval, nsel, rows, threads, out_rp, out_col, out_val, out_abs);
   }
   return 1;
 }

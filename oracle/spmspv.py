@@ -14,7 +14,10 @@ structural (an entry exists when some product exists, whatever its value).
 Duplicate indices in x contribute separately.  (x) and (+) are those of
 oracle.cpp: wrapping int64 multiply/add, IEEE fp64, uint32 saturating add /
 min, boolean and / or (uint8, output 0/1), select2nd (the matrix value) /
-int32 min.  For fp64 the sum of |products| per entry is returned beside it.
+int32 min, and the heterogeneous maxw_label: x holds float32 weights, A int32
+labels, y (weight, label) records; y_c is the pair of the heaviest x entry
+reaching c (IEEE 754 totalOrder on weights), the smaller label on ties.
+For fp64 the sum of |products| per entry is returned beside it.
 """
 from __future__ import annotations
 
@@ -22,6 +25,41 @@ import numpy as np
 
 _DT = {"plus_times_i64": np.int64, "plus_times_f64": np.float64, "min_plus_u32": np.uint32,
        "or_and_bool": np.uint8, "sel2nd_min_i32": np.int32}
+WLABEL = np.dtype([("w", "<f4"), ("label", "<i4")])
+
+
+def total_order_rank(w) -> np.ndarray:
+    """Integers ordered as IEEE 754 totalOrder orders the float32 weights w:
+    a weight with its sign bit clear keeps its magnitude encoding m, one with
+    the sign bit set maps to -m - 1 (so -0 < +0 and -NaN < -inf)."""
+    bits = np.asarray(w, dtype=np.float32).view(np.uint32).astype(np.int64)
+    mag = bits & 0x7FFFFFFF
+    return np.where(bits >> 31 != 0, -mag - 1, mag)
+
+
+def _spmspv_maxw_label(A, x_idx, x_val):
+    x_idx = np.asarray(x_idx, dtype=np.int64)
+    x_val = np.asarray(x_val, dtype=np.float32)
+    rp = np.asarray(A.row_ptr, dtype=np.int64)
+    cols, w, lab = [], [], []
+    for p, i in enumerate(x_idx):            # every product x_i (x) A(i, c) = (x_i, A(i, c))
+        for q in range(rp[i], rp[i + 1]):
+            cols.append(int(A.col[q]))
+            w.append(x_val[p])
+            lab.append(int(A.val[q]))
+    if not cols:
+        return np.zeros(0, np.int32), np.zeros(0, WLABEL), np.zeros(0)
+    cols = np.array(cols, np.int64)
+    w = np.array(w, np.float32)
+    lab = np.array(lab, np.int64)
+    order = np.lexsort((lab, -total_order_rank(w), cols))   # by column, heaviest first, then label
+    cols, w, lab = cols[order], w[order], lab[order]
+    head = np.ones(cols.size, dtype=bool)
+    head[1:] = cols[1:] != cols[:-1]
+    out = np.zeros(int(head.sum()), WLABEL)
+    out["w"] = w[head]
+    out["label"] = lab[head]
+    return cols[head].astype(np.int32), out, np.zeros(out.size)
 
 
 def _mul(semiring, a, b):
@@ -42,6 +80,8 @@ def _mul(semiring, a, b):
 def spmspv(semiring: str, A, x_idx, x_val):
     """y^T = x^T A: A is a CSR object (nrows, ncols, row_ptr, col, val), x a
     sparse vector of length A.nrows.  Returns (idx, val, absum), idx sorted."""
+    if semiring == "maxw_label":
+        return _spmspv_maxw_label(A, x_idx, x_val)
     dt = _DT[semiring]
     x_idx = np.asarray(x_idx, dtype=np.int64)
     x_val = np.asarray(x_val, dtype=dt)

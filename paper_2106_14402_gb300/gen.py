@@ -34,6 +34,12 @@ VALUE_DTYPE = {
 }
 SEMIRINGS = tuple(VALUE_DTYPE)
 
+# The heterogeneous semiring: A, B and C value types (C = (weight, label)
+# records, 8 bytes).
+WLABEL = np.dtype([("w", "<f4"), ("label", "<i4")])
+HETERO_DTYPES = {"maxw_label": (np.float32, np.int32, WLABEL)}
+HETERO_SEMIRINGS = tuple(HETERO_DTYPES)
+
 
 def splitmix64(x: int) -> int:
     """One step of the splitmix64 output function (Steele, Lea, Flood 2014)."""
@@ -246,6 +252,20 @@ def random_values(semiring: str, nnz: int, seed: int, lo=None, hi=None) -> np.nd
     raise ValueError(semiring)
 
 
+def hetero_values(semiring: str, operand: str, nnz: int, seed: int, levels: int = 0) -> np.ndarray:
+    """Values of a heterogeneous semiring's operand.  maxw_label: A = float32
+    weights in [0, 1) (with levels > 0 drawn from the `levels` values k/levels,
+    so equal weights are common), B = int32 labels uniform in [0, 2^30)."""
+    rng = rng_for(seed, 6 if operand == "A" else 7)
+    if semiring != "maxw_label":
+        raise ValueError(semiring)
+    if operand == "A":
+        if levels > 0:
+            return (rng.integers(0, levels, size=nnz) / levels).astype(np.float32)
+        return rng.random(nnz, dtype=np.float32)
+    return rng.integers(0, 1 << 30, size=nnz, dtype=np.int32)
+
+
 # ---------------------------------------------------------------------------
 # The workloads.  Each returns (semiring, A, B) triples; A and B share the
 # pattern when the product is a square (C = A.A).
@@ -270,6 +290,9 @@ def rmat_square(scale: int = 18, edgefactor: int = 16, cfg: int = 2,
         if sr == "sel2nd_min_i32":
             A = P.with_values(np.ones(P.nnz, dtype=np.int32))
             B = P.with_values(random_values(sr, P.nnz, subseed(cfg, 10 + k)))
+        elif sr in HETERO_DTYPES:
+            A = P.with_values(hetero_values(sr, "A", P.nnz, subseed(cfg, 10 + k)))
+            B = P.with_values(hetero_values(sr, "B", P.nnz, subseed(cfg, 10 + k)))
         else:
             A = P.with_values(random_values(sr, P.nnz, subseed(cfg, 10 + k)))
             B = A

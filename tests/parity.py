@@ -2,8 +2,9 @@
 the same seeded inputs and compare them element by element.
 
 The bar (per semiring):
-  * integer, bool and min/select semirings: bit-exact row pointers, columns
-    and values;
+  * integer, bool and min/select semirings and the heterogeneous
+    maxw_label (compared as raw record bits): bit-exact row pointers,
+    columns and values;
   * (+,x) fp64: identical pattern and |c - c_ref| <= 1e-12 * sum|a_ik b_kj|
     per entry (sum of |products| accumulated by the oracle).  For an entry
     with m products any two summation orders differ by at most about
@@ -34,6 +35,9 @@ def compare_rows(sr, got, want, rows=None, tol=FP64_TOL):
             np.zeros(0, np.int64)
         assert np.array_equal(g_col[idx], w_col), _first_diff("col", g_col[idx], w_col)
         gv, wv, ab = g_val[idx], w_val, w_abs
+    if sr == "maxw_label":  # (weight, label) records, compared as raw bits (NaN weights too)
+        gv = np.ascontiguousarray(gv).view(np.uint64)
+        wv = np.ascontiguousarray(wv).view(np.uint64)
     if sr == "plus_times_f64":
         err = np.abs(gv - wv)
         bad = err > tol * ab
