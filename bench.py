@@ -88,14 +88,18 @@ def fp64_traffic_per_product():
     return None
 
 
+# value bytes of A, B and C under the heterogeneous semiring
+HETERO_VAL_BYTES = {"maxw_label": (4, 4, 8)}
+
+
 def compulsory_bytes(sr, A, B, nnz_c, m):
     """bytes(A) + bytes(B rows touched, once) + bytes(C): row_ptr 8 B/row, col 4 B, val by type."""
-    v = VAL_BYTES[sr]
-    a = 8 * (A.nrows + 1) + A.nnz * (4 + v)
+    va, vb, vc = HETERO_VAL_BYTES.get(sr, (VAL_BYTES.get(sr),) * 3)
+    a = 8 * (A.nrows + 1) + A.nnz * (4 + va)
     touched = np.unique(A.col)
     blen = np.diff(B.row_ptr)[touched]
-    b = 8 * (touched.size + 1) + int(blen.sum()) * (4 + v)
-    c = 8 * (m + 1) + nnz_c * (4 + v)
+    b = 8 * (touched.size + 1) + int(blen.sum()) * (4 + vb)
+    c = 8 * (m + 1) + nnz_c * (4 + vc)
     return int(a + b + c)
 
 
@@ -455,6 +459,7 @@ def run_legs(args, cb, ctx, dprob, flush, plain_ms, products, dev, peak, peak_sr
     out["spmspv"] = run_spmspv_leg(args, cb, ctx, flush, dev, dprob, peak, peak_src)
     out["merge"] = run_merge_leg(args, cb, ctx, flush, dev, peak, peak_src)
     out["high_compression"] = run_high_compression(args, cb, ctx, flush, model, dev, peak, peak_src)
+    out["heterogeneous"] = run_hetero_leg(args, cb, ctx, flush, dev, peak, peak_src)
     if not args.no_multi:
         out["multi_spgemm"] = run_multi(args, cb, ctx, model)
     if not args.no_full:
@@ -651,6 +656,44 @@ def run_high_compression(args, cb, ctx, flush, model, dev, peak, peak_src):
     ctx.set_tune(**saved)
     res["peak_gbs"] = peak
     res["peak_source"] = peak_src
+    return res
+
+
+def run_hetero_leg(args, cb, ctx, flush, dev, peak, peak_src):
+    """The heterogeneous semiring (three value types) on the R-MAT s18 ef16
+    matrix: A float32 weights, B int32 labels, C (weight, label) records,
+    plain two-phase path into a pre-reserved C."""
+    import torch
+    from paper_2106_14402_gb300 import gen
+    (sr, A, B), = gen.rmat_square(18, 16, semirings=("maxw_label",))
+    dA = cb.DeviceCSR.from_host(A, sr, dev, operand="A")
+    dB = cb.DeviceCSR.from_host(B, sr, dev, operand="B")
+    C = cb.spgemm(sr, dA, dB, validate=True, ctx=ctx)
+    nnz = C.nnz
+    del C
+    out = cb.DeviceCSR(A.nrows, B.ncols, torch.empty(A.nrows + 1, dtype=torch.int64, device=dev),
+                       torch.empty(nnz, dtype=torch.int32, device=dev),
+                       torch.empty(nnz, dtype=cb.SEMIRING[sr][1], device=dev))
+    info = {}
+
+    def plain():
+        cb.spgemm(sr, dA, dB, validate=False, out=out, ctx=ctx, timing=True)
+        info.update(ctx.stats())
+
+    plain()
+    ms = timed(plain, max(1, min(args.steps, 3)), flush)
+    prods = info["flops"]
+    nbytes = compulsory_bytes(sr, A, B, nnz, A.nrows)
+    res = {"workload": "R-MAT s18 ef16 (same matrix as the headline), C = A.B with A float32 weights "
+                       "U[0,1), B int32 labels U[0,2^30), C (weight, label) records; (+) = heaviest "
+                       "weight (IEEE totalOrder), smaller label on ties",
+           "ms": ms, "products": prods, "nnz_c": nnz, "products_per_s": prods / (ms * 1e-3),
+           "nnz_per_s": nnz / (ms * 1e-3), "ms_symbolic": info["ms_symbolic"],
+           "ms_numeric": info["ms_numeric"], "algorithmic_bytes": nbytes,
+           "roofline_frac_numeric": round(nbytes / (info["ms_numeric"] * 1e-3) / 1e9 / peak, 4),
+           "peak_gbs": peak, "peak_source": peak_src}
+    del out, dA, dB
+    torch.cuda.empty_cache()
     return res
 
 

@@ -15,8 +15,11 @@
  * Data layout (all matrices): CSR by rows.
  *   row_ptr  int64[nrows + 1], row_ptr[0] = 0, non-decreasing, row_ptr[nrows] = nnz
  *   col      int32[nnz], 0 <= col < ncols (ncols <= INT32_MAX)
- *   val      nnz values of the semiring's type (bool stored as uint8 0/1;
- *            any nonzero input byte counts as true)
+ *   val      nnz values of the operand's type under the semiring (bool
+ *            stored as uint8 0/1, any nonzero input byte counts as true).
+ *            Semirings 1-5 use one type for A, B and C; the heterogeneous
+ *            CB_MAXW_LABEL takes three (paper Sec. 1: two input types and
+ *            one output type).
  * Inputs may have unsorted and duplicate columns within a row (duplicates
  * contribute separately).  Output rows always have strictly increasing
  * columns.  All cb_csr pointers are DEVICE pointers unless a function says
@@ -47,8 +50,20 @@ typedef enum {
   CB_PLUS_TIMES_F64 = 2, /* (+,x) over IEEE fp64 (any summation order, FMA ok)   */
   CB_MIN_PLUS_U32 = 3,   /* (min,+) over uint32, + saturates at UINT32_MAX (inf) */
   CB_OR_AND_BOOL = 4,    /* (or,and) over bool stored as uint8                   */
-  CB_SEL2ND_MIN_I32 = 5  /* (select2nd,min) over int32: (x)(a,b) = b, (+) = min  */
+  CB_SEL2ND_MIN_I32 = 5, /* (select2nd,min) over int32: (x)(a,b) = b, (+) = min  */
+  CB_MAXW_LABEL = 6      /* heterogeneous: A float32, B int32, C cb_wlabel (below) */
 } cb_semiring;
+
+/* Output value of CB_MAXW_LABEL (8 bytes: w at offset 0, label at 4).
+ * (x)(a, b) = {a, b} for an A weight a and a B label b; (+) keeps the pair
+ * with the larger w in IEEE 754 totalOrder (-NaN < -inf < ... < -0 < +0 <
+ * ... < +inf < +NaN), and of equal w the smaller label.  C(i,j) is thus the
+ * label B(k,j) reached through the heaviest edge A(i,k), with that weight.
+ * The order is exact (no arithmetic on w), so results are bit-exact. */
+typedef struct {
+  float w;
+  int32_t label;
+} cb_wlabel;
 
 /* Status codes. */
 enum {
@@ -318,7 +333,8 @@ int cb_autotune(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B, c
  * vector of length A->nrows (indices in any order, duplicates contribute
  * separately); y gets length A->ncols, indices strictly increasing, the
  * pattern structural.  (x) takes x's value on the left: with (select2nd,
- * min), y_c = min of A(i, c) over the x entries i.
+ * min), y_c = min of A(i, c) over the x entries i; under CB_MAXW_LABEL x
+ * holds float32 weights, A int32 labels and y cb_wlabel values.
  * The product is pushed into a dense accumulator kept in the context (one
  * value per column of A plus a bitmap); it is initialised once per width
  * and semiring and reset sparsely after each call.  The stream is
@@ -342,11 +358,14 @@ int cb_spvec_free_async(cb_ctx *ctx, cb_spvec *y);
  * C = P_0 (+) P_1 (+) ... (+) P_{k-1}, entry by entry over the union of the
  * patterns: the combination of the partial products of a SUMMA stage or of
  * the layers of the communication-avoiding SpGEMM (Sec. 3.2).  All parts are
- * device CSR of one shape (rows may be unsorted and hold duplicates, which
- * combine the same way); C has sorted, unique columns.  It runs as the
- * SpGEMM (selector) (+).(x) [P_0; ...; P_{k-1}], whose selector row i holds
- * the multiplicative identity at column l*m + i of every part l, so every
- * tier of the SpGEMM (and its one-launch kernel for small rows) serves it.
+ * device CSR of one shape holding values of the semiring's C type (rows may
+ * be unsorted and hold duplicates, which combine the same way); C has
+ * sorted, unique columns.  It runs as the SpGEMM (selector) (+).(x)
+ * [P_0; ...; P_{k-1}], whose selector row i holds the multiplicative
+ * identity at column l*m + i of every part l, so every tier of the SpGEMM
+ * (and its one-launch kernel for small rows) serves it; for CB_MAXW_LABEL
+ * the selector product runs in that semiring's merge form ((x) passes the
+ * part's cb_wlabel through, (+) is CB_MAXW_LABEL's).
  * opt: validate, out_capacity (caller buffers as for cb_spgemm_ex), flags;
  * exact sizing only, no budget.  Returns CB_ERR_SHAPE if the parts differ
  * in shape, CB_ERR_INDEX if k * nrows reaches INT32_MAX. */

@@ -19,13 +19,27 @@ from . import build as _build
 c_int64 = ctypes.c_int64
 c_void_p = ctypes.c_void_p
 
+# name -> (cb_semiring code, dtype of C's values)
 SEMIRING = {
     "plus_times_i64": (1, torch.int64),
     "plus_times_f64": (2, torch.float64),
     "min_plus_u32": (3, torch.uint32),
     "or_and_bool": (4, torch.uint8),
     "sel2nd_min_i32": (5, torch.int32),
+    # heterogeneous: A float32 weights, B int32 labels, C cb_wlabel records
+    # {float w; int32 label} held as one int64 each (see wlabel_split)
+    "maxw_label": (6, torch.int64),
 }
+
+# name -> dtypes of A's, B's and C's values
+OPERAND_DTYPES = {name: (dt, dt, dt) for name, (_, dt) in SEMIRING.items()}
+OPERAND_DTYPES["maxw_label"] = (torch.float32, torch.int32, torch.int64)
+
+
+def wlabel_split(val: torch.Tensor):
+    """(w float32, label int32) views of maxw_label values (int64 records)."""
+    pairs = val.view(torch.int32).view(-1, 2)
+    return pairs[:, 0].view(torch.float32), pairs[:, 1]
 
 SIZING = {"exact": 0, "learned": 1, "upper_bound": 2}
 
@@ -172,8 +186,10 @@ class DeviceCSR:
         return int(self.col.numel())
 
     @staticmethod
-    def from_host(M, semiring: str, device="cuda") -> "DeviceCSR":
-        dt = SEMIRING[semiring][1]
+    def from_host(M, semiring: str, device="cuda", operand: str = "A") -> "DeviceCSR":
+        """Copy a host CSR to the device with the value dtype of `operand`
+        ("A", "B" or "C") under the semiring."""
+        dt = OPERAND_DTYPES[semiring]["ABC".index(operand)]
         val = torch.from_numpy(np.ascontiguousarray(M.val).view(_np_view(dt)))
         return DeviceCSR(M.nrows, M.ncols,
                          torch.from_numpy(np.ascontiguousarray(M.row_ptr, dtype=np.int64)).to(device),
@@ -197,11 +213,11 @@ class DeviceCSR:
 
 def _np_view(dt):
     return {torch.int64: np.int64, torch.float64: np.float64, torch.uint32: np.int32,
-            torch.uint8: np.uint8, torch.int32: np.int32}[dt]
+            torch.uint8: np.uint8, torch.int32: np.int32, torch.float32: np.float32}[dt]
 
 
 _TYPESTR = {torch.int64: "<i8", torch.float64: "<f8", torch.uint32: "<u4", torch.uint8: "|u1",
-            torch.int32: "<i4"}
+            torch.int32: "<i4", torch.float32: "<f4"}
 
 
 class _Owner:
@@ -380,12 +396,13 @@ class _SpvOwner:
 def spmspv(semiring: str, A: DeviceCSR, x_idx: torch.Tensor, x_val: torch.Tensor, *,
            validate: bool = True, ctx: Context | None = None):
     """y^T = x^T A over the semiring (cb_spmspv): x is a sparse vector of length
-    A.nrows given by int32 indices and values of the semiring's type.  Returns
+    A.nrows given by int32 indices and values of the semiring's A type.  Returns
     (y_idx int32, y_val) device tensors, indices strictly increasing."""
     code, dt = SEMIRING[semiring]
     ctx = ctx or context()
-    if x_idx.dtype != torch.int32 or x_val.dtype != dt or x_idx.numel() != x_val.numel():
-        raise ValueError("x needs int32 indices and values of the semiring's dtype, equally many")
+    if x_idx.dtype != torch.int32 or x_val.dtype != OPERAND_DTYPES[semiring][0] or \
+            x_idx.numel() != x_val.numel():
+        raise ValueError("x needs int32 indices and values of the semiring's A dtype, equally many")
     sa = A.as_struct()
     nx = x_idx.numel()
     sx = cb_spvec(A.nrows, nx, x_idx.data_ptr() if nx else None, x_val.data_ptr() if nx else None)
@@ -401,7 +418,7 @@ def spmspv(semiring: str, A: DeviceCSR, x_idx: torch.Tensor, x_val: torch.Tensor
 def merge(semiring: str, parts, *, validate: bool = True, ctx: Context | None = None,
           timing: bool = False, fused: bool = True) -> DeviceCSR:
     """C = parts[0] (+) ... (+) parts[k-1] on the GPU (cb_merge); the parts are
-    DeviceCSR of one shape.  The library allocates C."""
+    DeviceCSR of one shape holding C-type values.  The library allocates C."""
     code, dt = SEMIRING[semiring]
     ctx = ctx or context()
     arr = (cb_csr * len(parts))(*[p.as_struct() for p in parts])

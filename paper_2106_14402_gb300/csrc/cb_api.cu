@@ -70,16 +70,33 @@ void fail(cb_ctx* ctx, int code, const std::string& msg) {
   throw Fail{code};
 }
 
-size_t value_size(int sr) {
+// Internal semiring id of the merge form of CB_MAXW_LABEL (Sem<7>): the
+// selector product of cb_merge; never accepted from callers.
+constexpr int kMergeMaxwLabel = 7;
+
+// Value sizes of A's, B's and C's arrays under a semiring (0: unknown).
+size_t a_value_size(int sr) {
   switch (sr) {
     case CB_PLUS_TIMES_I64: return 8;
     case CB_PLUS_TIMES_F64: return 8;
     case CB_MIN_PLUS_U32: return 4;
     case CB_OR_AND_BOOL: return 1;
     case CB_SEL2ND_MIN_I32: return 4;
+    case CB_MAXW_LABEL: return sizeof(float);
+    case kMergeMaxwLabel: return 1;
   }
   return 0;
 }
+size_t b_value_size(int sr) {
+  if (sr == CB_MAXW_LABEL) return sizeof(int32_t);
+  if (sr == kMergeMaxwLabel) return sizeof(cb_wlabel);
+  return a_value_size(sr);
+}
+size_t value_size(int sr) {
+  return sr == CB_MAXW_LABEL || sr == kMergeMaxwLabel ? sizeof(cb_wlabel) : a_value_size(sr);
+}
+// A semiring a caller may name (the internal merge form is not one).
+bool public_semiring(int sr) { return sr >= CB_PLUS_TIMES_I64 && sr <= CB_MAXW_LABEL; }
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
@@ -1041,10 +1058,11 @@ void batched_group(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, int n,
   sArp.alloc(8 * (size_t)(rowsA + 1));
   rcols.alloc(4 * (size_t)(rowsA + 1));
   sAcol.alloc(4 * (size_t)nnzA);
-  sAval.alloc((size_t)vsz * (size_t)nnzA);
+  const int64_t avs = (int64_t)a_value_size(sr), bvs = (int64_t)b_value_size(sr);
+  sAval.alloc((size_t)avs * (size_t)nnzA);
   sBrp.alloc(8 * (size_t)(rowsB + 1));
   sBcol.alloc(4 * (size_t)nnzB);
-  sBval.alloc((size_t)vsz * (size_t)nnzB);
+  sBval.alloc((size_t)bvs * (size_t)nnzB);
   const size_t psz = cb::stack_part_size();
   parts.alloc(2 * (size_t)n * psz);
   std::vector<unsigned char> hp(2 * (size_t)n * psz);
@@ -1058,9 +1076,9 @@ void batched_group(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, int n,
     bo += B[i].nnz;
   }
   CB_CUDA(cudaMemcpyAsync(parts.p, hp.data(), hp.size(), cudaMemcpyHostToDevice, ctx->stream));
-  cb::launch_stack(parts.p, n, (int)vsz, sArp.as<int64_t>(), sAcol.as<int32_t>(), sAval.p,
+  cb::launch_stack(parts.p, n, (int)avs, sArp.as<int64_t>(), sAcol.as<int32_t>(), sAval.p,
                    rcols.as<int32_t>(), ctx->stream, ctx->sms);
-  cb::launch_stack(static_cast<char*>(parts.p) + (size_t)n * psz, n, (int)vsz, sBrp.as<int64_t>(),
+  cb::launch_stack(static_cast<char*>(parts.p) + (size_t)n * psz, n, (int)bvs, sBrp.as<int64_t>(),
                    sBcol.as<int32_t>(), sBval.p, nullptr, ctx->stream, ctx->sms);
   CB_LAUNCHED();
   kernels += 2;
@@ -1258,7 +1276,7 @@ int cb_spgemm_ex(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, 
   if (C) saved = *C;
   try {
     if (!A || !B || !C) fail(ctx, CB_ERR_ARG, "null matrix argument");
-    if (value_size(sr) == 0) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
+    if (!public_semiring(sr)) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
     check_operand(ctx, A, "A");
     check_operand(ctx, B, "B");
     if (A->ncols != B->nrows) fail(ctx, CB_ERR_SHAPE, "A.ncols != B.nrows");
@@ -1298,7 +1316,7 @@ int cb_spgemm_fused(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* 
   ctx->stats.batches = 1;
   try {
     if (!A || !B || !C || !status) fail(ctx, CB_ERR_ARG, "null argument");
-    if (value_size(sr) == 0) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
+    if (!public_semiring(sr)) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
     check_operand(ctx, A, "A");
     check_operand(ctx, B, "B");
     if (A->ncols != B->nrows) fail(ctx, CB_ERR_SHAPE, "A.ncols != B.nrows");
@@ -1445,7 +1463,7 @@ int cb_spmspv(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_spvec* x, c
   if (y) saved = *y;
   try {
     if (!A || !x || !y) fail(ctx, CB_ERR_ARG, "null argument");
-    if (value_size(sr) == 0) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
+    if (!public_semiring(sr)) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
     check_operand(ctx, A, "A");
     if (x->n != A->nrows) fail(ctx, CB_ERR_SHAPE, "x's length differs from A.nrows");
     if (x->nnz < 0 || (x->nnz > 0 && (!x->idx || !x->val))) fail(ctx, CB_ERR_ARG, "bad x");
@@ -1582,7 +1600,7 @@ int cb_merge(cb_ctx* ctx, cb_semiring sr, int k, const cb_csr* parts, cb_csr* C,
   if (C) saved = *C;
   try {
     if (!parts || !C || k < 1) fail(ctx, CB_ERR_ARG, "cb_merge needs k >= 1 parts and an output");
-    if (value_size(sr) == 0) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
+    if (!public_semiring(sr)) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
     if (opt.budget_bytes > 0 || opt.sizing != CB_SIZING_EXACT)
       fail(ctx, CB_ERR_ARG, "cb_merge takes exact sizing and no budget");
     if (caller_buf && (!C->row_ptr || !C->col || !C->val))
@@ -1594,7 +1612,6 @@ int cb_merge(cb_ctx* ctx, cb_semiring sr, int k, const cb_csr* parts, cb_csr* C,
       if (parts[l].nrows != m || parts[l].ncols != n) fail(ctx, CB_ERR_SHAPE, "parts differ in shape");
       total += parts[l].nnz;
     }
-    if ((int64_t)k * m >= INT32_MAX) fail(ctx, CB_ERR_INDEX, "k * nrows beyond int32 indices");
     if (opt.validate) {
       ensure(ctx, &ctx->ws, &ctx->ws_cap, align_up(sizeof(int64_t) * cb::kCounters));
       int64_t* counters = static_cast<int64_t*>(ctx->ws);
@@ -1604,7 +1621,12 @@ int cb_merge(cb_ctx* ctx, cb_semiring sr, int k, const cb_csr* parts, cb_csr* C,
       read_counters(ctx, counters, nullptr, 0);
       if (ctx->host[cb::kError]) fail(ctx, CB_ERR_INDEX, "a part has invalid CSR index data");
     }
+    if ((int64_t)k * m >= INT32_MAX) fail(ctx, CB_ERR_INDEX, "k * nrows beyond int32 indices");
     const size_t vsz = value_size(sr);
+    // the selector product's semiring: the semiring itself, whose B and C
+    // types agree, or for CB_MAXW_LABEL its merge form (B = C = cb_wlabel)
+    const int msr = sr == CB_MAXW_LABEL ? kMergeMaxwLabel : (int)sr;
+    const size_t asz = a_value_size(msr);
     // B = [P_0; ...; P_{k-1}] stacked by rows; A = the selector (k entries per row)
     DevBuf sBrp(ctx), sBcol(ctx), sBval(ctx), hparts(ctx), aRp(ctx), aCol(ctx), aVal(ctx);
     sBrp.alloc(8 * (size_t)(k * m + 1));
@@ -1624,7 +1646,7 @@ int cb_merge(cb_ctx* ctx, cb_semiring sr, int k, const cb_csr* parts, cb_csr* C,
                                 nullptr, ctx->stream, ctx->sms);
     aRp.alloc(8 * (size_t)(m + 1));
     aCol.alloc(4 * (size_t)(k * m));
-    aVal.alloc(vsz * (size_t)(k * m));
+    aVal.alloc(asz * (size_t)(k * m));
     uint64_t one = 1;  // multiplicative identity: 1, 1.0, 0 (min,+), true
     if (sr == CB_PLUS_TIMES_F64) {
       const double d = 1.0;
@@ -1632,14 +1654,14 @@ int cb_merge(cb_ctx* ctx, cb_semiring sr, int k, const cb_csr* parts, cb_csr* C,
     } else if (sr == CB_MIN_PLUS_U32) {
       one = 0;
     }
-    cb::launch_merge_selector(m, k, (int)vsz, one, aRp.as<int64_t>(), aCol.as<int32_t>(), aVal.p,
+    cb::launch_merge_selector(m, k, (int)asz, one, aRp.as<int64_t>(), aCol.as<int32_t>(), aVal.p,
                               ctx->stream, ctx->sms);
     if (m == 0) CB_CUDA(cudaMemsetAsync(aRp.p, 0, sizeof(int64_t), ctx->stream));
     CB_LAUNCHED();
     const cb_csr sel{m, k * m, k * m, aRp.as<int64_t>(), aCol.as<int32_t>(), aVal.p};
     const DevCSR dB{k * m, n, sBrp.as<int64_t>(), sBcol.as<int32_t>(), sBval.p};
     opt.validate = 0;
-    spgemm_plain(ctx, (int)sr, &sel, dB, n, C, opt);
+    spgemm_plain(ctx, msr, &sel, dB, n, C, opt);
     ctx->stats.kernels += 2;
     return CB_OK;
   } catch (const Fail& f) {
@@ -1671,7 +1693,7 @@ int cb_spgemm_batched(cb_ctx* ctx, int count, const cb_semiring* sr, const cb_cs
     if (opt.sizing != CB_SIZING_EXACT && opt.sizing != CB_SIZING_LEARNED)
       fail(ctx, CB_ERR_ARG, "batched SpGEMM supports exact and learned sizing");
     for (int i = 0; i < count; ++i) {
-      if (value_size(sr[i]) == 0) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
+      if (!public_semiring(sr[i])) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
       check_operand(ctx, &A[i], "A[i]");
       check_operand(ctx, &B[i], "B[i]");
       if (A[i].ncols != B[i].nrows) fail(ctx, CB_ERR_SHAPE, "A[i].ncols != B[i].nrows");
@@ -1730,7 +1752,7 @@ int cb_autotune(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, c
   cb_csr C{};
   try {
     if (!A || !B) fail(ctx, CB_ERR_ARG, "null matrix argument");
-    if (value_size(sr) == 0) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
+    if (!public_semiring(sr)) fail(ctx, CB_ERR_SEMIRING, "unknown semiring");
     check_operand(ctx, A, "A");
     check_operand(ctx, B, "B");
     if (A->ncols != B->nrows) fail(ctx, CB_ERR_SHAPE, "A.ncols != B.nrows");

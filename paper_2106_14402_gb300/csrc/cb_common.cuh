@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <climits>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "cb_kernels.h"
@@ -12,70 +13,147 @@
 namespace cb {
 
 // ---------------------------------------------------------------------------
-// Semirings (paper Sec. 1: user-defined (+) and (x); the five below are the
-// ones this library instantiates).  A = accumulator type held in shared
-// memory; T = value type in the CSR arrays.  Every (+) here is commutative
-// and associative on A, so products may be combined in any order with
-// atomics; for fp64 that changes rounding only.
+// Semirings (paper Sec. 1: user-defined (+) and (x) over up to three value
+// types, two for the inputs and one for the output).  A semiring is one
+// specialisation of Sem<SR> with
+//   TA, TB  value types of A's and B's CSR arrays, TC of C's;
+//   A       accumulator type (shared memory or L2), with ident() the
+//           (+)-identity, mul(TA, TB) -> A the (x), add and atomic the (+),
+//           out(A) -> TC the conversion of a finished entry;
+//   kUsesA  false when (x) ignores A's value (A's values are not read);
+// plus one entry in CB_FOR_EACH_SEMIRING and the value sizes in cb_api.cu.
+// Every (+) here is commutative and associative on A, so products may be
+// combined in any order with atomics; for fp64 that changes rounding only.
 // ---------------------------------------------------------------------------
+#define CB_FOR_EACH_SEMIRING(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7)
+
 template <int SR> struct Sem;
 
+// Read-only cached load of a value of any semiring type: arithmetic types
+// directly, 8-byte records (cb_wlabel) as one 64-bit word.
+template <class T>
+__device__ __forceinline__ T ldg_val(const T* p) {
+  if constexpr (std::is_arithmetic<T>::value) {
+    return __ldg(p);
+  } else {
+    static_assert(sizeof(T) == 8, "record values are 8 bytes");
+    const unsigned long long u = __ldg(reinterpret_cast<const unsigned long long*>(p));
+    T r;
+    memcpy(&r, &u, sizeof r);
+    return r;
+  }
+}
+
 template <> struct Sem<1> {  // (+,x) over int64, wrapping
-  typedef int64_t T;
+  typedef int64_t TA, TB, TC;
   typedef unsigned long long A;
   static constexpr bool kUsesA = true;
   __device__ static __forceinline__ A ident() { return 0ull; }
-  __device__ static __forceinline__ A mul(T a, T b) { return (A)a * (A)b; }
+  __device__ static __forceinline__ A mul(TA a, TB b) { return (A)a * (A)b; }
   __device__ static __forceinline__ A add(A x, A y) { return x + y; }
   __device__ static __forceinline__ void atomic(A* p, A v) { atomicAdd(p, v); }
-  __device__ static __forceinline__ T out(A x) { return (T)x; }
+  __device__ static __forceinline__ TC out(A x) { return (TC)x; }
 };
 
 template <> struct Sem<2> {  // (+,x) over fp64
-  typedef double T;
+  typedef double TA, TB, TC;
   typedef double A;
   static constexpr bool kUsesA = true;
   __device__ static __forceinline__ A ident() { return 0.0; }
-  __device__ static __forceinline__ A mul(T a, T b) { return __dmul_rn(a, b); }
+  __device__ static __forceinline__ A mul(TA a, TB b) { return __dmul_rn(a, b); }
   __device__ static __forceinline__ A add(A x, A y) { return __dadd_rn(x, y); }
   __device__ static __forceinline__ void atomic(A* p, A v) { atomicAdd(p, v); }
-  __device__ static __forceinline__ T out(A x) { return x; }
+  __device__ static __forceinline__ TC out(A x) { return x; }
 };
 
 template <> struct Sem<3> {  // (min,+) over uint32, + saturating at UINT32_MAX
-  typedef uint32_t T;
+  typedef uint32_t TA, TB, TC;
   typedef unsigned A;
   static constexpr bool kUsesA = true;
   __device__ static __forceinline__ A ident() { return 0xFFFFFFFFu; }
-  __device__ static __forceinline__ A mul(T a, T b) {
+  __device__ static __forceinline__ A mul(TA a, TB b) {
     unsigned s = a + b;
     return s < a ? 0xFFFFFFFFu : s;
   }
   __device__ static __forceinline__ A add(A x, A y) { return x < y ? x : y; }
   __device__ static __forceinline__ void atomic(A* p, A v) { atomicMin(p, v); }
-  __device__ static __forceinline__ T out(A x) { return x; }
+  __device__ static __forceinline__ TC out(A x) { return x; }
 };
 
 template <> struct Sem<4> {  // (or,and) over bool (uint8 storage)
-  typedef uint8_t T;
+  typedef uint8_t TA, TB, TC;
   typedef unsigned A;
   static constexpr bool kUsesA = true;
   __device__ static __forceinline__ A ident() { return 0u; }
-  __device__ static __forceinline__ A mul(T a, T b) { return (a != 0 && b != 0) ? 1u : 0u; }
+  __device__ static __forceinline__ A mul(TA a, TB b) { return (a != 0 && b != 0) ? 1u : 0u; }
   __device__ static __forceinline__ A add(A x, A y) { return x | y; }
   __device__ static __forceinline__ void atomic(A* p, A v) { if (v) atomicOr(p, v); }
-  __device__ static __forceinline__ T out(A x) { return x ? 1 : 0; }
+  __device__ static __forceinline__ TC out(A x) { return x ? 1 : 0; }
 };
 
 template <> struct Sem<5> {  // (select2nd,min) over int32
-  typedef int32_t T;
+  typedef int32_t TA, TB, TC;
   typedef int A;
   static constexpr bool kUsesA = false;
   __device__ static __forceinline__ A ident() { return INT_MAX; }
-  __device__ static __forceinline__ A mul(T, T b) { return b; }
+  __device__ static __forceinline__ A mul(TA, TB b) { return b; }
   __device__ static __forceinline__ A add(A x, A y) { return x < y ? x : y; }
   __device__ static __forceinline__ void atomic(A* p, A v) { atomicMin(p, v); }
-  __device__ static __forceinline__ T out(A x) { return x; }
+  __device__ static __forceinline__ TC out(A x) { return x; }
+};
+
+// Heterogeneous (paper Sec. 1: three value types): A holds fp32 edge weights,
+// B int32 labels, C (weight, label) pairs.  (x)(w, l) = (w, l); (+) keeps the
+// pair with the larger weight in IEEE 754 totalOrder (-NaN < -inf < ... <
+// -0 < +0 < ... < +inf < +NaN), and of equal weights the smaller label.  So
+// C(i,j) is the label B(k,j) reached through the heaviest edge A(i,k).
+// The accumulator packs both into one 64-bit key whose unsigned order is
+// that order: high word = the weight's bits mapped monotonically (sign bit
+// set: all bits flipped; clear: the sign bit flipped), low word =
+// 0x7FFFFFFF - label (mod 2^32), which decreases with the label.
+struct WLabel {
+  float w;
+  int32_t label;
+};
+template <> struct Sem<6> {
+  typedef float TA;
+  typedef int32_t TB;
+  typedef WLabel TC;
+  typedef unsigned long long A;
+  static constexpr bool kUsesA = true;
+  __device__ static __forceinline__ A ident() { return 0ull; }
+  __device__ static __forceinline__ A mul(TA a, TB b) {
+    const unsigned u = __float_as_uint(a);
+    const unsigned hi = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    const unsigned lo = 0x7FFFFFFFu - (unsigned)b;
+    return ((A)hi << 32) | lo;
+  }
+  __device__ static __forceinline__ A add(A x, A y) { return x > y ? x : y; }
+  __device__ static __forceinline__ void atomic(A* p, A v) { atomicMax(p, v); }
+  __device__ static __forceinline__ TC out(A x) {
+    const unsigned hi = (unsigned)(x >> 32), lo = (unsigned)x;
+    TC r;
+    r.w = __uint_as_float((hi & 0x80000000u) ? (hi & 0x7FFFFFFFu) : ~hi);
+    r.label = (int32_t)(0x7FFFFFFFu - lo);
+    return r;
+  }
+  // the accumulator of a finished entry (used by the merge form below)
+  __device__ static __forceinline__ A in(TC v) { return mul(v.w, v.label); }
+};
+
+// Merge form of Sem<6> (internal, not an ABI semiring): the selector product
+// that (+)-combines partial results of Sem<6> has B and C of Sem<6>'s C
+// type; (x)(selector, c) = c and (+) is Sem<6>'s.
+template <> struct Sem<7> {
+  typedef uint8_t TA;
+  typedef WLabel TB, TC;
+  typedef unsigned long long A;
+  static constexpr bool kUsesA = false;
+  __device__ static __forceinline__ A ident() { return Sem<6>::ident(); }
+  __device__ static __forceinline__ A mul(TA, TB b) { return Sem<6>::in(b); }
+  __device__ static __forceinline__ A add(A x, A y) { return Sem<6>::add(x, y); }
+  __device__ static __forceinline__ void atomic(A* p, A v) { Sem<6>::atomic(p, v); }
+  __device__ static __forceinline__ TC out(A x) { return Sem<6>::out(x); }
 };
 
 // ---------------------------------------------------------------------------
@@ -380,11 +458,19 @@ struct BalancedSmem {
 // ranges (B row, or the B row's slice in [lo, hi) when `sorted` and not
 // `whole`) are compacted and prefix-summed, every warp takes an equal
 // contiguous share of the chunk's products and its lanes take consecutive
-// products (coalesced B reads).  Since ranges are nonempty, the 32 products
-// of one warp step start at most 31 new ranges: each lane reads one range
-// start, the warp ORs together the bits of the starts that fall inside the
-// step, and a lane's range is the step's first range plus the number of
-// starts at or before its product.  All threads of the CTA must call it.
+// products (coalesced B reads).  Short ranges (< kLongRange products) and
+// long ones are done in two rounds:
+//   * short: since ranges are nonempty, the 32 products of one warp step
+//     start at most 31 new ranges: each lane reads one range start, the warp
+//     ORs together the bits of the starts that fall inside the step, and a
+//     lane's range is the step's first range plus the number of starts at or
+//     before its product;
+//   * long: the warp walks its share range by range, 32 * U consecutive
+//     products of one range per iteration, with no per-product range
+//     bookkeeping (the A entry is uniform over the warp).
+// All threads of the CTA must call it.
+constexpr int kLongRange = 64;
+
 template <int U, class LD, class F>
 __device__ __forceinline__ void for_row_products_balanced_u(const DevCSR& A, const DevCSR& B,
                                                             int64_t i, int64_t lo, int64_t hi,
@@ -411,79 +497,119 @@ __device__ __forceinline__ void for_row_products_balanced_u(const DevCSR& A, con
       }
       len = q1 - q0;
     }
-    // one scan gives both the product offsets (high bits) and the slots of
-    // the nonempty ranges (low 11 bits; at most 1024 of them)
-    long long packed_total;
-    const long long packed =
-        cta_exclusive_scan64((len << 11) | (len > 0 ? 1 : 0), sm.scan, packed_total);
-    const long long total = packed_total >> 11;
-    const int ne = (int)(packed_total & 2047);
-    if (len > 0) {
-      const int slot = (int)(packed & 2047);
-      sm.off[slot] = packed >> 11;
-      sm.b0[slot] = q0;
-      sm.pa[slot] = tid;
-    }
-    __syncthreads();
-    const long long t_beg = total * warp / nwarp, t_end = total * (warp + 1) / nwarp;
-    if (t_beg < t_end) {
-      // range holding the warp's first product (the same search in every lane)
-      int l = 0, r = ne - 1;
-      while (l < r) {
-        const int mid = (l + r + 1) >> 1;
-        if (sm.off[mid] <= t_beg) l = mid;
-        else r = mid - 1;
+    for (int round = 0; round < 2; ++round) {
+      const long long lr = (round == 0) == (len < kLongRange) ? len : 0;
+      // one scan gives both the product offsets (high bits) and the slots of
+      // the nonempty ranges (low 11 bits; at most 1024 of them)
+      long long packed_total;
+      const long long packed =
+          cta_exclusive_scan64((lr << 11) | (lr > 0 ? 1 : 0), sm.scan, packed_total);
+      const long long total = packed_total >> 11;
+      const int ne = (int)(packed_total & 2047);
+      if (lr > 0) {
+        const int slot = (int)(packed & 2047);
+        sm.off[slot] = packed >> 11;
+        sm.b0[slot] = q0;
+        sm.pa[slot] = tid;
       }
-      int j0 = l;
-      long long nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;  // start of the next range
-      int jc = -1;          // the lane's current range, its B offset and A entry
-      int64_t qb = 0, pc = 0;
-      // U warp steps per iteration: positions first, then all loads, then
-      // the callbacks, so that U independent loads are in flight per lane
-      for (long long tb = t_beg; tb < t_end; tb += 32 * U) {
-        int64_t qu[U], pu[U];
-        bool vu[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const long long ts = tb + 32 * u;
-          int j = j0;
-          if (nxt <= ts + 31) {  // the step crosses range starts (uniform over the warp)
-            const int k = j0 + 1 + lane;
-            const long long st = k < ne ? sm.off[k] : LLONG_MAX;
-            const long long pos = st - ts;  // >= 1 by the choice of j0
-            const unsigned bits = __reduce_or_sync(0xffffffffu, pos < 32 ? 1u << (int)pos : 0u);
-            j = j0 + __popc(bits & ((2u << lane) - 1u));
-            j0 += __popc(bits);
-            nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;
-          }
-          const long long t = ts + lane;
-          vu[u] = t < t_end;
-          if (vu[u] && j != jc) {
-            jc = j;
-            qb = sm.b0[j] - sm.off[j];
-            pc = c0 + sm.pa[j];
-          }
-          qu[u] = qb + t;
-          pu[u] = pc;
-          // range holding product ts + 32 (ranges are nonempty, so at most one more start)
-          if (nxt <= ts + 32) {
-            ++j0;
-            nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;
-          }
+      __syncthreads();
+      const long long t_beg = total * warp / nwarp, t_end = total * (warp + 1) / nwarp;
+      if (round == 1 && t_beg < t_end) {
+        // range holding the warp's first product
+        int l = 0, r = ne - 1;
+        while (l < r) {
+          const int mid = (l + r + 1) >> 1;
+          if (sm.off[mid] <= t_beg) l = mid;
+          else r = mid - 1;
         }
-        int cu[U];
-        V vv[U];
+        int j = l;
+        for (long long t = t_beg; t < t_end; ++j) {  // uniform over the warp
+          const long long r_end = j + 1 < ne ? sm.off[j + 1] : total;
+          const long long e = r_end < t_end ? r_end : t_end;
+          const int64_t qb = sm.b0[j] - sm.off[j];
+          const int64_t pc = c0 + sm.pa[j];
+          for (long long tt = t; tt < e; tt += 32 * U) {
+            int64_t qu[U];
+            bool vu[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          cu[u] = vu[u] ? __ldg(B.col + qu[u]) : 0;
-          vv[u] = vu[u] ? ld(qu[u]) : V();
+            for (int u = 0; u < U; ++u) {
+              const long long x = tt + 32 * u + lane;
+              vu[u] = x < e;
+              qu[u] = qb + x;
+            }
+            int cu[U];
+            V vv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              cu[u] = vu[u] ? __ldg(B.col + qu[u]) : 0;
+              vv[u] = vu[u] ? ld(qu[u]) : V();
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              if (vu[u] && (!filter || (unsigned)((int64_t)cu[u] - lo) < width)) f(pc, qu[u], cu[u], vv[u]);
+          }
+          t = e;
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (vu[u] && (!filter || (unsigned)((int64_t)cu[u] - lo) < width)) f(pu[u], qu[u], cu[u], vv[u]);
       }
+      if (round == 0 && t_beg < t_end) {
+        // range holding the warp's first product (the same search in every lane)
+        int l = 0, r = ne - 1;
+        while (l < r) {
+          const int mid = (l + r + 1) >> 1;
+          if (sm.off[mid] <= t_beg) l = mid;
+          else r = mid - 1;
+        }
+        int j0 = l;
+        long long nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;  // start of the next range
+        int jc = -1;          // the lane's current range, its B offset and A entry
+        int64_t qb = 0, pc = 0;
+        // U warp steps per iteration: positions first, then all loads, then
+        // the callbacks, so that U independent loads are in flight per lane
+        for (long long tb = t_beg; tb < t_end; tb += 32 * U) {
+          int64_t qu[U], pu[U];
+          bool vu[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const long long ts = tb + 32 * u;
+            int j = j0;
+            if (nxt <= ts + 31) {  // the step crosses range starts (uniform over the warp)
+              const int k = j0 + 1 + lane;
+              const long long st = k < ne ? sm.off[k] : LLONG_MAX;
+              const long long pos = st - ts;  // >= 1 by the choice of j0
+              const unsigned bits = __reduce_or_sync(0xffffffffu, pos < 32 ? 1u << (int)pos : 0u);
+              j = j0 + __popc(bits & ((2u << lane) - 1u));
+              j0 += __popc(bits);
+              nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;
+            }
+            const long long t = ts + lane;
+            vu[u] = t < t_end;
+            if (vu[u] && j != jc) {
+              jc = j;
+              qb = sm.b0[j] - sm.off[j];
+              pc = c0 + sm.pa[j];
+            }
+            qu[u] = qb + t;
+            pu[u] = pc;
+            // range holding product ts + 32 (ranges are nonempty, so at most one more start)
+            if (nxt <= ts + 32) {
+              ++j0;
+              nxt = j0 + 1 < ne ? sm.off[j0 + 1] : LLONG_MAX;
+            }
+          }
+          int cu[U];
+          V vv[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            cu[u] = vu[u] ? __ldg(B.col + qu[u]) : 0;
+            vv[u] = vu[u] ? ld(qu[u]) : V();
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (vu[u] && (!filter || (unsigned)((int64_t)cu[u] - lo) < width)) f(pu[u], qu[u], cu[u], vv[u]);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 

@@ -124,12 +124,13 @@ __device__ __forceinline__ void bitonic_sort(unsigned (&key)[kFE], int g) {
 template <int SR, int G>
 __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int64_t* __restrict__ Crp,
                                                      int32_t* __restrict__ Ccol,
-                                                     typename Sem<SR>::T* __restrict__ Cval,
+                                                     typename Sem<SR>::TC* __restrict__ Cval,
                                                      int64_t cap, unsigned long long* tstat,
                                                      int64_t tstat_cap, unsigned* sync, int* status) {
   typedef Sem<SR> S;
   typedef typename S::A Acc;
-  typedef typename S::T T;
+  typedef typename S::TA TA;
+  typedef typename S::TB TB;
   constexpr int F = G * kFE;            // products per row at most
   constexpr int LOGF = clog2(F);
   constexpr int RPW = 32 / G;           // rows per warp
@@ -145,8 +146,8 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / G, g = lane % G;
-  const T* __restrict__ Aval = reinterpret_cast<const T*>(A.val);
-  const T* __restrict__ Bval = reinterpret_cast<const T*>(B.val);
+  const TA* __restrict__ Aval = reinterpret_cast<const TA*>(A.val);
+  const TB* __restrict__ Bval = reinterpret_cast<const TB*>(B.val);
   Acc* sv = &sval[warp][grp * F];
   unsigned* sk = &skey[warp][grp * F];
   // Bank swizzles of a row's shared arrays: entry t lives at t ^ h, h < 8,
@@ -172,13 +173,13 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
     }
     const int64_t nA = a1 - a0;
     int64_t b0 = 0;
-    T av = T();
+    TA av = TA();
     int len = 0;
     bool bad = nA > G;
     if (!bad && g < nA) {
       const int64_t p = a0 + g;
       const int k = __ldg(A.col + p);
-      if (S::kUsesA) av = __ldg(Aval + p);
+      if (S::kUsesA) av = ldg_val(Aval + p);
       b0 = __ldg(B.rp + k);
       const int64_t bl = __ldg(B.rp + k + 1) - b0;
       len = bl > F ? F + 1 : (int)bl;
@@ -224,12 +225,12 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
         valid = t < Fr;
       }
       const int64_t bq = __shfl_sync(kFull, b0, m, G);
-      const T a = S::kUsesA ? shfl_idx(av, m, G) : T();
+      const TA a = S::kUsesA ? shfl_idx(av, m, G) : TA();
       unsigned kt = kFPad;
       if (valid) {
         const int64_t q = bq + (t - first);
         kt = ((unsigned)__ldg(B.col + q) << LOGF) | (unsigned)t;
-        sv[pv(t)] = S::mul(a, __ldg(Bval + q));
+        sv[pv(t)] = S::mul(a, ldg_val(Bval + q));
       }
       sk[pk(t)] = kt;
     }
@@ -439,7 +440,7 @@ cudaError_t launch_fused_t(const DevCSR& A, const DevCSR& B, int64_t* Crp, int32
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_fused<SR, G>, A, B, Crp, Ccol,
-                            static_cast<typename Sem<SR>::T*>(Cval), cap, tstat, tstat_cap, sync,
+                            static_cast<typename Sem<SR>::TC*>(Cval), cap, tstat, tstat_cap, sync,
                             status);
 }
 
@@ -468,11 +469,9 @@ cudaError_t launch_fused(int sr, int lanes, const DevCSR& A, const DevCSR& B, in
                          int32_t* Ccol, void* Cval, int64_t cap, unsigned long long* tstat,
                          int64_t tstat_cap, unsigned* sync, int* status, cudaStream_t s, int sms) {
   switch (sr) {
-    case 1: return launch_fused_sr<1>(lanes, A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms);
-    case 2: return launch_fused_sr<2>(lanes, A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms);
-    case 3: return launch_fused_sr<3>(lanes, A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms);
-    case 4: return launch_fused_sr<4>(lanes, A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms);
-    case 5: return launch_fused_sr<5>(lanes, A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms);
+#define CB_CASE(SRV) case SRV: return launch_fused_sr<SRV>(lanes, A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms);
+    CB_FOR_EACH_SEMIRING(CB_CASE)
+#undef CB_CASE
   }
   return cudaErrorInvalidValue;
 }

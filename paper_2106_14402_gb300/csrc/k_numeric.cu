@@ -34,13 +34,14 @@ template <int SR, int CTA, int TEAM, int TABLE_MAX, bool LEARNED = false>
 __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int32_t* rows,
                                                   int64_t nrows_tier, const int64_t* flops,
                                                   const int64_t* nnz, const int64_t* Crp,
-                                                  int32_t* Ccol, typename Sem<SR>::T* Cval,
+                                                  int32_t* Ccol, typename Sem<SR>::TC* Cval,
                                                   int64_t* err, uint8_t* learned = nullptr,
                                                   int64_t* cnt_out = nullptr,
                                                   const int64_t* dcnt = nullptr, int tier = 0) {
   typedef Sem<SR> S;
   typedef typename S::A Acc;
-  typedef typename S::T T;
+  typedef typename S::TA TA;
+  typedef typename S::TB TB;
   constexpr int TEAMS = CTA / TEAM;
   constexpr int PER = TABLE_MAX / TEAM;
   if (dcnt) {  // tier sizes on the device (launch sequences without host synchronisation)
@@ -55,8 +56,8 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
   const int team = threadIdx.x / TEAM, lane = threadIdx.x % TEAM;
   Acc* vals = reinterpret_cast<Acc*>(num_smem) + team * TABLE_MAX;
   int* keys = reinterpret_cast<int*>(reinterpret_cast<Acc*>(num_smem) + TEAMS * TABLE_MAX) + team * TABLE_MAX;
-  const T* Aval = reinterpret_cast<const T*>(A.val);
-  const T* Bval = reinterpret_cast<const T*>(B.val);
+  const TA* Aval = reinterpret_cast<const TA*>(A.val);
+  const TB* Bval = reinterpret_cast<const TB*>(B.val);
 
   for (int64_t r = (int64_t)blockIdx.x * TEAMS + team; r < nrows_tier;
        r += (int64_t)gridDim.x * TEAMS) {
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
     const int G = 1 << gl, gq = lane & (G - 1), groups = TEAM >> gl;
     for (int64_t p = a0 + (lane >> gl); p < a1; p += groups) {
       const int k = A.col[p];
-      const T a = S::kUsesA ? Aval[p] : T();
+      const TA a = S::kUsesA ? Aval[p] : TA();
       const int64_t b1 = row_end(B, k);
       for (int64_t q = B.rp[k] + gq; q < b1; q += G) {
         const int c = B.col[q];
@@ -176,13 +177,14 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
                                                       const unsigned* hbits, int b_sorted,
                                                       const int64_t* flops, const int64_t* nnz,
                                                       const int64_t* Crp, int32_t* Ccol,
-                                                      typename Sem<SR>::T* Cval, int64_t* err,
+                                                      typename Sem<SR>::TC* Cval, int64_t* err,
                                                       int64_t num_hash_max,
                                                       typename Sem<SR>::A* racc,
                                                       const int64_t* dcounters = nullptr) {
   typedef Sem<SR> S;
   typedef typename S::A Acc;
-  typedef typename S::T T;
+  typedef typename S::TA TA;
+  typedef typename S::TB TB;
   constexpr int WCAP = NumLimits<SR>::kWcap;
   if (dcounters) {  // sizes on the device: heavy segment of the symbolic order, windows, sortedness
     heavy_rows += dcounters[kCntSym + 1] + dcounters[kCntSym + 2] + dcounters[kCntSym + 3];
@@ -208,8 +210,8 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
   const BalancedSmem sm{bal, bal + CTA, reinterpret_cast<int*>(bal + 2 * CTA), scan64, iscan};
   __shared__ long long s_base;
   const int tid = threadIdx.x, lane = tid & 31;
-  const T* Aval = reinterpret_cast<const T*>(A.val);
-  const T* Bval = reinterpret_cast<const T*>(B.val);
+  const TA* Aval = reinterpret_cast<const TA*>(A.val);
+  const TB* Bval = reinterpret_cast<const TB*>(B.val);
 
   for (int64_t u = blockIdx.x; u < n_wins; u += gridDim.x) {
     const Window wd = wins[u];
@@ -272,16 +274,16 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
     // pass 2: accumulate at the rank of each product's column (two warp
     // steps per iteration, B columns and values loaded before the atomics)
     int64_t p_last = -1;  // the lane's last A entry and its value
-    T a_last = T();
+    TA a_last = TA();
     for_row_products_balanced_u<2>(A, B, i, lo, hi, whole, b_sorted != 0, sm,
-                                   [&](int64_t q) { return __ldg(Bval + q); },
-                                   [&](int64_t p, int64_t, int c, T bv) {
+                                   [&](int64_t q) { return ldg_val(Bval + q); },
+                                   [&](int64_t p, int64_t, int c, TB bv) {
                                      const unsigned off = (unsigned)((int64_t)c - lo);
                                      const uint2 e = bp[off >> 5];
                                      const int slot = (int)e.y + __popc(e.x & ((1u << (off & 31)) - 1u));
                                      if (S::kUsesA && p != p_last) {
                                        p_last = p;
-                                       a_last = __ldg(Aval + p);
+                                       a_last = ldg_val(Aval + p);
                                      }
                                      if (slot < cnt) S::atomic(&wacc[slot], S::mul(a_last, bv));
                                    });
@@ -323,8 +325,8 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
                 const int64_t* Crp, int32_t* Ccol, void* Cval_, int64_t* err, cudaStream_t s,
                 int sms, int* launches, int64_t num_hash_max, void* racc) {
   typedef typename Sem<SR>::A Acc;
-  typedef typename Sem<SR>::T T;
-  T* Cval = reinterpret_cast<T*>(Cval_);
+  typedef typename Sem<SR>::TC TC;
+  TC* Cval = reinterpret_cast<TC*>(Cval_);
   constexpr size_t slot = sizeof(Acc) + sizeof(int);
   if (seg_count[kNumWarp]) {
     constexpr int CTA = 256, TEAM = 32, TBL = 2 * kNumWarpMax;
@@ -373,8 +375,8 @@ void numeric_dev_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const
                     const int32_t* perm_sym, const Window* wins, const int32_t* span_counts,
                     int64_t spans, void* racc, int64_t num_hash_max) {
   typedef typename Sem<SR>::A Acc;
-  typedef typename Sem<SR>::T T;
-  T* Cval = reinterpret_cast<T*>(Cval_);
+  typedef typename Sem<SR>::TC TC;
+  TC* Cval = reinterpret_cast<TC*>(Cval_);
   constexpr size_t slot = sizeof(Acc) + sizeof(int);
   const int64_t* dc = counters + kCntNum;
   {
@@ -412,8 +414,8 @@ void learned_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
                 const int64_t* stage_rp, int32_t* scol, void* sval_, uint8_t* learned,
                 int64_t* cnt, int64_t* overflows, cudaStream_t s, int sms, int* launches) {
   typedef typename Sem<SR>::A Acc;
-  typedef typename Sem<SR>::T T;
-  T* sval = reinterpret_cast<T*>(sval_);
+  typedef typename Sem<SR>::TC TC;
+  TC* sval = reinterpret_cast<TC*>(sval_);
   constexpr size_t slot = sizeof(Acc) + sizeof(int);
   if (seg_count[1]) {
     constexpr int CTA = 256, TEAM = 32, TBL = 2 * kNumWarpMax;
@@ -452,42 +454,37 @@ void launch_learned_numeric(int sr, const DevCSR& A, const DevCSR& B, const int3
   learned_sr<SRV>(A, B, perm, seg_begin, seg_count, flops, cap, stage_rp, scol, sval, learned, \
                   cnt, overflows, s, sms, launches)
   switch (sr) {
-    case 1: CB_LRN(1); break;
-    case 2: CB_LRN(2); break;
-    case 3: CB_LRN(3); break;
-    case 4: CB_LRN(4); break;
-    case 5: CB_LRN(5); break;
+#define CB_CASE(SRV) case SRV: CB_LRN(SRV); break;
+    CB_FOR_EACH_SEMIRING(CB_CASE)
+#undef CB_CASE
   }
 #undef CB_LRN
 }
 
 int learn_hash_max(int sr) {
   switch (sr) {
-    case 1: return NumLimits<1>::kLearnHashMax;
-    case 2: return NumLimits<2>::kLearnHashMax;
-    case 3: return NumLimits<3>::kLearnHashMax;
-    case 4: return NumLimits<4>::kLearnHashMax;
-    default: return NumLimits<5>::kLearnHashMax;
+#define CB_CASE(SRV) case SRV: return NumLimits<SRV>::kLearnHashMax;
+    CB_FOR_EACH_SEMIRING(CB_CASE)
+#undef CB_CASE
+    default: return 0;
   }
 }
 
 int num_window_cut(int sr) {
   switch (sr) {
-    case 1: return NumLimits<1>::kWcut;
-    case 2: return NumLimits<2>::kWcut;
-    case 3: return NumLimits<3>::kWcut;
-    case 4: return NumLimits<4>::kWcut;
-    default: return NumLimits<5>::kWcut;
+#define CB_CASE(SRV) case SRV: return NumLimits<SRV>::kWcut;
+    CB_FOR_EACH_SEMIRING(CB_CASE)
+#undef CB_CASE
+    default: return 0;
   }
 }
 
 int num_large_max(int sr) {
   switch (sr) {
-    case 1: return NumLimits<1>::kLargeMax;
-    case 2: return NumLimits<2>::kLargeMax;
-    case 3: return NumLimits<3>::kLargeMax;
-    case 4: return NumLimits<4>::kLargeMax;
-    default: return NumLimits<5>::kLargeMax;
+#define CB_CASE(SRV) case SRV: return NumLimits<SRV>::kLargeMax;
+    CB_FOR_EACH_SEMIRING(CB_CASE)
+#undef CB_CASE
+    default: return 0;
   }
 }
 
@@ -503,11 +500,9 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
                   span_counts, spans, hbits, b_sorted, Crp, Ccol, Cval, err, s, sms, launches, \
                   num_hash_max, racc)
   switch (sr) {
-    case 1: CB_NUM(1); break;
-    case 2: CB_NUM(2); break;
-    case 3: CB_NUM(3); break;
-    case 4: CB_NUM(4); break;
-    case 5: CB_NUM(5); break;
+#define CB_CASE(SRV) case SRV: CB_NUM(SRV); break;
+    CB_FOR_EACH_SEMIRING(CB_CASE)
+#undef CB_CASE
   }
 #undef CB_NUM
 }
@@ -535,11 +530,9 @@ void prepare_numeric_dev_sr() {
 void prepare_dev_launchers(int sr) {
   prepare_symbolic_dev();
   switch (sr) {
-    case 1: prepare_numeric_dev_sr<1>(); break;
-    case 2: prepare_numeric_dev_sr<2>(); break;
-    case 3: prepare_numeric_dev_sr<3>(); break;
-    case 4: prepare_numeric_dev_sr<4>(); break;
-    case 5: prepare_numeric_dev_sr<5>(); break;
+#define CB_CASE(SRV) case SRV: prepare_numeric_dev_sr<SRV>(); break;
+    CB_FOR_EACH_SEMIRING(CB_CASE)
+#undef CB_CASE
   }
 }
 
@@ -554,22 +547,18 @@ void launch_numeric_dev(int sr, const DevCSR& A, const DevCSR& B, const int32_t*
   numeric_dev_sr<SRV>(A, B, perm, counters, flops, nnz, Crp, Ccol, Cval, err, s, sms, m, perm_sym, \
                       wins, span_counts, spans, racc, num_hash_max)
   switch (sr) {
-    case 1: CB_NDEV(1); break;
-    case 2: CB_NDEV(2); break;
-    case 3: CB_NDEV(3); break;
-    case 4: CB_NDEV(4); break;
-    case 5: CB_NDEV(5); break;
+#define CB_CASE(SRV) case SRV: CB_NDEV(SRV); break;
+    CB_FOR_EACH_SEMIRING(CB_CASE)
+#undef CB_CASE
   }
 #undef CB_NDEV
 }
 
 size_t rank_scratch_bytes(int sr, int sms) {
   switch (sr) {
-    case 1: return rank_scratch_bytes_sr<1>(sms);
-    case 2: return rank_scratch_bytes_sr<2>(sms);
-    case 3: return rank_scratch_bytes_sr<3>(sms);
-    case 4: return rank_scratch_bytes_sr<4>(sms);
-    case 5: return rank_scratch_bytes_sr<5>(sms);
+#define CB_CASE(SRV) case SRV: return rank_scratch_bytes_sr<SRV>(sms);
+    CB_FOR_EACH_SEMIRING(CB_CASE)
+#undef CB_CASE
   }
   return 0;
 }

@@ -49,15 +49,16 @@ __global__ void __launch_bounds__(256) k_spa_init(typename Sem<SR>::A* spa, int6
 // K3.  cpre[p] = first chunk of x entry p, cpre[nx] = number of chunks.
 template <int SR>
 __global__ void __launch_bounds__(256) k_spmspv_push(DevCSR A, const int32_t* x_idx,
-                                                    const typename Sem<SR>::T* x_val, int64_t nx,
+                                                    const typename Sem<SR>::TA* x_val, int64_t nx,
                                                     const int64_t* cpre, typename Sem<SR>::A* spa,
                                                     unsigned* touched) {
   typedef Sem<SR> S;
-  typedef typename S::T T;
+  typedef typename S::TA TA;
+  typedef typename S::TB TB;
   const int lane = threadIdx.x & 31;
   const int64_t total = cpre[nx];
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const T* Aval = reinterpret_cast<const T*>(A.val);
+  const TB* Aval = reinterpret_cast<const TB*>(A.val);
   for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nwarps) {
     // x entry owning chunk w: the last p with cpre[p] <= w
     int64_t lo = 0, hi = nx - 1;
@@ -68,13 +69,13 @@ __global__ void __launch_bounds__(256) k_spmspv_push(DevCSR A, const int32_t* x_
     }
     const int64_t p = lo;
     const int i = __ldg(x_idx + p);
-    const T xv = S::kUsesA ? __ldg(x_val + p) : T();
+    const TA xv = S::kUsesA ? ldg_val(x_val + p) : TA();
     const int64_t r0 = __ldg(A.rp + i), r1 = __ldg(A.rp + i + 1);
     const int64_t q0 = r0 + (w - __ldg(cpre + p)) * kChunk;
     const int64_t q1 = min(q0 + kChunk, r1);
     for (int64_t q = q0 + lane; q < q1; q += 32) {
       const int c = __ldg(A.col + q);
-      S::atomic(&spa[c], S::mul(xv, __ldg(Aval + q)));
+      S::atomic(&spa[c], S::mul(xv, ldg_val(Aval + q)));
       const unsigned bit = 1u << (c & 31);
       if (!(touched[c >> 5] & bit)) atomicOr(&touched[c >> 5], bit);
     }
@@ -93,7 +94,7 @@ template <int SR>
 __global__ void __launch_bounds__(256) k_spmspv_compact(unsigned* touched, int64_t nw,
                                                        const int64_t* wpre,
                                                        typename Sem<SR>::A* spa, int32_t* y_idx,
-                                                       typename Sem<SR>::T* y_val, int64_t cap) {
+                                                       typename Sem<SR>::TC* y_val, int64_t cap) {
   typedef Sem<SR> S;
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw;
        w += (int64_t)gridDim.x * blockDim.x) {
@@ -126,7 +127,8 @@ void spmspv_sr(int step, const DevCSR& A, const int32_t* x_idx, const void* x_va
                int64_t* wcnt, const int64_t* wpre, int32_t* y_idx, void* y_val, int64_t cap,
                int64_t* err, cudaStream_t s, int sms) {
   typedef typename Sem<SR>::A Acc;
-  typedef typename Sem<SR>::T T;
+  typedef typename Sem<SR>::TA TA;
+  typedef typename Sem<SR>::TC TC;
   const int64_t nw = (n + 31) / 32;
   switch (step) {
     case 0:
@@ -136,7 +138,7 @@ void spmspv_sr(int step, const DevCSR& A, const int32_t* x_idx, const void* x_va
       k_spmspv_chunks<<<grid_of(nx, 256, sms * 8), 256, 0, s>>>(A, x_idx, nx, chunks, err);
       break;
     case 2:
-      k_spmspv_push<SR><<<sms * 8, 256, 0, s>>>(A, x_idx, static_cast<const T*>(x_val), nx, cpre,
+      k_spmspv_push<SR><<<sms * 8, 256, 0, s>>>(A, x_idx, static_cast<const TA*>(x_val), nx, cpre,
                                                static_cast<Acc*>(spa), touched);
       break;
     case 3:
@@ -144,7 +146,7 @@ void spmspv_sr(int step, const DevCSR& A, const int32_t* x_idx, const void* x_va
       break;
     case 4:
       k_spmspv_compact<SR><<<grid_of(nw, 256, sms * 8), 256, 0, s>>>(
-          touched, nw, wpre, static_cast<Acc*>(spa), y_idx, static_cast<T*>(y_val), cap);
+          touched, nw, wpre, static_cast<Acc*>(spa), y_idx, static_cast<TC*>(y_val), cap);
       break;
   }
 }
@@ -153,11 +155,9 @@ void spmspv_sr(int step, const DevCSR& A, const int32_t* x_idx, const void* x_va
 
 size_t spa_value_size(int sr) {
   switch (sr) {
-    case 1: return sizeof(Sem<1>::A);
-    case 2: return sizeof(Sem<2>::A);
-    case 3: return sizeof(Sem<3>::A);
-    case 4: return sizeof(Sem<4>::A);
-    case 5: return sizeof(Sem<5>::A);
+#define CB_CASE(SRV) case SRV: return sizeof(Sem<SRV>::A);
+    CB_FOR_EACH_SEMIRING(CB_CASE)
+#undef CB_CASE
   }
   return 0;
 }
@@ -171,11 +171,9 @@ void launch_spmspv_step(int sr, int step, const DevCSR& A, const int32_t* x_idx,
   spmspv_sr<SRV>(step, A, x_idx, x_val, nx, chunks, cpre, spa, touched, n, wcnt, wpre, y_idx, \
                  y_val, cap, err, s, sms)
   switch (sr) {
-    case 1: CB_SPV(1); break;
-    case 2: CB_SPV(2); break;
-    case 3: CB_SPV(3); break;
-    case 4: CB_SPV(4); break;
-    case 5: CB_SPV(5); break;
+#define CB_CASE(SRV) case SRV: CB_SPV(SRV); break;
+    CB_FOR_EACH_SEMIRING(CB_CASE)
+#undef CB_CASE
   }
 #undef CB_SPV
 }
