@@ -755,8 +755,9 @@ def run_merge_leg(args, cb, ctx, flush, dev, peak, peak_src):
 
 def run_spmspv_leg(args, cb, ctx, flush, dev, dprob, peak, peak_src):
     """SpMSpV y^T = x^T A (Sec. 4.3) on the workload's R-MAT matrix: random
-    frontiers of 1K, 16K and 128K vertices, (or,and) and (min,+); next to the
-    same product as a one-row SpGEMM."""
+    frontiers of 1K, 16K and 128K vertices, (or,and) and (min,+), with the
+    dense accumulator and in the bucket form; next to the same product as a
+    one-row SpGEMM."""
     import torch
     from paper_2106_14402_gb300 import gen
     out = {"workload": "R-MAT s18 ef16 (the step's matrix); x = seeded random distinct vertices",
@@ -788,6 +789,12 @@ def run_spmspv_leg(args, cb, ctx, flush, dev, dprob, peak, peak_src):
 
             as_spgemm()
             ms_g = timed(as_spgemm, max(3, args.steps), flush)
+
+            def bucket():
+                cb.spmspv(sr, dA, xi, xv, validate=False, ctx=ctx, bucket=True)
+
+            bucket()
+            ms_b = timed(bucket, max(3, args.steps), flush)
             lens = np.diff(A.row_ptr)[idx]
             prods = int(lens.sum())
             nbytes = f * (4 + v) + 16 * f + prods * (4 + v) + res["nnz"] * (4 + v)
@@ -795,7 +802,8 @@ def run_spmspv_leg(args, cb, ctx, flush, dev, dprob, peak, peak_src):
                                 "us": round(ms * 1e3, 2), "products_per_s": prods / (ms * 1e-3),
                                 "roofline_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
                                 "one_row_spgemm_us": round(ms_g * 1e3, 2),
-                                "vs_one_row_spgemm": ms_g / ms})
+                                "vs_one_row_spgemm": ms_g / ms,
+                                "bucket_form_us": round(ms_b * 1e3, 2)})
     out["peak_gbs"] = peak
     out["peak_source"] = peak_src
     return out

@@ -140,6 +140,8 @@ enum {
   CB_FLAG_SYNC_FREE = 32, /* cb_spgemm_batched: the launch sequence of CB_FLAG_GRAPH
                          without the capture; on_batch runs on the calling thread after
                          each wave (and may use CUDA) */
+  CB_FLAG_SPMSPV_BUCKET = 64, /* cb_spmspv: the bucket (propagation-blocking) form
+                         instead of the dense accumulator (see cb_spmspv) */
   CB_FLAG_NO_FUSED = 8 /* exact sizing: always run the two-phase path.  By default
                          a product whose rows all meet the bounds of
                          cb_spgemm_fused (below) is formed by that one launch
@@ -342,7 +344,14 @@ int cb_autotune(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B, c
  * library (free with cb_spvec_free_async) unless opt->out_capacity > 0, in
  * which case they are the caller's (CB_ERR_CAPACITY with y->nnz = needed if
  * too small).  opt->validate checks A (row pointers and columns); x's
- * indices are always checked on the device (CB_ERR_INDEX). */
+ * indices are always checked on the device (CB_ERR_INDEX).
+ * With opt->flags & CB_FLAG_SPMSPV_BUCKET the column-partitioned form of
+ * Sec. 4.3 runs instead (buckets that block y, also called propagation
+ * blocking): every product is appended to the bucket of its column (4096
+ * columns per bucket), each bucket is (+)-combined by one CTA in a shared-
+ * memory accumulator and written in column order; it keeps no state in the
+ * context and needs O(products) scratch, with two synchronisations (the
+ * product count and nnz(y)). */
 typedef struct {
   int64_t n;    /* length                                    */
   int64_t nnz;  /* stored entries                            */

@@ -337,6 +337,7 @@ FLAG_LEARNED_ROWS = 4
 FLAG_NO_FUSED = 8
 FLAG_GRAPH = 16
 FLAG_SYNC_FREE = 32
+FLAG_SPMSPV_BUCKET = 64
 
 # device status bits of cb_spgemm_fused
 FUSED_CAPACITY = 1
@@ -394,10 +395,12 @@ class _SpvOwner:
 
 
 def spmspv(semiring: str, A: DeviceCSR, x_idx: torch.Tensor, x_val: torch.Tensor, *,
-           validate: bool = True, ctx: Context | None = None):
+           validate: bool = True, ctx: Context | None = None, bucket: bool = False,
+           timing: bool = False):
     """y^T = x^T A over the semiring (cb_spmspv): x is a sparse vector of length
     A.nrows given by int32 indices and values of the semiring's A type.  Returns
-    (y_idx int32, y_val) device tensors, indices strictly increasing."""
+    (y_idx int32, y_val) device tensors, indices strictly increasing.
+    `bucket=True` runs the bucket (propagation-blocking) form."""
     code, dt = SEMIRING[semiring]
     ctx = ctx or context()
     if x_idx.dtype != torch.int32 or x_val.dtype != OPERAND_DTYPES[semiring][0] or \
@@ -407,7 +410,8 @@ def spmspv(semiring: str, A: DeviceCSR, x_idx: torch.Tensor, x_val: torch.Tensor
     nx = x_idx.numel()
     sx = cb_spvec(A.nrows, nx, x_idx.data_ptr() if nx else None, x_val.data_ptr() if nx else None)
     sy = cb_spvec()
-    opts = make_opts(validate=validate)
+    opts = make_opts(validate=validate, flags=(FLAG_SPMSPV_BUCKET if bucket else 0) |
+                     (FLAG_TIMING if timing else 0))
     ctx.check(ctx.lib.cb_spmspv(ctx.handle, code, ctypes.byref(sa), ctypes.byref(sx), ctypes.byref(sy),
                                 ctypes.byref(opts)))
     owner = _SpvOwner(ctx, cb_spvec(sy.n, sy.nnz, sy.idx, sy.val))

@@ -1449,6 +1449,92 @@ int cb_exclusive_scan(cb_ctx* ctx, const int64_t* in, int64_t n, int64_t* out) {
   }
 }
 
+// The bucket (propagation-blocking) SpMSpV: no state kept across calls; two
+// synchronisations (the product count, to size the buckets, and nnz(y)).
+void spmspv_bucket(cb_ctx* ctx, int sr, const cb_csr* A, const cb_spvec* x, cb_spvec* y,
+                   const cb_opts& opt, bool caller_buf) {
+  const int64_t n = A->ncols, nx = x->nnz;
+  const int64_t nb = cb::spmspv_buckets(n);
+  const size_t vsz = value_size(sr), avs = cb::spa_value_size(sr);
+  const int64_t big = std::max(nx, nb);
+  ensure(ctx, &ctx->ws, &ctx->ws_cap,
+         align_up(sizeof(int64_t) * cb::kCounters) + 2 * align_up(8 * (size_t)(nx + 1)) +
+             4 * align_up(8 * (size_t)(nb + 1)) + align_up(8 * (size_t)cb::scan_partials(big)));
+  Carver cv{static_cast<char*>(ctx->ws)};
+  int64_t* counters = cv.take<int64_t>(cb::kCounters);
+  int64_t* chunks = cv.take<int64_t>(nx + 1);
+  int64_t* cpre = cv.take<int64_t>(nx + 1);
+  int64_t* cur = cv.take<int64_t>(nb + 1);
+  int64_t* bpre = cv.take<int64_t>(nb + 1);
+  int64_t* bnnz = cv.take<int64_t>(nb + 1);
+  int64_t* ypre = cv.take<int64_t>(nb + 1);
+  int64_t* partial = cv.take<int64_t>(cb::scan_partials(big));
+  const DevCSR dA = dev(A);
+  unsigned long long* ucur = reinterpret_cast<unsigned long long*>(cur);
+  CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
+  CB_CUDA(cudaMemsetAsync(cur, 0, sizeof(int64_t) * (size_t)(nb + 1), ctx->stream));
+  mark(ctx, opt, 0);
+  cb::launch_spmspv_step(sr, 1, dA, x->idx, x->val, nx, chunks, nullptr, nullptr, nullptr, n, nullptr,
+                         nullptr, nullptr, nullptr, 0, counters + cb::kError, ctx->stream, ctx->sms);
+  cb::launch_exclusive_scan(chunks, nx, cpre, partial, ctx->stream);
+  cb::launch_spmspv_bucket_step(sr, 0, dA, x->idx, x->val, nx, cpre, ucur, nullptr, nullptr, nullptr,
+                                nb, n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
+                                ctx->stream, ctx->sms);
+  cb::launch_exclusive_scan(cur, nb, bpre, partial, ctx->stream);
+  CB_LAUNCHED();
+  read_counters(ctx, counters, bpre + nb, 1);
+  const int64_t products = ctx->host[cb::kCounters];
+  if (ctx->host[cb::kError]) fail(ctx, CB_ERR_INDEX, "an index of x is outside [0, A.nrows)");
+  ctx->stats.flops = products;
+  ctx->stats.kernels += 4;
+  if (products == 0) {
+    for (int e = 1; e <= 5; ++e) mark(ctx, opt, e);
+    collect_times(ctx, opt, true);
+    return;
+  }
+  DevBuf bcol(ctx), bval(ctx), scol(ctx), sval(ctx);
+  bcol.alloc(4 * (size_t)products);
+  bval.alloc(avs * (size_t)products);
+  scol.alloc(4 * (size_t)products);
+  sval.alloc(vsz * (size_t)products);
+  CB_CUDA(cudaMemcpyAsync(cur, bpre, sizeof(int64_t) * (size_t)nb, cudaMemcpyDeviceToDevice, ctx->stream));
+  cb::launch_spmspv_bucket_step(sr, 1, dA, x->idx, x->val, nx, cpre, ucur, bcol.as<int32_t>(), bval.p,
+                                nullptr, nb, n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
+                                ctx->stream, ctx->sms);
+  cb::launch_spmspv_bucket_step(sr, 2, dA, nullptr, nullptr, 0, nullptr, nullptr, bcol.as<int32_t>(),
+                                bval.p, bpre, nb, n, scol.as<int32_t>(), sval.p, bnnz, nullptr, nullptr,
+                                nullptr, 0, ctx->stream, ctx->sms);
+  cb::launch_exclusive_scan(bnnz, nb, ypre, partial, ctx->stream);
+  CB_LAUNCHED();
+  mark(ctx, opt, 1);
+  read_counters(ctx, counters, ypre + nb, 1);
+  const int64_t total = ctx->host[cb::kCounters];
+  y->nnz = total;
+  ctx->stats.nnz = total;
+  ctx->stats.kernels += 3;
+  if (caller_buf && total > opt.out_capacity) {
+    char msg[128];
+    std::snprintf(msg, sizeof msg, "y needs %lld entries, capacity %lld", (long long)total,
+                  (long long)opt.out_capacity);
+    ctx->err = msg;
+    throw Fail{CB_ERR_CAPACITY};
+  }
+  if (!caller_buf && total > 0) {
+    CB_CUDA(cudaMallocAsync((void**)&y->idx, 4 * (size_t)total, ctx->stream));
+    CB_CUDA(cudaMallocAsync(&y->val, vsz * (size_t)total, ctx->stream));
+  }
+  cb::launch_spmspv_bucket_step(sr, 3, dA, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, bpre,
+                                nb, n, scol.as<int32_t>(), sval.p, bnnz, ypre, y->idx, y->val, total,
+                                ctx->stream, ctx->sms);
+  CB_LAUNCHED();
+  ctx->stats.kernels += 1;
+  mark(ctx, opt, 2);
+  mark(ctx, opt, 3);
+  mark(ctx, opt, 4);
+  mark(ctx, opt, 5);
+  collect_times(ctx, opt, true);
+}
+
 int cb_spmspv(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_spvec* x, cb_spvec* y,
               const cb_opts* opt_in) {
   if (!ctx) return CB_ERR_ARG;
@@ -1486,6 +1572,10 @@ int cb_spmspv(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_spvec* x, c
       if (ctx->host[cb::kError]) fail(ctx, CB_ERR_INDEX, "A has invalid CSR index data");
     }
     if (n == 0 || nx == 0) return CB_OK;
+    if (opt.flags & CB_FLAG_SPMSPV_BUCKET) {
+      spmspv_bucket(ctx, (int)sr, A, x, y, opt, caller_buf);
+      return CB_OK;
+    }
     // the dense accumulator: (re)allocated for a wider A, re-initialised for another semiring
     const size_t avs = cb::spa_value_size((int)sr);
     if (ctx->spa_n < n) {

@@ -469,7 +469,7 @@ struct BalancedSmem {
 //     products of one range per iteration, with no per-product range
 //     bookkeeping (the A entry is uniform over the warp).
 // All threads of the CTA must call it.
-constexpr int kLongRange = 64;
+constexpr int kLongRange = 128;
 
 template <int U, class LD, class F>
 __device__ __forceinline__ void for_row_products_balanced_u(const DevCSR& A, const DevCSR& B,
@@ -497,7 +497,11 @@ __device__ __forceinline__ void for_row_products_balanced_u(const DevCSR& A, con
       }
       len = q1 - q0;
     }
+    // a round with no ranges of its kind in the chunk is skipped (uniform)
+    const int any_short = __syncthreads_or(len > 0 && len < kLongRange);
+    const int any_long = __syncthreads_or(len >= kLongRange);
     for (int round = 0; round < 2; ++round) {
+      if (!(round == 0 ? any_short : any_long)) continue;
       const long long lr = (round == 0) == (len < kLongRange) ? len : 0;
       // one scan gives both the product offsets (high bits) and the slots of
       // the nonempty ranges (low 11 bits; at most 1024 of them)

@@ -169,6 +169,16 @@ void launch_mlp_predict(const void* wb, const float* master, const float* norm, 
 // dst = max(dst, src) on the device (error words kept across launch sequences).
 void launch_merge_error(const int64_t* src, int64_t* dst, cudaStream_t s);
 size_t spa_value_size(int sr);
+// Bucket (propagation-blocking) SpMSpV steps (k_spmspv.cu): 0 products per
+// bucket into cur (zeroed), 1 products appended at cur (preset to bpre),
+// 2 per-bucket reduction into the staging area + bnnz, 3 copy to y at ypre.
+int64_t spmspv_buckets(int64_t n);
+void launch_spmspv_bucket_step(int sr, int step, const DevCSR& A, const int32_t* x_idx,
+                               const void* x_val, int64_t nx, const int64_t* cpre,
+                               unsigned long long* cur, int32_t* bcol, void* bval, const int64_t* bpre,
+                               int64_t nb, int64_t n, int32_t* scol, void* sval, int64_t* bnnz,
+                               const int64_t* ypre, int32_t* y_idx, void* y_val, int64_t cap,
+                               cudaStream_t s, int sms);
 void launch_spmspv_step(int sr, int step, const DevCSR& A, const int32_t* x_idx, const void* x_val,
                         int64_t nx, int64_t* chunks, const int64_t* cpre, void* spa,
                         unsigned* touched, int64_t n, int64_t* wcnt, const int64_t* wpre,

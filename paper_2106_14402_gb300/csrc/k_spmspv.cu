@@ -15,6 +15,16 @@
 //   K5  every touched entry is written in column order and its SPA slot and
 //       bitmap word are reset, so the next call starts clean without an O(n)
 //       initialisation.
+// The bucket form (Sec. 4.3: the column-partitioned SpMSpV merges through
+// buckets that block y, i.e. propagation blocking) keeps no O(n) state:
+//   B1  products per bucket of kBucketCols output columns (warp-aggregated
+//       counts), scanned into bucket offsets;
+//   B2  every product (c, x_i (x) A(i, c)) is appended to its bucket;
+//   B3  one CTA per bucket (+)-combines the bucket's products in a shared-
+//       memory accumulator with a touched bitmap and writes the bucket's
+//       entries, in column order, to a staging area at the bucket's offset,
+//       and the bucket's entry count;
+//   B4  after a scan of the counts, each bucket's entries are copied to y.
 #include "cb_common.cuh"
 #include "cb_kernels.h"
 
@@ -116,6 +126,151 @@ __global__ void __launch_bounds__(256) k_spmspv_compact(unsigned* touched, int64
   }
 }
 
+constexpr int kBucketLog = 12;
+constexpr int kBucketCols = 1 << kBucketLog;  // output columns per bucket
+
+// The x entry owning chunk w: the last p with cpre[p] <= w.
+__device__ __forceinline__ int64_t chunk_owner(const int64_t* cpre, int64_t nx, int64_t w) {
+  int64_t lo = 0, hi = nx - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(cpre + mid) <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// B1 (PASS 0) and B2 (PASS 1): every warp takes chunks; in each step of 32
+// products the lanes of one bucket are counted together (one atomic per
+// bucket and step).  PASS 1 appends (column, product) to the bucket at the
+// slot taken from cur[bucket].
+template <int SR, int PASS>
+__global__ void __launch_bounds__(256) k_bucket_fill(DevCSR A, const int32_t* x_idx,
+                                                    const typename Sem<SR>::TA* x_val, int64_t nx,
+                                                    const int64_t* cpre,
+                                                    unsigned long long* cur, int32_t* bcol,
+                                                    typename Sem<SR>::A* bval) {
+  typedef Sem<SR> S;
+  typedef typename S::TA TA;
+  typedef typename S::TB TB;
+  const int lane = threadIdx.x & 31;
+  const int64_t total = cpre[nx];
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const TB* Aval = reinterpret_cast<const TB*>(A.val);
+  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nwarps) {
+    const int64_t p = chunk_owner(cpre, nx, w);
+    const int i = __ldg(x_idx + p);
+    const int64_t r0 = __ldg(A.rp + i), r1 = __ldg(A.rp + i + 1);
+    const int64_t q0 = r0 + (w - __ldg(cpre + p)) * kChunk;
+    const int64_t q1 = min(q0 + kChunk, r1);
+    const TA xv = (PASS == 1 && S::kUsesA) ? ldg_val(x_val + p) : TA();
+    for (int64_t base = q0; base < q1; base += 32) {  // uniform over the warp
+      const int64_t q = base + lane;
+      const bool v = q < q1;
+      const int c = v ? __ldg(A.col + q) : 0;
+      const int b = v ? (c >> kBucketLog) : -1;
+      const unsigned same = __match_any_sync(0xffffffffu, b);
+      const int leader = __ffs(same) - 1;
+      unsigned long long slot = 0;
+      if (v && lane == leader) slot = atomicAdd(cur + b, (unsigned long long)__popc(same));
+      slot = __shfl_sync(0xffffffffu, slot, leader);
+      if (PASS == 1 && v) {
+        const unsigned long long at = slot + __popc(same & ((1u << lane) - 1u));
+        bcol[at] = c;
+        bval[at] = S::mul(xv, ldg_val(Aval + q));
+      }
+    }
+  }
+}
+
+// B3: one CTA (256 threads) per bucket.
+template <int SR>
+__global__ void __launch_bounds__(256) k_bucket_reduce(const int64_t* bpre, int64_t nb, int64_t n,
+                                                      const int32_t* bcol,
+                                                      const typename Sem<SR>::A* bval,
+                                                      int32_t* scol, typename Sem<SR>::TC* sval,
+                                                      int64_t* bnnz) {
+  typedef Sem<SR> S;
+  typedef typename S::A Acc;
+  __shared__ Acc acc[kBucketCols];
+  __shared__ unsigned bits[kBucketCols / 32];
+  __shared__ int wscan[kBucketCols / 32 + 1];
+  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    for (int t = threadIdx.x; t < kBucketCols; t += blockDim.x) acc[t] = S::ident();
+    for (int t = threadIdx.x; t < kBucketCols / 32; t += blockDim.x) bits[t] = 0u;
+    __syncthreads();
+    const int64_t e0 = bpre[b], e1 = bpre[b + 1];
+    const int64_t lo = b << kBucketLog;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int o = (int)(bcol[e] - lo);
+      S::atomic(&acc[o], bval[e]);
+      const unsigned bit = 1u << (o & 31);
+      if (!(bits[o >> 5] & bit)) atomicOr(&bits[o >> 5], bit);
+    }
+    __syncthreads();
+    // word offsets: exclusive scan of the 128 word popcounts (thread t < 128)
+    constexpr int NWD = kBucketCols / 32;
+    if (threadIdx.x < 32) {
+      int run = 0;
+      int cnt[NWD / 32];
+#pragma unroll
+      for (int j = 0; j < NWD / 32; ++j) {
+        cnt[j] = __popc(bits[threadIdx.x * (NWD / 32) + j]);
+        run += cnt[j];
+      }
+      int inc = run;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, d);
+        if ((int)threadIdx.x >= d) inc += y;
+      }
+      int off = inc - run;
+#pragma unroll
+      for (int j = 0; j < NWD / 32; ++j) {
+        wscan[threadIdx.x * (NWD / 32) + j] = off;
+        off += cnt[j];
+      }
+      if (threadIdx.x == 31) wscan[NWD] = inc;
+    }
+    __syncthreads();
+    // the bucket's entries in column order at the staging offset e0
+    for (int wd = threadIdx.x; wd < NWD; wd += blockDim.x) {
+      unsigned word = bits[wd];
+      int64_t o = e0 + wscan[wd];
+      while (word) {
+        const int bt = __ffs(word) - 1;
+        word &= word - 1;
+        const int c = wd * 32 + bt;
+        scol[o] = (int32_t)(lo + c);
+        sval[o] = S::out(acc[c]);
+        ++o;
+      }
+    }
+    if (threadIdx.x == 0) bnnz[b] = wscan[NWD];
+    (void)n;
+    __syncthreads();
+  }
+}
+
+// B4: bucket b's staged entries [bpre[b], bpre[b] + bnnz[b]) to y at ypre[b].
+template <int SR>
+__global__ void __launch_bounds__(256) k_bucket_copy(const int64_t* bpre, const int64_t* bnnz,
+                                                    const int64_t* ypre, int64_t nb,
+                                                    const int32_t* scol,
+                                                    const typename Sem<SR>::TC* sval,
+                                                    int32_t* y_idx, typename Sem<SR>::TC* y_val,
+                                                    int64_t cap) {
+  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const int64_t s0 = bpre[b], cnt = bnnz[b], d0 = ypre[b];
+    for (int64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+      if (d0 + t < cap) {
+        y_idx[d0 + t] = scol[s0 + t];
+        y_val[d0 + t] = sval[s0 + t];
+      }
+    }
+  }
+}
+
 inline unsigned grid_of(int64_t n, int threads, int cap) {
   const int64_t g = (n + threads - 1) / threads;
   return (unsigned)(g < 1 ? 1 : (g < cap ? g : cap));
@@ -151,7 +306,54 @@ void spmspv_sr(int step, const DevCSR& A, const int32_t* x_idx, const void* x_va
   }
 }
 
+template <int SR>
+void bucket_sr(int step, const DevCSR& A, const int32_t* x_idx, const void* x_val, int64_t nx,
+               const int64_t* cpre, unsigned long long* cur, int32_t* bcol, void* bval,
+               const int64_t* bpre, int64_t nb, int64_t n, int32_t* scol, void* sval, int64_t* bnnz,
+               const int64_t* ypre, int32_t* y_idx, void* y_val, int64_t cap, cudaStream_t s, int sms) {
+  typedef typename Sem<SR>::A Acc;
+  typedef typename Sem<SR>::TA TA;
+  typedef typename Sem<SR>::TC TC;
+  switch (step) {
+    case 0:
+      k_bucket_fill<SR, 0><<<sms * 8, 256, 0, s>>>(A, x_idx, static_cast<const TA*>(x_val), nx, cpre,
+                                                   cur, nullptr, nullptr);
+      break;
+    case 1:
+      k_bucket_fill<SR, 1><<<sms * 8, 256, 0, s>>>(A, x_idx, static_cast<const TA*>(x_val), nx, cpre,
+                                                   cur, bcol, static_cast<Acc*>(bval));
+      break;
+    case 2:
+      k_bucket_reduce<SR><<<grid_of(nb, 1, sms * 4), 256, 0, s>>>(
+          bpre, nb, n, bcol, static_cast<const Acc*>(bval), scol, static_cast<TC*>(sval), bnnz);
+      break;
+    case 3:
+      k_bucket_copy<SR><<<grid_of(nb, 1, sms * 8), 256, 0, s>>>(
+          bpre, bnnz, ypre, nb, scol, static_cast<const TC*>(sval), y_idx, static_cast<TC*>(y_val), cap);
+      break;
+  }
+}
+
 }  // namespace
+
+int64_t spmspv_buckets(int64_t n) { return (n + kBucketCols - 1) / kBucketCols; }
+
+void launch_spmspv_bucket_step(int sr, int step, const DevCSR& A, const int32_t* x_idx,
+                               const void* x_val, int64_t nx, const int64_t* cpre,
+                               unsigned long long* cur, int32_t* bcol, void* bval, const int64_t* bpre,
+                               int64_t nb, int64_t n, int32_t* scol, void* sval, int64_t* bnnz,
+                               const int64_t* ypre, int32_t* y_idx, void* y_val, int64_t cap,
+                               cudaStream_t s, int sms) {
+  switch (sr) {
+#define CB_CASE(SRV)                                                                             \
+  case SRV:                                                                                      \
+    bucket_sr<SRV>(step, A, x_idx, x_val, nx, cpre, cur, bcol, bval, bpre, nb, n, scol, sval, bnnz, \
+                   ypre, y_idx, y_val, cap, s, sms);                                             \
+    break;
+    CB_FOR_EACH_SEMIRING(CB_CASE)
+#undef CB_CASE
+  }
+}
 
 size_t spa_value_size(int sr) {
   switch (sr) {

@@ -179,10 +179,12 @@ def test_spmspv(cb):
     for nx in (1, 50, 2000):
         x_idx = rng.choice(A.nrows, nx, replace=False).astype(np.int32)
         x_val = gen.hetero_values(SR, "A", nx, 113 + nx, levels=4)
-        y_idx, y_val = cb.spmspv(SR, dA, torch.from_numpy(x_idx).cuda(), torch.from_numpy(x_val).cuda())
         w_idx, w_val, _ = spmspv_oracle(SR, A, x_idx, x_val)
-        assert np.array_equal(y_idx.cpu().numpy(), w_idx)
-        assert np.array_equal(y_val.cpu().numpy().view(np.uint64), w_val.view(np.uint64))
+        for bucket in (False, True):
+            y_idx, y_val = cb.spmspv(SR, dA, torch.from_numpy(x_idx).cuda(), torch.from_numpy(x_val).cuda(),
+                                     bucket=bucket)
+            assert np.array_equal(y_idx.cpu().numpy(), w_idx)
+            assert np.array_equal(y_val.cpu().numpy().view(np.uint64), w_val.view(np.uint64))
 
 
 def test_wlabel_split(cb):
