@@ -470,6 +470,7 @@ struct BalancedSmem {
 //     bookkeeping (the A entry is uniform over the warp).
 // All threads of the CTA must call it.
 constexpr int kLongRange = 128;
+constexpr int kLongUnroll = 2;   // warp steps per iteration of the long round, in units of U
 
 template <int U, class LD, class F>
 __device__ __forceinline__ void for_row_products_balanced_u(const DevCSR& A, const DevCSR& B,
@@ -527,29 +528,30 @@ __device__ __forceinline__ void for_row_products_balanced_u(const DevCSR& A, con
           else r = mid - 1;
         }
         int j = l;
+        constexpr int UL = U * kLongUnroll;
         for (long long t = t_beg; t < t_end; ++j) {  // uniform over the warp
           const long long r_end = j + 1 < ne ? sm.off[j + 1] : total;
           const long long e = r_end < t_end ? r_end : t_end;
           const int64_t qb = sm.b0[j] - sm.off[j];
           const int64_t pc = c0 + sm.pa[j];
-          for (long long tt = t; tt < e; tt += 32 * U) {
-            int64_t qu[U];
-            bool vu[U];
+          for (long long tt = t; tt < e; tt += 32 * UL) {
+            int64_t qu[UL];
+            bool vu[UL];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
+            for (int u = 0; u < UL; ++u) {
               const long long x = tt + 32 * u + lane;
               vu[u] = x < e;
               qu[u] = qb + x;
             }
-            int cu[U];
-            V vv[U];
+            int cu[UL];
+            V vv[UL];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
+            for (int u = 0; u < UL; ++u) {
               cu[u] = vu[u] ? __ldg(B.col + qu[u]) : 0;
               vv[u] = vu[u] ? ld(qu[u]) : V();
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u)
+            for (int u = 0; u < UL; ++u)
               if (vu[u] && (!filter || (unsigned)((int64_t)cu[u] - lo) < width)) f(pc, qu[u], cu[u], vv[u]);
           }
           t = e;
