@@ -347,7 +347,7 @@ int cb_autotune(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B, c
  * indices are always checked on the device (CB_ERR_INDEX).
  * With opt->flags & CB_FLAG_SPMSPV_BUCKET the column-partitioned form of
  * Sec. 4.3 runs instead (buckets that block y, also called propagation
- * blocking): every product is appended to the bucket of its column (4096
+ * blocking): every product is appended to the bucket of its column (1024
  * columns per bucket), each bucket is (+)-combined by one CTA in a shared-
  * memory accumulator and written in column order; it keeps no state in the
  * context and needs O(products) scratch, with two synchronisations (the

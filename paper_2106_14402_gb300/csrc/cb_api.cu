@@ -1471,15 +1471,26 @@ void spmspv_bucket(cb_ctx* ctx, int sr, const cb_csr* A, const cb_spvec* x, cb_s
   int64_t* partial = cv.take<int64_t>(cb::scan_partials(big));
   const DevCSR dA = dev(A);
   unsigned long long* ucur = reinterpret_cast<unsigned long long*>(cur);
+  // per-CTA bucket counters when the buckets fit shared memory
+  const int ncta = cb::spmspv_priv_ctas(nb, ctx->sms);
+  DevBuf ccnt(ctx);
+  if (ncta) ccnt.alloc(sizeof(int64_t) * (size_t)ncta * (size_t)nb);
   CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
   CB_CUDA(cudaMemsetAsync(cur, 0, sizeof(int64_t) * (size_t)(nb + 1), ctx->stream));
   mark(ctx, opt, 0);
   cb::launch_spmspv_step(sr, 1, dA, x->idx, x->val, nx, chunks, nullptr, nullptr, nullptr, n, nullptr,
                          nullptr, nullptr, nullptr, 0, counters + cb::kError, ctx->stream, ctx->sms);
   cb::launch_exclusive_scan(chunks, nx, cpre, partial, ctx->stream);
-  cb::launch_spmspv_bucket_step(sr, 0, dA, x->idx, x->val, nx, cpre, ucur, nullptr, nullptr, nullptr,
-                                nb, n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
-                                ctx->stream, ctx->sms);
+  if (ncta) {
+    cb::launch_spmspv_bucket_priv(sr, 0, dA, x->idx, x->val, nx, cpre, nb, ccnt.as<int64_t>(), nullptr,
+                                  nullptr, nullptr, nullptr, ctx->stream, ctx->sms);
+    cb::launch_spmspv_bucket_priv(sr, 2, dA, nullptr, nullptr, 0, nullptr, nb, ccnt.as<int64_t>(), nullptr,
+                                  cur, nullptr, nullptr, ctx->stream, ctx->sms);
+  } else {
+    cb::launch_spmspv_bucket_step(sr, 0, dA, x->idx, x->val, nx, cpre, ucur, nullptr, nullptr, nullptr,
+                                  nb, n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
+                                  ctx->stream, ctx->sms);
+  }
   cb::launch_exclusive_scan(cur, nb, bpre, partial, ctx->stream);
   CB_LAUNCHED();
   read_counters(ctx, counters, bpre + nb, 1);
@@ -1497,10 +1508,16 @@ void spmspv_bucket(cb_ctx* ctx, int sr, const cb_csr* A, const cb_spvec* x, cb_s
   bval.alloc(avs * (size_t)products);
   scol.alloc(4 * (size_t)products);
   sval.alloc(vsz * (size_t)products);
-  CB_CUDA(cudaMemcpyAsync(cur, bpre, sizeof(int64_t) * (size_t)nb, cudaMemcpyDeviceToDevice, ctx->stream));
-  cb::launch_spmspv_bucket_step(sr, 1, dA, x->idx, x->val, nx, cpre, ucur, bcol.as<int32_t>(), bval.p,
-                                nullptr, nb, n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
-                                ctx->stream, ctx->sms);
+  if (ncta) {
+    cb::launch_spmspv_bucket_priv(sr, 1, dA, x->idx, x->val, nx, cpre, nb, ccnt.as<int64_t>(), bpre,
+                                  nullptr, bcol.as<int32_t>(), bval.p, ctx->stream, ctx->sms);
+  } else {
+    CB_CUDA(cudaMemcpyAsync(cur, bpre, sizeof(int64_t) * (size_t)nb, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+    cb::launch_spmspv_bucket_step(sr, 1, dA, x->idx, x->val, nx, cpre, ucur, bcol.as<int32_t>(), bval.p,
+                                  nullptr, nb, n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
+                                  ctx->stream, ctx->sms);
+  }
   cb::launch_spmspv_bucket_step(sr, 2, dA, nullptr, nullptr, 0, nullptr, nullptr, bcol.as<int32_t>(),
                                 bval.p, bpre, nb, n, scol.as<int32_t>(), sval.p, bnnz, nullptr, nullptr,
                                 nullptr, 0, ctx->stream, ctx->sms);

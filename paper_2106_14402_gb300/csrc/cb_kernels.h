@@ -173,6 +173,14 @@ size_t spa_value_size(int sr);
 // bucket into cur (zeroed), 1 products appended at cur (preset to bpre),
 // 2 per-bucket reduction into the staging area + bnnz, 3 copy to y at ypre.
 int64_t spmspv_buckets(int64_t n);
+// Per-CTA counted form of steps 0 and 1 (CTAs = spmspv_priv_ctas(nb, sms), 0
+// when the buckets do not fit shared memory): pass 0 counts into ccnt[b][cta],
+// pass 2 scans ccnt over CTAs (bucket totals into tot), pass 1 scatters.
+int spmspv_priv_ctas(int64_t nb, int sms);
+void launch_spmspv_bucket_priv(int sr, int pass, const DevCSR& A, const int32_t* x_idx,
+                               const void* x_val, int64_t nx, const int64_t* cpre, int64_t nb,
+                               int64_t* ccnt, const int64_t* bpre, int64_t* tot, int32_t* bcol,
+                               void* bval, cudaStream_t s, int sms);
 void launch_spmspv_bucket_step(int sr, int step, const DevCSR& A, const int32_t* x_idx,
                                const void* x_val, int64_t nx, const int64_t* cpre,
                                unsigned long long* cur, int32_t* bcol, void* bval, const int64_t* bpre,

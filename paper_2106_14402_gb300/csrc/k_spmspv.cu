@@ -17,9 +17,11 @@
 //       initialisation.
 // The bucket form (Sec. 4.3: the column-partitioned SpMSpV merges through
 // buckets that block y, i.e. propagation blocking) keeps no O(n) state:
-//   B1  products per bucket of kBucketCols output columns (warp-aggregated
-//       counts), scanned into bucket offsets;
-//   B2  every product (c, x_i (x) A(i, c)) is appended to its bucket;
+//   B1  products per bucket of kBucketCols output columns (lanes of one
+//       bucket counted together; per-CTA counters in shared memory when the
+//       buckets fit, then a scan over CTAs), scanned into bucket offsets;
+//   B2  every product (c, x_i (x) A(i, c)) is appended to its bucket (from
+//       its CTA's own block of the bucket);
 //   B3  one CTA per bucket (+)-combines the bucket's products in a shared-
 //       memory accumulator with a touched bitmap and writes the bucket's
 //       entries, in column order, to a staging area at the bucket's offset,
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(256) k_spmspv_compact(unsigned* touched, int64
   }
 }
 
-constexpr int kBucketLog = 12;
+constexpr int kBucketLog = 10;
 constexpr int kBucketCols = 1 << kBucketLog;  // output columns per bucket
 
 // The x entry owning chunk w: the last p with cpre[p] <= w.
@@ -183,7 +185,90 @@ __global__ void __launch_bounds__(256) k_bucket_fill(DevCSR A, const int32_t* x_
   }
 }
 
-// B3: one CTA (256 threads) per bucket.
+// B1/B2 with per-CTA bucket counters in shared memory (nb <= kPrivBuckets):
+// PASS 0 counts each CTA's products per bucket into ccnt[b][cta]; after a
+// scan over CTAs (k_bucket_cta_scan) PASS 1 places them from the CTA's own
+// block of each bucket, so no global atomic is taken per product.  Both
+// passes give every CTA the same chunks (same grid).
+constexpr int kPrivBuckets = 2048;
+
+template <int SR, int PASS>
+__global__ void __launch_bounds__(256) k_bucket_fill_priv(DevCSR A, const int32_t* x_idx,
+                                                         const typename Sem<SR>::TA* x_val, int64_t nx,
+                                                         const int64_t* cpre, int64_t nb,
+                                                         int64_t* ccnt, const int64_t* bpre,
+                                                         int32_t* bcol, typename Sem<SR>::A* bval) {
+  typedef Sem<SR> S;
+  typedef typename S::TA TA;
+  typedef typename S::TB TB;
+  __shared__ long long s_base[kPrivBuckets];
+  __shared__ unsigned s_rel[kPrivBuckets];
+  for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) {
+    s_rel[b] = 0u;
+    s_base[b] = PASS == 1 ? bpre[b] + ccnt[b * (int64_t)gridDim.x + blockIdx.x] : 0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t total = cpre[nx];
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const TB* Aval = reinterpret_cast<const TB*>(A.val);
+  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nwarps) {
+    const int64_t p = chunk_owner(cpre, nx, w);
+    const int i = __ldg(x_idx + p);
+    const int64_t r0 = __ldg(A.rp + i), r1 = __ldg(A.rp + i + 1);
+    const int64_t q0 = r0 + (w - __ldg(cpre + p)) * kChunk;
+    const int64_t q1 = min(q0 + kChunk, r1);
+    const TA xv = (PASS == 1 && S::kUsesA) ? ldg_val(x_val + p) : TA();
+    for (int64_t base = q0; base < q1; base += 32) {  // uniform over the warp
+      const int64_t q = base + lane;
+      const bool v = q < q1;
+      const int c = v ? __ldg(A.col + q) : 0;
+      const int b = v ? (c >> kBucketLog) : -1;
+      const unsigned same = __match_any_sync(0xffffffffu, b);
+      const int leader = __ffs(same) - 1;
+      unsigned rel = 0;
+      if (v && lane == leader) rel = atomicAdd(&s_rel[b], (unsigned)__popc(same));
+      rel = __shfl_sync(0xffffffffu, rel, leader);
+      if (PASS == 1 && v) {
+        const long long at = s_base[b] + rel + __popc(same & ((1u << lane) - 1u));
+        bcol[at] = c;
+        bval[at] = S::mul(xv, ldg_val(Aval + q));
+      }
+    }
+  }
+  if (PASS == 0) {
+    __syncthreads();
+    for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) ccnt[b * (int64_t)gridDim.x + blockIdx.x] = s_rel[b];
+  }
+}
+
+// ccnt[b][c] becomes the exclusive prefix over CTAs c of bucket b's counts;
+// tot[b] the bucket's total.  One warp per bucket.
+__global__ void __launch_bounds__(256) k_bucket_cta_scan(int64_t* ccnt, int64_t nb, int ncta,
+                                                        int64_t* tot) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nb; b += nwarps) {
+    int64_t* row = ccnt + b * ncta;
+    long long run = 0;
+    for (int c0 = 0; c0 < ncta; c0 += 32) {  // uniform over the warp
+      const int c = c0 + lane;
+      const long long v = c < ncta ? row[c] : 0;
+      long long inc = v;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+      }
+      if (c < ncta) row[c] = run + inc - v;
+      run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) tot[b] = run;
+  }
+}
+
+// B3: one CTA (256 threads) per bucket (kBucketCols = 1024 columns: 32
+// words of bitmap, one warp scans them).
 template <int SR>
 __global__ void __launch_bounds__(256) k_bucket_reduce(const int64_t* bpre, int64_t nb, int64_t n,
                                                       const int32_t* bcol,
@@ -201,11 +286,24 @@ __global__ void __launch_bounds__(256) k_bucket_reduce(const int64_t* bpre, int6
     __syncthreads();
     const int64_t e0 = bpre[b], e1 = bpre[b + 1];
     const int64_t lo = b << kBucketLog;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int o = (int)(bcol[e] - lo);
-      S::atomic(&acc[o], bval[e]);
-      const unsigned bit = 1u << (o & 31);
-      if (!(bits[o >> 5] & bit)) atomicOr(&bits[o >> 5], bit);
+    constexpr int UR = 4;  // entries per thread per iteration, loaded before any is combined
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += (int64_t)UR * blockDim.x) {
+      int oc[UR];
+      Acc ov[UR];
+#pragma unroll
+      for (int u = 0; u < UR; ++u) {
+        const int64_t eu = e + (int64_t)u * blockDim.x;
+        oc[u] = eu < e1 ? (int)(__ldg(bcol + eu) - lo) : -1;
+        ov[u] = eu < e1 ? bval[eu] : S::ident();
+      }
+#pragma unroll
+      for (int u = 0; u < UR; ++u) {
+        if (oc[u] < 0) continue;
+        const int o = oc[u];
+        S::atomic(&acc[o], ov[u]);
+        const unsigned bit = 1u << (o & 31);
+        if (!(bits[o >> 5] & bit)) atomicOr(&bits[o >> 5], bit);
+      }
     }
     __syncthreads();
     // word offsets: exclusive scan of the 128 word popcounts (thread t < 128)
@@ -337,6 +435,34 @@ void bucket_sr(int step, const DevCSR& A, const int32_t* x_idx, const void* x_va
 }  // namespace
 
 int64_t spmspv_buckets(int64_t n) { return (n + kBucketCols - 1) / kBucketCols; }
+
+int spmspv_priv_ctas(int64_t nb, int sms) { return nb <= kPrivBuckets ? sms * 4 : 0; }
+
+void launch_spmspv_bucket_priv(int sr, int pass, const DevCSR& A, const int32_t* x_idx,
+                               const void* x_val, int64_t nx, const int64_t* cpre, int64_t nb,
+                               int64_t* ccnt, const int64_t* bpre, int64_t* tot, int32_t* bcol,
+                               void* bval, cudaStream_t s, int sms) {
+  const int ncta = spmspv_priv_ctas(nb, sms);
+  if (pass == 2) {
+    k_bucket_cta_scan<<<grid_of(nb, 8, sms * 4), 256, 0, s>>>(ccnt, nb, ncta, tot);
+    return;
+  }
+  switch (sr) {
+#define CB_CASE(SRV)                                                                               \
+  case SRV:                                                                                        \
+    if (pass == 0)                                                                                 \
+      k_bucket_fill_priv<SRV, 0><<<ncta, 256, 0, s>>>(                                             \
+          A, x_idx, static_cast<const Sem<SRV>::TA*>(x_val), nx, cpre, nb, ccnt, bpre, nullptr,  \
+          nullptr);                                                                                \
+    else                                                                                           \
+      k_bucket_fill_priv<SRV, 1><<<ncta, 256, 0, s>>>(                                             \
+          A, x_idx, static_cast<const Sem<SRV>::TA*>(x_val), nx, cpre, nb, ccnt, bpre, bcol,     \
+          static_cast<Sem<SRV>::A*>(bval));                                                        \
+    break;
+    CB_FOR_EACH_SEMIRING(CB_CASE)
+#undef CB_CASE
+  }
+}
 
 void launch_spmspv_bucket_step(int sr, int step, const DevCSR& A, const int32_t* x_idx,
                                const void* x_val, int64_t nx, const int64_t* cpre,

@@ -69,7 +69,7 @@ def test_long_rows_and_adversarial_matrix(cb, sr, bucket):
 
 @pytest.mark.parametrize("sr", ("plus_times_i64", "sel2nd_min_i32"))
 def test_bucket_form_wide_output(cb, sr):
-    """Columns over 24 buckets of 4096 and a ragged last one (n = 98,765):
+    """Columns over 96 buckets of 1024 and a ragged last one (n = 98,765):
     every bucket, its first and last column, and empty buckets in between."""
     n = 98765
     A = gen.random_csr(40, n, 0.01, seed=165, semiring=sr, empty_rows=0.1)
@@ -105,6 +105,24 @@ def test_repeated_calls_and_semiring_switch(cb):
     val = gen.random_values("plus_times_i64", 4, 191)
     check("plus_times_i64", run(cb, "plus_times_i64", B, idx, val, ctx=ctx),
           oracle.spmspv("plus_times_i64", B, idx, val))
+
+
+def test_bucket_form_many_buckets(cb):
+    """More buckets than shared memory holds per-CTA counters for (n over
+    2048 buckets of 1024 columns): the globally counted form."""
+    sr = "min_plus_u32"
+    n = 2048 * 4096 + 5003
+    rng = np.random.default_rng(175)
+    rows = []
+    for i in range(30):
+        rows.append(np.sort(rng.choice(n, 200, replace=False)))
+    rp = np.zeros(31, np.int64)
+    rp[1:] = np.cumsum([r.size for r in rows])
+    A = gen.CSR(30, n, rp, np.concatenate(rows).astype(np.int32),
+                gen.random_values(sr, int(rp[-1]), 176))
+    idx = rng.integers(0, 30, 50)
+    val = gen.random_values(sr, 50, 177)
+    check(sr, run(cb, sr, A, idx, val, bucket=True), oracle.spmspv(sr, A, idx, val))
 
 
 @pytest.mark.parametrize("bucket", [False, True])
