@@ -229,3 +229,20 @@ def test_merge_of_partial_products(cb):
         got = C.to_host()
         check_structure(got[0], got[1], 200)
         compare_rows(SR, got, oracle.merge(SR, hparts))
+
+
+@pytest.mark.parametrize("fused", [True, False])
+def test_golden_worked_example(cb, fused):
+    """The hand-derived example of tests/golden/maxw_label_example.json."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "maxw_label_example.json")))
+    A = gen.CSR(*g["A"]["shape"], np.array(g["A"]["row_ptr"], np.int64), np.array(g["A"]["col"], np.int32),
+                np.array(g["A"]["val"], np.float32))
+    B = gen.CSR(*g["B"]["shape"], np.array(g["B"]["row_ptr"], np.int64), np.array(g["B"]["col"], np.int32),
+                np.array(g["B"]["val"], np.int32))
+    rp, col, val = run(cb, A, B, fused=fused).to_host()
+    assert np.array_equal(rp, g["C"]["row_ptr"]) and np.array_equal(col, g["C"]["col"])
+    rec = val.view(oracle.WLABEL)
+    assert np.array_equal(rec["w"].view(np.uint32), np.array(g["C"]["w"], np.float32).view(np.uint32))
+    assert np.array_equal(rec["label"], g["C"]["label"])

@@ -256,3 +256,21 @@ def test_merge_of_partial_products_is_the_product():
     full = oracle.spgemm(SR, A, B)
     assert np.array_equal(merged[0], full[0]) and np.array_equal(merged[1], full[1])
     assert np.array_equal(merged[2].view(np.uint64), full[2].view(np.uint64))
+
+
+def test_golden_worked_example():
+    """The hand-derived example in tests/golden/maxw_label_example.json
+    (derivation in its "about" field), bit for bit, -0.0 included."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "maxw_label_example.json")))
+    A = gen.CSR(*g["A"]["shape"], np.array(g["A"]["row_ptr"], np.int64), np.array(g["A"]["col"], np.int32),
+                np.array(g["A"]["val"], np.float32))
+    B = gen.CSR(*g["B"]["shape"], np.array(g["B"]["row_ptr"], np.int64), np.array(g["B"]["col"], np.int32),
+                np.array(g["B"]["val"], np.int32))
+    rp, col, val, _ = oracle.spgemm(SR, A, B)
+    assert np.array_equal(rp, g["C"]["row_ptr"]) and np.array_equal(col, g["C"]["col"])
+    want_w = np.array(g["C"]["w"], np.float32)
+    assert np.array_equal(val["w"].view(np.uint32), want_w.view(np.uint32))
+    assert np.array_equal(val["label"], g["C"]["label"])
+    assert same(as_dict((rp, col, val, None)), brute(A, B))
