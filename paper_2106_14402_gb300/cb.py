@@ -205,10 +205,36 @@ class DeviceCSR:
             val = val.view(np.uint32)
         return self.row_ptr.cpu().numpy(), self.col.cpu().numpy(), val
 
+    @staticmethod
+    def from_scipy(M, semiring: str, device="cuda", operand: str = "A") -> "DeviceCSR":
+        """Copy a scipy.sparse matrix (any format; converted to CSR, its
+        entries kept as stored: duplicates and unsorted rows are allowed by
+        the ABI) with the value dtype of `operand` under the semiring."""
+        csr = M.tocsr()
+        dt = OPERAND_DTYPES[semiring]["ABC".index(operand)]
+        host = type("HostCSR", (), {})()
+        host.nrows, host.ncols = csr.shape
+        host.row_ptr = csr.indptr.astype(np.int64)
+        host.col = csr.indices.astype(np.int32)
+        host.val = np.ascontiguousarray(csr.data).astype(_np_dtype(dt))
+        return DeviceCSR.from_host(host, semiring, device, operand)
+
+    def to_scipy(self):
+        """This matrix as a scipy.sparse.csr_matrix on the host (one-type
+        semirings; cb_wlabel records have no scipy dtype)."""
+        import scipy.sparse as sp
+        rp, col, val = self.to_host()
+        return sp.csr_matrix((val, col, rp), shape=(self.nrows, self.ncols))
+
     def as_struct(self) -> cb_csr:
         return cb_csr(self.nrows, self.ncols, self.nnz, self.row_ptr.data_ptr(),
                       self.col.data_ptr() if self.nnz else None,
                       self.val.data_ptr() if self.nnz else None)
+
+
+def _np_dtype(dt):
+    return {torch.int64: np.int64, torch.float64: np.float64, torch.uint32: np.uint32,
+            torch.uint8: np.uint8, torch.int32: np.int32, torch.float32: np.float32}[dt]
 
 
 def _np_view(dt):
