@@ -116,6 +116,9 @@ typedef struct {
   const cb_mlp *mlp;    /* required when sizing == CB_SIZING_LEARNED                   */
   float margin;         /* learned sizing: table capacity = pred * (1 + margin)       */
   int32_t flags;        /* CB_FLAG_* bits, default 0                                  */
+  uint64_t *digests;    /* cb_spgemm_batched only, optional (default NULL): device
+                           uint64[2 * count] receiving a digest of every C_i, written
+                           before its wave's on_batch in every mode (see there)        */
 } cb_opts;
 
 /* cb_opts.flags bits. */
@@ -200,7 +203,25 @@ int cb_spgemm_ex(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B,
  * call; a nonzero return stops the batch (CB_OK).  opt->on_batch is
  * required; inputs are device CSR as for cb_spgemm_ex; sizing may be exact
  * or learned.  The stacked rows of each group must fit int32 indices
- * (CB_ERR_INDEX otherwise). */
+ * (CB_ERR_INDEX otherwise).
+ * Digests (opt->digests != NULL): outputs of batched calls are transient (in
+ * graph mode on_batch cannot even read them), so the call can leave a
+ * check of each product behind.  With sm(x) the splitmix64 output function
+ * (x += 0x9E3779B97F4A7C15; x = (x ^ x>>30) * 0xBF58476D1CE4E5B9;
+ * x = (x ^ x>>27) * 0x94D049BB133111EB; x ^ x>>31) and all arithmetic mod
+ * 2^64, product i's words are
+ *   digests[2i]   = sum over its rows r of sm(sm(2r) + len_r)
+ *                 + sum over its entries (row r, position j in the row,
+ *                   column c, value v) of sm(sm(sm(sm(2r+1) + j) + c) + bits(v)),
+ *                   bits(v) = v's bytes zero-extended to 64 bits, and 0 for
+ *                   CB_PLUS_TIMES_F64, whose first word covers the pattern only;
+ *   digests[2i+1] = for CB_PLUS_TIMES_F64, the bits of the double
+ *                   V = sum over entries of v * w(r, c), w(r, c) = 1 + 2^-53 *
+ *                   (sm(sm(2r+1) ^ c) >> 11), summed with compensated
+ *                   (Neumaier) summation in a fixed order, so that
+ *                   |V - exact| <= 16 u sum |v w| (u = 2^-53); else 0.
+ *   r counts the product's own rows from 0.  The digests cost one extra read
+ *   of C and one 16-byte scratch word per row of the largest wave. */
 int cb_spgemm_batched(cb_ctx *ctx, int count, const cb_semiring *sr, const cb_csr *A,
                       const cb_csr *B, const cb_opts *opt);
 
@@ -292,9 +313,16 @@ int cb_mlp_train(cb_ctx *ctx, cb_mlp *m, const float *feat, const int64_t *nnz, 
  *   the process exits.
  *   - n may be at most 268,435,456; larger n returns CB_ERR_SCRATCH and
  *     launches nothing.  Bad pointers or n < 0 return CB_ERR_ARG.
- *   - The first call on each device looks up the array's device address
- *     (with that device current) and caches it; make that first call before
- *     any stream capture.
+ *   - The array's device address belongs to a CUDA context.  The first call
+ *     in each context (the device's primary context, a context created after
+ *     cudaDeviceReset, or a driver-API context the caller made current) looks
+ *     the address up with that context current and caches it under the
+ *     context's unique id; make that first call before any stream capture.
+ *     A call on a thread with no current context makes the current device's
+ *     primary context current.
+ *   - Only errors of this call's own launches are reported: an error left
+ *     pending by an earlier CUDA call on the thread is neither reported nor
+ *     cleared.
  *   - Every call on a device shares the one array, and the array keeps the
  *     last call's contents (nothing needs clearing: each call writes every
  *     entry it reads).  Calls whose work overlaps on the GPU (unordered
@@ -430,6 +458,26 @@ typedef struct {
   float ms_stats, ms_symbolic, ms_scan, ms_numeric;
 } cb_stats;
 int cb_last_stats(const cb_ctx *ctx, cb_stats *out);
+
+/* ---- fault injection -----------------------------------------------------
+ * Test hooks for the failure paths (allocation failure, a bounded device wait
+ * that expires).  They make the failure on the host side or give a wait a
+ * producer that never publishes; nothing here faults, traps or hangs a GPU.
+ *   CB_FAULT_ALLOC: arg = k >= 1 makes the k-th device allocation that the
+ *     context makes from now on (its workspaces, C, staging buffers) fail as
+ *     if the device were out of memory, once; the call returns CB_ERR_OOM
+ *     with C zeroed and owning nothing, and the context stays usable.
+ *     arg = 0 turns it off.  arg2 is ignored.
+ *   CB_FAULT_SILENT_TILE: in the one-launch kernel (cb_spgemm_fused and the
+ *     automatic branch of cb_spgemm_ex) tile `arg` (>= 0; 32 rows per tile
+ *     at 8 lanes, 16 at 16, 8 at 32) never publishes its row total, and
+ *     every look-back wait gives up after arg2 polls (1 <= arg2 <= 2^20).
+ *     Waiting tiles record CB_FUSED_STALLED and publish anyway, so the launch
+ *     ends; cb_spgemm_ex returns CB_ERR_TIMEOUT with C zeroed.  arg < 0
+ *     restores the defaults (no silent tile, 2^20 polls).
+ * Returns CB_ERR_ARG for an unknown kind or an argument out of range. */
+enum { CB_FAULT_ALLOC = 1, CB_FAULT_SILENT_TILE = 2 };
+int cb_ctx_set_fault(cb_ctx *ctx, int kind, int64_t arg, int64_t arg2);
 
 #ifdef __cplusplus
 }

@@ -61,7 +61,8 @@ class cb_opts(ctypes.Structure):
     _fields_ = [("sizing", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("out_capacity", c_int64), ("budget_bytes", c_int64),
                 ("on_batch", BATCH_FN), ("user", c_void_p), ("mlp", c_void_p),
-                ("margin", ctypes.c_float), ("flags", ctypes.c_int32)]
+                ("margin", ctypes.c_float), ("flags", ctypes.c_int32),
+                ("digests", c_void_p)]
 
 
 class cb_tune(ctypes.Structure):
@@ -110,6 +111,7 @@ _SIGS = {
     "cb_exclusive_scan": ([c_void_p, c_void_p, c_int64, c_void_p], ctypes.c_int),
     "cb_exclusive_scan_noalloc": ([c_void_p, c_int64, c_void_p, c_void_p], ctypes.c_int),
     "cb_last_stats": ([c_void_p, ctypes.POINTER(cb_stats)], ctypes.c_int),
+    "cb_ctx_set_fault": ([c_void_p, ctypes.c_int, c_int64, c_int64], ctypes.c_int),
     "cb_spgemm_batched": ([c_void_p, ctypes.c_int, c_void_p, c_void_p, c_void_p,
                            ctypes.POINTER(cb_opts)], ctypes.c_int),
     "cb_ctx_set_tune": ([c_void_p, ctypes.POINTER(cb_tune)], ctypes.c_int),
@@ -316,6 +318,12 @@ class Context:
         self.check(self.lib.cb_ctx_get_tune(self.handle, ctypes.byref(t)))
         return {k: getattr(t, k) for k, _ in cb_tune._fields_}
 
+    def set_fault(self, kind: int, arg: int, arg2: int = 0) -> None:
+        """Fault injection (cb_ctx_set_fault): FAULT_ALLOC fails the arg-th device
+        allocation; FAULT_SILENT_TILE keeps tile arg of the one-launch kernel
+        from publishing, waits giving up after arg2 polls (arg < 0: defaults)."""
+        self.check(self.lib.cb_ctx_set_fault(self.handle, int(kind), int(arg), int(arg2)))
+
     def stats(self) -> dict:
         s = cb_stats()
         self.check(self.lib.cb_last_stats(self.handle, ctypes.byref(s)))
@@ -364,6 +372,10 @@ FLAG_NO_FUSED = 8
 FLAG_GRAPH = 16
 FLAG_SYNC_FREE = 32
 FLAG_SPMSPV_BUCKET = 64
+
+# fault injection kinds (cb_ctx_set_fault)
+FAULT_ALLOC = 1
+FAULT_SILENT_TILE = 2
 
 # device status bits of cb_spgemm_fused
 FUSED_CAPACITY = 1
@@ -670,7 +682,8 @@ def row_features(A: DeviceCSR, B: DeviceCSR, ctx: Context | None = None) -> torc
 
 def spgemm_batched(semirings, As, Bs, on_wave, *, budget_bytes: int = 0, validate: bool = True,
                    sizing: str = "exact", mlp=None, margin: float = 0.25,
-                   ctx: Context | None = None, mode: str = "host") -> dict:
+                   ctx: Context | None = None, mode: str = "host",
+                   digests: torch.Tensor | None = None) -> dict:
     """Batched products C_i = A_i (+).(x) B_i (cb_spgemm_batched).
 
     on_wave(wave, first, end, Cw) receives a DeviceCSR that stacks
@@ -682,6 +695,9 @@ def spgemm_batched(semirings, As, Bs, on_wave, *, budget_bytes: int = 0, validat
     node (no tensors: CUDA may not be used there; the return value is
     ignored).  Both cut waves by the flop bound; a group with a product whose
     bound alone exceeds the budget runs as mode "host".
+    `digests` (optional, an int64 CUDA tensor of 2 * len(As) entries) receives
+    each product's two digest words (cb.h, cb_spgemm_batched), as raw 64-bit
+    patterns.
     """
     flags = {"host": 0, "sync_free": FLAG_SYNC_FREE, "graph": FLAG_GRAPH}[mode]
     ctx = ctx or context()
@@ -710,6 +726,11 @@ def spgemm_batched(semirings, As, Bs, on_wave, *, budget_bytes: int = 0, validat
     fn = BATCH_FN(_cb)
     opts = make_opts(sizing=sizing, validate=validate, budget_bytes=budget_bytes, on_batch=fn,
                      mlp=mlp, margin=margin, flags=flags)
+    if digests is not None:
+        if digests.dtype != torch.int64 or not digests.is_cuda or digests.numel() < 2 * n \
+                or not digests.is_contiguous():
+            raise ValueError("digests must be a contiguous int64 CUDA tensor of 2 * count entries")
+        opts.digests = digests.data_ptr()
     ctx.check(ctx.lib.cb_spgemm_batched(ctx.handle, n, ctypes.cast(codes, c_void_p),
                                         ctypes.cast(sa, c_void_p), ctypes.cast(sb, c_void_p),
                                         ctypes.byref(opts)))

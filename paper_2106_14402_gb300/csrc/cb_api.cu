@@ -37,6 +37,11 @@ struct cb_ctx {
   int spa_sr = 0;
   std::string err;
   cb_stats stats{};
+  // fault injection (cb_ctx_set_fault)
+  int64_t fault_alloc = 0;    // the fault_alloc-th device allocation fails (0: off)
+  int64_t allocs_seen = 0;    // device allocations since the fault was set
+  unsigned fused_spin = cb::kFusedSpinDefault;  // polls per look-back wait
+  int64_t fused_silent = -1;  // tile of the one-launch kernel that never publishes
 };
 
 namespace {
@@ -64,6 +69,33 @@ struct Fail {
       throw Fail{CB_ERR_CUDA};                                                        \
     }                                                                                 \
   } while (0)
+
+// Every device allocation of the context goes through these, so that
+// CB_FAULT_ALLOC can fail the k-th one as an out-of-memory would.
+bool injected_alloc_failure(cb_ctx* ctx) {
+  if (ctx->fault_alloc <= 0) return false;
+  if (++ctx->allocs_seen < ctx->fault_alloc) return false;
+  ctx->fault_alloc = 0;
+  return true;
+}
+
+template <class T>
+cudaError_t dev_alloc(cb_ctx* ctx, T** p, size_t bytes) {
+  if (injected_alloc_failure(ctx)) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, ctx->stream);
+}
+
+template <class T>
+cudaError_t dev_alloc_sync(cb_ctx* ctx, T** p, size_t bytes) {
+  if (injected_alloc_failure(ctx)) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
 
 void fail(cb_ctx* ctx, int code, const std::string& msg) {
   ctx->err = msg;
@@ -118,7 +150,7 @@ void ensure(cb_ctx* ctx, void** buf, size_t* cap, size_t need) {
   if (*buf) CB_CUDA(cudaFreeAsync(*buf, ctx->stream));
   *buf = nullptr;
   *cap = 0;
-  CB_CUDA(cudaMallocAsync(buf, want, ctx->stream));
+  CB_CUDA(dev_alloc(ctx, buf, want));
   *cap = want;
 }
 
@@ -128,7 +160,7 @@ struct DevBuf {
   void* p = nullptr;
   explicit DevBuf(cb_ctx* c) : ctx(c) {}
   void alloc(size_t bytes) {
-    CB_CUDA(cudaMallocAsync(&p, bytes ? bytes : 1, ctx->stream));
+    CB_CUDA(dev_alloc(ctx, &p, bytes ? bytes : 1));
   }
   ~DevBuf() {
     if (p) cudaFreeAsync(p, ctx->stream);
@@ -203,7 +235,7 @@ void collect_times(cb_ctx* ctx, const cb_opts& opt, bool numeric_ran) {
 // epochs keep them valid across calls) and the epoch / finished-CTA words.
 void ensure_fused(cb_ctx* ctx, int64_t tiles) {
   if (!ctx->fsync) {
-    CB_CUDA(cudaMalloc((void**)&ctx->fsync, 64));
+    CB_CUDA(dev_alloc_sync(ctx, &ctx->fsync, 64));
     CB_CUDA(cudaMemsetAsync(ctx->fsync, 0, 64, ctx->stream));
   }
   if (tiles <= ctx->fstat_cap) return;
@@ -214,7 +246,7 @@ void ensure_fused(cb_ctx* ctx, int64_t tiles) {
     ctx->fstat = nullptr;
     ctx->fstat_cap = 0;
   }
-  CB_CUDA(cudaMalloc((void**)&ctx->fstat, sizeof(unsigned long long) * (size_t)want));
+  CB_CUDA(dev_alloc_sync(ctx, &ctx->fstat, sizeof(unsigned long long) * (size_t)want));
   CB_CUDA(cudaMemsetAsync(ctx->fstat, 0, sizeof(unsigned long long) * (size_t)want, ctx->stream));
   ctx->fstat_cap = want;
 }
@@ -235,7 +267,8 @@ void run_fused(cb_ctx* ctx, int sr, int lanes, const DevCSR& dA, const DevCSR& d
   }
   ensure_fused(ctx, cb::fused_tiles(lanes, dA.nrows));
   const cudaError_t e = cb::launch_fused(sr, lanes, dA, dB, rp, col, val, cap, ctx->fstat,
-                                         ctx->fstat_cap, ctx->fsync, status, ctx->stream, ctx->sms);
+                                         ctx->fstat_cap, ctx->fsync, status, ctx->stream, ctx->sms,
+                                         ctx->fused_spin, ctx->fused_silent);
   if (e != cudaSuccess) {
     ctx->err = std::string("fused launch: ") + cudaGetErrorString(e);
     throw Fail{CB_ERR_CUDA};
@@ -277,7 +310,7 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
     C->row_ptr = nullptr;
     C->col = nullptr;
     C->val = nullptr;
-    CB_CUDA(cudaMallocAsync((void**)&C->row_ptr, sizeof(int64_t) * (size_t)(m + 1), ctx->stream));
+    CB_CUDA(dev_alloc(ctx, &C->row_ptr, sizeof(int64_t) * (size_t)(m + 1)));
   }
   if (m == 0) {
     CB_CUDA(cudaMemsetAsync(C->row_ptr, 0, sizeof(int64_t), ctx->stream));
@@ -313,8 +346,8 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
       !dB.filter && dB.col_lo == 0) {
     const int64_t cap = caller_buf ? opt.out_capacity : ctx->stats.flops;
     if (!caller_buf && cap > 0) {
-      CB_CUDA(cudaMallocAsync((void**)&C->col, sizeof(int32_t) * (size_t)cap, ctx->stream));
-      CB_CUDA(cudaMallocAsync(&C->val, vsz * (size_t)cap, ctx->stream));
+      CB_CUDA(dev_alloc(ctx, &C->col, sizeof(int32_t) * (size_t)cap));
+      CB_CUDA(dev_alloc(ctx, &C->val, vsz * (size_t)cap));
     }
     ensure_fused(ctx, 0);
     int* st = reinterpret_cast<int*>(ctx->fsync + 4);
@@ -413,8 +446,8 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
       throw Fail{CB_ERR_CAPACITY};
     }
   } else if (total > 0) {
-    CB_CUDA(cudaMallocAsync((void**)&C->col, sizeof(int32_t) * (size_t)total, ctx->stream));
-    CB_CUDA(cudaMallocAsync(&C->val, vsz * (size_t)total, ctx->stream));
+    CB_CUDA(dev_alloc(ctx, &C->col, sizeof(int32_t) * (size_t)total));
+    CB_CUDA(dev_alloc(ctx, &C->val, vsz * (size_t)total));
   }
   if (total == 0) {
     collect_times(ctx, opt, false);
@@ -858,7 +891,7 @@ void CUDART_CB graph_wave_host(void* p) {
 bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB, const int32_t* rcols,
                          const std::vector<int64_t>& arow, int n, int first, int64_t kmax,
                          const cb_opts& opt, int& wave, int& kernels, int64_t& nnz_total,
-                         int64_t& flops_total, bool capture) {
+                         int64_t& flops_total, bool capture, const int64_t* prow_dev) {
   const int64_t vsz = (int64_t)value_size(sr), per = 4 + vsz;
   std::vector<int64_t> sizes;
   int64_t max_flops = 0;
@@ -897,8 +930,9 @@ bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB
     max_wins = std::max(max_wins, r * spans + f / wcut + 1);
   }
   // everything the graph touches is allocated before the capture
-  DevBuf orp(ctx), ocol(ctx), oval(ctx), wsb(ctx), errw(ctx);
+  DevBuf orp(ctx), ocol(ctx), oval(ctx), wsb(ctx), errw(ctx), dscr(ctx);
   orp.alloc(8 * (size_t)(max_rows + 1));
+  if (opt.digests) dscr.alloc(16 * (size_t)(max_rows + 1));
   ocol.alloc(4 * (size_t)max_cap);
   oval.alloc((size_t)vsz * (size_t)max_cap);
   const size_t mr = (size_t)max_rows + 1;
@@ -973,6 +1007,13 @@ bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB
                            perm_sym, wins, span_counts, spans, racc, num_max);
     // the symbolic phase's consistency word (window capacity, span cut) joins the error word
     cb::launch_merge_error(counters + cb::kError, errw.as<int64_t>(), ctx->stream);
+    if (opt.digests) {
+      cb::launch_digest((int)value_size(sr), sr == CB_PLUS_TIMES_F64, orp.as<int64_t>(), ocol.as<int32_t>(),
+                        oval.p, m, prow_dev + cut[w], cut[w + 1] - cut[w], r0, dscr.as<uint64_t>(),
+                        reinterpret_cast<double*>(dscr.as<uint64_t>() + max_rows + 1),
+                        opt.digests + 2 * (size_t)(first + cut[w]), ctx->stream, ctx->sms);
+      kernels += m > 0 ? 2 : 1;
+    }
     cudaMemcpyAsync(hnnz + w, orp.as<int64_t>() + m, sizeof(int64_t), cudaMemcpyDeviceToHost,
                     ctx->stream);
     gw[(size_t)w] = GraphWave{&opt, wave + w, first + cut[w], first + cut[w + 1],
@@ -1084,9 +1125,17 @@ void batched_group(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, int n,
   kernels += 2;
   const DevCSR dB{rowsB, kmax, sBrp.as<int64_t>(), sBcol.as<int32_t>(), sBval.p};
   const cb_csr sA{rowsA, rowsB, nnzA, sArp.as<int64_t>(), sAcol.as<int32_t>(), sAval.p};
+  // digests: every product's first stacked row, on the device
+  DevBuf prow(ctx);
+  if (opt.digests) {
+    prow.alloc(8 * (size_t)(n + 1));
+    CB_CUDA(cudaMemcpyAsync(prow.p, arow.data(), 8 * (size_t)(n + 1), cudaMemcpyHostToDevice,
+                            ctx->stream));
+  }
   if ((opt.flags & (CB_FLAG_GRAPH | CB_FLAG_SYNC_FREE)) &&
       batched_group_graph(ctx, sr, sA, dB, rcols.as<int32_t>(), arow, n, first, kmax, opt, wave,
-                          kernels, nnz_total, flops_total, (opt.flags & CB_FLAG_GRAPH) != 0))
+                          kernels, nnz_total, flops_total, (opt.flags & CB_FLAG_GRAPH) != 0,
+                          prow.as<int64_t>()))
     return;
 
   // waves: consecutive products whose output fits the budget
@@ -1119,7 +1168,11 @@ void batched_group(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, int n,
   cb_opts inner = opt;
   inner.validate = 0;
   inner.budget_bytes = 0;
-  DevBuf orp(ctx), ocol(ctx), oval(ctx);
+  DevBuf orp(ctx), ocol(ctx), oval(ctx), dscr(ctx);
+  int64_t max_wave_rows = 1;
+  for (size_t w = 0; w + 1 < cut.size(); ++w)
+    max_wave_rows = std::max(max_wave_rows, arow[cut[w + 1]] - arow[cut[w]]);
+  if (opt.digests) dscr.alloc(16 * (size_t)(max_wave_rows + 1));
   int64_t cap = 0;
   if (opt.budget_bytes > 0) {
     int64_t max_rows = 0;
@@ -1140,12 +1193,28 @@ void batched_group(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, int n,
     if (inner.out_capacity > 0) Cw = cb_csr{0, 0, 0, orp.as<int64_t>(), ocol.as<int32_t>(), oval.p};
     ctx->stats.kernels = 0;
     const int32_t* wr = rcols.as<int32_t>() + arow[w0];
-    if (opt.sizing == CB_SIZING_EXACT || !(opt.flags & CB_FLAG_LEARNED_ROWS))
-      spgemm_plain(ctx, sr, &Aw, dB, kmax, &Cw, inner, nullptr, nullptr, wr);
-    else spgemm_learned(ctx, sr, &Aw, dB, kmax, &Cw, inner, wr);
+    try {
+      if (opt.sizing == CB_SIZING_EXACT || !(opt.flags & CB_FLAG_LEARNED_ROWS))
+        spgemm_plain(ctx, sr, &Aw, dB, kmax, &Cw, inner, nullptr, nullptr, wr);
+      else spgemm_learned(ctx, sr, &Aw, dB, kmax, &Cw, inner, wr);
+    } catch (const Fail&) {
+      if (inner.out_capacity == 0)  // the wave's own output, allocated by the pipeline
+        for (void* q : {(void*)Cw.row_ptr, (void*)Cw.col, Cw.val})
+          if (q) cudaFreeAsync(q, ctx->stream);
+      throw;
+    }
     kernels += ctx->stats.kernels;
     nnz_total += Cw.nnz;
     flops_total += ctx->stats.flops;
+    if (opt.digests) {
+      const int64_t mw = arow[w1] - arow[w0];
+      cb::launch_digest((int)value_size(sr), sr == CB_PLUS_TIMES_F64, Cw.row_ptr, Cw.col, Cw.val, mw,
+                        prow.as<int64_t>() + w0, w1 - w0, arow[w0], dscr.as<uint64_t>(),
+                        reinterpret_cast<double*>(dscr.as<uint64_t>() + max_wave_rows + 1),
+                        opt.digests + 2 * (size_t)(first + w0), ctx->stream, ctx->sms);
+      CB_LAUNCHED();
+      kernels += mw > 0 ? 2 : 1;
+    }
     CB_CUDA(cudaStreamSynchronize(ctx->stream));
     const int stop = opt.on_batch(wave++, first + w0, first + w1, &Cw, opt.user);
     if (inner.out_capacity == 0) {
@@ -1537,8 +1606,8 @@ void spmspv_bucket(cb_ctx* ctx, int sr, const cb_csr* A, const cb_spvec* x, cb_s
     throw Fail{CB_ERR_CAPACITY};
   }
   if (!caller_buf && total > 0) {
-    CB_CUDA(cudaMallocAsync((void**)&y->idx, 4 * (size_t)total, ctx->stream));
-    CB_CUDA(cudaMallocAsync(&y->val, vsz * (size_t)total, ctx->stream));
+    CB_CUDA(dev_alloc(ctx, &y->idx, 4 * (size_t)total));
+    CB_CUDA(dev_alloc(ctx, &y->val, vsz * (size_t)total));
   }
   cb::launch_spmspv_bucket_step(sr, 3, dA, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, bpre,
                                 nb, n, scol.as<int32_t>(), sval.p, bnnz, ypre, y->idx, y->val, total,
@@ -1603,8 +1672,8 @@ int cb_spmspv(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_spvec* x, c
       ctx->spa_bits = nullptr;
       ctx->spa_n = 0;
       ctx->spa_sr = 0;
-      CB_CUDA(cudaMalloc(&ctx->spa, 8 * (size_t)n));
-      CB_CUDA(cudaMalloc((void**)&ctx->spa_bits, 4 * (size_t)nw));
+      CB_CUDA(dev_alloc_sync(ctx, &ctx->spa, 8 * (size_t)n));
+      CB_CUDA(dev_alloc_sync(ctx, &ctx->spa_bits, 4 * (size_t)nw));
       CB_CUDA(cudaMemsetAsync(ctx->spa_bits, 0, 4 * (size_t)nw, ctx->stream));
       ctx->spa_n = n;
     }
@@ -1647,8 +1716,8 @@ int cb_spmspv(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_spvec* x, c
     const bool bad_x = ctx->host[cb::kError] != 0;
     int64_t cap = caller_buf ? opt.out_capacity : total;
     if (!caller_buf && total > 0) {
-      CB_CUDA(cudaMallocAsync((void**)&y->idx, 4 * (size_t)total, ctx->stream));
-      CB_CUDA(cudaMallocAsync(&y->val, vsz * (size_t)total, ctx->stream));
+      CB_CUDA(dev_alloc(ctx, &y->idx, 4 * (size_t)total));
+      CB_CUDA(dev_alloc(ctx, &y->val, vsz * (size_t)total));
     }
     // compaction always runs: it also resets the accumulator for the next call
     cb::launch_spmspv_step((int)sr, 4, dA, nullptr, nullptr, 0, nullptr, nullptr, ctx->spa,
@@ -1870,8 +1939,8 @@ int cb_autotune(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, c
     CB_CUDA(cudaStreamSynchronize(ctx->stream));
     opt.out_capacity = C.nnz > 0 ? C.nnz : 1;
     if (C.nnz == 0) {
-      CB_CUDA(cudaMallocAsync((void**)&C.col, 4, ctx->stream));
-      CB_CUDA(cudaMallocAsync(&C.val, 8, ctx->stream));
+      CB_CUDA(dev_alloc(ctx, &C.col, 4));
+      CB_CUDA(dev_alloc(ctx, &C.val, 8));
     }
     const int big = cb::num_large_max((int)sr);
     const int syms[] = {512, 1024, 2048, 4096};
@@ -1928,6 +1997,28 @@ int cb_autotune(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, c
     cb_csr_free_async(ctx, &C);
     return f.code;
   }
+}
+
+int cb_ctx_set_fault(cb_ctx* ctx, int kind, int64_t arg, int64_t arg2) {
+  if (!ctx) return CB_ERR_ARG;
+  switch (kind) {
+    case CB_FAULT_ALLOC:
+      if (arg < 0) return CB_ERR_ARG;
+      ctx->fault_alloc = arg;
+      ctx->allocs_seen = 0;
+      return CB_OK;
+    case CB_FAULT_SILENT_TILE:
+      if (arg < 0) {
+        ctx->fused_silent = -1;
+        ctx->fused_spin = cb::kFusedSpinDefault;
+        return CB_OK;
+      }
+      if (arg2 < 1 || arg2 > (int64_t)cb::kFusedSpinDefault) return CB_ERR_ARG;
+      ctx->fused_silent = arg;
+      ctx->fused_spin = (unsigned)arg2;
+      return CB_OK;
+  }
+  return CB_ERR_ARG;
 }
 
 int cb_last_stats(const cb_ctx* ctx, cb_stats* out) {

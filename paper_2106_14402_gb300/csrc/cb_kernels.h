@@ -73,8 +73,15 @@ void launch_scatter_sym(int64_t m, int64_t ncols, const int64_t* flops, int32_t*
                         int64_t sym_hash_max = 512, const int32_t* rcols = nullptr);
 
 // K4: out[0] = 0, out[i+1] = out[i] + in[i]; partial needs scan_partials(n) int64.
+// Entries per scan tile (one partial sum per tile); the allocation-free
+// variant sizes its static scratch from it.
+constexpr int64_t kScanTileItems = 4096;
+// Largest tile count one scan launch takes (the grid's x limit).
+constexpr int64_t kScanMaxTiles = 2147483647;
 int64_t scan_partials(int64_t n);
-void launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* partial,
+// Returns the error of its own launches (cudaErrorInvalidValue when n needs
+// more than kScanMaxTiles tiles), not an error left pending by earlier calls.
+cudaError_t launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* partial,
                            cudaStream_t s);
 
 // out[j] = prefix[idx[j]] for j < n.
@@ -147,6 +154,13 @@ void launch_merge_selector(int64_t m, int k, int vsz, uint64_t one_bits, int64_t
                            void* val, cudaStream_t s, int sms);
 void launch_stack(const void* parts_dev, int nparts, int vsz, int64_t* rp_out, int32_t* col_out,
                   void* val_out, int32_t* rcols_out, cudaStream_t s, int sms);
+// Digests of the nprod products of a wave (cb_opts.digests; definition in
+// cb_batched.cu): the wave's stacked C (m rows) starts at stacked row
+// row_base; product p of the wave holds stacked rows [prow[p], prow[p+1]).
+// rdig / rsum: scratch of m entries each; out: 2 words per product.
+void launch_digest(int vsz, bool f64, const int64_t* rp, const int32_t* col, const void* val, int64_t m,
+                   const int64_t* prow, int nprod, int64_t row_base, uint64_t* rdig, double* rsum,
+                   uint64_t* out, cudaStream_t s, int sms);
 
 // Learned sizer (k_mlp.cu).
 const void* mlp_bf16(const cb_mlp* m);
@@ -213,8 +227,14 @@ void launch_numeric_dev(int sr, const DevCSR& A, const DevCSR& B, const int32_t*
 size_t rank_scratch_bytes(int sr, int sms);
 int64_t fused_tiles(int lanes, int64_t nrows);
 int64_t fused_max_cols(int lanes);
+// Each look-back wait polls an earlier tile at most spin_limit times
+// (kFusedSpinDefault, about a second), then records CB_FUSED_STALLED and
+// publishes anyway.  silent_tile >= 0 (fault injection) is a tile that
+// never publishes its total.
+constexpr unsigned kFusedSpinDefault = 1u << 20;
 cudaError_t launch_fused(int sr, int lanes, const DevCSR& A, const DevCSR& B, int64_t* Crp,
                          int32_t* Ccol, void* Cval, int64_t cap, unsigned long long* tstat,
-                         int64_t tstat_cap, unsigned* sync, int* status, cudaStream_t s, int sms);
+                         int64_t tstat_cap, unsigned* sync, int* status, cudaStream_t s, int sms,
+                         unsigned spin_limit = kFusedSpinDefault, int64_t silent_tile = -1);
 
 }  // namespace cb

@@ -26,7 +26,8 @@
 // always being worked on.  Tile status words carry a launch epoch that the
 // last CTA to finish advances, so no reset is needed between launches (CUDA
 // graph replays included).  Polls are bounded: a tile that gives up records
-// an error and publishes anyway, so no CTA waits forever.
+// an error and publishes anyway, so no CTA waits forever.  (spin_limit and
+// silent_tile serve fault injection: a tile that never publishes.)
 #include <algorithm>
 
 #include "cb.h"
@@ -41,7 +42,6 @@ constexpr int kFE = 8;                // products per lane
 constexpr int kFWarps = 8;            // warps per CTA
 constexpr int kFThreads = kFWarps * 32;
 constexpr unsigned kFPad = 0xFFFFFFFFu;
-constexpr unsigned kFSpin = 1u << 20;  // polls of one earlier tile before giving up (~1 s)
 
 // tile status word: [63:40] launch epoch (24 bits), [39:38] kind, [37:0] value
 constexpr int kEpochShift = 40;
@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
                                                      int32_t* __restrict__ Ccol,
                                                      typename Sem<SR>::TC* __restrict__ Cval,
                                                      int64_t cap, unsigned long long* tstat,
-                                                     int64_t tstat_cap, unsigned* sync, int* status) {
+                                                     int64_t tstat_cap, unsigned* sync, int* status,
+                                                     unsigned spin_limit, int64_t silent_tile) {
   typedef Sem<SR> S;
   typedef typename S::A Acc;
   typedef typename S::TA TA;
@@ -319,7 +320,8 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
       const int agg = __shfl_sync(kFull, inc, 31);
       if (lane == 0) {
         s_red[0] = agg;
-        atomicExch(&tstat[tile], ep | (tile == 0 ? kKindInc : kKindAgg) | (unsigned long long)agg);
+        if (tile != silent_tile)  // fault injection: a producer that never publishes
+          atomicExch(&tstat[tile], ep | (tile == 0 ? kKindInc : kKindAgg) | (unsigned long long)agg);
       }
     }
     __syncthreads();
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
         for (;;) {
           w = ld_volatile(&tstat[j]);
           if ((w & ~((1ull << kEpochShift) - 1)) == ep && (w & kKindMask)) break;
-          if (++spins >= kFSpin) {
+          if (++spins >= spin_limit) {
             atomicOr(status, CB_FUSED_STALLED);
             w = ep | kKindInc;
             break;
@@ -364,7 +366,8 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
       if (stop < kFThreads) break;
     }
     if (threadIdx.x == 0) {
-      if (tile > 0) atomicExch(&tstat[tile], ep | kKindInc | (unsigned long long)(excl + agg));
+      if (tile > 0 && tile != silent_tile)
+        atomicExch(&tstat[tile], ep | kKindInc | (unsigned long long)(excl + agg));
       s_base = excl;
     }
     __syncthreads();
@@ -418,7 +421,8 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
 template <int SR, int G>
 cudaError_t launch_fused_t(const DevCSR& A, const DevCSR& B, int64_t* Crp, int32_t* Ccol, void* Cval,
                            int64_t cap, unsigned long long* tstat, int64_t tstat_cap, unsigned* sync,
-                           int* status, cudaStream_t s, int sms) {
+                           int* status, cudaStream_t s, int sms, unsigned spin_limit,
+                           int64_t silent_tile) {
   constexpr int TR = kFWarps * (32 / G);
   static int per_sm = 0;  // resident CTAs per SM (same for every device of one kind)
   if (per_sm == 0) {
@@ -441,17 +445,18 @@ cudaError_t launch_fused_t(const DevCSR& A, const DevCSR& B, int64_t* Crp, int32
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_fused<SR, G>, A, B, Crp, Ccol,
                             static_cast<typename Sem<SR>::TC*>(Cval), cap, tstat, tstat_cap, sync,
-                            status);
+                            status, spin_limit < 1 ? 1u : spin_limit, silent_tile);
 }
 
 template <int SR>
 cudaError_t launch_fused_sr(int lanes, const DevCSR& A, const DevCSR& B, int64_t* Crp, int32_t* Ccol,
                             void* Cval, int64_t cap, unsigned long long* tstat, int64_t tstat_cap,
-                            unsigned* sync, int* status, cudaStream_t s, int sms) {
+                            unsigned* sync, int* status, cudaStream_t s, int sms, unsigned spin,
+                            int64_t silent) {
   switch (lanes) {
-    case 8: return launch_fused_t<SR, 8>(A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms);
-    case 16: return launch_fused_t<SR, 16>(A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms);
-    case 32: return launch_fused_t<SR, 32>(A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms);
+    case 8: return launch_fused_t<SR, 8>(A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms, spin, silent);
+    case 16: return launch_fused_t<SR, 16>(A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms, spin, silent);
+    case 32: return launch_fused_t<SR, 32>(A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms, spin, silent);
   }
   return cudaErrorInvalidValue;
 }
@@ -467,9 +472,10 @@ int64_t fused_max_cols(int lanes) { return (1ll << (32 - clog2(lanes * kFE))) - 
 
 cudaError_t launch_fused(int sr, int lanes, const DevCSR& A, const DevCSR& B, int64_t* Crp,
                          int32_t* Ccol, void* Cval, int64_t cap, unsigned long long* tstat,
-                         int64_t tstat_cap, unsigned* sync, int* status, cudaStream_t s, int sms) {
+                         int64_t tstat_cap, unsigned* sync, int* status, cudaStream_t s, int sms,
+                         unsigned spin_limit, int64_t silent_tile) {
   switch (sr) {
-#define CB_CASE(SRV) case SRV: return launch_fused_sr<SRV>(lanes, A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms);
+#define CB_CASE(SRV) case SRV: return launch_fused_sr<SRV>(lanes, A, B, Crp, Ccol, Cval, cap, tstat, tstat_cap, sync, status, s, sms, spin_limit, silent_tile);
     CB_FOR_EACH_SEMIRING(CB_CASE)
 #undef CB_CASE
   }

@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(256) k_tier_scatter(int64_t m, TierBySize tier
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
+static_assert(kScanTile == kScanTileItems, "scan tile size is shared with the allocation-free scan");
 
 __device__ __forceinline__ long long block_exclusive_scan(long long x, long long* warp_tot,
                                                          long long& block_total) {
@@ -284,16 +285,27 @@ void launch_merge_error(const int64_t* src, int64_t* dst, cudaStream_t s) {
 
 int64_t scan_partials(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
-void launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* partial,
-                           cudaStream_t s) {
-  if (n == 0) {
-    cudaMemsetAsync(out, 0, sizeof(int64_t), s);
-    return;
-  }
+// The kernels are launched with cudaLaunchKernel, whose return value is the
+// error of that launch alone (a <<<>>> launch is only seen through
+// cudaGetLastError, which also reports errors left by earlier calls).
+cudaError_t launch_exclusive_scan(const int64_t* in, int64_t n, int64_t* out, int64_t* partial,
+                                  cudaStream_t s) {
+  if (n < 0) return cudaErrorInvalidValue;
+  if (n == 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), s);
   const int64_t nb = (n + kScanTile - 1) / kScanTile;
-  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial);
-  k_scan_partials<<<1, kScanThreads, 0, s>>>(partial, nb, out + n);
-  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial, out);
+  if (nb > kScanMaxTiles) return cudaErrorInvalidValue;
+  int64_t* total = out + n;
+  void* reduce_args[] = {(void*)&in, (void*)&n, (void*)&partial};
+  void* partials_args[] = {(void*)&partial, (void*)&nb, (void*)&total};
+  void* apply_args[] = {(void*)&in, (void*)&n, (void*)&partial, (void*)&out};
+  cudaError_t e = cudaLaunchKernel((const void*)k_scan_reduce, dim3((unsigned)nb), dim3(kScanThreads),
+                                   reduce_args, 0, s);
+  if (e == cudaSuccess)
+    e = cudaLaunchKernel((const void*)k_scan_partials, dim3(1), dim3(kScanThreads), partials_args, 0, s);
+  if (e == cudaSuccess)
+    e = cudaLaunchKernel((const void*)k_scan_apply, dim3((unsigned)nb), dim3(kScanThreads), apply_args,
+                         0, s);
+  return e;
 }
 
 void launch_gather(const int64_t* prefix, const int64_t* idx, int64_t n, int64_t* out,

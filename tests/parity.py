@@ -77,3 +77,61 @@ def sample_rows(m, flops, frac=0.01, top=100, seed=0):
     pick = rng.choice(m, size=min(k, m), replace=False)
     heavy = np.argsort(-np.asarray(flops), kind="stable")[:top]
     return np.unique(np.concatenate([pick, heavy])).astype(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# per-product digests (the definition cb.h states for cb_opts.digests),
+# computed here from host arrays, e.g. the oracle's output
+# ---------------------------------------------------------------------------
+
+_U = np.uint64
+
+
+def _sm64(x):
+    """splitmix64 output function on uint64 arrays (wrapping arithmetic)."""
+    x = x + _U(0x9E3779B97F4A7C15)
+    x = (x ^ (x >> _U(30))) * _U(0xBF58476D1CE4E5B9)
+    x = (x ^ (x >> _U(27))) * _U(0x94D049BB133111EB)
+    return x ^ (x >> _U(31))
+
+
+def digest(sr, rp, col, val):
+    """(D0, V): the pattern/value digest word, and for (+,x) fp64 the weighted
+    checksum V = sum v * w(r, c) (the exactly rounded sum of the rounded
+    terms; None for the other semirings)."""
+    import math
+    rp = np.asarray(rp, dtype=np.int64)
+    n = rp.size - 1
+    lens = np.diff(rp)
+    with np.errstate(over="ignore"):
+        r = np.arange(n, dtype=np.uint64)
+        d = np.sum(_sm64(_sm64(_U(2) * r) + lens.astype(np.uint64)), dtype=np.uint64)
+        row_of = np.repeat(r, lens)
+        j = (np.arange(col.size, dtype=np.int64) - np.repeat(rp[:-1], lens)).astype(np.uint64)
+        hr = _sm64(_U(2) * row_of + _U(1))
+        c = np.asarray(col, dtype=np.int64).astype(np.uint64)
+        f64 = sr == "plus_times_f64"
+        if f64:
+            bits = _U(0)
+        else:
+            v = np.ascontiguousarray(val)
+            bits = v.view({1: np.uint8, 4: np.uint32, 8: np.uint64}[v.dtype.itemsize]).astype(np.uint64)
+        d = d + np.sum(_sm64(_sm64(_sm64(hr + j) + c) + bits), dtype=np.uint64)
+        V = None
+        if f64:
+            w = 1.0 + (_sm64(hr ^ c) >> _U(11)).astype(np.float64) * 2.0 ** -53
+            V = math.fsum((np.asarray(val, dtype=np.float64) * w).tolist())
+    return int(d), V
+
+
+def digest_words(dig, i):
+    """Product i's two words from the digests copied to the host (int64 numpy
+    array of 2 * count entries), as (unsigned D0, float V)."""
+    w = np.ascontiguousarray(dig[2 * i:2 * i + 2], dtype=np.int64)
+    return int(w[:1].view(np.uint64)[0]), float(w[1:].view(np.float64)[0])
+
+
+# |V_gpu - V_ref| <= (2 * 1e-12 + 40 u) * sum of the oracle's |a b| sums: each
+# entry is within 1e-12 sum|ab| (R4) and weighted by w < 2, plus the rounding
+# of the weighted terms and of both summations (<= 16 u sum|v w| on the device).
+CHECKSUM_TOL = 2 * FP64_TOL + 40 * 2.0 ** -53

@@ -243,7 +243,9 @@ def test_row_stats_and_row_nnz(cb):
     assert np.array_equal(nz.cpu().numpy(), np.diff(rp))
 
 
-@pytest.mark.parametrize("n", [0, 1, 4095, 4096, 4097, 1_000_003])
+# 5,000,011 entries take 1,221 tiles: the scan of tile sums carries across
+# two chunks of 1,024 tiles.
+@pytest.mark.parametrize("n", [0, 1, 4095, 4096, 4097, 1_000_003, 5_000_011])
 def test_exclusive_scan(cb, n):
     x = torch.randint(0, 1 << 20, (n,), dtype=torch.int64, device="cuda")
     out = cb.exclusive_scan(x).cpu().numpy()
