@@ -76,16 +76,33 @@ def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
+# the sources the fp64 numeric phase's kernels are built from: the measured
+# traffic holds only while these are unchanged since the capture
+NUMERIC_SOURCES = ("paper_2106_14402_gb300/csrc/k_numeric.cu", "paper_2106_14402_gb300/csrc/cb_common.cuh")
+
+
+def sources_digest(paths=NUMERIC_SOURCES) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def fp64_traffic_per_product():
-    """DRAM bytes per product of the fp64 numeric phase from the committed ncu summary."""
-    path = os.path.join(ROOT, "profiles", "k_num_rank_k_sym_bitmap_rmat_s16.md")
+    """(DRAM bytes per product of the fp64 numeric phase, source note) from
+    profiles/traffic.json, or (None, why) when absent or captured from other
+    kernel sources."""
     try:
-        for line in open(path):
-            if line.startswith("traffic_bytes_per_product_fp64_numeric:"):
-                return float(line.split(":")[1])
-    except OSError:
-        pass
-    return None
+        with open(TRAFFIC_JSON) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None, "no traffic capture"
+    if t.get("sources_digest") != sources_digest():
+        return None, "kernel sources changed since the traffic capture"
+    return float(t["fp64_numeric_bytes_per_product"]), t.get("capture", "")
 
 
 # value bytes of A, B and C under the heterogeneous semiring
@@ -162,10 +179,11 @@ class ClockSampler:
 # CPU oracle on a bounded row sample (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
-def oracle_sample_rate(problems, target_s: float = 12.0, seed: int = 0):
+def oracle_sample_rate(problems, target_s: float = 12.0, seed: int = 0, keep=None):
     """Time the oracle on a seeded row sample of each product, sized to ~target_s in total.
 
-    Returns (products/s, nnz/s, cores, description, seconds)."""
+    Returns (products/s, nnz/s, cores, description, seconds); with `keep` (a
+    dict) the sampled rows and the oracle's output go to keep[semiring]."""
     import oracle
     cores = oracle.max_threads()
     rng = np.random.default_rng(seed)
@@ -189,13 +207,45 @@ def oracle_sample_rate(problems, target_s: float = 12.0, seed: int = 0):
     for sr, A, B, flops, perm in samples:
         rows = np.sort(perm[: max(1, int(A.nrows * frac))])
         t0 = time.perf_counter()
-        rp, _, _, _ = oracle.spgemm(sr, A, B, rows=rows)
+        res = oracle.spgemm(sr, A, B, rows=rows)
         t += time.perf_counter() - t0
+        rp = res[0]
+        if keep is not None:
+            keep[sr] = (rows, res)
         prod += int(flops[rows].sum())
         nnz += int(rp[-1])
     desc = (f"seeded {frac * 100:.2f}% row sample of every product "
             f"({prod:.3e} products, {nnz:.3e} nnz(C)), oracle std::map Gustavson, OpenMP")
     return prod / t, nnz / t, cores, desc, t
+
+
+def sampled_parity(dprob, kept):
+    """The timed steps' last outputs on the oracle's sampled rows: exact
+    equality for the integer, bool and min semirings; for (+,x) fp64 the
+    largest |c - c_ref| / sum|a b| over the sampled entries (bound 1e-12)."""
+    out = {}
+    for sr, A, B, dA, dB, C, nnz in dprob:
+        if sr not in kept:
+            continue
+        rows, (w_rp, w_col, w_val, w_abs) = kept[sr]
+        g_rp = C.row_ptr[:A.nrows + 1].cpu().numpy()
+        idx = np.concatenate([np.arange(g_rp[r], g_rp[r + 1]) for r in rows]) if len(rows) else \
+            np.zeros(0, np.int64)
+        it = __import__("torch").as_tensor(idx, device=C.col.device)
+        g_col = C.col[it].cpu().numpy()
+        v = C.val[it]
+        g_val = v.view(__import__("torch").int32).cpu().numpy().view(np.uint32) \
+            if str(v.dtype) == "torch.uint32" else v.cpu().numpy()
+        same = bool(np.array_equal(np.diff(g_rp)[rows], np.diff(w_rp)) and np.array_equal(g_col, w_col))
+        rec = {"rows": int(len(rows)), "entries": int(idx.size), "pattern_equal": same}
+        if sr == "plus_times_f64":
+            ratio = np.abs(g_val - w_val) / np.where(w_abs > 0, w_abs, 1.0) if same else np.array([np.inf])
+            rec["max_err_ratio"] = float(ratio.max()) if ratio.size else 0.0
+            rec["bound"] = 1e-12
+        else:
+            rec["values_equal"] = bool(same and np.array_equal(g_val, w_val))
+        out[sr] = rec
+    return out
 
 
 def run_reference(args):
@@ -332,16 +382,15 @@ def main_gpu(args):
         # the dominant kernel: the numeric phase of the (+,x) fp64 product
         f = per_sr["plus_times_f64"]
         a64 = f["compulsory_bytes"] / (f["ms_numeric"] * 1e-3) / 1e9 if f["ms_numeric"] > 0 else 0.0
-        tpp = fp64_traffic_per_product()
+        tpp, tsrc = fp64_traffic_per_product()
         roofline = {"bound": "hbm", "achieved": round(a64, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(a64 / peak, 4),
                     "traffic": round(tpp * f["products"]) if tpp else None,
                     "kernel": "numeric phase of the (+,x) f64 product (k_num_rank<2> + k_num_hash<2,...>), "
                               "per SpGEMM",
                     "algorithmic_bytes": f["compulsory_bytes"], "ms_in_kernel": f["ms_numeric"],
-                    "traffic_source": "ncu dram bytes per product of the same kernels on R-MAT s16 "
-                                      "(profiles/k_num_rank_k_sym_bitmap_rmat_s16.md) x this product's "
-                                      "products" if tpp else None,
+                    "traffic_source": ("ncu DRAM bytes per product of the same kernels (profiles/traffic.json: "
+                                       + tsrc + ") x this product's products") if tpp else tsrc,
                     "peak_source": peak_src, "all_semirings": all_sr}
     else:
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -363,9 +412,12 @@ def main_gpu(args):
         legs["one_launch_er16k"] = run_one_launch(args, cb, ctx, flush, dev, peak, peak_src)
 
     cpu = None
+    parity = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        r, nr, cores, sample, _ = oracle_sample_rate(problems, target_s=args.ref_seconds)
+        kept = {}
+        r, nr, cores, sample, _ = oracle_sample_rate(problems, target_s=args.ref_seconds, keep=kept)
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        parity = sampled_parity(dprob, kept)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -379,7 +431,8 @@ def main_gpu(args):
                            "parallelism": f"replicas x{world}"},
                 "nnz_per_s": nnz_rate, "per_semiring": per_sr, "phase_ms_per_step":
                     {k: round(v, 4) for k, v in phase_tot.items()},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, **legs,
+                "roofline": roofline, "cpu_baseline": cpu, "parity_sample": parity, "e2e": e2e,
+                **legs,
                 "gpu_launches": launches, "clocks": clocks, "wall_s_timed": round(wall, 3)}
         print(json.dumps(line), flush=True)
     if dist:
@@ -811,9 +864,13 @@ def run_spmspv_leg(args, cb, ctx, flush, dev, dprob, peak, peak_src):
 
 def run_multi(args, cb, ctx, model):
     """4096 independent ER products (n log-uniform in [256, 65536], degree 4..64;
-    half (min,+) u32, half (+,x) fp64), generated on the device: one batched
-    call with waves under a 24 GB output budget, against one plain call per
-    product.  Outputs are consumed (dropped) as they are produced."""
+    half (min,+) u32, half (+,x) fp64), generated on the device: batched calls
+    with waves under a 24 GB output budget in every mode, against one call per
+    product, and against the two-phase path (no work-queue kernel) under each
+    semiring's own autotuned bounds.  Outputs are consumed (dropped) as they are
+    produced.  Each figure is the median of `reps` timed calls after one
+    untimed call (host wall clock around a synchronised call, inputs
+    resident)."""
     import time
 
     import torch
@@ -823,49 +880,45 @@ def run_multi(args, cb, ctx, model):
     plan, As, Bs = gen_device.batched_workload(count)
     srs = [p["semiring"] for p in plan]
     torch.cuda.synchronize()
-    # tier bounds for this workload, tuned on its largest product of each semiring
-    tuned = {}
-    for sr in ("min_plus_u32", "plus_times_f64"):
-        i = max((k for k, p in enumerate(plan) if p["semiring"] == sr), key=lambda k: plan[k]["n"])
-        tuned[sr] = cb.autotune(sr, As[i], Bs[i], ctx=ctx)
-    ctx.set_tune(**tuned["plus_times_f64"][0])
     budget = 24 << 30
-    res = {"products": count, "budget_bytes": budget, "tune": {k: v[0] for k, v in tuned.items()},
-           "workload": "ER n log-U[256,65536], deg U{4..64}; half (min,+) u32 [1,1000], half (+,x) f64 U(-1,1)"}
-    for mode in ("exact", "learned"):
+    reps = 5
+    res = {"products": count, "budget_bytes": budget, "reps": reps,
+           "workload": "ER n log-U[256,65536], deg U{4..64}; half (min,+) u32 [1,1000], half (+,x) f64 U(-1,1)",
+           "timing": "median of %d host wall-clock timed calls (synchronised), after one untimed call; "
+                     "inputs resident" % reps}
+
+    def median_time(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts)
+
+    def batched(mode, sizing="exact", fused=True, lo=0, hi=None):
+        hi = count if hi is None else hi
         info = {}
 
         def run():
-            info.update(cb.spgemm_batched(srs, As, Bs, lambda *a: False, budget_bytes=budget,
-                                          validate=False, sizing=mode,
-                                          mlp=model if mode == "learned" else None, ctx=ctx))
+            info.update(cb.spgemm_batched(srs[lo:hi], As[lo:hi], Bs[lo:hi],
+                                          (lambda *a: None) if mode == "graph" else (lambda *a: False),
+                                          budget_bytes=budget, validate=False, sizing=sizing,
+                                          mlp=model if sizing == "learned" else None, ctx=ctx,
+                                          mode=mode, fused=fused))
             torch.cuda.synchronize()
+        sec = median_time(run)
+        return sec, info
 
-        run()
-        t0 = time.perf_counter()
-        run()
-        sec = time.perf_counter() - t0
-        res["batched_" + mode] = {"seconds": sec, "waves": info["batches"],
-                                  "products_per_s": info["flops"] / sec,
-                                  "nnz_per_s": info["nnz"] / sec}
+    for key, mode, sizing in (("batched_graph", "graph", "exact"), ("batched_sync_free", "sync_free", "exact"),
+                              ("batched_exact", "host", "exact"), ("batched_learned", "host", "learned")):
+        sec, info = batched(mode, sizing)
+        res[key] = {"seconds": sec, "waves": info["batches"], "products_per_s": info["flops"] / sec,
+                    "nnz_per_s": info["nnz"] / sec}
     flops = info["flops"]
-    # every wave captured into one CUDA graph (exact, waves cut by the flop bound)
-    ginfo = {}
-
-    def graph():
-        ginfo.update(cb.spgemm_batched(srs, As, Bs, lambda *a: None, budget_bytes=budget,
-                                       validate=False, ctx=ctx, mode="graph"))
-        torch.cuda.synchronize()
-
-    graph()
-    t0 = time.perf_counter()
-    graph()
-    sec_g = time.perf_counter() - t0
-    res["batched_graph"] = {"seconds": sec_g, "waves": ginfo["batches"],
-                            "products_per_s": ginfo["flops"] / sec_g,
-                            "nnz_per_s": ginfo["nnz"] / sec_g,
-                            "note": "one CUDA graph per semiring group (capture + instantiate + launch "
-                                    "inside the timed call)"}
+    res["batched_graph"]["note"] = ("one CUDA graph per semiring group; capture, instantiation and launch "
+                                    "inside the timed call (batched_sync_free: the same launch sequence "
+                                    "without the capture)")
 
     def plain():
         for sr, A, B in zip(srs, As, Bs):
@@ -873,16 +926,25 @@ def run_multi(args, cb, ctx, model):
             del C
         torch.cuda.synchronize()
 
-    plain()
-    t0 = time.perf_counter()
-    plain()
-    sec = time.perf_counter() - t0
+    sec = median_time(plain)
     res["plain_per_product"] = {"seconds": sec, "products_per_s": flops / sec}
-    res["batched_vs_plain"] = sec / res["batched_exact"]["seconds"]
-    res["learned_batched_vs_plain"] = sec / res["batched_learned"]["seconds"]
-    res["graph_batched_vs_plain"] = sec / res["batched_graph"]["seconds"]
-    res["timing"] = "host wall clock with device synchronisation, inputs resident"
+    # the two-phase path (hash tiers and rank windows, no work-queue kernel) in
+    # graph mode, each semiring group under its own autotuned bounds
+    half = count // 2
+    two = 0.0
+    tuned = {}
+    for lo, hi in ((0, half), (half, count)):
+        sr = srs[lo]
+        i = max(range(lo, hi), key=lambda k: plan[k]["n"] * plan[k]["deg"] ** 2)
+        tuned[sr], _ = cb.autotune(sr, As[i], Bs[i], ctx=ctx)
+        ctx.set_tune(**tuned[sr])
+        sec_g, _ = batched("graph", fused=False, lo=lo, hi=hi)
+        two += sec_g
     ctx.set_tune()
+    res["two_phase_graph"] = {"seconds": two, "products_per_s": flops / two, "tune": tuned}
+    for key in ("batched_graph", "batched_sync_free", "batched_exact", "batched_learned"):
+        res[key]["vs_plain_per_product"] = res["plain_per_product"]["seconds"] / res[key]["seconds"]
+        res[key]["vs_two_phase_graph"] = two / res[key]["seconds"]
     del As, Bs
     torch.cuda.empty_cache()
     return res

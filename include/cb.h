@@ -146,10 +146,18 @@ enum {
   CB_FLAG_SPMSPV_BUCKET = 64, /* cb_spmspv: the bucket (propagation-blocking) form
                          instead of the dense accumulator (see cb_spmspv) */
   CB_FLAG_NO_FUSED = 8 /* exact sizing: always run the two-phase path.  By default
-                         a product whose rows all meet the bounds of
-                         cb_spgemm_fused (below) is formed by that one launch
-                         after the flop count, with a library-allocated C sized
-                         by flops (an upper bound of nnz(C)) */
+                         (1) when the mean row lengths of A and B fit the bounds of
+                         cb_spgemm_fused (below), that one launch is tried first,
+                         with no flop count (a library-allocated C then holds up to
+                         8 x lanes entries per row); if a row exceeds the bounds the
+                         call continues with the flop count; (2) a product whose rows
+                         all meet those bounds is formed by that one launch after the
+                         flop count, C sized by flops (an upper bound of nnz(C));
+                         (3) otherwise, when every output row has at most 4096
+                         products and at most 65536 columns (B's, or the stacked
+                         product's own), one persistent launch forms the rows in
+                         one pass each, taking them from a device work queue (also
+                         per wave of cb_spgemm_batched in every mode) */
 };
 
 /* Fill *opt with defaults (exact sizing, validation on, library-allocated C). */
@@ -344,7 +352,9 @@ int cb_exclusive_scan_noalloc(const int64_t *in, int64_t n, int64_t *out, void *
  *   learn_max     with learned or upper-bound sizing, rows whose capacity is
  *                 <= this skip the symbolic phase (0..8192, default 512).
  * cb_ctx_set_tune clamps the values into range (and writes back what it set).
- * cb_autotune times cb_spgemm_ex-equivalent runs of A.B under a grid of
+ * cb_autotune times cb_spgemm_ex-equivalent runs of A.B on the two-phase
+ * path (the bounds steer only that path; the one-launch and work-queue
+ * kernels are left out) under a grid of
  * bounds (learn_max too when opt->sizing is learned), keeps the fastest in
  * the context and returns it with its time in ms; it allocates and frees its
  * own output and synchronises the stream. */
@@ -470,8 +480,9 @@ int cb_last_stats(const cb_ctx *ctx, cb_stats *out);
  *     arg = 0 turns it off.  arg2 is ignored.
  *   CB_FAULT_SILENT_TILE: in the one-launch kernel (cb_spgemm_fused and the
  *     automatic branch of cb_spgemm_ex) tile `arg` (>= 0; 32 rows per tile
- *     at 8 lanes, 16 at 16, 8 at 32) never publishes its row total, and
- *     every look-back wait gives up after arg2 polls (1 <= arg2 <= 2^20).
+ *     at 8 lanes, 16 at 16, 8 at 32), and in the work-queue kernel row
+ *     `arg`, never publishes its total, and every look-back wait gives up
+ *     after arg2 polls (1 <= arg2 <= 2^20).
  *     Waiting tiles record CB_FUSED_STALLED and publish anyway, so the launch
  *     ends; cb_spgemm_ex returns CB_ERR_TIMEOUT with C zeroed.  arg < 0
  *     restores the defaults (no silent tile, 2^20 polls).

@@ -683,7 +683,7 @@ def row_features(A: DeviceCSR, B: DeviceCSR, ctx: Context | None = None) -> torc
 def spgemm_batched(semirings, As, Bs, on_wave, *, budget_bytes: int = 0, validate: bool = True,
                    sizing: str = "exact", mlp=None, margin: float = 0.25,
                    ctx: Context | None = None, mode: str = "host",
-                   digests: torch.Tensor | None = None) -> dict:
+                   digests: torch.Tensor | None = None, fused: bool = True) -> dict:
     """Batched products C_i = A_i (+).(x) B_i (cb_spgemm_batched).
 
     on_wave(wave, first, end, Cw) receives a DeviceCSR that stacks
@@ -697,9 +697,11 @@ def spgemm_batched(semirings, As, Bs, on_wave, *, budget_bytes: int = 0, validat
     bound alone exceeds the budget runs as mode "host".
     `digests` (optional, an int64 CUDA tensor of 2 * len(As) entries) receives
     each product's two digest words (cb.h, cb_spgemm_batched), as raw 64-bit
-    patterns.
+    patterns.  `fused=False` keeps every wave on the two-phase path (no
+    one-launch or work-queue kernel).
     """
-    flags = {"host": 0, "sync_free": FLAG_SYNC_FREE, "graph": FLAG_GRAPH}[mode]
+    flags = {"host": 0, "sync_free": FLAG_SYNC_FREE, "graph": FLAG_GRAPH}[mode] | \
+        (0 if fused else FLAG_NO_FUSED)
     ctx = ctx or context()
     n = len(As)
     assert len(Bs) == n and len(semirings) == n

@@ -277,15 +277,121 @@ void run_fused(cb_ctx* ctx, int sr, int lanes, const DevCSR& dA, const DevCSR& d
   ctx->stats.kernels += 1;
 }
 
+// One launch of the one-launch kernel into C (capacity cap) with the
+// context's status word, then one read-back of nnz(C), the status bits and
+// the product count (synchronises).  Returns the status bits.
+int fused_pass(cb_ctx* ctx, int sr, int lanes, const DevCSR& dA, const DevCSR& dB, cb_csr* C,
+               int64_t cap, const cb_opts& opt) {
+  ensure_fused(ctx, 0);
+  int* st = reinterpret_cast<int*>(ctx->fsync + 4);
+  CB_CUDA(cudaMemsetAsync(st, 0, sizeof(int), ctx->stream));
+  mark(ctx, opt, 4);
+  run_fused(ctx, sr, lanes, dA, dB, C->row_ptr, C->col, C->val, cap, st);
+  mark(ctx, opt, 5);
+  // words 2..7 of the sync area: nnz(C), status, product count
+  CB_CUDA(cudaMemcpyAsync(ctx->host, ctx->fsync + 2, 6 * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  CB_CUDA(cudaStreamSynchronize(ctx->stream));
+  return (int)(ctx->host[1] & 0xFFFFFFFF);
+}
+
+// One launch of the work-queue kernel over the m rows of A.B into C
+// (capacity cap), then one read-back of nnz(C) and the status bits
+// (synchronises).  Returns the status bits.
+int queue_pass(cb_ctx* ctx, int sr, const DevCSR& dA, const DevCSR& dB, int64_t m, cb_csr* C,
+               int64_t cap, const cb_opts& opt) {
+  ensure_fused(ctx, m);
+  int* st = reinterpret_cast<int*>(ctx->fsync + 4);
+  CB_CUDA(cudaMemsetAsync(st, 0, sizeof(int), ctx->stream));
+  mark(ctx, opt, 4);
+  const cudaError_t e = cb::launch_queue_rows(sr, dA, dB, m, C->row_ptr, C->col, C->val, cap,
+                                              ctx->fstat, ctx->fstat_cap, ctx->fsync, st, ctx->stream,
+                                              ctx->sms, ctx->fused_spin, ctx->fused_silent);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("queued SpGEMM launch: ") + cudaGetErrorString(e);
+    throw Fail{CB_ERR_CUDA};
+  }
+  ctx->stats.kernels += 1;
+  mark(ctx, opt, 5);
+  CB_CUDA(cudaMemcpyAsync(ctx->host, ctx->fsync + 2, 6 * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  CB_CUDA(cudaStreamSynchronize(ctx->stream));
+  return (int)(ctx->host[1] & 0xFFFFFFFF);
+}
+
+// Results of a fused pass that had no row beyond its bounds.
+void finish_fused(cb_ctx* ctx, cb_csr* C, int bits, int64_t cap, const cb_opts& opt) {
+  const int64_t total = ctx->host[0];
+  C->nnz = total;
+  ctx->stats.nnz = total;
+  ctx->stats.flops = ctx->host[2];
+  if (bits & CB_FUSED_STALLED) fail(ctx, CB_ERR_TIMEOUT, "fused SpGEMM: a tile wait expired");
+  if (bits & CB_FUSED_CAPACITY) {
+    char msg[128];
+    std::snprintf(msg, sizeof msg, "output needs %lld entries, capacity %lld", (long long)total,
+                  (long long)cap);
+    ctx->err = msg;
+    throw Fail{CB_ERR_CAPACITY};
+  }
+  collect_times(ctx, opt, true);
+}
+
+// Largest C the speculative path allocates itself (entries): 8 * lanes per
+// row is its bound of nnz(C) before any row has been counted.
+constexpr int64_t kSpeculativeMaxEntries = int64_t(1) << 24;
+
+// The speculative one-launch pass (see spgemm_plain).  Lanes come from the
+// mean row lengths of A and B (every row must fit them; the kernel checks).
+// Returns true when the product is complete, false to take the classified
+// path (nothing of C kept).
+bool try_fused_speculatively(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_t b_nnz,
+                             cb_csr* C, const cb_opts& opt, bool caller_buf, size_t vsz) {
+  const int64_t m = A->nrows;
+  if (m == 0 || dB.nrows == 0) return false;
+  const double mean_a = (double)A->nnz / (double)m, mean_b = (double)b_nnz / (double)dB.nrows;
+  int lanes = 0;
+  for (int g : {8, 16, 32})
+    if (mean_a <= g && mean_a * mean_b <= 8.0 * g && dB.ncols <= cb::fused_max_cols(g)) {
+      lanes = g;
+      break;
+    }
+  if (!lanes) return false;
+  const int64_t bound = 8 * (int64_t)lanes * m;  // nnz(C) when every row fits
+  const int64_t cap = caller_buf ? opt.out_capacity : bound;
+  if (!caller_buf && bound > kSpeculativeMaxEntries) return false;
+  if (!caller_buf) {
+    CB_CUDA(dev_alloc(ctx, &C->col, sizeof(int32_t) * (size_t)cap));
+    CB_CUDA(dev_alloc(ctx, &C->val, vsz * (size_t)cap));
+  }
+  mark(ctx, opt, 0);
+  mark(ctx, opt, 1);
+  mark(ctx, opt, 2);
+  mark(ctx, opt, 3);
+  const int bits = fused_pass(ctx, sr, lanes, dev(A), dB, C, cap, opt);
+  if (bits & CB_FUSED_ROW_TOO_LARGE) {  // a row beyond the lanes' bounds: classify first
+    if (!caller_buf) {
+      CB_CUDA(cudaFreeAsync(C->col, ctx->stream));
+      CB_CUDA(cudaFreeAsync(C->val, ctx->stream));
+      C->col = nullptr;
+      C->val = nullptr;
+    }
+    return false;
+  }
+  finish_fused(ctx, C, bits, cap, opt);
+  return true;
+}
+
 // Everything from K1 to the allocation of C and the numeric phase.
 // The plain (unbatched) path on a possibly windowed view dB of B; C gets
 // C->ncols = out_ncols.  Inputs are assumed valid (validation happens first).
 // skip (optional): rows already computed elsewhere; their sizes are preset[i]
 // and the exact phases leave them out.
 // a_rcols (optional): per-row output width of A's rows (stacked batches).
+// b_nnz (optional, >= 0): B's stored entries, for the speculative one-launch path.
 void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_t out_ncols,
                   cb_csr* C, const cb_opts& opt, const uint8_t* skip = nullptr,
-                  const int64_t* preset = nullptr, const int32_t* a_rcols = nullptr) {
+                  const int64_t* preset = nullptr, const int32_t* a_rcols = nullptr,
+                  int64_t b_nnz = -1) {
   const int64_t m = A->nrows, ncols = dB.ncols;
   const bool caller_buf = opt.out_capacity > 0;
   const size_t vsz = value_size(sr);
@@ -319,6 +425,14 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
 
   DevCSR dA = dev(A);
   dA.rcols = a_rcols;
+  const bool fused_ok = !(opt.flags & CB_FLAG_NO_FUSED) && !skip && !preset && !a_rcols && !dB.rpe &&
+                        !dB.filter && dB.col_lo == 0;
+  // Speculative one-launch path: when the operands' mean row lengths say that
+  // every row is probably small, launch the one-launch kernel right away.  It
+  // checks every row's bounds itself; only if a row exceeds them is the
+  // product recomputed by the path below, which classifies the rows first.
+  if (fused_ok && b_nnz >= 0 && try_fused_speculatively(ctx, sr, A, dB, b_nnz, C, opt, caller_buf, vsz))
+    return;
   CB_CUDA(cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream));
   mark(ctx, opt, 0);
   cb::launch_check_sorted(dB, counters, ctx->stream, ctx->sms);
@@ -342,39 +456,36 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
   // Every row small: one launch forms, sorts and places all rows (k_fused),
   // into C sized by flops (an upper bound of nnz(C)).
   const int lanes = fused_fit(ctx->host[cb::kMaxArow], ctx->host[cb::kMaxFlops], ncols);
-  if (lanes && !(opt.flags & CB_FLAG_NO_FUSED) && !skip && !preset && !a_rcols && !dB.rpe &&
-      !dB.filter && dB.col_lo == 0) {
+  if (lanes && fused_ok) {
     const int64_t cap = caller_buf ? opt.out_capacity : ctx->stats.flops;
     if (!caller_buf && cap > 0) {
       CB_CUDA(dev_alloc(ctx, &C->col, sizeof(int32_t) * (size_t)cap));
       CB_CUDA(dev_alloc(ctx, &C->val, vsz * (size_t)cap));
     }
-    ensure_fused(ctx, 0);
-    int* st = reinterpret_cast<int*>(ctx->fsync + 4);
-    CB_CUDA(cudaMemsetAsync(st, 0, sizeof(int), ctx->stream));
     mark(ctx, opt, 2);
     mark(ctx, opt, 3);
-    mark(ctx, opt, 4);
-    run_fused(ctx, sr, lanes, dA, dB, C->row_ptr, C->col, C->val, cap, st);
-    mark(ctx, opt, 5);
-    CB_CUDA(cudaMemcpyAsync(ctx->host, C->row_ptr + m, sizeof(int64_t), cudaMemcpyDeviceToHost,
-                            ctx->stream));
-    CB_CUDA(cudaMemcpyAsync(ctx->host + 1, st, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    CB_CUDA(cudaStreamSynchronize(ctx->stream));
-    const int64_t total = ctx->host[0];
-    const int bits = (int)(ctx->host[1] & 0xFFFFFFFF);
-    C->nnz = total;
-    ctx->stats.nnz = total;
-    if (bits & CB_FUSED_STALLED) fail(ctx, CB_ERR_TIMEOUT, "fused SpGEMM: a tile wait expired");
+    const int bits = fused_pass(ctx, sr, lanes, dA, dB, C, cap, opt);
     if (bits & CB_FUSED_ROW_TOO_LARGE) fail(ctx, CB_ERR_CUDA, "fused SpGEMM: row bound violated");
-    if (bits & CB_FUSED_CAPACITY) {
-      char msg[128];
-      std::snprintf(msg, sizeof msg, "output needs %lld entries, capacity %lld", (long long)total,
-                    (long long)cap);
-      ctx->err = msg;
-      throw Fail{CB_ERR_CAPACITY};
+    finish_fused(ctx, C, bits, cap, opt);
+    return;
+  }
+  // Every row of bounded size and width: one persistent launch takes the rows
+  // from a work queue and forms each in one pass (k_queue_rows), into C sized
+  // by flops.
+  if (!(opt.flags & CB_FLAG_NO_FUSED) && !skip && !preset && ncols <= cb::kQueueWidth &&
+      ctx->host[cb::kMaxFlops] <= cb::kQueueAcc) {
+    const int64_t flops = ctx->stats.flops;
+    const int64_t cap = caller_buf ? opt.out_capacity : flops;
+    if (!caller_buf && cap > 0) {
+      CB_CUDA(dev_alloc(ctx, &C->col, sizeof(int32_t) * (size_t)cap));
+      CB_CUDA(dev_alloc(ctx, &C->val, vsz * (size_t)cap));
     }
-    collect_times(ctx, opt, true);
+    mark(ctx, opt, 2);
+    mark(ctx, opt, 3);
+    const int bits = queue_pass(ctx, sr, dA, dB, m, C, cap, opt);
+    if (bits & CB_FUSED_ROW_TOO_LARGE) fail(ctx, CB_ERR_CUDA, "queued SpGEMM: row bound violated");
+    finish_fused(ctx, C, bits, cap, opt);
+    ctx->stats.flops = flops;
     return;
   }
 
@@ -963,6 +1074,16 @@ bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB
   } hfree{hnnz};
   std::vector<GraphWave> gw((size_t)nw);
   CB_CUDA(cudaMemsetAsync(errw.p, 0, sizeof(int64_t), ctx->stream));
+  // Rows of bounded size and width (every output row <= kQueueAcc entries,
+  // <= kQueueWidth columns): each wave is one launch of the work-queue kernel.
+  const bool queued = !(opt.flags & CB_FLAG_NO_FUSED) && max_flops <= cb::kQueueAcc &&
+                      kmax <= cb::kQueueWidth;
+  int* qstatus = nullptr;
+  if (queued) {
+    ensure_fused(ctx, max_rows);
+    qstatus = reinterpret_cast<int*>(ctx->fsync + 4);
+    CB_CUDA(cudaMemsetAsync(qstatus, 0, sizeof(int), ctx->stream));
+  }
   cb::prepare_dev_launchers(sr);  // kernel attributes are set outside the capture
   CB_CUDA(cudaStreamSynchronize(ctx->stream));
 
@@ -993,20 +1114,36 @@ bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB
     const cb_csr Aw{m, sA.ncols, 0, sA.row_ptr + r0, sA.col, sA.val};
     DevCSR dA = dev(&Aw);
     dA.rcols = rcols + r0;
-    cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream);
-    cb::launch_check_sorted(dB, counters, ctx->stream, ctx->sms);
-    cb::launch_classify_sym(dA, dB, flops, nullptr, counters, ctx->stream, ctx->sms, nullptr, sym_max);
-    cb::launch_scatter_sym(m, kmax, flops, perm_sym, nnz, counters, ctx->stream, ctx->sms, nullptr,
-                           nullptr, sym_max, dA.rcols);
-    cb::launch_symbolic_dev(dA, dB, perm_sym, counters, flops, nnz, span_counts, span_wins, wcut, wins,
-                            max_wins, ctx->stream, ctx->sms);
-    cb::launch_exclusive_scan(nnz, m, orp.as<int64_t>(), partial, ctx->stream);
-    cb::launch_classify_num(sr, m, nnz, perm_num, counters, ctx->stream, ctx->sms, nullptr, num_max);
-    cb::launch_numeric_dev(sr, dA, dB, perm_num, counters, flops, nnz, orp.as<int64_t>(),
-                           ocol.as<int32_t>(), oval.p, errw.as<int64_t>(), ctx->stream, ctx->sms,
-                           perm_sym, wins, span_counts, spans, racc, num_max);
-    // the symbolic phase's consistency word (window capacity, span cut) joins the error word
-    cb::launch_merge_error(counters + cb::kError, errw.as<int64_t>(), ctx->stream);
+    if (queued) {
+      const cudaError_t qe = cb::launch_queue_rows(sr, dA, dB, m, orp.as<int64_t>(), ocol.as<int32_t>(),
+                                                   oval.p, max_cap, ctx->fstat, ctx->fstat_cap,
+                                                   ctx->fsync, qstatus, ctx->stream, ctx->sms,
+                                                   ctx->fused_spin, ctx->fused_silent);
+      if (qe != cudaSuccess) {
+        if (!capture) {
+          ctx->err = std::string("queued SpGEMM launch: ") + cudaGetErrorString(qe);
+          throw Fail{CB_ERR_CUDA};
+        }
+        if (cap_err == cudaSuccess) cap_err = qe;
+      }
+      kernels += 1;
+    } else {
+      cudaMemsetAsync(counters, 0, sizeof(int64_t) * cb::kCounters, ctx->stream);
+      cb::launch_check_sorted(dB, counters, ctx->stream, ctx->sms);
+      cb::launch_classify_sym(dA, dB, flops, nullptr, counters, ctx->stream, ctx->sms, nullptr, sym_max);
+      cb::launch_scatter_sym(m, kmax, flops, perm_sym, nnz, counters, ctx->stream, ctx->sms, nullptr,
+                             nullptr, sym_max, dA.rcols);
+      cb::launch_symbolic_dev(dA, dB, perm_sym, counters, flops, nnz, span_counts, span_wins, wcut, wins,
+                              max_wins, ctx->stream, ctx->sms);
+      cb::launch_exclusive_scan(nnz, m, orp.as<int64_t>(), partial, ctx->stream);
+      cb::launch_classify_num(sr, m, nnz, perm_num, counters, ctx->stream, ctx->sms, nullptr, num_max);
+      cb::launch_numeric_dev(sr, dA, dB, perm_num, counters, flops, nnz, orp.as<int64_t>(),
+                             ocol.as<int32_t>(), oval.p, errw.as<int64_t>(), ctx->stream, ctx->sms,
+                             perm_sym, wins, span_counts, spans, racc, num_max);
+      // the symbolic phase's consistency word (window capacity, span cut) joins the error word
+      cb::launch_merge_error(counters + cb::kError, errw.as<int64_t>(), ctx->stream);
+      kernels += 2 + 2 + 3 + 3 + 2 + 3;
+    }
     if (opt.digests) {
       cb::launch_digest((int)value_size(sr), sr == CB_PLUS_TIMES_F64, orp.as<int64_t>(), ocol.as<int32_t>(),
                         oval.p, m, prow_dev + cut[w], cut[w + 1] - cut[w], r0, dscr.as<uint64_t>(),
@@ -1019,7 +1156,6 @@ bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB
     gw[(size_t)w] = GraphWave{&opt, wave + w, first + cut[w], first + cut[w + 1],
                               cb_csr{m, kmax, 0, orp.as<int64_t>(), ocol.as<int32_t>(), oval.p},
                               hnnz + w};
-    kernels += 2 + 2 + 3 + 3 + 2 + 3;
     if (capture) {
       cudaLaunchHostFunc(ctx->stream, graph_wave_host, &gw[(size_t)w]);
       cap_err = cudaGetLastError();
@@ -1038,10 +1174,19 @@ bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB
       }
     }
   }
+  // status bits of the work-queue kernel (all waves)
+  const auto check_queue = [&]() {
+    if (!queued) return;
+    int bits = 0;
+    CB_CUDA(cudaMemcpy(&bits, qstatus, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bits & CB_FUSED_STALLED) fail(ctx, CB_ERR_TIMEOUT, "queued SpGEMM: a row wait expired");
+    if (bits) fail(ctx, CB_ERR_CUDA, "queued SpGEMM: row bound or capacity violated");
+  };
   if (!capture) {
     int64_t err_word = 0;
     CB_CUDA(cudaMemcpy(&err_word, errw.p, sizeof(int64_t), cudaMemcpyDeviceToHost));
     if (err_word) fail(ctx, CB_ERR_CUDA, "sync-free wave: internal consistency check failed");
+    check_queue();
     for (int w = 0; w < nw; ++w) nnz_total += hnnz[w];
     for (int i = 0; i < n; ++i) flops_total += sizes[(size_t)i];
     wave += nw;
@@ -1068,6 +1213,7 @@ bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB
   int64_t err_word = 0;
   CB_CUDA(cudaMemcpy(&err_word, errw.p, sizeof(int64_t), cudaMemcpyDeviceToHost));
   if (err_word) fail(ctx, CB_ERR_CUDA, "graph wave: internal consistency check failed");
+  check_queue();
   for (int w = 0; w < nw; ++w) nnz_total += hnnz[w];
   for (int i = 0; i < n; ++i) flops_total += sizes[(size_t)i];
   wave += nw;
@@ -1362,7 +1508,8 @@ int cb_spgemm_ex(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, 
       return CB_OK;
     }
     if (opt.validate) run_validation(ctx, A, B);
-    if (opt.sizing == CB_SIZING_EXACT) spgemm_plain(ctx, (int)sr, A, dev(B), B->ncols, C, opt);
+    if (opt.sizing == CB_SIZING_EXACT)
+      spgemm_plain(ctx, (int)sr, A, dev(B), B->ncols, C, opt, nullptr, nullptr, nullptr, B->nnz);
     else spgemm_learned(ctx, (int)sr, A, dev(B), B->ncols, C, opt);
     return CB_OK;
   } catch (const Fail& f) {
@@ -1923,7 +2070,7 @@ int cb_autotune(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, c
   else cb_opts_default(&opt);
   opt.budget_bytes = 0;
   opt.validate = 0;
-  opt.flags = 0;
+  opt.flags = CB_FLAG_NO_FUSED;  // the bounds only steer the two-phase path
   const cb::Tune saved = ctx->tune;
   cb_csr C{};
   try {

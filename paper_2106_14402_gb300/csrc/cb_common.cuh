@@ -29,15 +29,19 @@ namespace cb {
 
 template <int SR> struct Sem;
 
-// Read-only cached load of a value of any semiring type: arithmetic types
-// directly, 8-byte records (cb_wlabel) as one 64-bit word.
+// Read-only cached load of a value of any semiring type: integer types
+// directly; floating-point values and 8-byte records (cb_wlabel) as their
+// bits (an unsigned word of the same size), so that every bit pattern, NaN
+// payloads included, arrives unchanged (a float load through __ldg lost NaN
+// weights of the heterogeneous semiring).
 template <class T>
 __device__ __forceinline__ T ldg_val(const T* p) {
-  if constexpr (std::is_arithmetic<T>::value) {
+  if constexpr (std::is_integral<T>::value) {
     return __ldg(p);
   } else {
-    static_assert(sizeof(T) == 8, "record values are 8 bytes");
-    const unsigned long long u = __ldg(reinterpret_cast<const unsigned long long*>(p));
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "values are 4 or 8 bytes");
+    typedef typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned>::type U;
+    const U u = __ldg(reinterpret_cast<const U*>(p));
     T r;
     memcpy(&r, &u, sizeof r);
     return r;
@@ -363,6 +367,82 @@ __device__ __forceinline__ void for_row_products(const DevCSR& A, const DevCSR& 
   }
 }
 
+// Write the column of every set bit of a bitmap in order, with coalesced
+// stores: word w < nw holds word(w), and prefix(w) set bits come before it
+// (nondecreasing in w).  Each warp takes runs of 32 consecutive words (warp
+// `warp` of `nwarps`); for the run's entries, 32 at a time, lane l finds the
+// word holding entry o by a search over the lanes' prefixes and the bit by
+// __fns, and calls store(o, w, bit).  All lanes of each warp must call it.
+template <class W, class P, class S>
+__device__ __forceinline__ void bitmap_columns_coalesced(int nw, int warp, int nwarps, W&& word_of,
+                                                         P&& prefix_of, S&& store) {
+  const int lane = threadIdx.x & 31;
+  for (int w0 = warp * 32; w0 < nw; w0 += nwarps * 32) {
+    const int w = w0 + lane;
+    const unsigned word = w < nw ? word_of(w) : 0u;
+    const int pw = w < nw ? prefix_of(w) : INT_MAX;
+    const int first = __shfl_sync(0xffffffffu, pw, 0);
+    const int total = __reduce_add_sync(0xffffffffu, __popc(word));
+    for (int s0 = 0; s0 < total; s0 += 32) {  // uniform over the warp
+      const int o = first + s0 + lane;
+      int k = 0;  // the last lane whose word starts at or before entry o
+#pragma unroll
+      for (int d = 16; d >= 1; d >>= 1) {
+        const int pk = __shfl_sync(0xffffffffu, pw, k + d);
+        if (pk <= o) k += d;
+      }
+      const unsigned wk = __shfl_sync(0xffffffffu, word, k);
+      const int pk = __shfl_sync(0xffffffffu, pw, k);
+      if (s0 + lane < total) store(o, w0 + k, (int)__fns(wk, 0, o - pk + 1));
+    }
+  }
+}
+
+// The same write-out staged through shared memory: the entries are taken
+// in chunks of `cap` (stage: int[cap]); for each chunk the words holding its
+// entries (found by a search over the prefixes) are unpacked by one thread
+// each into stage[o - chunk start] = 32 w + bit, then the chunk is stored
+// with coalesced writes by store(o, 32 w + bit).  Every word is unpacked once
+// (a word straddling two chunks twice).  All threads of the CTA must call it.
+template <class W, class P, class S>
+__device__ __forceinline__ void bitmap_columns_staged(int nw, int cnt, int* stage, int cap, W&& word_of,
+                                                      P&& prefix_of, S&& store) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int c0 = 0; c0 < cnt; c0 += cap) {
+    const int c1 = min(cnt, c0 + cap);
+    // words [wa, wb) hold the chunk's entries: the last word starting at or
+    // before c0, up to the first word starting at or after c1
+    int lo = 0, hi = nw - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix_of(mid) <= c0) lo = mid;
+      else hi = mid - 1;
+    }
+    const int wa = lo;
+    lo = wa;
+    hi = nw;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (prefix_of(mid) < c1) lo = mid + 1;
+      else hi = mid;
+    }
+    const int wb = lo;
+    for (int w = wa + tid; w < wb; w += nthr) {
+      unsigned word = word_of(w);
+      int o = prefix_of(w);
+      while (word) {
+        const int b = __ffs(word) - 1;
+        word &= word - 1;
+        if (o >= c0 && o < c1) stage[o - c0] = 32 * w + b;
+        ++o;
+      }
+    }
+    __syncthreads();
+    for (int o = c0 + tid; o < c1; o += nthr) store(o, stage[o - c0]);
+    __syncthreads();
+  }
+}
+
 // Exclusive scan of one int per thread across a team of TEAM threads.
 template <int TEAM>
 __device__ __forceinline__ int team_exclusive_scan(int x, int* scratch /* >= 33 ints */, int& total) {
@@ -616,6 +696,133 @@ __device__ __forceinline__ void for_row_products_balanced_u(const DevCSR& A, con
       }
       __syncthreads();
     }
+  }
+}
+
+// Piece-wise form for a whole CTA: the row's stored A entries are taken in
+// chunks of blockDim.x; each entry's product range (its B row, or the B
+// row's slice in [lo, hi) when `sorted` and not `whole`) is cut into pieces
+// of at most 32 * U consecutive products, the chunk's pieces are numbered
+// by one CTA scan, and every warp takes an equal contiguous run of pieces.
+// Inside a piece the A entry is the same for the whole warp and lane l
+// takes products l, l + 32, ...: no per-product bookkeeping, coalesced B
+// reads, all loads of a piece in flight before the callbacks.
+//   on_entry(p): called (warp-uniformly) when the warp reaches the pieces of
+//                A entry p; returns a token (e.g. A's value) for them;
+//   f(t, c, v):  one product: the token, column c and the value ld(q) of its
+//                B entry.
+// All threads of the CTA must call it.
+struct PieceSmem {
+  int* poff;        // [blockDim.x] first piece of each nonempty range (chunk numbering)
+  long long* q0;    // [blockDim.x] first B index of the range
+  long long* len;   // [blockDim.x] products in the range
+  int* pa;          // [blockDim.x] A entry of the range (relative to the chunk)
+  long long* scan;  // [33]
+  static constexpr size_t kBytesPerThread = sizeof(int) + 2 * sizeof(long long) + sizeof(int);
+};
+
+template <int U, class LD, class FA, class F>
+__device__ __forceinline__ void for_row_pieces(const DevCSR& A, const DevCSR& B, int64_t i,
+                                               int64_t lo, int64_t hi, bool whole, bool sorted,
+                                               const PieceSmem& sm, LD&& ld, FA&& on_entry, F&& f) {
+  typedef decltype(ld(int64_t(0))) V;
+  typedef decltype(on_entry(int64_t(0))) T;
+  constexpr int P = 32 * U;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthr = blockDim.x, nwarp = nthr >> 5;
+  const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
+  const bool filter = !whole && !sorted;
+  const unsigned width = (unsigned)(hi - lo);
+  for (int64_t c0 = a0; c0 < a1; c0 += nthr) {
+    const int nch = (int)min((int64_t)nthr, a1 - c0);
+    long long len = 0;
+    int64_t q0 = 0;
+    if (tid < nch) {
+      const int k = A.col[c0 + tid];
+      q0 = B.rp[k];
+      int64_t q1 = row_end(B, k);
+      if (!whole && sorted) {
+        const int64_t s0 = seq_lower_bound(B.col, q0, q1, lo);
+        q1 = seq_lower_bound(B.col, s0, q1, hi);
+        q0 = s0;
+      }
+      len = q1 - q0;
+    }
+    const long long np = (len + P - 1) / P;
+    // one scan numbers the pieces (high bits) and the nonempty ranges (low 11 bits)
+    long long packed_total;
+    const long long packed = cta_exclusive_scan64((np << 11) | (np > 0 ? 1 : 0), sm.scan, packed_total);
+    const long long npieces = packed_total >> 11;
+    const int ne = (int)(packed_total & 2047);
+    if (np > 0) {
+      const int slot = (int)(packed & 2047);
+      sm.poff[slot] = (int)(packed >> 11);
+      sm.q0[slot] = q0;
+      sm.len[slot] = len;
+      sm.pa[slot] = tid;
+    }
+    __syncthreads();
+    const long long k_beg = npieces * warp / nwarp, k_end = npieces * (warp + 1) / nwarp;
+    if (k_beg < k_end) {  // uniform over the warp
+      int l = 0, r = ne - 1;  // range holding piece k_beg
+      while (l < r) {
+        const int mid = (l + r + 1) >> 1;
+        if (sm.poff[mid] <= k_beg) l = mid;
+        else r = mid - 1;
+      }
+      int j = l;
+      long long pj = sm.poff[j];
+      long long nxt = j + 1 < ne ? sm.poff[j + 1] : LLONG_MAX;
+      int64_t qj = sm.q0[j];
+      long long lj = sm.len[j];
+      T tok = on_entry(c0 + sm.pa[j]);
+      // one piece: its products' columns and values in registers
+      struct Piece {
+        int n;
+        T tok;
+        int c[U];
+        V v[U];
+      };
+      const auto load = [&](long long k, Piece& pc) {
+        if (k >= nxt) {  // the next range starts here (ranges are nonempty)
+          ++j;
+          pj = nxt;
+          nxt = j + 1 < ne ? sm.poff[j + 1] : LLONG_MAX;
+          qj = sm.q0[j];
+          lj = sm.len[j];
+          tok = on_entry(c0 + sm.pa[j]);
+        }
+        const long long s0 = (k - pj) * P;
+        pc.n = (int)min((long long)P, lj - s0);
+        pc.tok = tok;
+        const int64_t qs = qj + s0;
+        const int32_t* cp = B.col + qs;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int x = u * 32 + lane;
+          pc.c[u] = 0;
+          pc.v[u] = V();
+          if (u * 32 < pc.n && x < pc.n) {
+            pc.c[u] = __ldg(cp + x);
+            pc.v[u] = ld(qs + x);
+          }
+        }
+      };
+      const auto consume = [&](const Piece& pc) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int x = u * 32 + lane;
+          if (u * 32 < pc.n && x < pc.n && (!filter || (unsigned)((int64_t)pc.c[u] - lo) < width))
+            f(pc.tok, pc.c[u], pc.v[u]);
+        }
+      };
+      for (long long k = k_beg; k < k_end; ++k) {
+        Piece cur;
+        load(k, cur);
+        consume(cur);
+      }
+    }
+    __syncthreads();
   }
 }
 

@@ -174,8 +174,11 @@ void launch_mlp_predict(const void* wb, const float* master, const float* norm, 
 // One-launch SpGEMM for products whose rows are all small (k_fused.cu):
 // every row of A holds at most `lanes` entries and every output row at most
 // 8 * lanes products (lanes = 8, 16 or 32), columns below fused_max_cols.
-// tstat holds at least fused_tiles(lanes, A.nrows) words and sync two words,
+// tstat holds at least fused_tiles(lanes, A.nrows) words and sync 16 words,
 // all zero when first used; they must not be shared by launches in flight.
+// sync: [0] launch epoch, [1] finished CTAs, [2..3] nnz(C) of the last
+// launch (int64), [6..7] its product count, [8..9] the product accumulator;
+// words 4 and 5 are free for the caller (the context keeps a status there).
 // SpMSpV steps (k_spmspv.cu): 0 SPA init over n, 1 chunk counts of the x
 // entries (bad indices set *err), 2 push into the SPA (cpre = scanned chunk
 // counts, cpre[nx] = total), 3 popcounts of the touched bitmap, 4 compaction
@@ -232,6 +235,18 @@ int64_t fused_max_cols(int lanes);
 // publishes anyway.  silent_tile >= 0 (fault injection) is a tile that
 // never publishes its total.
 constexpr unsigned kFusedSpinDefault = 1u << 20;
+// One-pass rows from a device work queue (k_queue.cu): every row of A.B with
+// at most kQueueAcc entries and an output width (B's columns, or A.rcols[i])
+// of at most kQueueWidth; one CTA per row at a time, rows dequeued in order,
+// offsets by look-back.  Shares the one-launch kernel's tile-status array
+// (one word per row, tstat_cap >= m) and sync words (its queue counter at
+// words 10..11; nnz(C) at 2..3 as there); status gets CB_FUSED_* bits.
+constexpr int kQueueAcc = 4096;
+constexpr int64_t kQueueWidth = 65536;
+cudaError_t launch_queue_rows(int sr, const DevCSR& A, const DevCSR& B, int64_t m, int64_t* Crp,
+                              int32_t* Ccol, void* Cval, int64_t cap, unsigned long long* tstat,
+                              int64_t tstat_cap, unsigned* sync, int* status, cudaStream_t s, int sms,
+                              unsigned spin_limit = kFusedSpinDefault, int64_t silent_row = -1);
 cudaError_t launch_fused(int sr, int lanes, const DevCSR& A, const DevCSR& B, int64_t* Crp,
                          int32_t* Ccol, void* Cval, int64_t cap, unsigned long long* tstat,
                          int64_t tstat_cap, unsigned* sync, int* status, cudaStream_t s, int sms,

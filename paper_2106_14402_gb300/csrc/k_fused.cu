@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
   __shared__ __align__(16) Acc sval[kFWarps][32 * kFE];
   __shared__ __align__(16) unsigned skey[kFWarps][32 * kFE];
   __shared__ int snz[TR];
+  __shared__ int sfl[TR];  // products of each row of the tile
   __shared__ long long soff[TR];
   __shared__ long long s_red[kFWarps];
   __shared__ int s_min[kFWarps];
@@ -301,7 +302,10 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
         }
       }
     }
-    if (g == 0) snz[warp * RPW + grp] = bad ? 0 : nz;
+    if (g == 0) {
+      snz[warp * RPW + grp] = bad ? 0 : nz;
+      sfl[warp * RPW + grp] = Fr;
+    }
     if (bad && g == 0 && i < A.nrows) atomicOr(status, CB_FUSED_ROW_TOO_LARGE);
     if (threadIdx.x == 0 && tile == blockIdx.x) s_epoch = epoch0;
     __syncthreads();
@@ -318,6 +322,9 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
       }
       if (lane < TR) soff[lane] = inc - v;
       const int agg = __shfl_sync(kFull, inc, 31);
+      // the tile's product count joins the launch's total (sync[8..9])
+      const int tf = __reduce_add_sync(kFull, lane < TR ? sfl[lane] : 0);
+      if (lane == 0 && tf) atomicAdd(reinterpret_cast<unsigned long long*>(sync + 8), (unsigned long long)tf);
       if (lane == 0) {
         s_red[0] = agg;
         if (tile != silent_tile)  // fault injection: a producer that never publishes
@@ -377,7 +384,10 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
     if (threadIdx.x < TR) {
       const int64_t ir = tile * TR + threadIdx.x;
       if (ir < A.nrows) Crp[ir] = base + soff[threadIdx.x];
-      if (ir == A.nrows - 1) Crp[A.nrows] = base + agg;
+      if (ir == A.nrows - 1) {
+        Crp[A.nrows] = base + agg;
+        __threadfence();  // before this CTA counts itself finished
+      }
     }
     if (base + agg > cap) {
       if (threadIdx.x == 0) atomicOr(status, CB_FUSED_CAPACITY);
@@ -406,6 +416,14 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
   }
   __syncthreads();
   if (s_last) {
+    // totals of the launch for the host: nnz(C) (sync[2..3]) and the
+    // product count (sync[6..7]); the product accumulator restarts at 0
+    if (threadIdx.x == 0) {
+      __threadfence();
+      unsigned long long* s64 = reinterpret_cast<unsigned long long*>(sync);
+      s64[1] = (unsigned long long)*reinterpret_cast<volatile int64_t*>(Crp + A.nrows);
+      s64[3] = atomicExch(s64 + 4, 0ull);
+    }
     const unsigned ne = (s_epoch + 1) & kEpochMask;
     if (ne == 0)
       for (int64_t j = threadIdx.x; j < tstat_cap; j += kFThreads) tstat[j] = 0;

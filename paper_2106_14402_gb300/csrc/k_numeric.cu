@@ -9,11 +9,15 @@
 //   after accumulation the team compacts the occupied slots, bitonic-sorts
 //   them by column in shared memory and writes the row with coalesced stores.
 //   * heavier:    rank windows (cut by the symbolic phase).  One CTA per
-//                 window rebuilds the window's column bitmap from the row's
-//                 product stream, prefix-counts it, and accumulates each
-//                 product at its column's rank in a dense shared-memory array;
-//                 the window then reads out in column order without a sort.
-// Products are combined with the semiring's atomic (+) on shared memory.
+//                 window takes the window's column bitmap (stored by the
+//                 symbolic phase, or rebuilt from the row's products),
+//                 prefix-counts it, and accumulates each product at its
+//                 column's rank in a dense array (shared memory for 4-byte
+//                 accumulators, a per-CTA slice in L2 for 8-byte ones); the
+//                 window then reads out in column order without a sort.  The
+//                 products are walked in pieces of 128 consecutive products
+//                 of one B row per warp (for_row_pieces).
+// Products are combined with the semiring's atomic (+).
 #include "cb_common.cuh"
 #include "cb_kernels.h"
 
@@ -170,6 +174,11 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
 // row's products), prefix-count its words, then accumulate every product
 // into the dense accumulator at its column's rank and write the window's
 // slice of the row in column order.
+// How a window's column indices are written: 0 each thread its words' bits
+// in turn, 1 coalesced with a warp search per entry, 2 staged through
+// shared memory then coalesced.
+constexpr int kRankColumns = 2;
+
 template <int SR, int CTA>
 __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B, const int32_t* heavy_rows,
                                                       const Window* wins, int64_t n_wins,
@@ -206,8 +215,8 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
   long long* bal = reinterpret_cast<long long*>(bp + kSpanWords);
   __shared__ int scratch[33];
   __shared__ long long scan64[33];
-  __shared__ int iscan[33];
-  const BalancedSmem sm{bal, bal + CTA, reinterpret_cast<int*>(bal + 2 * CTA), scan64, iscan};
+  const PieceSmem sm{reinterpret_cast<int*>(bal + 2 * CTA), bal, bal + CTA,
+                     reinterpret_cast<int*>(bal + 2 * CTA) + CTA, scan64};
   __shared__ long long s_base;
   const int tid = threadIdx.x, lane = tid & 31;
   const TA* Aval = reinterpret_cast<const TA*>(A.val);
@@ -242,12 +251,12 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
     __syncthreads();
 
     if (!hbits) {  // pass 1: rebuild the window's columns
-      for_row_products_balanced(A, B, i, lo, hi, whole, b_sorted != 0, sm,
-                                [&](int64_t, int64_t, int c) {
-                                  const unsigned off = (unsigned)((int64_t)c - lo);
-                                  const unsigned bit = 1u << (off & 31);
-                                  if (!(bp[off >> 5].x & bit)) atomicOr(&bp[off >> 5].x, bit);
-                                });
+      for_row_pieces<2>(A, B, i, lo, hi, whole, b_sorted != 0, sm, [](int64_t) { return 0; },
+                               [](int64_t) { return 0; }, [&](int, int c, int) {
+                          const unsigned off = (unsigned)((int64_t)c - lo);
+                          const unsigned bit = 1u << (off & 31);
+                          if (!(bp[off >> 5].x & bit)) atomicOr(&bp[off >> 5].x, bit);
+                        });
       __syncthreads();
     }
     // exclusive prefix of word popcounts
@@ -271,36 +280,46 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
       if (tid == 0 && total != wd.count) flag_error(err, 23);
     }
     __syncthreads();
-    // pass 2: accumulate at the rank of each product's column (two warp
-    // steps per iteration, B columns and values loaded before the atomics)
-    int64_t p_last = -1;  // the lane's last A entry and its value
-    TA a_last = TA();
-    for_row_products_balanced_u<2>(A, B, i, lo, hi, whole, b_sorted != 0, sm,
-                                   [&](int64_t q) { return ldg_val(Bval + q); },
-                                   [&](int64_t p, int64_t, int c, TB bv) {
-                                     const unsigned off = (unsigned)((int64_t)c - lo);
-                                     const uint2 e = bp[off >> 5];
-                                     const int slot = (int)e.y + __popc(e.x & ((1u << (off & 31)) - 1u));
-                                     if (S::kUsesA && p != p_last) {
-                                       p_last = p;
-                                       a_last = ldg_val(Aval + p);
-                                     }
-                                     if (slot < cnt) S::atomic(&wacc[slot], S::mul(a_last, bv));
-                                   });
+    // pass 2: accumulate at the rank of each product's column (pieces of
+    // 128 products of one B row per warp, loads first, then the atomics)
+    const unsigned lo32 = (unsigned)lo;
+    for_row_pieces<4>(A, B, i, lo, hi, whole, b_sorted != 0, sm,
+                      [&](int64_t q) { return ldg_val(Bval + q); },
+                      [&](int64_t p) { return S::kUsesA ? ldg_val(Aval + p) : TA(); },
+                      [&](TA a_cur, int c, TB bv) {
+                        const unsigned off = (unsigned)c - lo32;
+                        const uint2 e = bp[off >> 5];
+                        const int slot = (int)e.y + __popc(e.x & ((1u << (off & 31)) - 1u));
+                        if (slot < cnt) S::atomic(&wacc[slot], S::mul(a_cur, bv));
+                      });
     __syncthreads();
     // write the window: values by slot (coalesced), columns by word
     const int64_t out = Crp[i] + s_base;
     const int64_t row_end = Crp[i + 1];
     for (int t = tid; t < cnt; t += CTA)
       if (out + t < row_end) Cval[out + t] = S::out(kL2 ? __ldcg(wacc + t) : wacc[t]);
-    for (int w = tid; w < nw; w += CTA) {
-      unsigned word = bp[w].x;
-      int64_t o = out + bp[w].y;
-      while (word) {
-        const int b = __ffs(word) - 1;
-        word &= word - 1;
-        if (o < row_end) Ccol[o] = (int32_t)(lo + 32 * w + b);
-        ++o;
+    if constexpr (kRankColumns == 2) {  // staged in the (now free) piece scratch
+      bitmap_columns_staged(nw, cnt, reinterpret_cast<int*>(bal),
+                            (int)(CTA * PieceSmem::kBytesPerThread / sizeof(int)),
+                            [&](int w) { return bp[w].x; }, [&](int w) { return (int)bp[w].y; },
+                            [&](int o, int v) {
+                              if (out + o < row_end) Ccol[out + o] = (int32_t)(lo + v);
+                            });
+    } else if constexpr (kRankColumns == 1) {
+      bitmap_columns_coalesced(nw, tid >> 5, CTA / 32, [&](int w) { return bp[w].x; },
+                               [&](int w) { return (int)bp[w].y; }, [&](int o, int w, int b) {
+                                 if (out + o < row_end) Ccol[out + o] = (int32_t)(lo + 32 * w + b);
+                               });
+    } else {
+      for (int w = tid; w < nw; w += CTA) {
+        unsigned word = bp[w].x;
+        int64_t o = out + bp[w].y;
+        while (word) {
+          const int b = __ffs(word) - 1;
+          word &= word - 1;
+          if (o < row_end) Ccol[o] = (int32_t)(lo + 32 * w + b);
+          ++o;
+        }
       }
     }
     __syncthreads();
@@ -356,8 +375,7 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
     constexpr int CTA = NumLimits<SR>::kL2Acc ? 512 : 1024;
     constexpr int PER_SM = 1024 / CTA;
     constexpr size_t smem = (NumLimits<SR>::kL2Acc ? 0 : NumLimits<SR>::kWcap * sizeof(Acc)) +
-                            2 * kSpanWords * sizeof(unsigned) + 2 * CTA * sizeof(long long) +
-                            CTA * sizeof(int);
+                            2 * kSpanWords * sizeof(unsigned) + CTA * PieceSmem::kBytesPerThread;
     set_smem(k_num_rank<SR, CTA>, smem);
     k_num_rank<SR, CTA><<<capped(n_wins, (int64_t)sms * PER_SM), CTA, smem, s>>>(
         A, B, heavy_rows, wins, n_wins, span_counts, spans, hbits, b_sorted, flops, nnz, Crp, Ccol,
@@ -400,8 +418,7 @@ void numeric_dev_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const
     constexpr int CTA = NumLimits<SR>::kL2Acc ? 512 : 1024;
     constexpr int PER_SM = 1024 / CTA;
     constexpr size_t smem = (NumLimits<SR>::kL2Acc ? 0 : NumLimits<SR>::kWcap * sizeof(Acc)) +
-                            2 * kSpanWords * sizeof(unsigned) + 2 * CTA * sizeof(long long) +
-                            CTA * sizeof(int);
+                            2 * kSpanWords * sizeof(unsigned) + CTA * PieceSmem::kBytesPerThread;
     k_num_rank<SR, CTA><<<sms * PER_SM, CTA, smem, s>>>(
         A, B, perm_sym, wins, 0, span_counts, spans, nullptr, 0, flops, nnz, Crp, Ccol, Cval, err,
         num_hash_max, static_cast<Acc*>(racc), counters);
@@ -522,8 +539,7 @@ void prepare_numeric_dev_sr() {
   set_smem(k_num_hash<SR, CTA, TEAM, TBL>, TBL * (sizeof(Acc) + sizeof(int)));
   constexpr int RCTA = NumLimits<SR>::kL2Acc ? 512 : 1024;
   constexpr size_t rsmem = (NumLimits<SR>::kL2Acc ? 0 : NumLimits<SR>::kWcap * sizeof(Acc)) +
-                           2 * kSpanWords * sizeof(unsigned) + 2 * RCTA * sizeof(long long) +
-                           RCTA * sizeof(int);
+                           2 * kSpanWords * sizeof(unsigned) + RCTA * PieceSmem::kBytesPerThread;
   set_smem(k_num_rank<SR, RCTA>, rsmem);
 }
 

@@ -86,7 +86,6 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
   extern __shared__ __align__(16) unsigned sym_bm[];
   __shared__ int scratch[33];
   __shared__ long long scan64[33];
-  __shared__ int iscan[33];
   __shared__ int wstart[kMaxWindowsPerSpan];
   __shared__ int wrank[kMaxWindowsPerSpan];
   __shared__ long long wbase;
@@ -100,7 +99,8 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
   const int64_t units = n_heavy * spans;
   const int bm_words = (int)min((int64_t)kSpanWords, (B.ncols + 31) / 32);
   long long* bal = reinterpret_cast<long long*>(sym_bm + ((bm_words + 3) & ~3));
-  const BalancedSmem sm{bal, bal + 1024, reinterpret_cast<int*>(bal + 2048), scan64, iscan};
+  const PieceSmem sm{reinterpret_cast<int*>(bal + 2048), bal, bal + 1024,
+                     reinterpret_cast<int*>(bal + 2048) + 1024, scan64};
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int64_t h = u / spans, sp = u - h * spans;
     const int i = heavy_rows[h];
@@ -116,13 +116,13 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
     const int nwords = (int)((hi - lo + 31) / 32);
     for (int w = tid; w < nwords; w += 1024) sym_bm[w] = 0u;
     __syncthreads();
-    for_row_products_balanced_u<2>(A, B, i, lo, hi, spans == 1 && !B.filter, b_sorted != 0, sm,
-                                   [](int64_t) { return 0; },
-                                   [&](int64_t, int64_t, int c, int) {
-                                     const unsigned off = (unsigned)((int64_t)c - lo);
-                                     const unsigned bit = 1u << (off & 31);
-                                     if (!(sym_bm[off >> 5] & bit)) atomicOr(&sym_bm[off >> 5], bit);
-                                   });
+    const unsigned lo32 = (unsigned)lo;
+    for_row_pieces<4>(A, B, i, lo, hi, spans == 1 && !B.filter, b_sorted != 0, sm,
+                             [](int64_t) { return 0; }, [](int64_t) { return 0; }, [&](int, int c, int) {
+                        const unsigned off = (unsigned)c - lo32;
+                        const unsigned bit = 1u << (off & 31);
+                        if (!(sym_bm[off >> 5] & bit)) atomicOr(&sym_bm[off >> 5], bit);
+                      });
     __syncthreads();
     if (hbits) {
       unsigned* dst = hbits + (size_t)(h * spans + sp) * kSpanWords;
@@ -236,8 +236,7 @@ void launch_check_sorted(const DevCSR& B, int64_t* counters, cudaStream_t s, int
 void prepare_symbolic_dev() {
   constexpr int CTA = 512, TEAM = 512, TBL = 2 * kSymLargeMax;
   set_smem(k_sym_hash<CTA, TEAM, TBL>, TBL * sizeof(int));
-  set_smem(k_sym_bitmap, (size_t)kSpanWords * sizeof(unsigned) + 2 * 1024 * sizeof(long long) +
-                             1024 * sizeof(int));
+  set_smem(k_sym_bitmap, (size_t)kSpanWords * sizeof(unsigned) + 1024 * PieceSmem::kBytesPerThread);
 }
 
 void launch_symbolic_dev(const DevCSR& A, const DevCSR& B, const int32_t* perm, int64_t* counters,
@@ -249,8 +248,7 @@ void launch_symbolic_dev(const DevCSR& A, const DevCSR& B, const int32_t* perm, 
     const int64_t spans = (B.ncols + kSpanCols - 1) / kSpanCols;
     const int64_t width = B.ncols < kSpanCols ? B.ncols : kSpanCols;
     const size_t bm_words = (size_t)((width + 31) / 32);
-    const size_t smem = ((bm_words + 3) & ~(size_t)3) * sizeof(unsigned) + 2 * 1024 * sizeof(long long) +
-                        1024 * sizeof(int);
+    const size_t smem = ((bm_words + 3) & ~(size_t)3) * sizeof(unsigned) + 1024 * PieceSmem::kBytesPerThread;
     k_sym_bitmap<<<sms * 2, 1024, smem, s>>>(A, B, perm, 0, spans, flops, wcut, nnz, span_counts,
                                              span_wins, wins, win_cap, nullptr, -1, counters);
   }
@@ -305,8 +303,7 @@ void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,
     const int64_t spans = (B.ncols + kSpanCols - 1) / kSpanCols;
     const int64_t width = B.ncols < kSpanCols ? B.ncols : kSpanCols;
     const size_t bm_words = (size_t)((width + 31) / 32);
-    const size_t smem = ((bm_words + 3) & ~(size_t)3) * sizeof(unsigned) + 2 * 1024 * sizeof(long long) +
-                        1024 * sizeof(int);
+    const size_t smem = ((bm_words + 3) & ~(size_t)3) * sizeof(unsigned) + 1024 * PieceSmem::kBytesPerThread;
     set_smem(k_sym_bitmap, smem);
     k_sym_bitmap<<<capped(seg_count[kSymHeavy] * spans, (int64_t)sms * 2), 1024, smem, s>>>(
         A, B, perm + seg_begin[kSymHeavy], seg_count[kSymHeavy], spans, flops, wcut, nnz,

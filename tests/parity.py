@@ -120,8 +120,27 @@ def digest(sr, rp, col, val):
         V = None
         if f64:
             w = 1.0 + (_sm64(hr ^ c) >> _U(11)).astype(np.float64) * 2.0 ** -53
-            V = math.fsum((np.asarray(val, dtype=np.float64) * w).tolist())
+            V = exact_sum(np.asarray(val, dtype=np.float64) * w)
     return int(d), V
+
+
+def exact_sum(x):
+    """The sum of a float64 array, rounded once (up to a few ulps of |sum| in
+    total): a pairwise tree whose every addition's rounding error is kept
+    (TwoSum, Knuth) and summed separately, the level sums then combined by
+    math.fsum."""
+    import math
+    x = np.asarray(x, dtype=np.float64)
+    parts = []
+    while x.size > 1:
+        if x.size % 2:
+            x = np.append(x, 0.0)
+        a, b = x[0::2], x[1::2]
+        s = a + b
+        bb = s - a
+        parts.append(float(np.sum((a - (s - bb)) + (b - bb))))
+        x = s
+    return math.fsum(([float(x[0])] if x.size else []) + parts)
 
 
 def digest_words(dig, i):
@@ -132,6 +151,7 @@ def digest_words(dig, i):
 
 
 # |V_gpu - V_ref| <= (2 * 1e-12 + 40 u) * sum of the oracle's |a b| sums: each
-# entry is within 1e-12 sum|ab| (R4) and weighted by w < 2, plus the rounding
-# of the weighted terms and of both summations (<= 16 u sum|v w| on the device).
+# entry is within 1e-12 sum|ab| (R4) and weighted by w < 2 (so |v w| <= 2
+# sum|ab|), plus the rounding of the weighted terms (u each side), of the
+# device's compensated sum (<= 16 u sum|v w|) and of exact_sum (a few u |V|).
 CHECKSUM_TOL = 2 * FP64_TOL + 40 * 2.0 ** -53

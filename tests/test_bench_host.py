@@ -31,6 +31,17 @@ def test_compulsory_bytes_counts_each_operand_once():
     assert bench.compulsory_bytes("maxw_label", A, B, nnz_c, 3) == a + b + c
 
 
-def test_traffic_figure_is_read_from_the_profile_summary():
-    t = bench.fp64_traffic_per_product()
-    assert t is not None and 3.0 < t < 8.0
+def test_traffic_figure_holds_only_for_the_captured_kernel_sources(tmp_path, monkeypatch):
+    """profiles/traffic.json's figure is used only while the numeric kernels'
+    sources are the ones it was captured from."""
+    import json
+    path = tmp_path / "traffic.json"
+    monkeypatch.setattr(bench, "TRAFFIC_JSON", str(path))
+    assert bench.fp64_traffic_per_product() == (None, "no traffic capture")
+    path.write_text(json.dumps({"fp64_numeric_bytes_per_product": 4.5, "capture": "s16",
+                                "sources_digest": bench.sources_digest()}))
+    assert bench.fp64_traffic_per_product() == (4.5, "s16")
+    path.write_text(json.dumps({"fp64_numeric_bytes_per_product": 4.5, "capture": "s16",
+                                "sources_digest": "0" * 16}))
+    t, why = bench.fp64_traffic_per_product()
+    assert t is None and "changed" in why

@@ -52,6 +52,7 @@ class Workload:
         self._host = {}
         self._full = {}
         self._rows = {}
+        self._dig = {}
         self.digests = {}   # mode -> host int64 array of 2 * COUNT words
 
     def host(self, i):
@@ -65,6 +66,14 @@ class Workload:
             A, B = self.host(i)
             self._full[i] = oracle.spgemm(self.plan[i]["semiring"], A, B)
         return self._full[i]
+
+    def digest(self, i):
+        """The oracle's digest words of product i, and the sum of its |a b| sums."""
+        if i not in self._dig:
+            rp, col, val, absum = self.full(i)
+            d0, V = digest(self.plan[i]["semiring"], rp, col, val)
+            self._dig[i] = (d0, V, float(absum.sum()))
+        return self._dig[i]
 
     def sample_rows(self, i):
         n = self.plan[i]["n"]
@@ -160,12 +169,11 @@ def run_mode(cb, work, mode, sizing, model):
 
 def check_digest(work, i, words):
     sr = work.plan[i]["semiring"]
-    rp, col, val, absum = work.full(i)
-    d0, V = digest(sr, rp, col, val)
+    d0, V, abs_total = work.digest(i)
     g0, gv = digest_words(words, i)
     assert g0 == d0, f"product {i}: digest {g0:#x} != oracle {d0:#x}"
     if sr == "plus_times_f64":
-        tol = CHECKSUM_TOL * float(absum.sum())
+        tol = CHECKSUM_TOL * abs_total
         assert abs(gv - V) <= tol, f"product {i}: checksum {gv!r} vs oracle {V!r} (tol {tol:.3g})"
 
 

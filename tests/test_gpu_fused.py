@@ -229,7 +229,53 @@ def test_automatic_branch_matches_two_phase(cb, sr):
     k1 = ctx.stats()["kernels"]
     C2 = cb.spgemm(sr, dA, dB, fused=False)
     k2 = ctx.stats()["kernels"]
-    assert k1 == 6 and k2 > k1
+    # the operands' mean row lengths fit 8 lanes, so the one-launch kernel is
+    # tried first; rows of 16 entries exceed them and the call falls back to
+    # the classified path: validation (2) + the tried launch (1) + sortedness,
+    # flops and binning (3) + the one-launch kernel at 16 lanes (1)
+    assert k1 == 7 and k2 > k1
     want = oracle.spgemm(sr, A, B)
     compare_rows(sr, C1.to_host(), want)
     compare_rows(sr, C2.to_host(), want)
+
+
+def test_speculative_launch_falls_back_on_one_large_row(cb):
+    """Mean row lengths small enough for 8 lanes, but one dense row of A
+    (300 entries): the speculative one-launch pass reports it, nothing of its
+    output is kept, and the classified path computes the exact product."""
+    sr = "plus_times_i64"
+    (_, A, _), = gen.er_square(n=2048, deg=4, cfg=81)
+    rng = np.random.default_rng(82)
+    dense = np.sort(rng.choice(2048, 300, replace=False)).astype(np.int32)
+    rp = A.row_ptr.copy()
+    col = np.concatenate([A.col[:rp[5]], dense, A.col[rp[6]:]])
+    rp[6:] += 300 - (rp[6] - rp[5])
+    M = gen.CSR(2048, 2048, rp, col)
+    M = M.with_values(gen.random_values(sr, M.nnz, 83))
+    dM = cb.DeviceCSR.from_host(M, sr)
+    ctx = cb.context()
+    C = cb.spgemm(sr, dM, dM, ctx=ctx)
+    assert ctx.stats()["kernels"] > 3
+    compare_rows(sr, C.to_host(), oracle.spgemm(sr, M, M))
+
+
+def test_speculative_launch_into_caller_buffers(cb):
+    """Exact-degree ER: the speculative pass alone forms C (validation + one
+    launch), into caller buffers; a buffer one entry short is reported as a
+    capacity error."""
+    (sr, A, _), = gen.er_square(n=4096, deg=8, cfg=84)
+    dA = cb.DeviceCSR.from_host(A, sr)
+    want = oracle.spgemm(sr, A, A)
+    nnz = int(want[0][-1])
+    ctx = cb.context()
+    out = cb.DeviceCSR(A.nrows, A.ncols, torch.empty(A.nrows + 1, dtype=torch.int64, device="cuda"),
+                       torch.empty(nnz, dtype=torch.int32, device="cuda"),
+                       torch.empty(nnz, dtype=torch.int64, device="cuda"))
+    C = cb.spgemm(sr, dA, dA, out=out, ctx=ctx)
+    st = ctx.stats()
+    assert st["kernels"] == 3 and st["nnz"] == nnz and st["flops"] == A.nrows * 64
+    compare_rows(sr, C.to_host(), want)
+    short = cb.DeviceCSR(A.nrows, A.ncols, out.row_ptr, out.col[:nnz - 1], out.val[:nnz - 1])
+    with pytest.raises(cb.CBError) as e:
+        cb.spgemm(sr, dA, dA, out=short, ctx=ctx)
+    assert e.value.code == 9

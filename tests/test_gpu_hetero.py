@@ -78,6 +78,29 @@ def test_duplicates_unsorted_and_special_weights(cb, fused):
     parity(cb, A, B, fused=fused)
 
 
+SPECIAL = np.concatenate([np.array([-0.0, 0.0, np.inf, -np.inf, 0.5, -0.5, 1e-45], np.float32),
+                          np.array([0x7FC00000, 0xFFC00000, 0x7F800001, 0xFFFFFFFF],
+                                   np.uint32).view(np.float32)])
+
+
+@pytest.mark.parametrize("case", ["one_launch", "queue", "rank_windows"])
+def test_special_weights_on_every_path(cb, case):
+    """NaN payloads, infinities and signed zeros as weights through the
+    one-launch kernel (ER, 8 per row), the work-queue kernel (ER rows of 40
+    entries) and the hash tiers plus rank windows (R-MAT scale 12)."""
+    if case == "one_launch":
+        P = gen.er_exact(4096, 4096, 8, gen.subseed(90, 0))
+    elif case == "queue":
+        P = gen.er_exact(3000, 3000, 40, gen.subseed(90, 1))
+    else:
+        P = gen.rmat(12, 16, *gen.RMAT_ABCD, seed=gen.subseed(90, 2))
+    A = P.with_values(SPECIAL[np.random.default_rng(91).integers(0, SPECIAL.size, P.nnz)])
+    B = labels(P, 92, hi=6)
+    got = parity(cb, A, B)
+    if case == "rank_windows":
+        assert np.diff(got[0]).max() > 512
+
+
 @pytest.mark.parametrize("fused", [True, False])
 def test_er_small_rows(cb, fused):
     P = gen.er_exact(16384, 16384, 8, gen.subseed(60, 0))

@@ -5,7 +5,7 @@ import math
 
 import numpy as np
 
-from parity import _sm64, digest, digest_words
+from parity import _sm64, digest, digest_words, exact_sum
 
 
 def _case():
@@ -58,3 +58,12 @@ def test_fp64_digest_is_the_pattern_plus_a_weighted_checksum():
 def test_digest_words_reads_raw_bits():
     words = np.array([-1, np.float64(2.5).view(np.int64)], np.int64)
     assert digest_words(words, 0) == (2 ** 64 - 1, 2.5)
+
+
+def test_exact_sum_is_correctly_rounded_where_plain_sums_are_not():
+    rng = np.random.default_rng(7)
+    x = np.concatenate([rng.standard_normal(100_001) * 10.0 ** rng.integers(-8, 8, 100_001),
+                        [1e16, -1e16, 3.0]])
+    assert exact_sum(x) == math.fsum(x.tolist())
+    assert exact_sum(np.array([1e16, 1.0, -1e16])) == 1.0 != np.sum(np.array([1e16, 1.0, -1e16]))
+    assert exact_sum(np.zeros(0)) == 0.0
