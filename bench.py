@@ -231,11 +231,13 @@ def sampled_parity(dprob, kept):
         g_rp = C.row_ptr[:A.nrows + 1].cpu().numpy()
         idx = np.concatenate([np.arange(g_rp[r], g_rp[r + 1]) for r in rows]) if len(rows) else \
             np.zeros(0, np.int64)
-        it = __import__("torch").as_tensor(idx, device=C.col.device)
+        torch = __import__("torch")
+        it = torch.as_tensor(idx, device=C.col.device)
         g_col = C.col[it].cpu().numpy()
-        v = C.val[it]
-        g_val = v.view(__import__("torch").int32).cpu().numpy().view(np.uint32) \
-            if str(v.dtype) == "torch.uint32" else v.cpu().numpy()
+        if C.val.dtype == torch.uint32:  # no indexing kernels for uint32: go through int32
+            g_val = C.val.view(torch.int32)[it].cpu().numpy().view(np.uint32)
+        else:
+            g_val = C.val[it].cpu().numpy()
         same = bool(np.array_equal(np.diff(g_rp)[rows], np.diff(w_rp)) and np.array_equal(g_col, w_col))
         rec = {"rows": int(len(rows)), "entries": int(idx.size), "pattern_equal": same}
         if sr == "plus_times_f64":
@@ -1050,9 +1052,20 @@ def main():
     ap.add_argument("--no-full", action="store_true", help="skip the memory-constrained R-MAT workloads")
     ap.add_argument("--multi-count", type=int, default=4096)
     ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--multi-only", action="store_true",
+                    help="time only the batched leg (--multi-count products) and print its record")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.multi_only:
+        import torch
+
+        from paper_2106_14402_gb300 import cb
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        cb.load()
+        model, _ = load_sizer(cb)
+        print(json.dumps({"multi_spgemm": run_multi(args, cb, cb.context(), model)}), flush=True)
+        return 0
     return main_gpu(args)
 
 

@@ -350,8 +350,18 @@ int cb_exclusive_scan_noalloc(const int64_t *in, int64_t n, int64_t *out, void *
  *                 in-row sort, the rest in rank windows (sym_hash_max..4096,
  *                 default 512);
  *   learn_max     with learned or upper-bound sizing, rows whose capacity is
- *                 <= this skip the symbolic phase (0..8192, default 512).
- * cb_ctx_set_tune clamps the values into range (and writes back what it set).
+ *                 <= this skip the symbolic phase (0..8192, default 512);
+ *   cf_esc, cf_prereduce  the accumulator of a hash-tier row by its
+ *                 compression ratio cf = flops_i / nnz(C_i) (paper Sec. 4.1:
+ *                 hash for high compression, merging for low, chosen per
+ *                 line): cf <= cf_esc expands the products into the table in
+ *                 arrival order, sorts them and combines each column's run
+ *                 (0..2, default 1.25; 0 = never); cf >= cf_prereduce combines
+ *                 the products of each warp step that share a column before
+ *                 the hash probe (>= 1, default 4; 1e30 = never); otherwise
+ *                 one hash probe per product.
+ * cb_ctx_set_tune clamps the values into range (and writes back what it set);
+ * cb_autotune tries the compression-ratio bounds after the tier bounds.
  * cb_autotune times cb_spgemm_ex-equivalent runs of A.B on the two-phase
  * path (the bounds steer only that path; the one-launch and work-queue
  * kernels are left out) under a grid of
@@ -360,6 +370,7 @@ int cb_exclusive_scan_noalloc(const int64_t *in, int64_t n, int64_t *out, void *
  * own output and synchronises the stream. */
 typedef struct {
   int32_t sym_hash_max, num_hash_max, learn_max;
+  float cf_esc, cf_prereduce;
 } cb_tune;
 int cb_ctx_set_tune(cb_ctx *ctx, cb_tune *tune);
 int cb_ctx_get_tune(const cb_ctx *ctx, cb_tune *tune);

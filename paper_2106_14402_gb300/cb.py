@@ -67,7 +67,8 @@ class cb_opts(ctypes.Structure):
 
 class cb_tune(ctypes.Structure):
     _fields_ = [("sym_hash_max", ctypes.c_int32), ("num_hash_max", ctypes.c_int32),
-                ("learn_max", ctypes.c_int32)]
+                ("learn_max", ctypes.c_int32), ("cf_esc", ctypes.c_float),
+                ("cf_prereduce", ctypes.c_float)]
 
 
 class cb_stats(ctypes.Structure):
@@ -308,8 +309,9 @@ class Context:
         if rc != 0:
             raise CBError(rc, self.error())
 
-    def set_tune(self, sym_hash_max=512, num_hash_max=512, learn_max=512) -> dict:
-        t = cb_tune(sym_hash_max, num_hash_max, learn_max)
+    def set_tune(self, sym_hash_max=512, num_hash_max=512, learn_max=512, cf_esc=1.25,
+                 cf_prereduce=4.0) -> dict:
+        t = cb_tune(sym_hash_max, num_hash_max, learn_max, cf_esc, cf_prereduce)
         self.check(self.lib.cb_ctx_set_tune(self.handle, ctypes.byref(t)))
         return {k: getattr(t, k) for k, _ in cb_tune._fields_}
 

@@ -569,7 +569,8 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
   mark(ctx, opt, 4);
   cb::launch_numeric(sr, dA, dB, perm_num, num_beg, num_cnt, flops, nnz, heavy_rows, wins,
                      n_units, span_counts, spans, hbits, b_sorted, C->row_ptr, C->col, C->val,
-                     counters + cb::kError, ctx->stream, ctx->sms, &launches, num_hash_max, racc);
+                     counters + cb::kError, ctx->stream, ctx->sms, &launches, num_hash_max, racc,
+                     cb::CfBounds{ctx->tune.cf_esc, ctx->tune.cf_pre});
   CB_LAUNCHED();
   mark(ctx, opt, 5);
   ctx->stats.kernels += launches;
@@ -1139,7 +1140,8 @@ bool batched_group_graph(cb_ctx* ctx, int sr, const cb_csr& sA, const DevCSR& dB
       cb::launch_classify_num(sr, m, nnz, perm_num, counters, ctx->stream, ctx->sms, nullptr, num_max);
       cb::launch_numeric_dev(sr, dA, dB, perm_num, counters, flops, nnz, orp.as<int64_t>(),
                              ocol.as<int32_t>(), oval.p, errw.as<int64_t>(), ctx->stream, ctx->sms,
-                             perm_sym, wins, span_counts, spans, racc, num_max);
+                             perm_sym, wins, span_counts, spans, racc, num_max,
+                             cb::CfBounds{ctx->tune.cf_esc, ctx->tune.cf_pre});
       // the symbolic phase's consistency word (window capacity, span cut) joins the error word
       cb::launch_merge_error(counters + cb::kError, errw.as<int64_t>(), ctx->stream);
       kernels += 2 + 2 + 3 + 3 + 2 + 3;
@@ -2046,10 +2048,17 @@ int cb_ctx_set_tune(cb_ctx* ctx, cb_tune* t) {
   u.sym_hash_max = clamp(t->sym_hash_max, cb::kSymSmallMax, cb::kSymLargeMax);
   u.num_hash_max = clamp(t->num_hash_max, u.sym_hash_max, 4096);
   u.learn_max = clamp(t->learn_max, 0, 8192);
+  // compression-ratio bounds: 0 <= cf_esc <= 2 (a row's products must fit
+  // its table), cf_prereduce >= 1 (NaN or above 1e30: off)
+  const float esc = t->cf_esc, pre = t->cf_prereduce;
+  u.cf_esc = !(esc > 0.0f) ? 0.0f : esc > 2.0f ? 2.0f : esc;
+  u.cf_pre = !(pre >= 1.0f) ? (pre != pre ? 1e30f : 1.0f) : pre > 1e30f ? 1e30f : pre;
   ctx->tune = u;
   t->sym_hash_max = u.sym_hash_max;
   t->num_hash_max = u.num_hash_max;
   t->learn_max = u.learn_max;
+  t->cf_esc = u.cf_esc;
+  t->cf_prereduce = u.cf_pre;
   return CB_OK;
 }
 
@@ -2058,6 +2067,8 @@ int cb_ctx_get_tune(const cb_ctx* ctx, cb_tune* t) {
   t->sym_hash_max = ctx->tune.sym_hash_max;
   t->num_hash_max = ctx->tune.num_hash_max;
   t->learn_max = ctx->tune.learn_max;
+  t->cf_esc = ctx->tune.cf_esc;
+  t->cf_prereduce = ctx->tune.cf_pre;
   return CB_OK;
 }
 
@@ -2130,12 +2141,26 @@ int cb_autotune(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, c
           }
         }
       }
+    // then the compression-ratio bounds of the hash tiers, under the best tier bounds
+    const float escs[] = {0.0f, 1.25f, 2.0f};
+    const float pres[] = {2.0f, 4.0f, 16.0f, 1e30f};
+    const cb::Tune tiers = best_u;
+    for (float ce : escs)
+      for (float cp : pres) {
+        cb::Tune u = tiers;
+        u.cf_esc = ce;
+        u.cf_pre = cp;
+        if (ce == tiers.cf_esc && cp == tiers.cf_pre) continue;  // timed above
+        trial(u);
+      }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->tune = best_u;
     best->sym_hash_max = best_u.sym_hash_max;
     best->num_hash_max = best_u.num_hash_max;
     best->learn_max = best_u.learn_max;
+    best->cf_esc = best_u.cf_esc;
+    best->cf_prereduce = best_u.cf_pre;
     if (best_ms) *best_ms = best_t;
     cb_csr_free_async(ctx, &C);
     return CB_OK;

@@ -367,82 +367,6 @@ __device__ __forceinline__ void for_row_products(const DevCSR& A, const DevCSR& 
   }
 }
 
-// Write the column of every set bit of a bitmap in order, with coalesced
-// stores: word w < nw holds word(w), and prefix(w) set bits come before it
-// (nondecreasing in w).  Each warp takes runs of 32 consecutive words (warp
-// `warp` of `nwarps`); for the run's entries, 32 at a time, lane l finds the
-// word holding entry o by a search over the lanes' prefixes and the bit by
-// __fns, and calls store(o, w, bit).  All lanes of each warp must call it.
-template <class W, class P, class S>
-__device__ __forceinline__ void bitmap_columns_coalesced(int nw, int warp, int nwarps, W&& word_of,
-                                                         P&& prefix_of, S&& store) {
-  const int lane = threadIdx.x & 31;
-  for (int w0 = warp * 32; w0 < nw; w0 += nwarps * 32) {
-    const int w = w0 + lane;
-    const unsigned word = w < nw ? word_of(w) : 0u;
-    const int pw = w < nw ? prefix_of(w) : INT_MAX;
-    const int first = __shfl_sync(0xffffffffu, pw, 0);
-    const int total = __reduce_add_sync(0xffffffffu, __popc(word));
-    for (int s0 = 0; s0 < total; s0 += 32) {  // uniform over the warp
-      const int o = first + s0 + lane;
-      int k = 0;  // the last lane whose word starts at or before entry o
-#pragma unroll
-      for (int d = 16; d >= 1; d >>= 1) {
-        const int pk = __shfl_sync(0xffffffffu, pw, k + d);
-        if (pk <= o) k += d;
-      }
-      const unsigned wk = __shfl_sync(0xffffffffu, word, k);
-      const int pk = __shfl_sync(0xffffffffu, pw, k);
-      if (s0 + lane < total) store(o, w0 + k, (int)__fns(wk, 0, o - pk + 1));
-    }
-  }
-}
-
-// The same write-out staged through shared memory: the entries are taken
-// in chunks of `cap` (stage: int[cap]); for each chunk the words holding its
-// entries (found by a search over the prefixes) are unpacked by one thread
-// each into stage[o - chunk start] = 32 w + bit, then the chunk is stored
-// with coalesced writes by store(o, 32 w + bit).  Every word is unpacked once
-// (a word straddling two chunks twice).  All threads of the CTA must call it.
-template <class W, class P, class S>
-__device__ __forceinline__ void bitmap_columns_staged(int nw, int cnt, int* stage, int cap, W&& word_of,
-                                                      P&& prefix_of, S&& store) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int c0 = 0; c0 < cnt; c0 += cap) {
-    const int c1 = min(cnt, c0 + cap);
-    // words [wa, wb) hold the chunk's entries: the last word starting at or
-    // before c0, up to the first word starting at or after c1
-    int lo = 0, hi = nw - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (prefix_of(mid) <= c0) lo = mid;
-      else hi = mid - 1;
-    }
-    const int wa = lo;
-    lo = wa;
-    hi = nw;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (prefix_of(mid) < c1) lo = mid + 1;
-      else hi = mid;
-    }
-    const int wb = lo;
-    for (int w = wa + tid; w < wb; w += nthr) {
-      unsigned word = word_of(w);
-      int o = prefix_of(w);
-      while (word) {
-        const int b = __ffs(word) - 1;
-        word &= word - 1;
-        if (o >= c0 && o < c1) stage[o - c0] = 32 * w + b;
-        ++o;
-      }
-    }
-    __syncthreads();
-    for (int o = c0 + tid; o < c1; o += nthr) store(o, stage[o - c0]);
-    __syncthreads();
-  }
-}
-
 // Exclusive scan of one int per thread across a team of TEAM threads.
 template <int TEAM>
 __device__ __forceinline__ int team_exclusive_scan(int x, int* scratch /* >= 33 ints */, int& total) {

@@ -18,6 +18,16 @@ struct Tune {
   int sym_hash_max = 512;
   int num_hash_max = 512;
   int learn_max = 512;
+  // hash-tier rows by compression ratio cf = flops / nnz (k_num_hash):
+  // expand-sort-compress at cf <= cf_esc, warp pre-reduction at cf >= cf_pre
+  float cf_esc = 1.25f;
+  float cf_pre = 4.0f;
+};
+
+// The compression-ratio bounds a numeric launch uses (from Tune).
+struct CfBounds {
+  float esc = 0.0f;
+  float pre = 1e30f;
 };
 
 struct Window;
@@ -141,7 +151,7 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
                     int64_t n_wins, const int32_t* span_counts, int64_t spans,
                     const unsigned* hbits, int b_sorted, const int64_t* Crp, int32_t* Ccol,
                     void* Cval, int64_t* err, cudaStream_t s, int sms, int* launches,
-                    int64_t num_hash_max = 512, void* racc = nullptr);
+                    int64_t num_hash_max = 512, void* racc = nullptr, CfBounds cf = {});
 
 // Batched products (cb_batched.cu): stack parts into one CSR.
 size_t stack_part_size();
@@ -224,7 +234,8 @@ void launch_numeric_dev(int sr, const DevCSR& A, const DevCSR& B, const int32_t*
                         const int64_t* counters, const int64_t* flops, const int64_t* nnz,
                         const int64_t* Crp, int32_t* Ccol, void* Cval, int64_t* err, cudaStream_t s,
                         int sms, const int32_t* perm_sym, const Window* wins,
-                        const int32_t* span_counts, int64_t spans, void* racc, int64_t num_hash_max);
+                        const int32_t* span_counts, int64_t spans, void* racc, int64_t num_hash_max,
+                        CfBounds cf = {});
 // Bytes of the global accumulator slices of the rank-window numeric kernel
 // (semirings whose windows accumulate in L2; 0 otherwise).
 size_t rank_scratch_bytes(int sr, int sms);

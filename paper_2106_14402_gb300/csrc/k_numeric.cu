@@ -34,6 +34,19 @@ __device__ __forceinline__ void flag_error(int64_t* err, int64_t code) {
 // its size goes to cnt_out[i]; a row that overflows its capacity (full
 // table or more entries than predicted) is marked learned[i] = 0 and
 // recomputed later by the exact path.
+//
+// Accumulator by the row's compression ratio cf = flops_i / nnz(C_i) (paper
+// Sec. 4.1: hash accumulators suit high compression, merging ones low
+// compression, and a hybrid picks per output line), exact sizes only:
+//   * cf <= cf_esc (and flops_i within the table): expand-sort-compress --
+//     the products go to consecutive table slots in arrival order (one
+//     shared-memory atomic per warp step reserves them), are sorted by column
+//     with the bitonic network, and each column's run is combined;
+//   * cf >= cf_pre: hash, with the products of each warp step that share a
+//     column combined first (__match_any_sync groups them, the group's first
+//     lane adds the others' products from a per-warp scratch), so that one
+//     probe and one atomic serve the group;
+//   * otherwise: hash, one probe and one atomic per product.
 template <int SR, int CTA, int TEAM, int TABLE_MAX, bool LEARNED = false>
 __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int32_t* rows,
                                                   int64_t nrows_tier, const int64_t* flops,
@@ -41,7 +54,8 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
                                                   int32_t* Ccol, typename Sem<SR>::TC* Cval,
                                                   int64_t* err, uint8_t* learned = nullptr,
                                                   int64_t* cnt_out = nullptr,
-                                                  const int64_t* dcnt = nullptr, int tier = 0) {
+                                                  const int64_t* dcnt = nullptr, int tier = 0,
+                                                  float cf_esc = 0.0f, float cf_pre = 1e30f) {
   typedef Sem<SR> S;
   typedef typename S::A Acc;
   typedef typename S::TA TA;
@@ -57,6 +71,8 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
   extern __shared__ __align__(16) unsigned char num_smem[];
   __shared__ int scan_scratch[TEAMS][33];
   __shared__ int overflow[TEAMS];
+  __shared__ int esc_cnt[TEAMS];
+  __shared__ typename Sem<SR>::A pre_scratch[CTA / 32][32];
   const int team = threadIdx.x / TEAM, lane = threadIdx.x % TEAM;
   Acc* vals = reinterpret_cast<Acc*>(num_smem) + team * TABLE_MAX;
   int* keys = reinterpret_cast<int*>(reinterpret_cast<Acc*>(num_smem) + TEAMS * TABLE_MAX) + team * TABLE_MAX;
@@ -71,17 +87,25 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
     const int tsize = 1 << bits;
     const uint32_t mask = (uint32_t)tsize - 1;
     const int shift = 32 - bits;
+    const int64_t f = flops[i];
+    int mode = 0;  // 0 hash, 1 hash with warp pre-reduction, 2 expand-sort-compress
+    if (!LEARNED) {
+      if (f <= tsize && (float)f <= cf_esc * (float)nz) mode = 2;
+      else if ((float)f >= cf_pre * (float)nz) mode = 1;
+    }
     for (int s = lane; s < tsize; s += TEAM) {
       keys[s] = kEmptyKey;
       vals[s] = S::ident();
     }
     if (LEARNED && lane == 0) overflow[team] = 0;
+    if (lane == 0) esc_cnt[team] = 0;
     team_sync<TEAM>();
 
     // accumulate every product of row i
     const int64_t a0 = A.rp[i], a1 = A.rp[i + 1];
-    const int gl = group_log2<TEAM>(flops[i], a1 - a0);
+    const int gl = group_log2<TEAM>(f, a1 - a0);
     const int G = 1 << gl, gq = lane & (G - 1), groups = TEAM >> gl;
+    const int wl = threadIdx.x & 31;
     for (int64_t p = a0 + (lane >> gl); p < a1; p += groups) {
       const int k = A.col[p];
       const TA a = S::kUsesA ? Aval[p] : TA();
@@ -89,11 +113,38 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
       for (int64_t q = B.rp[k] + gq; q < b1; q += G) {
         const int c = B.col[q];
         if (!in_window(B, c)) continue;
-        bool ins;
-        const int slot = probe_insert(keys, mask, shift, c, ins);
-        if (slot >= 0) S::atomic(&vals[slot], S::mul(a, Bval[q]));
-        else if (LEARNED) overflow[team] = 1;
-        else flag_error(err, 20);
+        const Acc v = S::mul(a, Bval[q]);
+        if (mode == 2) {  // the next free slots, one atomic per warp step
+          const unsigned am = __activemask();
+          const int leader = __ffs(am) - 1;
+          int base = 0;
+          if (wl == leader) base = atomicAdd(&esc_cnt[team], __popc(am));
+          base = __shfl_sync(am, base, leader);
+          const int t = base + __popc(am & ((1u << wl) - 1u));
+          keys[t] = c;
+          vals[t] = v;
+          continue;
+        }
+        Acc sum = v;
+        bool lead = true;
+        if (mode == 1) {  // combine the warp step's products of one column first
+          const unsigned am = __activemask();
+          const unsigned peers = __match_any_sync(am, c);
+          lead = wl == __ffs(peers) - 1;
+          pre_scratch[threadIdx.x >> 5][wl] = v;
+          __syncwarp(am);
+          if (lead)
+            for (unsigned o = peers & (peers - 1); o; o &= o - 1)
+              sum = S::add(sum, pre_scratch[threadIdx.x >> 5][__ffs(o) - 1]);
+          __syncwarp(am);
+        }
+        if (lead) {
+          bool ins;
+          const int slot = probe_insert(keys, mask, shift, c, ins);
+          if (slot >= 0) S::atomic(&vals[slot], sum);
+          else if (LEARNED) overflow[team] = 1;
+          else flag_error(err, 20);
+        }
       }
     }
     team_sync<TEAM>();
@@ -156,6 +207,30 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
       }
     }
 
+    if (mode == 2) {  // combine each column's run of the sorted products
+      const int per = (total + TEAM - 1) / TEAM;
+      const int t0 = lane * per, t1 = min(total, t0 + per);
+      int h = 0;
+      for (int t = t0; t < t1; ++t) h += t == 0 || keys[t] != keys[t - 1];
+      int heads;
+      int hpos = team_exclusive_scan<TEAM>(h, scan_scratch[team], heads);
+      if (heads != nz && lane == 0) flag_error(err, 21);
+      const int64_t off = Crp[i];
+      for (int t = t0; t < t1; ++t) {
+        if (t == 0 || keys[t] != keys[t - 1]) {
+          Acc v = vals[t];
+          for (int u = t + 1; u < total && keys[u] == keys[t]; ++u) v = S::add(v, vals[u]);
+          if (hpos < nz) {
+            Ccol[off + hpos] = keys[t];
+            Cval[off + hpos] = S::out(v);
+          }
+          ++hpos;
+        }
+      }
+      team_sync<TEAM>();
+      continue;
+    }
+
     // write the sorted row
     if (!LEARNED && total != nz && lane == 0) flag_error(err, 21);
     if (LEARNED && lane == 0) cnt_out[i] = total;
@@ -174,11 +249,6 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
 // row's products), prefix-count its words, then accumulate every product
 // into the dense accumulator at its column's rank and write the window's
 // slice of the row in column order.
-// How a window's column indices are written: 0 each thread its words' bits
-// in turn, 1 coalesced with a warp search per entry, 2 staged through
-// shared memory then coalesced.
-constexpr int kRankColumns = 2;
-
 template <int SR, int CTA>
 __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B, const int32_t* heavy_rows,
                                                       const Window* wins, int64_t n_wins,
@@ -298,28 +368,14 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
     const int64_t row_end = Crp[i + 1];
     for (int t = tid; t < cnt; t += CTA)
       if (out + t < row_end) Cval[out + t] = S::out(kL2 ? __ldcg(wacc + t) : wacc[t]);
-    if constexpr (kRankColumns == 2) {  // staged in the (now free) piece scratch
-      bitmap_columns_staged(nw, cnt, reinterpret_cast<int*>(bal),
-                            (int)(CTA * PieceSmem::kBytesPerThread / sizeof(int)),
-                            [&](int w) { return bp[w].x; }, [&](int w) { return (int)bp[w].y; },
-                            [&](int o, int v) {
-                              if (out + o < row_end) Ccol[out + o] = (int32_t)(lo + v);
-                            });
-    } else if constexpr (kRankColumns == 1) {
-      bitmap_columns_coalesced(nw, tid >> 5, CTA / 32, [&](int w) { return bp[w].x; },
-                               [&](int w) { return (int)bp[w].y; }, [&](int o, int w, int b) {
-                                 if (out + o < row_end) Ccol[out + o] = (int32_t)(lo + 32 * w + b);
-                               });
-    } else {
-      for (int w = tid; w < nw; w += CTA) {
-        unsigned word = bp[w].x;
-        int64_t o = out + bp[w].y;
-        while (word) {
-          const int b = __ffs(word) - 1;
-          word &= word - 1;
-          if (o < row_end) Ccol[o] = (int32_t)(lo + 32 * w + b);
-          ++o;
-        }
+    for (int w = tid; w < nw; w += CTA) {
+      unsigned word = bp[w].x;
+      int64_t o = out + bp[w].y;
+      while (word) {
+        const int b = __ffs(word) - 1;
+        word &= word - 1;
+        if (o < row_end) Ccol[o] = (int32_t)(lo + 32 * w + b);
+        ++o;
       }
     }
     __syncthreads();
@@ -342,7 +398,7 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
                 const int32_t* heavy_rows, const Window* wins, int64_t n_wins,
                 const int32_t* span_counts, int64_t spans, const unsigned* hbits, int b_sorted,
                 const int64_t* Crp, int32_t* Ccol, void* Cval_, int64_t* err, cudaStream_t s,
-                int sms, int* launches, int64_t num_hash_max, void* racc) {
+                int sms, int* launches, int64_t num_hash_max, void* racc, CfBounds cf) {
   typedef typename Sem<SR>::A Acc;
   typedef typename Sem<SR>::TC TC;
   TC* Cval = reinterpret_cast<TC*>(Cval_);
@@ -351,14 +407,16 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
     constexpr int CTA = 256, TEAM = 32, TBL = 2 * kNumWarpMax;
     const size_t smem = (CTA / TEAM) * TBL * slot;
     k_num_hash<SR, CTA, TEAM, TBL><<<capped((seg_count[kNumWarp] + 7) / 8, sms * 8), CTA, smem, s>>>(
-        A, B, perm + seg_begin[kNumWarp], seg_count[kNumWarp], flops, nnz, Crp, Ccol, Cval, err);
+        A, B, perm + seg_begin[kNumWarp], seg_count[kNumWarp], flops, nnz, Crp, Ccol, Cval, err, nullptr,
+        nullptr, nullptr, 0, cf.esc, cf.pre);
     ++*launches;
   }
   if (seg_count[kNumSmall]) {
     constexpr int CTA = 256, TEAM = 256, TBL = 2 * kNumSmallMax;
     const size_t smem = TBL * slot;
     k_num_hash<SR, CTA, TEAM, TBL><<<capped(seg_count[kNumSmall], sms * 8), CTA, smem, s>>>(
-        A, B, perm + seg_begin[kNumSmall], seg_count[kNumSmall], flops, nnz, Crp, Ccol, Cval, err);
+        A, B, perm + seg_begin[kNumSmall], seg_count[kNumSmall], flops, nnz, Crp, Ccol, Cval, err, nullptr,
+        nullptr, nullptr, 0, cf.esc, cf.pre);
     ++*launches;
   }
   if (seg_count[kNumLarge]) {
@@ -366,7 +424,8 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
     const size_t smem = TBL * slot;
     set_smem(k_num_hash<SR, CTA, TEAM, TBL>, smem);
     k_num_hash<SR, CTA, TEAM, TBL><<<capped(seg_count[kNumLarge], sms * 4), CTA, smem, s>>>(
-        A, B, perm + seg_begin[kNumLarge], seg_count[kNumLarge], flops, nnz, Crp, Ccol, Cval, err);
+        A, B, perm + seg_begin[kNumLarge], seg_count[kNumLarge], flops, nnz, Crp, Ccol, Cval, err, nullptr,
+        nullptr, nullptr, 0, cf.esc, cf.pre);
     ++*launches;
   }
   if (n_wins) {
@@ -391,7 +450,7 @@ void numeric_dev_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const
                     const int64_t* flops, const int64_t* nnz, const int64_t* Crp, int32_t* Ccol,
                     void* Cval_, int64_t* err, cudaStream_t s, int sms, int64_t m,
                     const int32_t* perm_sym, const Window* wins, const int32_t* span_counts,
-                    int64_t spans, void* racc, int64_t num_hash_max) {
+                    int64_t spans, void* racc, int64_t num_hash_max, CfBounds cf) {
   typedef typename Sem<SR>::A Acc;
   typedef typename Sem<SR>::TC TC;
   TC* Cval = reinterpret_cast<TC*>(Cval_);
@@ -401,18 +460,18 @@ void numeric_dev_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const
     constexpr int CTA = 256, TEAM = 32, TBL = 2 * kNumWarpMax;
     const size_t smem = (CTA / TEAM) * TBL * slot;
     k_num_hash<SR, CTA, TEAM, TBL><<<capped((m + 7) / 8, sms * 8), CTA, smem, s>>>(
-        A, B, perm, 0, flops, nnz, Crp, Ccol, Cval, err, nullptr, nullptr, dc, kNumWarp);
+        A, B, perm, 0, flops, nnz, Crp, Ccol, Cval, err, nullptr, nullptr, dc, kNumWarp, cf.esc, cf.pre);
   }
   {
     constexpr int CTA = 256, TEAM = 256, TBL = 2 * kNumSmallMax;
     k_num_hash<SR, CTA, TEAM, TBL><<<capped(m, sms * 8), CTA, TBL * slot, s>>>(
-        A, B, perm, 0, flops, nnz, Crp, Ccol, Cval, err, nullptr, nullptr, dc, kNumSmall);
+        A, B, perm, 0, flops, nnz, Crp, Ccol, Cval, err, nullptr, nullptr, dc, kNumSmall, cf.esc, cf.pre);
   }
   {  // shared-memory attribute set by prepare_dev_launchers
     constexpr int CTA = 512, TEAM = 512, TBL = 2 * NumLimits<SR>::kLargeMax;
     const size_t smem = TBL * slot;
     k_num_hash<SR, CTA, TEAM, TBL><<<capped(m, sms * 4), CTA, smem, s>>>(
-        A, B, perm, 0, flops, nnz, Crp, Ccol, Cval, err, nullptr, nullptr, dc, kNumLarge);
+        A, B, perm, 0, flops, nnz, Crp, Ccol, Cval, err, nullptr, nullptr, dc, kNumLarge, cf.esc, cf.pre);
   }
   {  // rank windows of the heavy rows (window count read on the device)
     constexpr int CTA = NumLimits<SR>::kL2Acc ? 512 : 1024;
@@ -511,11 +570,11 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
                     int64_t n_wins, const int32_t* span_counts, int64_t spans,
                     const unsigned* hbits, int b_sorted, const int64_t* Crp, int32_t* Ccol,
                     void* Cval, int64_t* err, cudaStream_t s, int sms, int* launches,
-                    int64_t num_hash_max, void* racc) {
+                    int64_t num_hash_max, void* racc, CfBounds cf) {
 #define CB_NUM(SRV)                                                                        \
   numeric_sr<SRV>(A, B, perm, seg_begin, seg_count, flops, nnz, heavy_rows, wins, n_wins,   \
                   span_counts, spans, hbits, b_sorted, Crp, Ccol, Cval, err, s, sms, launches, \
-                  num_hash_max, racc)
+                  num_hash_max, racc, cf)
   switch (sr) {
 #define CB_CASE(SRV) case SRV: CB_NUM(SRV); break;
     CB_FOR_EACH_SEMIRING(CB_CASE)
@@ -556,12 +615,13 @@ void launch_numeric_dev(int sr, const DevCSR& A, const DevCSR& B, const int32_t*
                         const int64_t* counters, const int64_t* flops, const int64_t* nnz,
                         const int64_t* Crp, int32_t* Ccol, void* Cval, int64_t* err, cudaStream_t s,
                         int sms, const int32_t* perm_sym, const Window* wins,
-                        const int32_t* span_counts, int64_t spans, void* racc, int64_t num_hash_max) {
+                        const int32_t* span_counts, int64_t spans, void* racc, int64_t num_hash_max,
+                        CfBounds cf) {
   const int64_t m = A.nrows;
   if (m == 0) return;
 #define CB_NDEV(SRV)                                                                            \
   numeric_dev_sr<SRV>(A, B, perm, counters, flops, nnz, Crp, Ccol, Cval, err, s, sms, m, perm_sym, \
-                      wins, span_counts, spans, racc, num_hash_max)
+                      wins, span_counts, spans, racc, num_hash_max, cf)
   switch (sr) {
 #define CB_CASE(SRV) case SRV: CB_NDEV(SRV); break;
     CB_FOR_EACH_SEMIRING(CB_CASE)

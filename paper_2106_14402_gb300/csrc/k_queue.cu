@@ -36,9 +36,6 @@ constexpr int kQThreads = 256;
 constexpr int kQWarps = kQThreads / 32;
 constexpr int kQWords = kQueueWidth / 32;   // bitmap words of the widest row
 constexpr unsigned kQFull = 0xFFFFFFFFu;
-// column write-out: 0 each thread its words' bits in turn, 1 coalesced with
-// a warp search per entry
-constexpr int kQColumns = 1;
 
 // status words: [63:40] epoch, [39:38] kind, [37:0] value (as in k_fused.cu)
 constexpr int kQEpochShift = 40;
@@ -220,20 +217,13 @@ __global__ void __launch_bounds__(kQThreads) k_queue_rows(DevCSR A, DevCSR B, in
         if (t < n) Cval[base + t] = S::out(acc[t]);
         acc[t] = S::ident();
       }
-      if constexpr (kQColumns == 1) {
-        bitmap_columns_coalesced(nw, warp, kQWarps, [&](int w) { return bits[w]; },
-                                 [&](int w) { return (int)pre[w]; }, [&](int o, int w, int b) {
-                                   Ccol[base + o] = (int32_t)(B.col_lo + 32 * (int64_t)w + b);
-                                 });
-      } else {
-        for (int w = tid; w < nw; w += kQThreads) {
-          unsigned word = bits[w];
-          long long o = base + pre[w];
-          while (word) {
-            const int b = __ffs(word) - 1;
-            word &= word - 1;
-            Ccol[o++] = (int32_t)(B.col_lo + 32 * (int64_t)w + b);
-          }
+      for (int w = tid; w < nw; w += kQThreads) {
+        unsigned word = bits[w];
+        long long o = base + pre[w];
+        while (word) {
+          const int b = __ffs(word) - 1;
+          word &= word - 1;
+          Ccol[o++] = (int32_t)(B.col_lo + 32 * (int64_t)w + b);
         }
       }
     }

@@ -59,6 +59,50 @@ def test_autotune_keeps_a_valid_setting(cb, problem):
     assert ms > 0
     assert ctx.get_tune() == best
     assert 512 <= best["sym_hash_max"] <= best["num_hash_max"] <= 4096
+    assert 0.0 <= best["cf_esc"] <= 2.0 and best["cf_prereduce"] >= 1.0
     C = cb.spgemm(sr, dA, dA, ctx=ctx)
     rows = np.arange(0, A.nrows, 53)
     compare_rows(sr, C.to_host(), oracle.spgemm(sr, A, A, rows=rows), rows=rows)
+
+
+# ---------------------------------------------------------------------------
+# accumulator of hash-tier rows by compression ratio (expand-sort-compress,
+# hash, hash with warp pre-reduction)
+# ---------------------------------------------------------------------------
+
+CF_SETTINGS = {"esc_all_low": (2.0, 1e30), "prereduce_all": (0.0, 1.0), "hash_only": (0.0, 1e30),
+               "default": (1.25, 4.0)}
+
+
+@pytest.mark.parametrize("setting", sorted(CF_SETTINGS))
+@pytest.mark.parametrize("sr", gen.SEMIRINGS + gen.HETERO_SEMIRINGS)
+def test_accumulator_by_compression_ratio(cb, sr, setting):
+    """Every accumulator choice gives the oracle's result: R-MAT scale 12
+    (hash-tier rows of low compression), a block-clustered matrix (high
+    compression) and duplicate, unsorted inputs."""
+    esc, pre = CF_SETTINGS[setting]
+    ctx = cb.Context()
+    t = ctx.set_tune(512, 4096, 512, esc, pre)
+    assert abs(t["cf_esc"] - esc) < 1e-6 and (t["cf_prereduce"] == pre or pre >= 1e30)
+    inputs = [gen.rmat(12, 16, *gen.RMAT_ABCD, seed=710), gen.block_clustered(1 << 11, 256, 0.5, 1.0, seed=711)]
+    dup = gen.random_csr(500, 400, 0.02, seed=712, duplicates=True, shuffle=True, empty_rows=0.1)
+    for k, P in enumerate(inputs + [dup]):
+        B = P if k < 2 else gen.random_csr(400, 300, 0.03, seed=713, duplicates=True, shuffle=True)
+        if sr in gen.HETERO_SEMIRINGS:
+            A = P.with_values(gen.hetero_values(sr, "A", P.nnz, 714 + k, levels=4))
+            Bv = B.with_values(gen.hetero_values(sr, "B", B.nnz, 715 + k))
+        else:
+            A = P.with_values(gen.random_values(sr, P.nnz, 714 + k))
+            Bv = B.with_values(gen.random_values(sr, B.nnz, 715 + k))
+        dA = cb.DeviceCSR.from_host(A, sr, operand="A")
+        dB = cb.DeviceCSR.from_host(Bv, sr, operand="B")
+        C = cb.spgemm(sr, dA, dB, ctx=ctx, check=True, fused=False)
+        compare_rows(sr, C.to_host(), oracle.spgemm(sr, A, Bv))
+
+
+def test_set_tune_clamps_compression_bounds(cb):
+    ctx = cb.Context()
+    t = ctx.set_tune(512, 512, 512, 5.0, 0.5)
+    assert t["cf_esc"] == 2.0 and t["cf_prereduce"] == 1.0
+    t = ctx.set_tune(512, 512, 512, -1.0, float("nan"))
+    assert t["cf_esc"] == 0.0 and t["cf_prereduce"] >= 1e30
