@@ -48,6 +48,30 @@ __device__ __forceinline__ T ldg_val(const T* p) {
   }
 }
 
+// Store of a value written once and not read again by the kernel (C's
+// entries, stored bitmaps): with kStreamOut an evict-first store, so that the
+// output streaming through L2 does not push out the operands being gathered.
+constexpr bool kStreamOut = true;
+template <class T>
+__device__ __forceinline__ void st_out(T* p, T v) {
+  if constexpr (!kStreamOut) {
+    *p = v;
+  } else if constexpr (sizeof(T) == 8) {
+    unsigned long long u;
+    memcpy(&u, &v, sizeof u);
+    __stcs(reinterpret_cast<unsigned long long*>(p), u);
+  } else if constexpr (sizeof(T) == 4) {
+    unsigned u;
+    memcpy(&u, &v, sizeof u);
+    __stcs(reinterpret_cast<unsigned*>(p), u);
+  } else {
+    static_assert(sizeof(T) == 1, "values of 1, 4 or 8 bytes");
+    unsigned char u;
+    memcpy(&u, &v, sizeof u);
+    __stcs(reinterpret_cast<unsigned char*>(p), u);
+  }
+}
+
 template <> struct Sem<1> {  // (+,x) over int64, wrapping
   typedef int64_t TA, TB, TC;
   typedef unsigned long long A;

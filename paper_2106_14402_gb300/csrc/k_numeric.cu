@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
     const int nw = wd.w_hi - wd.w_lo;
     if (hbits) {
       const unsigned* src = hbits + (size_t)((int64_t)wd.h * spans + wd.span) * kSpanWords + wd.w_lo;
-      for (int w = tid; w < nw; w += CTA) bp[w].x = src[w];
+      for (int w = tid; w < nw; w += CTA) bp[w].x = kStreamOut ? __ldcs(src + w) : src[w];
     } else {
       for (int w = tid; w < nw; w += CTA) bp[w].x = 0u;
     }
@@ -367,14 +367,14 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
     const int64_t out = Crp[i] + s_base;
     const int64_t row_end = Crp[i + 1];
     for (int t = tid; t < cnt; t += CTA)
-      if (out + t < row_end) Cval[out + t] = S::out(kL2 ? __ldcg(wacc + t) : wacc[t]);
+      if (out + t < row_end) st_out(Cval + out + t, S::out(kL2 ? __ldcg(wacc + t) : wacc[t]));
     for (int w = tid; w < nw; w += CTA) {
       unsigned word = bp[w].x;
       int64_t o = out + bp[w].y;
       while (word) {
         const int b = __ffs(word) - 1;
         word &= word - 1;
-        if (o < row_end) Ccol[o] = (int32_t)(lo + 32 * w + b);
+        if (o < row_end) st_out(Ccol + o, (int32_t)(lo + 32 * w + b));
         ++o;
       }
     }

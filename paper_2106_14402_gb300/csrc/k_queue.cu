@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kQThreads) k_queue_rows(DevCSR A, DevCSR B, in
       for (int t = tid; t < s_touched; t += kQThreads) acc[t] = S::ident();
     } else {
       for (int t = tid; t < s_touched; t += kQThreads) {
-        if (t < n) Cval[base + t] = S::out(acc[t]);
+        if (t < n) st_out(Cval + base + t, S::out(acc[t]));
         acc[t] = S::ident();
       }
       for (int w = tid; w < nw; w += kQThreads) {
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kQThreads) k_queue_rows(DevCSR A, DevCSR B, in
         while (word) {
           const int b = __ffs(word) - 1;
           word &= word - 1;
-          Ccol[o++] = (int32_t)(B.col_lo + 32 * (int64_t)w + b);
+          st_out(Ccol + o++, (int32_t)(B.col_lo + 32 * (int64_t)w + b));
         }
       }
     }

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
     __syncthreads();
     if (hbits) {
       unsigned* dst = hbits + (size_t)(h * spans + sp) * kSpanWords;
-      for (int w = tid; w < nwords; w += 1024) dst[w] = sym_bm[w];
+      for (int w = tid; w < nwords; w += 1024) st_out(dst + w, sym_bm[w]);
     }
 
     // exclusive prefix of the word popcounts (WPT consecutive words per thread)
