@@ -660,6 +660,9 @@ __device__ __forceinline__ void for_row_products_balanced_u(const DevCSR& A, con
 //   f(t, c, v):  one product: the token, column c and the value ld(q) of its
 //                B entry.
 // All threads of the CTA must call it.
+// Whether full pieces take a path without per-product bounds checks.
+constexpr bool kFullPieces = true;
+
 struct PieceSmem {
   int* poff;        // [blockDim.x] first piece of each nonempty range (chunk numbering)
   long long* q0;    // [blockDim.x] first B index of the range
@@ -745,6 +748,14 @@ __device__ __forceinline__ void for_row_pieces(const DevCSR& A, const DevCSR& B,
         pc.tok = tok;
         const int64_t qs = qj + s0;
         const int32_t* cp = B.col + qs;
+        if (kFullPieces && pc.n == P) {  // a full piece: no bounds to check (uniform)
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            pc.c[u] = __ldg(cp + u * 32 + lane);
+            pc.v[u] = ld(qs + u * 32 + lane);
+          }
+          return;
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int x = u * 32 + lane;
@@ -757,6 +768,11 @@ __device__ __forceinline__ void for_row_pieces(const DevCSR& A, const DevCSR& B,
         }
       };
       const auto consume = [&](const Piece& pc) {
+        if (kFullPieces && pc.n == P && !filter) {
+#pragma unroll
+          for (int u = 0; u < U; ++u) f(pc.tok, pc.c[u], pc.v[u]);
+          return;
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int x = u * 32 + lane;

@@ -249,6 +249,8 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
 // row's products), prefix-count its words, then accumulate every product
 // into the dense accumulator at its column's rank and write the window's
 // slice of the row in column order.
+constexpr bool kRankInPlace = true;
+
 template <int SR, int CTA>
 __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B, const int32_t* heavy_rows,
                                                       const Window* wins, int64_t n_wins,
@@ -276,6 +278,11 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
   // 64-bit atomics cost more than L2 reductions, and without shared
   // accumulators two 512-thread CTAs share an SM.
   constexpr bool kL2 = NumLimits<SR>::kL2Acc;
+  // (+,x) over int64 and fp64 accumulate in L2 directly in the window's
+  // output entries (their accumulator bits are the output value's), so the
+  // values need no copy out of a scratch slice; other 8-byte semirings use
+  // the slice and convert on the way out.
+  constexpr bool kInPlace = kL2 && kRankInPlace && (SR == 1 || SR == 2);
   constexpr int WPT = kSpanWords / CTA;
   extern __shared__ __align__(16) unsigned char rank_smem[];
   // shared layout: [accumulators (shared-memory windows only)] [bp] [iterator scratch]
@@ -309,8 +316,6 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
     } else {
       for (int w = tid; w < nw; w += CTA) bp[w].x = 0u;
     }
-    Acc* wacc = kL2 ? racc + (size_t)blockIdx.x * WCAP : acc;
-    for (int t = tid; t < cnt; t += CTA) wacc[t] = S::ident();
     if (tid < 32) {
       long long o = 0;
       for (int64_t t = lane; t < wd.span; t += 32) o += span_counts[(int64_t)wd.h * spans + t];
@@ -319,13 +324,21 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
       if (lane == 0) s_base = o + wd.rank;
     }
     __syncthreads();
+    // the window's slice of the row: C entries [out, out + cnt)
+    const int64_t out = Crp[i] + s_base;
+    const int64_t row_end = Crp[i + 1];
+    Acc* wacc = kInPlace ? reinterpret_cast<Acc*>(Cval + out)
+                         : (kL2 ? racc + (size_t)blockIdx.x * WCAP : acc);
+    // slots past the row's end (an inconsistent count) are dropped
+    const int lim = kInPlace ? (int)max((int64_t)0, min((int64_t)cnt, row_end - out)) : cnt;
+    for (int t = tid; t < lim; t += CTA) wacc[t] = S::ident();
 
     if (!hbits) {  // pass 1: rebuild the window's columns
       for_row_pieces<2>(A, B, i, lo, hi, whole, b_sorted != 0, sm, [](int64_t) { return 0; },
                                [](int64_t) { return 0; }, [&](int, int c, int) {
                           const unsigned off = (unsigned)((int64_t)c - lo);
                           const unsigned bit = 1u << (off & 31);
-                          if (!(bp[off >> 5].x & bit)) atomicOr(&bp[off >> 5].x, bit);
+                          atomicOr(&bp[off >> 5].x, bit);
                         });
       __syncthreads();
     }
@@ -360,14 +373,14 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
                         const unsigned off = (unsigned)c - lo32;
                         const uint2 e = bp[off >> 5];
                         const int slot = (int)e.y + __popc(e.x & ((1u << (off & 31)) - 1u));
-                        if (slot < cnt) S::atomic(&wacc[slot], S::mul(a_cur, bv));
+                        if (slot < lim) S::atomic(&wacc[slot], S::mul(a_cur, bv));
                       });
     __syncthreads();
-    // write the window: values by slot (coalesced), columns by word
-    const int64_t out = Crp[i] + s_base;
-    const int64_t row_end = Crp[i + 1];
-    for (int t = tid; t < cnt; t += CTA)
-      if (out + t < row_end) st_out(Cval + out + t, S::out(kL2 ? __ldcg(wacc + t) : wacc[t]));
+    // write the window: values by slot (coalesced; in place they are there
+    // already), columns by word
+    if (!kInPlace)
+      for (int t = tid; t < cnt; t += CTA)
+        if (out + t < row_end) st_out(Cval + out + t, S::out(kL2 ? __ldcg(wacc + t) : wacc[t]));
     for (int w = tid; w < nw; w += CTA) {
       unsigned word = bp[w].x;
       int64_t o = out + bp[w].y;

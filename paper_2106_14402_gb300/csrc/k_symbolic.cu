@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
                              [](int64_t) { return 0; }, [](int64_t) { return 0; }, [&](int, int c, int) {
                         const unsigned off = (unsigned)c - lo32;
                         const unsigned bit = 1u << (off & 31);
-                        if (!(sym_bm[off >> 5] & bit)) atomicOr(&sym_bm[off >> 5], bit);
+                        atomicOr(&sym_bm[off >> 5], bit);
                       });
     __syncthreads();
     if (hbits) {
