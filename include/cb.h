@@ -119,6 +119,16 @@ typedef struct {
   uint64_t *digests;    /* cb_spgemm_batched only, optional (default NULL): device
                            uint64[2 * count] receiving a digest of every C_i, written
                            before its wave's on_batch in every mode (see there)        */
+  int64_t resume_col;   /* column-batched calls (budget_bytes > 0): form only the
+                           columns [resume_col, B.ncols) (default 0; 0..B.ncols, else
+                           CB_ERR_ARG).  To resume a stopped or failed call, pass the
+                           col_lo of the first batch not consumed and resume_batch =
+                           its index: with exact sizing the same arguments then give
+                           the same batches from there on; with learned sizing the
+                           remaining columns are cut afresh (paper Sec. 7.2: the
+                           batches are independent)                                 */
+  int32_t resume_batch; /* index on_batch receives for the first batch formed
+                           (default 0, >= 0)                                         */
 } cb_opts;
 
 /* cb_opts.flags bits. */
@@ -162,6 +172,11 @@ enum {
 
 /* Fill *opt with defaults (exact sizing, validation on, library-allocated C). */
 void cb_opts_default(cb_opts *opt);
+
+/* sizeof of the ABI's structs as this library was compiled (for bindings
+ * that lay them out by hand): which = 0 cb_csr, 1 cb_opts, 2 cb_tune,
+ * 3 cb_stats, 4 cb_spvec, 5 cb_wlabel; -1 for any other value. */
+int64_t cb_struct_size(int which);
 
 /* Create a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy
  * default stream) on the current device.  The context owns a reusable device
@@ -377,6 +392,40 @@ int cb_ctx_get_tune(const cb_ctx *ctx, cb_tune *tune);
 int cb_autotune(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B, const cb_opts *opt,
                 cb_tune *best, float *best_ms);
 
+/* ---- autotune cache (host only) -------------------------------------------
+ * Tuned bounds persist in a JSON file keyed by device name, semiring, sizing
+ * mode and size class of the operands, so a later run skips the timing grid.
+ * The file is {"format": "cb-tune-cache-1", "entries": {key: {"sym_hash_max",
+ * "num_hash_max", "learn_max", "cf_esc", "cf_prereduce", "ms"}}}; updates
+ * rewrite it through a temporary file and a rename.
+ *
+ * cb_tune_key writes "<device>|sr<id>|sizing<mode>|m2^a|a2^b|b2^c" into
+ * buf (buf_len bytes including the terminator), where a, b, c are the
+ * nearest powers of two of nrows, nnz(A) and nnz(B) (0 for sizes <= 1).
+ * CB_ERR_ARG on a null or too small buffer or a negative size.
+ *
+ * cb_tune_cache_get: *found = 1 and *tune (and *ms when not NULL) filled
+ * when key is present; *found = 0 when the key or the file is absent.
+ * CB_ERR_ARG when the file cannot be read or is not such a cache (it is
+ * then left untouched by cb_tune_cache_put as well).
+ *
+ * cb_tune_cache_put inserts or replaces key's entry (CB_ERR_ARG when the
+ * file cannot be read back as a cache or written).
+ *
+ * cb_autotune_cached: with the key of this context's device and the
+ * operands, a cached entry is set on the context (clamped as by
+ * cb_ctx_set_tune) and returned with its recorded time and *hit = 1, with no
+ * GPU work; otherwise it runs cb_autotune, stores the result and returns it
+ * with *hit = 0.  A cache error returns CB_ERR_ARG with the reason in
+ * cb_last_error. */
+int cb_tune_key(const char *device_name, cb_semiring sr, int32_t sizing, int64_t nrows, int64_t nnz_a,
+                int64_t nnz_b, char *buf, int64_t buf_len);
+int cb_tune_cache_get(const char *path, const char *key, cb_tune *tune, float *ms, int *found);
+int cb_tune_cache_put(const char *path, const char *key, const cb_tune *tune, float ms);
+int cb_autotune_cached(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B,
+                       const cb_opts *opt, const char *cache_path, cb_tune *best, float *best_ms,
+                       int *hit);
+
 /* ---- semiring SpMSpV ----------------------------------------------------------
  * y^T = x^T A over a semiring: y_c = (+) over stored x entries (i, x_i) and
  * stored A(i, c) of x_i (x) A(i, c) (Sec. 4.3, SpMSpV; the row form suits
@@ -497,9 +546,27 @@ int cb_last_stats(const cb_ctx *ctx, cb_stats *out);
  *     Waiting tiles record CB_FUSED_STALLED and publish anyway, so the launch
  *     ends; cb_spgemm_ex returns CB_ERR_TIMEOUT with C zeroed.  arg < 0
  *     restores the defaults (no silent tile, 2^20 polls).
+ *   CB_FAULT_SHORT_ROW: on the two-phase path, row `arg`'s exact size is made
+ *     one short after the symbolic phase (the inconsistent count a faulty
+ *     symbolic kernel would leave); arg < 0 turns it off.  Every write of the
+ *     numeric phase stays inside C's arrays: the normal library drops the
+ *     row's surplus entry (CB_FLAG_CHECK reports it as a consistency failure
+ *     when a hash tier forms the row), the CB_CHECK debug library reports
+ *     the failed bound (see the debug build below).
  * Returns CB_ERR_ARG for an unknown kind or an argument out of range. */
-enum { CB_FAULT_ALLOC = 1, CB_FAULT_SILENT_TILE = 2 };
+enum { CB_FAULT_ALLOC = 1, CB_FAULT_SILENT_TILE = 2, CB_FAULT_SHORT_ROW = 3 };
 int cb_ctx_set_fault(cb_ctx *ctx, int kind, int64_t arg, int64_t arg2);
+
+/* ---- debug build -----------------------------------------------------------
+ * libcb_check.so is this library compiled with -DCB_CHECK: the same entry
+ * points, plus a run-time bounds check on every CSR write and every shared or
+ * global hash-table access of the SpGEMM kernels (flop count, symbolic,
+ * numeric, one-launch and work-queue kernels, the learned-sizing copy).  A
+ * failed check skips the access and records its code and index on the device
+ * (no trap); cb_spgemm_ex, cb_spgemm_batched, cb_spgemm_fused and cb_merge
+ * then synchronise and return CB_ERR_CUDA with "bounds check <code> failed at
+ * index <i> (<file> kernels)" in cb_last_error (C zeroed when library-
+ * allocated).  It is slower and meant for tests and debugging. */
 
 #ifdef __cplusplus
 }

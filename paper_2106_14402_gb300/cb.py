@@ -62,7 +62,7 @@ class cb_opts(ctypes.Structure):
                 ("out_capacity", c_int64), ("budget_bytes", c_int64),
                 ("on_batch", BATCH_FN), ("user", c_void_p), ("mlp", c_void_p),
                 ("margin", ctypes.c_float), ("flags", ctypes.c_int32),
-                ("digests", c_void_p)]
+                ("digests", c_void_p), ("resume_col", c_int64), ("resume_batch", ctypes.c_int32)]
 
 
 class cb_tune(ctypes.Structure):
@@ -120,6 +120,16 @@ _SIGS = {
     "cb_autotune": ([c_void_p, ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr),
                      ctypes.POINTER(cb_opts), ctypes.POINTER(cb_tune), ctypes.POINTER(ctypes.c_float)],
                     ctypes.c_int),
+    "cb_autotune_cached": ([c_void_p, ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_csr),
+                            ctypes.POINTER(cb_opts), ctypes.c_char_p, ctypes.POINTER(cb_tune),
+                            ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "cb_tune_key": ([ctypes.c_char_p, ctypes.c_int, ctypes.c_int32, c_int64, c_int64, c_int64,
+                     ctypes.c_char_p, c_int64], ctypes.c_int),
+    "cb_tune_cache_get": ([ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(cb_tune),
+                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "cb_tune_cache_put": ([ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(cb_tune), ctypes.c_float],
+                          ctypes.c_int),
+    "cb_struct_size": ([ctypes.c_int], c_int64),
     "cb_spmspv": ([c_void_p, ctypes.c_int, ctypes.POINTER(cb_csr), ctypes.POINTER(cb_spvec),
                    ctypes.POINTER(cb_spvec), ctypes.POINTER(cb_opts)], ctypes.c_int),
     "cb_spvec_free_async": ([c_void_p, ctypes.POINTER(cb_spvec)], ctypes.c_int),
@@ -145,19 +155,21 @@ _SIGS = {
 
 
 def library_path() -> str:
-    return _build.LIB
+    """libcb.so, or the bounds-checking debug build libcb_check.so when the
+    environment variable CB_LIBRARY is "check" (debugging and tests only)."""
+    return _build.LIB_CHECK if os.environ.get("CB_LIBRARY", "") == "check" else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Load libcb.so (building it first if allowed); raises if it is unavailable."""
+    """Load the library (building it first if allowed); raises if it is unavailable."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
+            path = library_path()
             if not os.path.exists(path):
                 if not build_if_missing:
-                    raise RuntimeError(f"libcb.so not built at {path}")
-                _build.build()
+                    raise RuntimeError(f"{os.path.basename(path)} not built at {path}")
+                _build.build(check=path == _build.LIB_CHECK)
             lib = ctypes.CDLL(path)
             for name, (args, res) in _SIGS.items():
                 fn = getattr(lib, name)
@@ -323,7 +335,9 @@ class Context:
     def set_fault(self, kind: int, arg: int, arg2: int = 0) -> None:
         """Fault injection (cb_ctx_set_fault): FAULT_ALLOC fails the arg-th device
         allocation; FAULT_SILENT_TILE keeps tile arg of the one-launch kernel
-        from publishing, waits giving up after arg2 polls (arg < 0: defaults)."""
+        from publishing, waits giving up after arg2 polls (arg < 0: defaults);
+        FAULT_SHORT_ROW makes row arg's exact size one short after the
+        symbolic phase (arg < 0: off)."""
         self.check(self.lib.cb_ctx_set_fault(self.handle, int(kind), int(arg), int(arg2)))
 
     def stats(self) -> dict:
@@ -378,6 +392,7 @@ FLAG_SPMSPV_BUCKET = 64
 # fault injection kinds (cb_ctx_set_fault)
 FAULT_ALLOC = 1
 FAULT_SILENT_TILE = 2
+FAULT_SHORT_ROW = 3
 
 # device status bits of cb_spgemm_fused
 FUSED_CAPACITY = 1
@@ -553,13 +568,15 @@ def _view(ptr, n, dtype, device):
 def spgemm_column_batches(semiring: str, A: DeviceCSR, B: DeviceCSR, budget_bytes: int, on_batch,
                           *, validate: bool = True, ctx: Context | None = None,
                           sizing: str = "exact", timing: bool = False, mlp=None,
-                          margin: float = 0.25) -> dict:
+                          margin: float = 0.25, resume_col: int = 0, resume_batch: int = 0) -> dict:
     """Column-batched C = A (+).(x) B (cb_spgemm_ex with budget_bytes > 0).
 
     on_batch(batch, col_lo, col_hi, Cb) is called for each batch with a
     DeviceCSR view of C[:, col_lo:col_hi) (global column indices) that is
     valid only during the call; return True to stop early.  Returns the
-    call's statistics (batches, flops, nnz, ...).
+    call's statistics (batches, flops, nnz, ...).  resume_col / resume_batch
+    restart a stopped call at the col_lo and index of its first unconsumed
+    batch (only columns [resume_col, B.ncols) are formed).
     """
     code, dt = SEMIRING[semiring]
     ctx = ctx or context()
@@ -580,6 +597,8 @@ def spgemm_column_batches(semiring: str, A: DeviceCSR, B: DeviceCSR, budget_byte
     sa, sb = A.as_struct(), B.as_struct()
     opts = make_opts(sizing=sizing, validate=validate, budget_bytes=budget_bytes, on_batch=fn,
                      flags=FLAG_TIMING if timing else 0, mlp=mlp, margin=margin)
+    opts.resume_col = int(resume_col)
+    opts.resume_batch = int(resume_batch)
     sc = cb_csr()
     ctx.check(ctx.lib.cb_spgemm_ex(ctx.handle, code, ctypes.byref(sa), ctypes.byref(sb),
                                    ctypes.byref(sc), ctypes.byref(opts)))
@@ -756,3 +775,56 @@ def autotune(semiring: str, A: DeviceCSR, B: DeviceCSR, *, sizing: str = "exact"
     ctx.check(ctx.lib.cb_autotune(ctx.handle, code, ctypes.byref(sa), ctypes.byref(sb), ctypes.byref(opts),
                                   ctypes.byref(t), ctypes.byref(ms)))
     return {k: getattr(t, k) for k, _ in cb_tune._fields_}, ms.value
+
+
+def autotune_cached(semiring: str, A: DeviceCSR, B: DeviceCSR, cache_path: str, *,
+                    sizing: str = "exact", mlp=None, margin: float = 0.25,
+                    ctx: Context | None = None):
+    """cb_autotune through the JSON cache at cache_path (keyed by device name,
+    semiring, sizing and size class): a hit sets the cached bounds with no GPU
+    work.  Returns (bounds dict, milliseconds, hit)."""
+    ctx = ctx or context()
+    code, _ = SEMIRING[semiring]
+    sa, sb = A.as_struct(), B.as_struct()
+    opts = make_opts(sizing=sizing, mlp=mlp, margin=margin)
+    t = cb_tune()
+    ms = ctypes.c_float()
+    hit = ctypes.c_int()
+    ctx.check(ctx.lib.cb_autotune_cached(ctx.handle, code, ctypes.byref(sa), ctypes.byref(sb),
+                                         ctypes.byref(opts), os.fsencode(cache_path), ctypes.byref(t),
+                                         ctypes.byref(ms), ctypes.byref(hit)))
+    return {k: getattr(t, k) for k, _ in cb_tune._fields_}, ms.value, bool(hit.value)
+
+
+def tune_key(device_name: str, semiring: str, nrows: int, nnz_a: int, nnz_b: int,
+             sizing: str = "exact") -> str:
+    """The autotune cache key (cb_tune_key); host only."""
+    lib = load()
+    buf = ctypes.create_string_buffer(512)
+    rc = lib.cb_tune_key(device_name.encode(), SEMIRING[semiring][0], SIZING[sizing], nrows, nnz_a,
+                         nnz_b, buf, len(buf))
+    if rc:
+        raise CBError(rc, "cb_tune_key: bad argument")
+    return buf.value.decode()
+
+
+def tune_cache_get(path: str, key: str):
+    """(bounds dict, ms) for key from the cache file, or None; host only."""
+    lib = load()
+    t, ms, found = cb_tune(), ctypes.c_float(), ctypes.c_int()
+    rc = lib.cb_tune_cache_get(os.fsencode(path), key.encode(), ctypes.byref(t), ctypes.byref(ms),
+                               ctypes.byref(found))
+    if rc:
+        raise CBError(rc, f"tune cache {path} unreadable or not a tune cache")
+    if not found.value:
+        return None
+    return {k: getattr(t, k) for k, _ in cb_tune._fields_}, ms.value
+
+
+def tune_cache_put(path: str, key: str, bounds: dict, ms: float) -> None:
+    """Insert or replace key's entry in the cache file; host only."""
+    lib = load()
+    t = cb_tune(**bounds)
+    rc = lib.cb_tune_cache_put(os.fsencode(path), key.encode(), ctypes.byref(t), float(ms))
+    if rc:
+        raise CBError(rc, f"tune cache {path} unreadable or not writable")

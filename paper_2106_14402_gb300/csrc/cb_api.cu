@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/cb.h"
 #include "cb_common.cuh"
 #include "cb_kernels.h"
@@ -27,6 +29,7 @@ struct cb_ctx {
   size_t ws2_cap = 0;
   int64_t* host = nullptr;  // pinned read-back buffer
   cudaEvent_t ev[6] = {};   // phase boundaries (CB_FLAG_TIMING)
+  nvtxRangeId_t nvtx = 0;   // the open NVTX range of the current phase (0: none)
   cb::Tune tune;            // tier bounds (cb_ctx_set_tune / cb_autotune)
   unsigned long long* fstat = nullptr;  // tile status words of the one-launch path
   int64_t fstat_cap = 0;
@@ -42,6 +45,7 @@ struct cb_ctx {
   int64_t allocs_seen = 0;    // device allocations since the fault was set
   unsigned fused_spin = cb::kFusedSpinDefault;  // polls per look-back wait
   int64_t fused_silent = -1;  // tile of the one-launch kernel that never publishes
+  int64_t fault_short_row = -1;  // row whose exact size is made one short (-1: off)
 };
 
 namespace {
@@ -209,13 +213,48 @@ void run_validation(cb_ctx* ctx, const cb_csr* A, const cb_csr* B) {
   }
 }
 
+// Debug build: fail the call when a kernel recorded a failed bounds check
+// (synchronises; nothing happens in the normal build).
+void check_words(cb_ctx* ctx) {
+  if constexpr (!cb::kChecked) return;
+  struct {
+    const char* file;
+    int64_t (*take)(cudaStream_t, int64_t*);
+  } const readers[] = {{"numeric", cb::check_take_numeric},   {"symbolic", cb::check_take_symbolic},
+                       {"queue", cb::check_take_queue},       {"rows", cb::check_take_rows},
+                       {"fused", cb::check_take_fused}};
+  for (const auto& r : readers) {
+    int64_t index = 0;
+    const int64_t code = r.take(ctx->stream, &index);
+    if (code == 0) continue;
+    char msg[160];
+    if (code < 0) std::snprintf(msg, sizeof msg, "bounds check word of %s unreadable", r.file);
+    else std::snprintf(msg, sizeof msg, "bounds check %lld failed at index %lld (%s kernels)",
+                       (long long)code, (long long)index, r.file);
+    fail(ctx, CB_ERR_CUDA, msg);
+  }
+}
+
+// Phase boundary k of a product: 0 before the flop count (K1), 1 before the
+// symbolic phase, 2 before the scan, 3 after it (C allocated next), 4 before
+// the numeric phase, 5 after it.  Each phase is an NVTX range on the host
+// thread ("cb.stats" ... "cb.numeric", free without a profiler attached);
+// with CB_FLAG_TIMING an event is also recorded on ctx's stream.
 void mark(cb_ctx* ctx, const cb_opts& opt, int k) {
+  static const char* const kPhase[5] = {"cb.stats", "cb.symbolic", "cb.scan", "cb.alloc",
+                                        "cb.numeric"};
+  if (ctx->nvtx) nvtxRangeEnd(ctx->nvtx);
+  ctx->nvtx = k < 5 ? nvtxRangeStartA(kPhase[k]) : 0;
   if (!(opt.flags & CB_FLAG_TIMING)) return;
   if (!ctx->ev[k]) CB_CUDA(cudaEventCreate(&ctx->ev[k]));
   CB_CUDA(cudaEventRecord(ctx->ev[k], ctx->stream));
 }
 
 void collect_times(cb_ctx* ctx, const cb_opts& opt, bool numeric_ran) {
+  if (ctx->nvtx) {  // the product is done: close its last phase's range
+    nvtxRangeEnd(ctx->nvtx);
+    ctx->nvtx = 0;
+  }
   if (!(opt.flags & CB_FLAG_TIMING)) return;
   CB_CUDA(cudaEventSynchronize(ctx->ev[numeric_ran ? 5 : 3]));
   float t = 0.f;
@@ -520,6 +559,10 @@ void spgemm_plain(cb_ctx* ctx, int sr, const cb_csr* A, const DevCSR& dB, int64_
   cb::launch_symbolic(dA, dB, perm_sym, sym_beg, sym_cnt, flops, nnz, span_counts, span_wins, wcut,
                       wins, win_cap, hbits, b_sorted, counters, ctx->stream, ctx->sms, &launches);
   mark(ctx, opt, 2);
+  if (ctx->fault_short_row >= 0 && ctx->fault_short_row < m && !skip) {
+    cb::launch_fault_shrink(nnz + ctx->fault_short_row, ctx->stream);
+    ctx->stats.kernels += 1;
+  }
   cb::launch_exclusive_scan(nnz, m, C->row_ptr, partial, ctx->stream);
   // the hash tier's table bounds the row size it can take for this value type
   const int64_t num_hash_max = std::min<int64_t>(ctx->tune.num_hash_max, cb::num_large_max(sr));
@@ -739,6 +782,9 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
   if (opt.budget_bytes < rp_bytes + per)
     fail(ctx, CB_ERR_BUDGET, "budget smaller than one row-pointer array plus one entry");
   const int64_t cap = (opt.budget_bytes - rp_bytes) / per;
+  if (opt.resume_col < 0 || opt.resume_col > k)
+    fail(ctx, CB_ERR_ARG, "resume_col outside [0, B.ncols]");
+  if (opt.resume_batch < 0) fail(ctx, CB_ERR_ARG, "resume_batch must be >= 0");
   if (opt.validate) run_validation(ctx, A, B);
   C->nrows = m;
   C->ncols = k;
@@ -747,7 +793,7 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
   C->col = nullptr;
   C->val = nullptr;
   ctx->stats.batches = 0;
-  if (m == 0 || k == 0 || A->nnz == 0 || B->nnz == 0) return;
+  if (m == 0 || k == 0 || A->nnz == 0 || B->nnz == 0 || opt.resume_col == k) return;
 
   const DevCSR dA = dev(A), dBfull = dev(B);
   DevBuf brp(ctx), bcol(ctx), bval(ctx), rownnz(ctx);
@@ -820,20 +866,29 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
   // from the output density (entries per column) the finished batches
   // showed, aiming at kFill of the budget, so that the predictor's bias
   // costs neither extra batches nor overflowing ones.
+  // A resumed call (resume_col > 0) covers columns [resume_col, k) only: with
+  // exact sizing its ranges are the same equal ranges, the first one cut at
+  // resume_col, so a call resumed at the col_lo of batch b forms batches b,
+  // b+1, ... as the full call did (the batches are independent: paper
+  // Sec. 7.2).
   constexpr double kFill = 0.9;
   const bool adaptive = opt.sizing == CB_SIZING_LEARNED;
+  const int64_t start = opt.resume_col;
   std::deque<Range> todo;
   int64_t next_lo = k;
   const int64_t* next_plo = nullptr;
   double width = 0.0;
   if (!adaptive) {
-    const int64_t* pos = b_sorted ? slabs_for(bnd) : nullptr;
-    for (int64_t j = 0; j < nb; ++j)
-      todo.push_back(Range{bnd[(size_t)j], bnd[(size_t)j + 1], pos ? pos + (size_t)j * n : nullptr,
-                           pos ? pos + (size_t)(j + 1) * n : nullptr});
+    std::vector<int64_t> b2{start};
+    for (int64_t j = 1; j <= nb; ++j)
+      if (bnd[(size_t)j] > start) b2.push_back(bnd[(size_t)j]);
+    const int64_t* pos = b_sorted ? slabs_for(b2) : nullptr;
+    for (size_t j = 0; j + 1 < b2.size(); ++j)
+      todo.push_back(Range{b2[j], b2[j + 1], pos ? pos + j * (size_t)n : nullptr,
+                           pos ? pos + (j + 1) * (size_t)n : nullptr});
   } else {
-    next_lo = 0;
-    next_plo = b_sorted ? slabs_for(std::vector<int64_t>{0}) : nullptr;
+    next_lo = start;
+    next_plo = b_sorted ? slabs_for(std::vector<int64_t>{start}) : nullptr;
     width = (double)k * kFill * (double)cap / (double)std::max<int64_t>(total, 1);
   }
   int64_t done_cols = 0, done_nnz = 0;
@@ -842,7 +897,7 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
   inner.validate = 0;
   inner.budget_bytes = 0;
   inner.out_capacity = cap;
-  int64_t nnz_sum = 0, batch = 0;
+  int64_t nnz_sum = 0, batch = opt.resume_batch;
   int kernels = ctx->stats.kernels;
   for (;;) {
     if (todo.empty()) {
@@ -895,7 +950,7 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
   }
   ctx->stats.flops = sym_flops;
   ctx->stats.nnz = nnz_sum;
-  ctx->stats.batches = (int32_t)batch;
+  ctx->stats.batches = (int32_t)(batch - opt.resume_batch);
   ctx->stats.kernels = kernels;
   C->nnz = nnz_sum;
 }
@@ -1409,6 +1464,18 @@ int cb_row_features(cb_ctx* ctx, const cb_csr* A, const cb_csr* B, float* feat) 
   }
 }
 
+int64_t cb_struct_size(int which) {
+  switch (which) {
+    case 0: return (int64_t)sizeof(cb_csr);
+    case 1: return (int64_t)sizeof(cb_opts);
+    case 2: return (int64_t)sizeof(cb_tune);
+    case 3: return (int64_t)sizeof(cb_stats);
+    case 4: return (int64_t)sizeof(cb_spvec);
+    case 5: return (int64_t)sizeof(cb_wlabel);
+  }
+  return -1;
+}
+
 void cb_opts_default(cb_opts* opt) {
   if (!opt) return;
   std::memset(opt, 0, sizeof *opt);
@@ -1507,12 +1574,14 @@ int cb_spgemm_ex(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, 
     if (opt.budget_bytes > 0) {
       if (!opt.on_batch) fail(ctx, CB_ERR_ARG, "budget_bytes > 0 needs on_batch");
       spgemm_colbatch(ctx, (int)sr, A, B, C, opt);
+      check_words(ctx);
       return CB_OK;
     }
     if (opt.validate) run_validation(ctx, A, B);
     if (opt.sizing == CB_SIZING_EXACT)
       spgemm_plain(ctx, (int)sr, A, dev(B), B->ncols, C, opt, nullptr, nullptr, nullptr, B->nnz);
     else spgemm_learned(ctx, (int)sr, A, dev(B), B->ncols, C, opt);
+    check_words(ctx);
     return CB_OK;
   } catch (const Fail& f) {
     if (!caller_buf && C) {
@@ -1547,6 +1616,7 @@ int cb_spgemm_fused(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* 
     C->ncols = B->ncols;
     C->nnz = -1;
     run_fused(ctx, (int)sr, lanes, dev(A), dev(B), C->row_ptr, C->col, C->val, capacity, status);
+    check_words(ctx);
     return CB_OK;
   } catch (const Fail& f) {
     return f.code;
@@ -1988,6 +2058,7 @@ int cb_merge(cb_ctx* ctx, cb_semiring sr, int k, const cb_csr* parts, cb_csr* C,
     opt.validate = 0;
     spgemm_plain(ctx, msr, &sel, dB, n, C, opt);
     ctx->stats.kernels += 2;
+    check_words(ctx);
     return CB_OK;
   } catch (const Fail& f) {
     if (!caller_buf && C) {
@@ -2031,6 +2102,7 @@ int cb_spgemm_batched(cb_ctx* ctx, int count, const cb_semiring* sr, const cb_cs
       batched_group(ctx, (int)sr[g0], A + g0, B + g0, g1 - g0, g0, opt, wave, kernels, nnz, flops);
       g0 = g1;
     }
+    check_words(ctx);
   } catch (const Fail& f) {
     if (f.code != -1) return f.code;  // -1: the consumer stopped early
   }
@@ -2171,6 +2243,52 @@ int cb_autotune(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B, c
   }
 }
 
+int cb_autotune_cached(cb_ctx* ctx, cb_semiring sr, const cb_csr* A, const cb_csr* B,
+                       const cb_opts* opt, const char* cache_path, cb_tune* best, float* best_ms,
+                       int* hit) {
+  if (!ctx || !best || !cache_path || !hit) return CB_ERR_ARG;
+  *hit = 0;
+  ctx->err.clear();
+  if (!A || !B) {
+    ctx->err = "null matrix argument";
+    return CB_ERR_ARG;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) {
+    ctx->err = "cudaGetDeviceProperties failed";
+    return CB_ERR_CUDA;
+  }
+  char key[512];
+  const int32_t sizing = opt ? opt->sizing : CB_SIZING_EXACT;
+  if (cb_tune_key(prop.name, sr, sizing, A->nrows, A->nnz, B->nnz, key, sizeof key) != CB_OK) {
+    ctx->err = "tune cache key too long";
+    return CB_ERR_ARG;
+  }
+  cb_tune t{};
+  float ms = 0.f;
+  int found = 0;
+  if (cb_tune_cache_get(cache_path, key, &t, &ms, &found) != CB_OK) {
+    ctx->err = std::string("tune cache unreadable or not a cb tune cache: ") + cache_path;
+    return CB_ERR_ARG;
+  }
+  if (found) {
+    cb_ctx_set_tune(ctx, &t);  // clamps into range
+    *best = t;
+    if (best_ms) *best_ms = ms;
+    *hit = 1;
+    return CB_OK;
+  }
+  float tms = 0.f;
+  const int rc = cb_autotune(ctx, sr, A, B, opt, best, &tms);
+  if (rc != CB_OK) return rc;
+  if (best_ms) *best_ms = tms;
+  if (cb_tune_cache_put(cache_path, key, best, tms) != CB_OK) {
+    ctx->err = std::string("tune cache not writable: ") + cache_path;
+    return CB_ERR_ARG;
+  }
+  return CB_OK;
+}
+
 int cb_ctx_set_fault(cb_ctx* ctx, int kind, int64_t arg, int64_t arg2) {
   if (!ctx) return CB_ERR_ARG;
   switch (kind) {
@@ -2178,6 +2296,9 @@ int cb_ctx_set_fault(cb_ctx* ctx, int kind, int64_t arg, int64_t arg2) {
       if (arg < 0) return CB_ERR_ARG;
       ctx->fault_alloc = arg;
       ctx->allocs_seen = 0;
+      return CB_OK;
+    case CB_FAULT_SHORT_ROW:
+      ctx->fault_short_row = arg < 0 ? -1 : arg;
       return CB_OK;
     case CB_FAULT_SILENT_TILE:
       if (arg < 0) {

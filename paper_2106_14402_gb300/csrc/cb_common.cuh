@@ -27,6 +27,72 @@ namespace cb {
 // ---------------------------------------------------------------------------
 #define CB_FOR_EACH_SEMIRING(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7)
 
+// ---------------------------------------------------------------------------
+// Debug build (compiled with -DCB_CHECK, library libcb_check.so): the index
+// of every CSR write and of every shared or global hash-table access is
+// checked at run time.  A failed check records (code, index) in the check
+// word of its translation unit (the first failure wins) and the access is
+// skipped, so nothing is written out of bounds; the host reads the words
+// after every call and fails it (CB_ERR_CUDA, "bounds check ...").  In the
+// normal build chk() is constant true and guard() is the plain condition.
+// ---------------------------------------------------------------------------
+#ifdef CB_CHECK
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+namespace {
+__device__ unsigned long long g_check_word[2];  // (code, index), one per translation unit
+}
+
+__device__ __forceinline__ void check_record(int code, int64_t index) {
+  if (atomicCAS(&g_check_word[0], 0ull, (unsigned long long)code) == 0ull)
+    g_check_word[1] = (unsigned long long)index;
+}
+
+// A check that only the debug build makes: true in the normal build.
+__device__ __forceinline__ bool chk(bool ok, int code, int64_t index) {
+  if constexpr (kChecked) {
+    if (!ok) check_record(code, index);
+    return ok;
+  } else {
+    return true;
+  }
+}
+
+// A bound every build keeps (the access is skipped when it fails); the
+// debug build also records the failure.
+__device__ __forceinline__ bool guard(bool ok, int code, int64_t index) {
+  if constexpr (kChecked) {
+    if (!ok) check_record(code, index);
+  }
+  return ok;
+}
+
+// Host side, one per translation unit that includes this header: reads and
+// clears the unit's check word on stream s (synchronises).  Returns the
+// code (0: no failure) and the index in *index.  Always 0 in the normal build.
+#define CB_CHECK_READER(NAME)                                                              \
+  int64_t check_take_##NAME(cudaStream_t s, int64_t* index) {                              \
+    *index = 0;                                                                            \
+    if constexpr (!kChecked) {                                                             \
+      return 0;                                                                            \
+    } else {                                                                               \
+      unsigned long long w[2] = {0, 0};                                                    \
+      if (cudaMemcpyFromSymbolAsync(w, g_check_word, sizeof w, 0, cudaMemcpyDeviceToHost,  \
+                                    s) != cudaSuccess)                                     \
+        return -1;                                                                         \
+      const unsigned long long z[2] = {0, 0};                                              \
+      if (cudaMemcpyToSymbolAsync(g_check_word, z, sizeof z, 0, cudaMemcpyHostToDevice,    \
+                                  s) != cudaSuccess ||                                     \
+          cudaStreamSynchronize(s) != cudaSuccess)                                         \
+        return -1;                                                                         \
+      *index = (int64_t)w[1];                                                              \
+      return (int64_t)w[0];                                                                \
+    }                                                                                      \
+  }
+
 template <int SR> struct Sem;
 
 // Read-only cached load of a value of any semiring type: integer types

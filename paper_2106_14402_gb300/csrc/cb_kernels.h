@@ -263,4 +263,17 @@ cudaError_t launch_fused(int sr, int lanes, const DevCSR& A, const DevCSR& B, in
                          int64_t tstat_cap, unsigned* sync, int* status, cudaStream_t s, int sms,
                          unsigned spin_limit = kFusedSpinDefault, int64_t silent_tile = -1);
 
+// Fault injection: *nnz_row -= 1 when positive (one launch of one thread).
+void launch_fault_shrink(int64_t* nnz_row, cudaStream_t s);
+
+// Debug build (-DCB_CHECK): read and clear the bounds-check word of each
+// kernel file on stream s (synchronises); returns the first failed check's
+// code (0: none, -1: the read failed) and its index in *index.  Always 0 in
+// the normal build.
+int64_t check_take_numeric(cudaStream_t s, int64_t* index);
+int64_t check_take_symbolic(cudaStream_t s, int64_t* index);
+int64_t check_take_queue(cudaStream_t s, int64_t* index);
+int64_t check_take_rows(cudaStream_t s, int64_t* index);
+int64_t check_take_fused(cudaStream_t s, int64_t* index);
+
 }  // namespace cb

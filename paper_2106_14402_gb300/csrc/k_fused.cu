@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(kFThreads, 4) k_fused(DevCSR A, DevCSR B, int6
         const long long off = base + soff[row];
         const unsigned* rk = &skey[warp][rr * F];
         const Acc* rv = &sval[warp][rr * F];
+        if (!chk(off + n <= cap && n <= F, 46, off + n)) continue;
         for (int t = lane; t < n; t += 32) {
           Ccol[off + t] = (int32_t)rk[t ^ (((t >> 5) | rr * (G / 4)) & 7)];
           Cval[off + t] = S::out(rv[t ^ (((t >> 4) | rr * (G / 2)) & 7)]);
@@ -499,5 +500,7 @@ cudaError_t launch_fused(int sr, int lanes, const DevCSR& A, const DevCSR& B, in
   }
   return cudaErrorInvalidValue;
 }
+
+CB_CHECK_READER(fused)
 
 }  // namespace cb

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
     const int64_t nz = nnz[i];
     const int bits = max(ceil_log2(2 * nz), 5);
     const int tsize = 1 << bits;
+    if (!chk(tsize <= TABLE_MAX, 30, i)) continue;  // uniform over the team
     const uint32_t mask = (uint32_t)tsize - 1;
     const int shift = 32 - bits;
     const int64_t f = flops[i];
@@ -121,8 +122,10 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
           if (wl == leader) base = atomicAdd(&esc_cnt[team], __popc(am));
           base = __shfl_sync(am, base, leader);
           const int t = base + __popc(am & ((1u << wl) - 1u));
-          keys[t] = c;
-          vals[t] = v;
+          if (chk(t < tsize, 31, t)) {
+            keys[t] = c;
+            vals[t] = v;
+          }
           continue;
         }
         Acc sum = v;
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
           const int slot = probe_insert(keys, mask, shift, c, ins);
           if (slot >= 0) S::atomic(&vals[slot], sum);
           else if (LEARNED) overflow[team] = 1;
-          else flag_error(err, 20);
+          else if (chk(false, 32, i)) flag_error(err, 20);
         }
       }
     }
@@ -178,8 +181,10 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
       if (mk[j] != kEmptyKey) {
-        keys[pos] = mk[j];
-        vals[pos] = mv[j];
+        if (chk(pos < tsize, 33, pos)) {
+          keys[pos] = mk[j];
+          vals[pos] = mv[j];
+        }
         ++pos;
       }
     }
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
         if (t == 0 || keys[t] != keys[t - 1]) {
           Acc v = vals[t];
           for (int u = t + 1; u < total && keys[u] == keys[t]; ++u) v = S::add(v, vals[u]);
-          if (hpos < nz) {
+          if (guard(hpos < nz, 34, off + hpos)) {
             Ccol[off + hpos] = keys[t];
             Cval[off + hpos] = S::out(v);
           }
@@ -233,6 +238,7 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
 
     // write the sorted row
     if (!LEARNED && total != nz && lane == 0) flag_error(err, 21);
+    if (lane == 0) chk(LEARNED || total <= nz, 35, i);
     if (LEARNED && lane == 0) cnt_out[i] = total;
     const int nw = total < nz ? total : (int)nz;
     const int64_t off = Crp[i];
@@ -338,7 +344,7 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
                                [](int64_t) { return 0; }, [&](int, int c, int) {
                           const unsigned off = (unsigned)((int64_t)c - lo);
                           const unsigned bit = 1u << (off & 31);
-                          atomicOr(&bp[off >> 5].x, bit);
+                          if (chk(off < 32u * (unsigned)nw, 36, c)) atomicOr(&bp[off >> 5].x, bit);
                         });
       __syncthreads();
     }
@@ -371,23 +377,25 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
                       [&](int64_t p) { return S::kUsesA ? ldg_val(Aval + p) : TA(); },
                       [&](TA a_cur, int c, TB bv) {
                         const unsigned off = (unsigned)c - lo32;
+                        if (!chk(off < 32u * (unsigned)nw, 36, c)) return;
                         const uint2 e = bp[off >> 5];
                         const int slot = (int)e.y + __popc(e.x & ((1u << (off & 31)) - 1u));
-                        if (slot < lim) S::atomic(&wacc[slot], S::mul(a_cur, bv));
+                        if (guard(slot < lim, 37, out + slot)) S::atomic(&wacc[slot], S::mul(a_cur, bv));
                       });
     __syncthreads();
     // write the window: values by slot (coalesced; in place they are there
     // already), columns by word
     if (!kInPlace)
       for (int t = tid; t < cnt; t += CTA)
-        if (out + t < row_end) st_out(Cval + out + t, S::out(kL2 ? __ldcg(wacc + t) : wacc[t]));
+        if (guard(out + t < row_end, 38, out + t))
+          st_out(Cval + out + t, S::out(kL2 ? __ldcg(wacc + t) : wacc[t]));
     for (int w = tid; w < nw; w += CTA) {
       unsigned word = bp[w].x;
       int64_t o = out + bp[w].y;
       while (word) {
         const int b = __ffs(word) - 1;
         word &= word - 1;
-        if (o < row_end) st_out(Ccol + o, (int32_t)(lo + 32 * w + b));
+        if (guard(o < row_end, 39, o)) st_out(Ccol + o, (int32_t)(lo + 32 * w + b));
         ++o;
       }
     }
@@ -651,5 +659,7 @@ size_t rank_scratch_bytes(int sr, int sms) {
   }
   return 0;
 }
+
+CB_CHECK_READER(numeric)
 
 }  // namespace cb

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kQThreads) k_queue_rows(DevCSR A, DevCSR B, in
       const int64_t q1 = row_end(B, k);
       for (int64_t q = __ldg(B.rp + k) + lane; q < q1; q += 32) {
         const unsigned c = (unsigned)__ldg(B.col + q) - (unsigned)B.col_lo;
-        if (c < (unsigned)width) atomicOr(&bits[c >> 5], 1u << (c & 31));
+        if (guard(c < (unsigned)width, 42, c)) atomicOr(&bits[c >> 5], 1u << (c & 31));
       }
     }
     __syncthreads();
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kQThreads) k_queue_rows(DevCSR A, DevCSR B, in
         if (c < (unsigned)width) {
           const unsigned wb = bits[c >> 5];
           const int slot = (int)pre[c >> 5] + __popc(wb & ((1u << (c & 31)) - 1u));
-          if (slot < kQueueAcc) S::atomic(&acc[slot], S::mul(a, ldg_val(Bval + q)));
+          if (guard(slot < kQueueAcc, 43, slot)) S::atomic(&acc[slot], S::mul(a, ldg_val(Bval + q)));
         }
       }
     }
@@ -223,7 +223,8 @@ __global__ void __launch_bounds__(kQThreads) k_queue_rows(DevCSR A, DevCSR B, in
         while (word) {
           const int b = __ffs(word) - 1;
           word &= word - 1;
-          st_out(Ccol + o++, (int32_t)(B.col_lo + 32 * (int64_t)w + b));
+          if (chk(o < base + n, 44, o)) st_out(Ccol + o, (int32_t)(B.col_lo + 32 * (int64_t)w + b));
+          ++o;
         }
       }
     }
@@ -291,5 +292,7 @@ cudaError_t launch_queue_rows(int sr, const DevCSR& A, const DevCSR& B, int64_t 
   }
   return cudaErrorInvalidValue;
 }
+
+CB_CHECK_READER(queue)
 
 }  // namespace cb

@@ -350,6 +350,12 @@ __global__ void __launch_bounds__(256) k_learn_caps(int64_t m, const int64_t* pr
   }
 }
 
+// Fault injection: one row's exact size one short, as a faulty symbolic
+// phase would leave it.
+__global__ void k_fault_shrink(int64_t* n) {
+  if (*n > 0) *n -= 1;
+}
+
 // Copy the rows computed in one pass from their staging slots into C.
 // One warp per row.
 template <class T>
@@ -362,11 +368,16 @@ __global__ void __launch_bounds__(256) k_compact_rows(int64_t m, const uint8_t* 
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += nwarps) {
     if (!learned[i]) continue;
     const int64_t src = stage_rp[i], dst = Crp[i], n = cnt[i];
+    if (!chk(dst + n <= Crp[i + 1], 45, dst + n)) continue;
     for (int64_t t = lane; t < n; t += 32) {
       Ccol[dst + t] = scol[src + t];
       Cval[dst + t] = sval[src + t];
     }
   }
+}
+
+void launch_fault_shrink(int64_t* nnz_row, cudaStream_t s) {
+  k_fault_shrink<<<1, 1, 0, s>>>(nnz_row);
 }
 
 void launch_learn_caps(int64_t m, const int64_t* pred, const int64_t* flops, int64_t ncols,
@@ -407,5 +418,7 @@ void launch_compact_rows(int vsz, int64_t m, const uint8_t* learned, const int64
                                                 static_cast<uint8_t*>(Cval));
   }
 }
+
+CB_CHECK_READER(rows)
 
 }  // namespace cb

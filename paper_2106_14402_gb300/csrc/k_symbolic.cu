@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(CTA) k_sym_hash(DevCSR A, DevCSR B, const int3
         const int c = B.col[q];
         if (!in_window(B, c)) continue;
         bool ins;
-        probe_insert(keys, mask, shift, c, ins);
+        chk(probe_insert(keys, mask, shift, c, ins) >= 0, 41, i);
         cnt += ins;
       }
     }
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
                              [](int64_t) { return 0; }, [](int64_t) { return 0; }, [&](int, int c, int) {
                         const unsigned off = (unsigned)c - lo32;
                         const unsigned bit = 1u << (off & 31);
-                        atomicOr(&sym_bm[off >> 5], bit);
+                        if (chk(off < 32u * (unsigned)nwords, 40, c)) atomicOr(&sym_bm[off >> 5], bit);
                       });
     __syncthreads();
     if (hbits) {
@@ -311,5 +311,7 @@ void launch_symbolic(const DevCSR& A, const DevCSR& B, const int32_t* perm,
     ++*launches;
   }
 }
+
+CB_CHECK_READER(symbolic)
 
 }  // namespace cb

@@ -48,3 +48,12 @@ def test_status_strings_without_gpu():
     lib = cb.load()
     assert lib.cb_status_str(0) == b"ok"
     assert b"too small" in lib.cb_status_str(9)
+
+
+def test_debug_library_exports_the_same_symbols():
+    from paper_2106_14402_gb300 import build
+    path = build.build(check=True)
+    assert path.endswith("libcb_check.so")
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing

@@ -30,7 +30,17 @@ def test_option_defaults(lib):
     o = cb.cb_opts()
     lib.cb_opts_default(ctypes.byref(o))
     assert (o.sizing, o.validate, o.out_capacity, o.budget_bytes, o.flags) == (0, 1, 0, 0, 0)
+    assert (o.resume_col, o.resume_batch, o.digests) == (0, 0, None)
     assert abs(o.margin - 0.25) < 1e-7
+
+
+def test_binding_structs_match_the_library_layout(lib):
+    lib.cb_struct_size.restype = ctypes.c_int64
+    want = [cb.cb_csr, cb.cb_opts, cb.cb_tune, cb.cb_stats, cb.cb_spvec]
+    for which, struct in enumerate(want):
+        assert lib.cb_struct_size(which) == ctypes.sizeof(struct), struct.__name__
+    assert lib.cb_struct_size(5) == 8          # cb_wlabel {float, int32}
+    assert lib.cb_struct_size(6) == -1
 
 
 def test_fused_column_bound(lib):

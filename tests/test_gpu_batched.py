@@ -21,7 +21,7 @@ def cb():
     return _cb
 
 
-def run_batches(cb, sr, A, B, budget, stop_after=None):
+def run_batches(cb, sr, A, B, budget, stop_after=None, **kw):
     dA = cb.DeviceCSR.from_host(A, sr)
     dB = dA if B is A else cb.DeviceCSR.from_host(B, sr)
     got = []
@@ -34,7 +34,7 @@ def run_batches(cb, sr, A, B, budget, stop_after=None):
         got.append((b, lo, hi, rp, col, val))
         return stop_after is not None and len(got) >= stop_after
 
-    st = cb.spgemm_column_batches(sr, dA, dB, budget, on_batch)
+    st = cb.spgemm_column_batches(sr, dA, dB, budget, on_batch, **kw)
     return got, st
 
 
@@ -129,3 +129,82 @@ def test_early_stop_and_budget_errors(cb):
     batches, st = run_batches(cb, sr, A, A, 1 << 34)
     assert len(batches) == 1
     compare_rows(sr, assemble(batches, A.nrows), want)
+
+
+def same_batch(x, y):
+    return (x[0], x[1], x[2]) == (y[0], y[1], y[2]) and all(
+        np.array_equal(a, b) for a, b in zip(x[3:], y[3:]))
+
+
+@pytest.mark.parametrize("stop", [1, 3, 5])
+def test_resume_at_batch_b_repeats_the_remaining_batches(cb, stop):
+    """A call stopped after `stop` batches and resumed at the next batch's
+    col_lo and index gives exactly the full call's remaining batches (exact
+    sizing), and the two parts together are the product."""
+    sr = "plus_times_f64"
+    P = gen.rmat(13, 16, *gen.RMAT_ABCD, seed=340)
+    A = P.with_values(gen.random_values(sr, P.nnz, 341))
+    want = oracle.spgemm(sr, A, A)
+    budget = bytes_of(sr, A.nrows, int(want[0][-1]) // 6)
+    full, st = run_batches(cb, sr, A, A, budget)
+    assert len(full) > stop + 1
+    head, _ = run_batches(cb, sr, A, A, budget, stop_after=stop)
+    assert all(same_batch(x, y) for x, y in zip(head, full[:stop]))
+    nxt = full[stop]
+    tail, st2 = run_batches(cb, sr, A, A, budget, resume_col=nxt[1], resume_batch=nxt[0])
+    assert st2["batches"] == len(tail) == len(full) - stop
+    assert all(same_batch(x, y) for x, y in zip(tail, full[stop:]))
+    compare_rows(sr, assemble(head + tail, A.nrows), want)
+
+
+def test_resume_after_a_split_and_with_learned_sizing(cb):
+    """Resuming inside the skewed product whose front ranges are halved
+    (exact sizing), and resuming a learned-sizing call (its remaining
+    columns are cut afresh): the parts still reassemble to the product."""
+    sr = "min_plus_u32"
+    n, ncols = 3000, 100000
+    rng = np.random.default_rng(350)
+    lens = rng.integers(1, 60, n)
+    cols = [np.sort(rng.choice(ncols // 10, size=l, replace=False)) for l in lens]
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = np.cumsum(lens)
+    B = gen.CSR(n, ncols, rp, np.concatenate(cols).astype(np.int32))
+    B = B.with_values(gen.random_values(sr, B.nnz, 351))
+    A = gen.random_csr(400, n, 0.01, seed=352, semiring=sr)
+    want = oracle.spgemm(sr, A, B)
+    budget = bytes_of(sr, A.nrows, int(want[0][-1]) // 3)
+    full, _ = run_batches(cb, sr, A, B, budget)
+    k = 2
+    tail, _ = run_batches(cb, sr, A, B, budget, resume_col=full[k][1], resume_batch=k)
+    assert all(same_batch(x, y) for x, y in zip(tail, full[k:])) and len(tail) == len(full) - k
+    # learned sizing: stop after two batches, resume where they ended
+    from paper_2106_14402_gb300 import sizer
+    model, _ = sizer.load()
+    dA, dB = cb.DeviceCSR.from_host(A, sr), cb.DeviceCSR.from_host(B, sr)
+    parts = []
+
+    def keep(limit):
+        def on_batch(b, lo, hi, Cb):
+            parts.append((b, lo, hi) + tuple(Cb.to_host()))
+            return limit is not None and len(parts) >= limit
+        return on_batch
+
+    cb.spgemm_column_batches(sr, dA, dB, budget, keep(2), sizing="learned", mlp=model)
+    assert len(parts) == 2
+    cb.spgemm_column_batches(sr, dA, dB, budget, keep(None), sizing="learned", mlp=model,
+                             resume_col=parts[-1][2], resume_batch=2)
+    assert [p[0] for p in parts] == list(range(len(parts)))
+    assert parts[-1][2] == B.ncols
+    compare_rows(sr, assemble(parts, A.nrows), want)
+
+
+def test_resume_arguments_are_checked(cb):
+    sr = "plus_times_i64"
+    P = gen.rmat(10, 8, *gen.RMAT_ABCD, seed=360)
+    A = P.with_values(gen.random_values(sr, P.nnz, 361))
+    for kw in ({"resume_col": -1}, {"resume_col": A.ncols + 1}, {"resume_batch": -1}):
+        with pytest.raises(cb.CBError) as e:
+            run_batches(cb, sr, A, A, 1 << 30, **kw)
+        assert e.value.code == 1
+    got, st = run_batches(cb, sr, A, A, 1 << 30, resume_col=A.ncols)   # nothing left
+    assert got == [] and st["batches"] == 0

@@ -106,3 +106,31 @@ def test_set_tune_clamps_compression_bounds(cb):
     assert t["cf_esc"] == 2.0 and t["cf_prereduce"] == 1.0
     t = ctx.set_tune(512, 512, 512, -1.0, float("nan"))
     assert t["cf_esc"] == 0.0 and t["cf_prereduce"] >= 1e30
+
+
+def test_autotune_cache_hit_skips_the_grid(cb, problem, tmp_path):
+    """The first cached autotune times the grid and stores the result under
+    this device's key; a second call (fresh context) finds it, sets the same
+    bounds and reports a hit; a foreign file is an argument error."""
+    sr = "min_plus_u32"
+    A = problem.with_values(gen.random_values(sr, problem.nnz, 720))
+    dA = cb.DeviceCSR.from_host(A, sr)
+    path = str(tmp_path / "tune.json")
+    ctx1 = cb.Context()
+    best, ms, hit = cb.autotune_cached(sr, dA, dA, path, ctx=ctx1)
+    assert not hit and ms > 0 and ctx1.get_tune() == best
+    key = cb.tune_key(torch.cuda.get_device_name(), sr, A.nrows, A.nnz, A.nnz)
+    cached, cms = cb.tune_cache_get(path, key)
+    assert cached == best and cms == ms
+    ctx2 = cb.Context()
+    best2, ms2, hit2 = cb.autotune_cached(sr, dA, dA, path, ctx=ctx2)
+    assert hit2 and best2 == best and ms2 == ms and ctx2.get_tune() == best
+    C = cb.spgemm(sr, dA, dA, ctx=ctx2)
+    rows = np.arange(0, A.nrows, 61)
+    compare_rows(sr, C.to_host(), oracle.spgemm(sr, A, A, rows=rows), rows=rows)
+    bad = tmp_path / "bad.json"
+    bad.write_text("not json")
+    with pytest.raises(cb.CBError) as e:
+        cb.autotune_cached(sr, dA, dA, str(bad), ctx=ctx2)
+    assert e.value.code == 1 and "tune cache" in ctx2.error()
+    assert bad.read_text() == "not json"
