@@ -866,11 +866,13 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
   // from the output density (entries per column) the finished batches
   // showed, aiming at kFill of the budget, so that the predictor's bias
   // costs neither extra batches nor overflowing ones.
-  // A resumed call (resume_col > 0) covers columns [resume_col, k) only: with
-  // exact sizing its ranges are the same equal ranges, the first one cut at
-  // resume_col, so a call resumed at the col_lo of batch b forms batches b,
-  // b+1, ... as the full call did (the batches are independent: paper
-  // Sec. 7.2).
+  // A resumed call (resume_col > 0) covers columns [resume_col, k) only.  With
+  // exact sizing it retraces the full call's halvings: a range that holds
+  // resume_col past its start must have overflowed in the full call, so it
+  // is halved (the right half queued) until resume_col starts a range; the
+  // ranges then follow in the full call's order.  A call resumed at the
+  // col_lo of batch b thus forms batches b, b+1, ... as the full call did
+  // (the batches are independent: paper Sec. 7.2).
   constexpr double kFill = 0.9;
   const bool adaptive = opt.sizing == CB_SIZING_LEARNED;
   const int64_t start = opt.resume_col;
@@ -879,13 +881,27 @@ void spgemm_colbatch(cb_ctx* ctx, int sr, const cb_csr* A, const cb_csr* B, cb_c
   const int64_t* next_plo = nullptr;
   double width = 0.0;
   if (!adaptive) {
-    std::vector<int64_t> b2{start};
-    for (int64_t j = 1; j <= nb; ++j)
-      if (bnd[(size_t)j] > start) b2.push_back(bnd[(size_t)j]);
+    size_t j = 0;  // the equal range [bnd[j], bnd[j+1]) holding start
+    while (bnd[j + 1] <= start) ++j;
+    int64_t a = bnd[j], b = bnd[j + 1];
+    std::vector<int64_t> right;  // queued right halves' ends, outermost first
+    while (a < start) {          // here b - a >= 2, so the halves are nonempty
+      const int64_t mid = a + (b - a) / 2;
+      if (start < mid) {
+        right.push_back(b);
+        b = mid;
+      } else {
+        a = mid;
+      }
+    }
+    std::vector<int64_t> b2{start, b};
+    for (auto it = right.rbegin(); it != right.rend(); ++it) b2.push_back(*it);
+    for (size_t t = j + 1; t <= (size_t)nb; ++t)
+      if (bnd[t] > b2.back()) b2.push_back(bnd[t]);
     const int64_t* pos = b_sorted ? slabs_for(b2) : nullptr;
-    for (size_t j = 0; j + 1 < b2.size(); ++j)
-      todo.push_back(Range{b2[j], b2[j + 1], pos ? pos + j * (size_t)n : nullptr,
-                           pos ? pos + (j + 1) * (size_t)n : nullptr});
+    for (size_t q = 0; q + 1 < b2.size(); ++q)
+      todo.push_back(Range{b2[q], b2[q + 1], pos ? pos + q * (size_t)n : nullptr,
+                           pos ? pos + (q + 1) * (size_t)n : nullptr});
   } else {
     next_lo = start;
     next_plo = b_sorted ? slabs_for(std::vector<int64_t>{start}) : nullptr;

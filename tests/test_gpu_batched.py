@@ -132,8 +132,15 @@ def test_early_stop_and_budget_errors(cb):
 
 
 def same_batch(x, y):
-    return (x[0], x[1], x[2]) == (y[0], y[1], y[2]) and all(
-        np.array_equal(a, b) for a, b in zip(x[3:], y[3:]))
+    """Same index, column range, row pointers and columns; the same values
+    (fp64 within summation-order rounding: atomics combine in any order)."""
+    if (x[0], x[1], x[2]) != (y[0], y[1], y[2]):
+        return False
+    if not (np.array_equal(x[3], y[3]) and np.array_equal(x[4], y[4])):
+        return False
+    if x[5].dtype.kind == "f":
+        return bool(np.allclose(x[5], y[5], rtol=1e-12, atol=1e-12))
+    return np.array_equal(x[5], y[5])
 
 
 @pytest.mark.parametrize("stop", [1, 3, 5])

@@ -56,6 +56,48 @@ def run_child(body: str) -> dict:
     return json.loads(line[7:])
 
 
+def test_debug_library_on_adversarial_cases(cb):
+    """All products in one column, dense rows, ncols = 1, nrows = 0, an
+    empty A, rows in every tier over several bitmap spans: no check fires,
+    results equal the oracle."""
+    out = run_child("""
+        cases = 0
+        n = 5000
+        hot = gen.CSR(n, 10, np.arange(n + 1, dtype=np.int64), np.full(n, 7, np.int32))
+        A = gen.random_csr(30, n, 0.3, seed=820)
+        for sr in ("plus_times_f64", "min_plus_u32"):
+            for fused in (True, False):
+                Av = A.with_values(gen.random_values(sr, A.nnz, 821))
+                Bv = hot.with_values(gen.random_values(sr, hot.nnz, 822))
+                C = cb.spgemm(sr, cb.DeviceCSR.from_host(Av, sr), cb.DeviceCSR.from_host(Bv, sr),
+                              fused=fused, check=True)
+                compare_rows(sr, C.to_host(), oracle.spgemm(sr, Av, Bv))
+                cases += 1
+        # a dense row of A against a random B; ncols = 1; nrows = 0; an empty matrix
+        shapes = [(gen.random_csr(40, 3000, 0.01, seed=823, full_rows=0.05), gen.random_csr(3000, 2000, 0.01, seed=824)),
+                  (gen.random_csr(300, 200, 0.05, seed=825), gen.random_csr(200, 1, 0.5, seed=826)),
+                  (gen.random_csr(0, 50, 0.1, seed=827), gen.random_csr(50, 60, 0.1, seed=828)),
+                  (gen.random_csr(20, 30, 0.0, seed=829), gen.random_csr(30, 40, 0.2, seed=830))]
+        for P, Q in shapes:
+            for sr in ("plus_times_i64", "or_and_bool"):
+                Av = P.with_values(gen.random_values(sr, P.nnz, 833))
+                Bv = Q.with_values(gen.random_values(sr, Q.nnz, 834))
+                C = cb.spgemm(sr, cb.DeviceCSR.from_host(Av, sr), cb.DeviceCSR.from_host(Bv, sr),
+                              check=True)
+                compare_rows(sr, C.to_host(), oracle.spgemm(sr, Av, Bv))
+                cases += 1
+        # rows in every tier over three bitmap spans (600000 columns)
+        from test_gpu_parity import _tiered_inputs
+        for sr in ("plus_times_i64", "or_and_bool"):
+            Av, Bv = _tiered_inputs(sr, seed=835, ncols=600000)
+            C = cb.spgemm(sr, cb.DeviceCSR.from_host(Av, sr), cb.DeviceCSR.from_host(Bv, sr), check=True)
+            compare_rows(sr, C.to_host(), oracle.spgemm(sr, Av, Bv))
+            cases += 1
+        out["cases"] = cases
+    """)
+    assert out["cases"] == 14
+
+
 def test_debug_library_is_silent_on_valid_products(cb):
     out = run_child("""
         checked = []
