@@ -410,7 +410,10 @@ int cb_autotune(cb_ctx *ctx, cb_semiring sr, const cb_csr *A, const cb_csr *B, c
  * then left untouched by cb_tune_cache_put as well).
  *
  * cb_tune_cache_put inserts or replaces key's entry (CB_ERR_ARG when the
- * file cannot be read back as a cache or written).
+ * file cannot be read back as a cache or written).  Readers never see a
+ * partial file; of two processes updating the file at once the later rename
+ * wins, so the other's new entry may be lost (it is tuned again on its next
+ * miss).
  *
  * cb_autotune_cached: with the key of this context's device and the
  * operands, a cached entry is set on the context (clamped as by

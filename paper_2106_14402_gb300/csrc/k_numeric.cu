@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
 constexpr bool kRankInPlace = true;
 
 template <int SR, int CTA>
-__global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B, const int32_t* heavy_rows,
+__global__ void __launch_bounds__(CTA, CTA == 512 ? 3 : 1) k_num_rank(DevCSR A, DevCSR B, const int32_t* heavy_rows,
                                                       const Window* wins, int64_t n_wins,
                                                       const int32_t* span_counts, int64_t spans,
                                                       const unsigned* hbits, int b_sorted,
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
   }
   // 8-byte accumulators reduce in L2 (a per-CTA slice of racc): shared-memory
   // 64-bit atomics cost more than L2 reductions, and without shared
-  // accumulators two 512-thread CTAs share an SM.
+  // accumulators three 512-thread CTAs share an SM (40 registers each).
   constexpr bool kL2 = NumLimits<SR>::kL2Acc;
   // (+,x) over int64 and fp64 accumulate in L2 directly in the window's
   // output entries (their accumulator bits are the output value's), so the
@@ -290,12 +290,18 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
   // the slice and convert on the way out.
   constexpr bool kInPlace = kL2 && kRankInPlace && (SR == 1 || SR == 2);
   constexpr int WPT = kSpanWords / CTA;
+  static_assert(WCAP <= 65535, "a window's entry counts are kept in 16 bits");
   extern __shared__ __align__(16) unsigned char rank_smem[];
-  // shared layout: [accumulators (shared-memory windows only)] [bp] [iterator scratch]
+  // shared layout: [accumulators (shared-memory windows only)] [bx] [by] [iterator scratch]
   Acc* acc = reinterpret_cast<Acc*>(rank_smem);
-  // word w of the window: .x = its column bits, .y = entries before it
-  uint2* bp = reinterpret_cast<uint2*>(rank_smem + (kL2 ? 0 : (size_t)WCAP * sizeof(Acc)));
-  long long* bal = reinterpret_cast<long long*>(bp + kSpanWords);
+  // word w of the window: bx[w] = its column bits, by[w] = entries of the
+  // window before it (< 2^16: a window holds at most kWcap entries).  Two
+  // arrays, not one of pairs: a product's lookup of both words then meets
+  // fewer shared-memory bank conflicts; 16-bit counts leave room for a third
+  // CTA per SM.
+  unsigned* bx = reinterpret_cast<unsigned*>(rank_smem + (kL2 ? 0 : (size_t)WCAP * sizeof(Acc)));
+  unsigned short* by = reinterpret_cast<unsigned short*>(bx + kSpanWords);
+  long long* bal = reinterpret_cast<long long*>(by + kSpanWords);
   __shared__ int scratch[33];
   __shared__ long long scan64[33];
   const PieceSmem sm{reinterpret_cast<int*>(bal + 2 * CTA), bal, bal + CTA,
@@ -318,9 +324,9 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
     const int nw = wd.w_hi - wd.w_lo;
     if (hbits) {
       const unsigned* src = hbits + (size_t)((int64_t)wd.h * spans + wd.span) * kSpanWords + wd.w_lo;
-      for (int w = tid; w < nw; w += CTA) bp[w].x = kStreamOut ? __ldcs(src + w) : src[w];
+      for (int w = tid; w < nw; w += CTA) bx[w] = kStreamOut ? __ldcs(src + w) : src[w];
     } else {
-      for (int w = tid; w < nw; w += CTA) bp[w].x = 0u;
+      for (int w = tid; w < nw; w += CTA) bx[w] = 0u;
     }
     if (tid < 32) {
       long long o = 0;
@@ -344,7 +350,7 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
                                [](int64_t) { return 0; }, [&](int, int c, int) {
                           const unsigned off = (unsigned)((int64_t)c - lo);
                           const unsigned bit = 1u << (off & 31);
-                          if (chk(off < 32u * (unsigned)nw, 36, c)) atomicOr(&bp[off >> 5].x, bit);
+                          if (chk(off < 32u * (unsigned)nw, 36, c)) atomicOr(&bx[off >> 5], bit);
                         });
       __syncthreads();
     }
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
 #pragma unroll
       for (int j = 0; j < WPT; ++j) {
         const int w = tid * WPT + j;
-        c[j] = w < nw ? __popc(bp[w].x) : 0;
+        c[j] = w < nw ? __popc(bx[w]) : 0;
         mine += c[j];
       }
       int total;
@@ -363,7 +369,7 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
 #pragma unroll
       for (int j = 0; j < WPT; ++j) {
         const int w = tid * WPT + j;
-        if (w < nw) bp[w].y = (unsigned)run;
+        if (w < nw) by[w] = (unsigned short)run;
         run += c[j];
       }
       if (tid == 0 && total != wd.count) flag_error(err, 23);
@@ -378,7 +384,7 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
                       [&](TA a_cur, int c, TB bv) {
                         const unsigned off = (unsigned)c - lo32;
                         if (!chk(off < 32u * (unsigned)nw, 36, c)) return;
-                        const uint2 e = bp[off >> 5];
+                        const uint2 e = make_uint2(bx[off >> 5], by[off >> 5]);
                         const int slot = (int)e.y + __popc(e.x & ((1u << (off & 31)) - 1u));
                         if (guard(slot < lim, 37, out + slot)) S::atomic(&wacc[slot], S::mul(a_cur, bv));
                       });
@@ -390,8 +396,8 @@ __global__ void __launch_bounds__(CTA, 1024 / CTA) k_num_rank(DevCSR A, DevCSR B
         if (guard(out + t < row_end, 38, out + t))
           st_out(Cval + out + t, S::out(kL2 ? __ldcg(wacc + t) : wacc[t]));
     for (int w = tid; w < nw; w += CTA) {
-      unsigned word = bp[w].x;
-      int64_t o = out + bp[w].y;
+      unsigned word = bx[w];
+      int64_t o = out + by[w];
       while (word) {
         const int b = __ffs(word) - 1;
         word &= word - 1;
@@ -450,12 +456,12 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
     ++*launches;
   }
   if (n_wins) {
-    // windows accumulating in L2 need no shared accumulators: two 512-thread
-    // CTAs per SM then work on two windows at once
+    // windows accumulating in L2 need no shared accumulators: three 512-thread
+    // CTAs per SM then work on three windows at once
     constexpr int CTA = NumLimits<SR>::kL2Acc ? 512 : 1024;
-    constexpr int PER_SM = 1024 / CTA;
+    constexpr int PER_SM = CTA == 512 ? 3 : 1;
     constexpr size_t smem = (NumLimits<SR>::kL2Acc ? 0 : NumLimits<SR>::kWcap * sizeof(Acc)) +
-                            2 * kSpanWords * sizeof(unsigned) + CTA * PieceSmem::kBytesPerThread;
+                            kSpanWords * (sizeof(unsigned) + sizeof(unsigned short)) + CTA * PieceSmem::kBytesPerThread;
     set_smem(k_num_rank<SR, CTA>, smem);
     k_num_rank<SR, CTA><<<capped(n_wins, (int64_t)sms * PER_SM), CTA, smem, s>>>(
         A, B, heavy_rows, wins, n_wins, span_counts, spans, hbits, b_sorted, flops, nnz, Crp, Ccol,
@@ -496,9 +502,9 @@ void numeric_dev_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const
   }
   {  // rank windows of the heavy rows (window count read on the device)
     constexpr int CTA = NumLimits<SR>::kL2Acc ? 512 : 1024;
-    constexpr int PER_SM = 1024 / CTA;
+    constexpr int PER_SM = CTA == 512 ? 3 : 1;
     constexpr size_t smem = (NumLimits<SR>::kL2Acc ? 0 : NumLimits<SR>::kWcap * sizeof(Acc)) +
-                            2 * kSpanWords * sizeof(unsigned) + CTA * PieceSmem::kBytesPerThread;
+                            kSpanWords * (sizeof(unsigned) + sizeof(unsigned short)) + CTA * PieceSmem::kBytesPerThread;
     k_num_rank<SR, CTA><<<sms * PER_SM, CTA, smem, s>>>(
         A, B, perm_sym, wins, 0, span_counts, spans, nullptr, 0, flops, nnz, Crp, Ccol, Cval, err,
         num_hash_max, static_cast<Acc*>(racc), counters);
@@ -606,9 +612,9 @@ void launch_numeric(int sr, const DevCSR& A, const DevCSR& B, const int32_t* per
 
 template <int SR>
 size_t rank_scratch_bytes_sr(int sms) {
-  // one slice of kWcap accumulators per resident CTA (two 512-thread CTAs per SM)
+  // one slice of kWcap accumulators per resident CTA (three 512-thread CTAs per SM)
   return NumLimits<SR>::kL2Acc
-             ? 2 * (size_t)sms * NumLimits<SR>::kWcap * sizeof(typename Sem<SR>::A)
+             ? 3 * (size_t)sms * NumLimits<SR>::kWcap * sizeof(typename Sem<SR>::A)
              : 0;
 }
 
@@ -619,7 +625,7 @@ void prepare_numeric_dev_sr() {
   set_smem(k_num_hash<SR, CTA, TEAM, TBL>, TBL * (sizeof(Acc) + sizeof(int)));
   constexpr int RCTA = NumLimits<SR>::kL2Acc ? 512 : 1024;
   constexpr size_t rsmem = (NumLimits<SR>::kL2Acc ? 0 : NumLimits<SR>::kWcap * sizeof(Acc)) +
-                           2 * kSpanWords * sizeof(unsigned) + RCTA * PieceSmem::kBytesPerThread;
+                           kSpanWords * (sizeof(unsigned) + sizeof(unsigned short)) + RCTA * PieceSmem::kBytesPerThread;
   set_smem(k_num_rank<SR, RCTA>, rsmem);
 }
 
