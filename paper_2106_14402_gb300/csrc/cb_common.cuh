@@ -779,7 +779,10 @@ __device__ __forceinline__ void for_row_pieces(const DevCSR& A, const DevCSR& B,
       sm.pa[slot] = tid;
     }
     __syncthreads();
-    const long long k_beg = npieces * warp / nwarp, k_end = npieces * (warp + 1) / nwarp;
+    // equal runs of pieces per warp; nwarp is a power of two (512- and
+    // 1024-thread CTAs), so the split needs no 64-bit division
+    const int lgw = 31 - __clz(nwarp);
+    const long long k_beg = (npieces * warp) >> lgw, k_end = (npieces * (warp + 1)) >> lgw;
     if (k_beg < k_end) {  // uniform over the warp
       int l = 0, r = ne - 1;  // range holding piece k_beg
       while (l < r) {

@@ -154,16 +154,23 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
       wstart[0] = 0;
       wrank[0] = 0;
     }
+    // kcur = the window of the word before the current one; one division
+    // per thread, then a comparison per word (a word adds at most 32 <= wcut
+    // entries, so it crosses at most one multiple of wcut)
+    int kcur = 0, nextb = wcut;
+    if (tid * WPT > 0 && tid * WPT < nwords) {
+      kcur = (run - __popc(sym_bm[tid * WPT - 1])) / wcut;
+      nextb = (kcur + 1) * wcut;
+    }
 #pragma unroll
     for (int j = 0; j < WPT; ++j) {
       const int w = tid * WPT + j;
-      if (w > 0 && w < nwords) {
-        const int before = run;
-        const int before_prev = run - (j > 0 ? c[j - 1] : __popc(sym_bm[w - 1]));
-        const int kk = before / wcut;
-        if (kk < K && before_prev / wcut < kk) {
-          wstart[kk] = w;
-          wrank[kk] = before;
+      if (w > 0 && w < nwords && run >= nextb) {  // word w opens window kcur + 1
+        ++kcur;
+        nextb += wcut;
+        if (kcur < K) {
+          wstart[kcur] = w;
+          wrank[kcur] = run;
         }
       }
       run += c[j];
