@@ -956,10 +956,10 @@ def run_e2e(args, cb, ctx, dprob, dev, world, dist, products):
     """Same metric through the public call with host buffers: per step the
     inputs are copied from pinned host memory, C is computed, and all of C is
     read back into pinned host memory (a reused 2 GiB staging area), inside
-    the timed region.  The read-back of one product runs on two copy streams
-    (1 GiB chunks alternating between them) while the next product computes
-    (two output buffers alternate), so a step costs about the larger of the
-    compute and the device-to-host traffic rather than their sum."""
+    the timed region.  The read-back of one product runs on a copy stream
+    while the next product computes (two output buffers alternate), so a step
+    costs about the larger of the compute and the device-to-host traffic
+    rather than their sum."""
     import torch
     hosts = []
     for sr, A, B, dA, dB, out, nnz in dprob:
@@ -971,29 +971,24 @@ def run_e2e(args, cb, ctx, dprob, dev, world, dist, products):
     vmax = max(VAL_BYTES[p[0]] for p in dprob)
     # C is read back through a pinned staging area of 2 x 1 GiB, reused chunk by
     # chunk (every byte of C crosses to the host; the host keeps 2 GiB per rank)
-    # chunks alternate between two copy streams (two copy engines in flight)
     chunk = 1 << 30
     stage = [torch.empty(chunk, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
     nstage = [0]
-    cstreams = [torch.cuda.Stream(device=dev) for _ in range(2)]
 
     def to_host(src_bytes):
         n = src_bytes.numel()
         for o in range(0, n, chunk):
             k = min(chunk, n - o)
-            j = nstage[0] & 1
-            with torch.cuda.stream(cstreams[j]):
-                stage[j][:k].copy_(src_bytes[o:o + k], non_blocking=True)
+            stage[nstage[0] & 1][:k].copy_(src_bytes[o:o + k], non_blocking=True)
             nstage[0] += 1
     # two device output buffers (raw bytes for the values, viewed per semiring)
     bufs = [(torch.empty(max_rows + 1, dtype=torch.int64, device=dev),
              torch.empty(max(max_nnz, 1), dtype=torch.int32, device=dev),
              torch.empty(max(max_nnz, 1) * vmax, dtype=torch.uint8, device=dev)) for _ in range(2)]
-    # copied[b][j]: copy stream j finished reading output buffer b
-    copied = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(2)]
-    for pair in copied:
-        for e in pair:
-            e.record(ctx.stream)
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    for e in copied:
+        e.record(ctx.stream)
+    cstream = torch.cuda.Stream(device=dev)
     moved = {"h2d": 0, "d2h": 0}
     turn = [0]
 
@@ -1010,8 +1005,7 @@ def run_e2e(args, cb, ctx, dprob, dev, world, dist, products):
             b = turn[0]
             turn[0] ^= 1
             rp, col, raw = bufs[b]
-            for e in copied[b]:                    # its previous read-back is done
-                ctx.stream.wait_event(e)
+            ctx.stream.wait_event(copied[b])       # its previous read-back is done
             dt = cb.SEMIRING[sr][1]
             vals = raw.view(torch.int32).view(torch.uint32) if dt == torch.uint32 else raw.view(dt)
             o = cb.DeviceCSR(A.nrows, B.ncols, rp, col, vals)
@@ -1019,14 +1013,13 @@ def run_e2e(args, cb, ctx, dprob, dev, world, dist, products):
             n = C.nnz
             ready = torch.cuda.Event()
             ready.record(ctx.stream)
-            for cs in cstreams:
-                cs.wait_event(ready)
+            cstream.wait_event(ready)
             nb = n * VAL_BYTES[sr]
-            to_host(rp[: C.nrows + 1].view(torch.uint8))
-            to_host(col[:n].view(torch.uint8))
-            to_host(raw[:nb])
-            for j, cs in enumerate(cstreams):
-                copied[b][j].record(cs)
+            with torch.cuda.stream(cstream):
+                to_host(rp[: C.nrows + 1].view(torch.uint8))
+                to_host(col[:n].view(torch.uint8))
+                to_host(raw[:nb])
+            copied[b].record(cstream)
             if count:
                 moved["d2h"] += (C.nrows + 1) * 8 + n * 4 + nb
         torch.cuda.synchronize()
@@ -1043,7 +1036,7 @@ def run_e2e(args, cb, ctx, dprob, dev, world, dist, products):
             "h2d_bytes_per_step": moved["h2d"] // steps, "d2h_bytes_per_step": moved["d2h"] // steps,
             "ms_per_step": el * 1e3, "steps": steps,
             "timing": "host wall clock, synchronised; read-back of a product overlaps the next "
-                      "product's compute (two copy streams, two output buffers)"}
+                      "product's compute (copy stream, two output buffers)"}
 
 def main():
     ap = argparse.ArgumentParser()

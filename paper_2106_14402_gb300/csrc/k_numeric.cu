@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
     for (int k = 2; k <= P; k <<= 1) {
       for (int j = k >> 1; j > 0; j >>= 1) {
         for (int t = lane; t < (P >> 1); t += TEAM) {
-          const int lo = ((t / j) * (j << 1)) + (t % j);
+          const int lo = ((t & ~(j - 1)) << 1) | (t & (j - 1));  // j is a power of two
           const int hi = lo + j;
           const bool asc = (lo & k) == 0;
           const int ka = keys[lo], kb = keys[hi];

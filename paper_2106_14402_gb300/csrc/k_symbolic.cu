@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
   const PieceSmem sm{reinterpret_cast<int*>(bal + 2048), bal, bal + 1024,
                      reinterpret_cast<int*>(bal + 2048) + 1024, scan64};
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int64_t h = u / spans, sp = u - h * spans;
+    const int64_t h = spans == 1 ? u : u / spans, sp = u - h * spans;
     const int i = heavy_rows[h];
     const int64_t lo = B.col_lo + sp * (int64_t)kSpanCols;
     const int64_t hi = min(lo + (int64_t)kSpanCols, B.col_lo + row_width(A, B, i));
