@@ -101,6 +101,10 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
   long long* bal = reinterpret_cast<long long*>(sym_bm + ((bm_words + 3) & ~3));
   const PieceSmem sm{reinterpret_cast<int*>(bal + 2048), bal, bal + 1024,
                      reinterpret_cast<int*>(bal + 2048) + 1024, scan64};
+  // the bitmap starts clear; each unit clears the words it set once it has
+  // read them, so no unit starts with a clearing pass of its own
+  for (int w = tid; w < bm_words; w += 1024) sym_bm[w] = 0u;
+  __syncthreads();
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int64_t h = spans == 1 ? u : u / spans, sp = u - h * spans;
     const int i = heavy_rows[h];
@@ -114,8 +118,6 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
       continue;
     }
     const int nwords = (int)((hi - lo + 31) / 32);
-    for (int w = tid; w < nwords; w += 1024) sym_bm[w] = 0u;
-    __syncthreads();
     const unsigned lo32 = (unsigned)lo;
     for_row_pieces<4>(A, B, i, lo, hi, spans == 1 && !B.filter, b_sorted != 0, sm,
                              [](int64_t) { return 0; }, [](int64_t) { return 0; }, [&](int, int c, int) {
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
       span_counts[h * spans + sp] = total;
       if (total) atomicAdd((unsigned long long*)&nnz[i], (unsigned long long)total);
     }
+    for (int w = tid; w < nwords; w += 1024) sym_bm[w] = 0u;  // every read of them is done
     __syncthreads();
   }
 }
