@@ -56,6 +56,10 @@ def workload(name: str):
     if name == "er16k":
         desc = "ER n=16384, 8 distinct cols/row, (+,x) int64 U{1..10}; C=A.A"
         return desc, gen.er_square()
+    if name == "blockclust":
+        desc = ("block-clustered n=131072, clusters of 256, density 0.5, ~1 inter-cluster edge per "
+                "vertex; C=A.A over (+,x) f64 (high-compression profiling case)")
+        return desc, gen.high_compression()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -1046,7 +1050,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", default="rmat18", choices=("rmat18", "rmat16", "er16k"))
+    ap.add_argument("--workload", default="rmat18", choices=("rmat18", "rmat16", "er16k", "blockclust"))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-legs", action="store_true")
