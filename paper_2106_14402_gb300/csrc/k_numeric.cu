@@ -257,6 +257,22 @@ __global__ void __launch_bounds__(CTA) k_num_hash(DevCSR A, DevCSR B, const int3
 // slice of the row in column order.
 constexpr bool kRankInPlace = true;
 
+// Launch shape of the rank windows per semiring: 512-thread CTAs, three per
+// SM, when the accumulators take little or no shared memory (8-byte ones
+// reduce in L2; (or,and) keeps one bit per slot), else one 1024-thread CTA
+// per SM holding kWcap 4-byte shared accumulators.
+template <int SR>
+struct RankShape {
+  static constexpr bool kBits = SR == 4;
+  static constexpr int kCta = (NumLimits<SR>::kL2Acc || kBits) ? 512 : 1024;
+  static constexpr size_t kAccBytes =
+      NumLimits<SR>::kL2Acc ? 0
+      : kBits ? (size_t)NumLimits<SR>::kWcap / 8
+              : (size_t)NumLimits<SR>::kWcap * sizeof(typename Sem<SR>::A);
+  static constexpr size_t kSmem = kAccBytes + kSpanWords * (sizeof(unsigned) + sizeof(unsigned short)) +
+                                  (size_t)kCta * PieceSmem::kBytesPerThread;
+};
+
 // L2 residency of the windows that accumulate in C (fp64 and int64): the
 // zeroing stores and the reductions carry an evict_last policy, so that the
 // lines a window is still reducing into outlive the streaming traffic around
@@ -297,6 +313,7 @@ __global__ void __launch_bounds__(CTA, CTA == 512 ? 3 : 1) k_num_rank(DevCSR A, 
   typedef typename S::A Acc;
   typedef typename S::TA TA;
   typedef typename S::TB TB;
+  typedef typename S::TC TC;
   constexpr int WCAP = NumLimits<SR>::kWcap;
   if (dcounters) {  // sizes on the device: heavy segment of the symbolic order, windows, sortedness
     heavy_rows += dcounters[kCntSym + 1] + dcounters[kCntSym + 2] + dcounters[kCntSym + 3];
@@ -324,7 +341,9 @@ __global__ void __launch_bounds__(CTA, CTA == 512 ? 3 : 1) k_num_rank(DevCSR A, 
   // arrays, not one of pairs: a product's lookup of both words then meets
   // fewer shared-memory bank conflicts; 16-bit counts leave room for a third
   // CTA per SM.
-  unsigned* bx = reinterpret_cast<unsigned*>(rank_smem + (kL2 ? 0 : (size_t)WCAP * sizeof(Acc)));
+  constexpr bool kBits = RankShape<SR>::kBits;  // (or,and): one accumulator bit per slot
+  unsigned* accbits = reinterpret_cast<unsigned*>(rank_smem);
+  unsigned* bx = reinterpret_cast<unsigned*>(rank_smem + RankShape<SR>::kAccBytes);
   unsigned short* by = reinterpret_cast<unsigned short*>(bx + kSpanWords);
   long long* bal = reinterpret_cast<long long*>(by + kSpanWords);
   __shared__ int scratch[33];
@@ -377,6 +396,8 @@ __global__ void __launch_bounds__(CTA, CTA == 512 ? 3 : 1) k_num_rank(DevCSR A, 
         memcpy(&zb, &z, 8);
         st_hint(wacc + t, zb, pol);
       }
+    } else if constexpr (kBits) {
+      for (int t = tid; t < (lim + 31) / 32; t += CTA) accbits[t] = 0u;
     } else {
       for (int t = tid; t < lim; t += CTA) wacc[t] = S::ident();
     }
@@ -423,8 +444,13 @@ __global__ void __launch_bounds__(CTA, CTA == 512 ? 3 : 1) k_num_rank(DevCSR A, 
                         const uint2 e = make_uint2(bx[off >> 5], by[off >> 5]);
                         const int slot = (int)e.y + __popc(e.x & ((1u << (off & 31)) - 1u));
                         if (guard(slot < lim, 37, out + slot)) {
-                          if constexpr (kInPlace) red_add_hint(&wacc[slot], S::mul(a_cur, bv), pol);
-                          else S::atomic(&wacc[slot], S::mul(a_cur, bv));
+                          if constexpr (kInPlace) {
+                            red_add_hint(&wacc[slot], S::mul(a_cur, bv), pol);
+                          } else if constexpr (kBits) {
+                            if (S::mul(a_cur, bv)) atomicOr(&accbits[slot >> 5], 1u << (slot & 31));
+                          } else {
+                            S::atomic(&wacc[slot], S::mul(a_cur, bv));
+                          }
                         }
                       });
     __syncthreads();
@@ -436,10 +462,15 @@ __global__ void __launch_bounds__(CTA, CTA == 512 ? 3 : 1) k_num_rank(DevCSR A, 
     }
     // write the window: values by slot (coalesced; in place they are there
     // already), columns by word
-    if (!kInPlace)
+    if constexpr (kBits) {
+      for (int t = tid; t < cnt; t += CTA)
+        if (guard(out + t < row_end, 38, out + t))
+          st_out(Cval + out + t, (TC)((accbits[t >> 5] >> (t & 31)) & 1u));
+    } else if constexpr (!kInPlace) {
       for (int t = tid; t < cnt; t += CTA)
         if (guard(out + t < row_end, 38, out + t))
           st_out(Cval + out + t, S::out(kL2 ? __ldcg(wacc + t) : wacc[t]));
+    }
     for (int w = tid; w < nw; w += CTA) {
       unsigned word = bx[w];
       int64_t o = out + by[w];
@@ -501,12 +532,11 @@ void numeric_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const int
     ++*launches;
   }
   if (n_wins) {
-    // windows accumulating in L2 need no shared accumulators: three 512-thread
-    // CTAs per SM then work on three windows at once
-    constexpr int CTA = NumLimits<SR>::kL2Acc ? 512 : 1024;
+    // windows whose accumulators take little or no shared memory run three
+    // 512-thread CTAs per SM, three windows at once (RankShape)
+    constexpr int CTA = RankShape<SR>::kCta;
     constexpr int PER_SM = CTA == 512 ? 3 : 1;
-    constexpr size_t smem = (NumLimits<SR>::kL2Acc ? 0 : NumLimits<SR>::kWcap * sizeof(Acc)) +
-                            kSpanWords * (sizeof(unsigned) + sizeof(unsigned short)) + CTA * PieceSmem::kBytesPerThread;
+    constexpr size_t smem = RankShape<SR>::kSmem;
     set_smem(k_num_rank<SR, CTA>, smem);
     k_num_rank<SR, CTA><<<capped(n_wins, (int64_t)sms * PER_SM), CTA, smem, s>>>(
         A, B, heavy_rows, wins, n_wins, span_counts, spans, hbits, b_sorted, flops, nnz, Crp, Ccol,
@@ -546,10 +576,9 @@ void numeric_dev_sr(const DevCSR& A, const DevCSR& B, const int32_t* perm, const
         A, B, perm, 0, flops, nnz, Crp, Ccol, Cval, err, nullptr, nullptr, dc, kNumLarge, cf.esc, cf.pre);
   }
   {  // rank windows of the heavy rows (window count read on the device)
-    constexpr int CTA = NumLimits<SR>::kL2Acc ? 512 : 1024;
+    constexpr int CTA = RankShape<SR>::kCta;
     constexpr int PER_SM = CTA == 512 ? 3 : 1;
-    constexpr size_t smem = (NumLimits<SR>::kL2Acc ? 0 : NumLimits<SR>::kWcap * sizeof(Acc)) +
-                            kSpanWords * (sizeof(unsigned) + sizeof(unsigned short)) + CTA * PieceSmem::kBytesPerThread;
+    constexpr size_t smem = RankShape<SR>::kSmem;
     k_num_rank<SR, CTA><<<sms * PER_SM, CTA, smem, s>>>(
         A, B, perm_sym, wins, 0, span_counts, spans, nullptr, 0, flops, nnz, Crp, Ccol, Cval, err,
         num_hash_max, static_cast<Acc*>(racc), counters);
@@ -668,9 +697,8 @@ void prepare_numeric_dev_sr() {
   typedef typename Sem<SR>::A Acc;
   constexpr int CTA = 512, TEAM = 512, TBL = 2 * NumLimits<SR>::kLargeMax;
   set_smem(k_num_hash<SR, CTA, TEAM, TBL>, TBL * (sizeof(Acc) + sizeof(int)));
-  constexpr int RCTA = NumLimits<SR>::kL2Acc ? 512 : 1024;
-  constexpr size_t rsmem = (NumLimits<SR>::kL2Acc ? 0 : NumLimits<SR>::kWcap * sizeof(Acc)) +
-                           kSpanWords * (sizeof(unsigned) + sizeof(unsigned short)) + RCTA * PieceSmem::kBytesPerThread;
+  constexpr int RCTA = RankShape<SR>::kCta;
+  constexpr size_t rsmem = RankShape<SR>::kSmem;
   set_smem(k_num_rank<SR, RCTA>, rsmem);
 }
 
