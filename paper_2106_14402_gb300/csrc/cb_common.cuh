@@ -302,6 +302,99 @@ struct Window {
   int32_t h, span, w_lo, w_hi, count, rank;
 };
 
+// Popcounts of the WPT consecutive bitmap words first .. first + WPT - 1 of
+// a shared-memory bitmap (first a multiple of WPT, bits 16-byte aligned),
+// words at or past nw counted as 0.  A thread's words are consecutive, so a
+// load of one word per thread would put a warp's lanes 4*WPT bytes apart on
+// a few banks (a WPT-way bank conflict); 16-byte loads of 4 words each take
+// a quarter of the shared-memory wavefronts.
+template <int WPT>
+__device__ __forceinline__ void popc_words(const unsigned* bits, int first, int nw, int (&c)[WPT]) {
+  static_assert(WPT % 4 == 0, "whole 16-byte vectors per thread");
+  const uint4* v = reinterpret_cast<const uint4*>(bits + first);
+#pragma unroll
+  for (int q = 0; q < WPT / 4; ++q) {
+    const int w = first + 4 * q;
+    const uint4 x = w < nw ? v[q] : make_uint4(0u, 0u, 0u, 0u);
+    c[4 * q + 0] = __popc(x.x);
+    c[4 * q + 1] = w + 1 < nw ? __popc(x.y) : 0;
+    c[4 * q + 2] = w + 2 < nw ? __popc(x.z) : 0;
+    c[4 * q + 3] = w + 3 < nw ? __popc(x.w) : 0;
+  }
+}
+
+// The running counts before each of those words, as 16-bit values (a
+// window holds fewer than 2^16 entries), stored 8 per 16-byte vector:
+// pre[first + j] = run + c[0] + ... + c[j - 1].  Vectors wholly past nw are
+// not stored; counts past nw inside a stored vector are never read.
+template <int WPT>
+__device__ __forceinline__ void store_counts(unsigned short* pre, int first, int nw, int run,
+                                             const int (&c)[WPT]) {
+  static_assert(WPT % 8 == 0, "whole 16-byte vectors per thread");
+  uint4* v = reinterpret_cast<uint4*>(pre + first);
+#pragma unroll
+  for (int q = 0; q < WPT / 8; ++q) {
+    unsigned p[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const unsigned lo16 = (unsigned)run & 0xFFFFu;
+      run += c[8 * q + 2 * h];
+      const unsigned hi16 = (unsigned)run & 0xFFFFu;
+      run += c[8 * q + 2 * h + 1];
+      p[h] = lo16 | (hi16 << 16);
+    }
+    if (first + 8 * q < nw) v[q] = make_uint4(p[0], p[1], p[2], p[3]);
+  }
+}
+
+// The set bits of a column bitmap, read out in column order: word w covers
+// columns 32w .. 32w + 31 of the range, pre[w] counts the set bits of the
+// words before it, and emit(j, c) receives the j-th set bit overall (c its
+// column offset in the range), every j once.  Two walks, picked by the
+// average number of set bits per word:
+//   * dense (at least DENSE per word, DENSE > 0): one word per warp step; lane
+//     l takes bit l, at the word's offset plus the bits set below it, so the
+//     entries of one store instruction are consecutive (one or two L2
+//     requests for up to 32 entries);
+//   * sparse: one word per thread, its bits in turn.  A lane's entries are
+//     consecutive and the lanes' words start a few entries apart.
+// Walking a dense bitmap a word per thread places the 32 lanes' entries of
+// one store a word's count apart, one L2 request per entry.
+// The dense walk pays for that only where the kernel is bound by its
+// requests to L2 (rank windows reducing in L2: R-MAT s18 fp64 numeric 55.7 ->
+// 54.5 ms); where shared-memory accumulators bound it, its extra
+// instructions and broadcast loads cost as much as they save (u32 and bool
+// numeric unchanged at a bound of 8, 2-4 ms slower at 4), so those kernels
+// pass DENSE = 0.
+#ifndef CB_DENSE_WORD_BITS
+#define CB_DENSE_WORD_BITS 8
+#endif
+constexpr int kDenseWordBits = CB_DENSE_WORD_BITS;
+template <int DENSE, int CTA, class F>
+__device__ __forceinline__ void for_bitmap_columns(const unsigned* bits, const unsigned short* pre,
+                                                   int nw, int cnt, F&& emit) {
+  const int tid = threadIdx.x;
+  if (DENSE > 0 && (int64_t)cnt >= (int64_t)DENSE * nw) {  // uniform over the CTA
+    const int lane = tid & 31;
+    const unsigned below = (1u << lane) - 1u;
+    for (int w = tid >> 5; w < nw; w += CTA / 32) {
+      const unsigned word = bits[w];
+      if ((word >> lane) & 1u) emit((int)pre[w] + __popc(word & below), 32 * w + lane);
+    }
+  } else {
+    for (int w = tid; w < nw; w += CTA) {
+      unsigned word = bits[w];
+      int j = pre[w];
+      while (word) {
+        const int b = __ffs(word) - 1;
+        word &= word - 1;
+        emit(j, 32 * w + b);
+        ++j;
+      }
+    }
+  }
+}
+
 enum SymTier { kSymEmpty = 0, kSymWarp = 1, kSymSmall = 2, kSymLarge = 3, kSymHeavy = 4, kSymTiers = 5 };
 enum NumTier { kNumEmpty = 0, kNumWarp = 1, kNumSmall = 2, kNumLarge = 3, kNumHeavy = 4, kNumTiers = 5 };
 

@@ -414,21 +414,13 @@ __global__ void __launch_bounds__(CTA, CTA == 512 ? 3 : 1) k_num_rank(DevCSR A, 
     // exclusive prefix of word popcounts
     {
       int c[WPT];
+      popc_words<WPT>(bx, tid * WPT, nw, c);
       int mine = 0;
 #pragma unroll
-      for (int j = 0; j < WPT; ++j) {
-        const int w = tid * WPT + j;
-        c[j] = w < nw ? __popc(bx[w]) : 0;
-        mine += c[j];
-      }
+      for (int j = 0; j < WPT; ++j) mine += c[j];
       int total;
-      int run = team_exclusive_scan<CTA>(mine, scratch, total);
-#pragma unroll
-      for (int j = 0; j < WPT; ++j) {
-        const int w = tid * WPT + j;
-        if (w < nw) by[w] = (unsigned short)run;
-        run += c[j];
-      }
+      const int run = team_exclusive_scan<CTA>(mine, scratch, total);
+      store_counts<WPT>(by, tid * WPT, nw, run, c);
       if (tid == 0 && total != wd.count) flag_error(err, 23);
     }
     __syncthreads();
@@ -471,16 +463,10 @@ __global__ void __launch_bounds__(CTA, CTA == 512 ? 3 : 1) k_num_rank(DevCSR A, 
         if (guard(out + t < row_end, 38, out + t))
           st_out(Cval + out + t, S::out(kL2 ? __ldcg(wacc + t) : wacc[t]));
     }
-    for (int w = tid; w < nw; w += CTA) {
-      unsigned word = bx[w];
-      int64_t o = out + by[w];
-      while (word) {
-        const int b = __ffs(word) - 1;
-        word &= word - 1;
-        if (guard(o < row_end, 39, o)) st_out(Ccol + o, (int32_t)(lo + 32 * w + b));
-        ++o;
-      }
-    }
+    for_bitmap_columns<kL2 ? kDenseWordBits : 0, CTA>(bx, by, nw, cnt, [&](int j, int c) {
+      const int64_t o = out + j;
+      if (guard(o < row_end, 39, o)) st_out(Ccol + o, (int32_t)(lo + c));
+    });
     __syncthreads();
   }
 }

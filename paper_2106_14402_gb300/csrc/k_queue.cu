@@ -217,16 +217,10 @@ __global__ void __launch_bounds__(kQThreads) k_queue_rows(DevCSR A, DevCSR B, in
         if (t < n) st_out(Cval + base + t, S::out(acc[t]));
         acc[t] = S::ident();
       }
-      for (int w = tid; w < nw; w += kQThreads) {
-        unsigned word = bits[w];
-        long long o = base + pre[w];
-        while (word) {
-          const int b = __ffs(word) - 1;
-          word &= word - 1;
-          if (chk(o < base + n, 44, o)) st_out(Ccol + o, (int32_t)(B.col_lo + 32 * (int64_t)w + b));
-          ++o;
-        }
-      }
+      for_bitmap_columns<kDenseWordBits, kQThreads>(bits, pre, nw, n, [&](int j, int c) {
+        const long long o = base + j;
+        if (chk(o < base + n, 44, o)) st_out(Ccol + o, (int32_t)(B.col_lo + c));
+      });
     }
     __syncthreads();
   }

@@ -133,13 +133,10 @@ __global__ void __launch_bounds__(1024, 2) k_sym_bitmap(DevCSR A, DevCSR B, cons
 
     // exclusive prefix of the word popcounts (WPT consecutive words per thread)
     int c[WPT];
+    popc_words<WPT>(sym_bm, tid * WPT, nwords, c);
     int mine = 0;
 #pragma unroll
-    for (int j = 0; j < WPT; ++j) {
-      const int w = tid * WPT + j;
-      c[j] = w < nwords ? __popc(sym_bm[w]) : 0;
-      mine += c[j];
-    }
+    for (int j = 0; j < WPT; ++j) mine += c[j];
     int total;
     int run = team_exclusive_scan<1024>(mine, scratch, total);  // entries before my first word
     // Windows: word w belongs to window floor(before(w) / wcut), where

@@ -137,6 +137,41 @@ def test_heavy_rows_several_spans(cb, sr):
     assert cb.context().stats()["heavy_units"] > A.nrows
 
 
+@pytest.mark.parametrize("sr", SR)
+def test_rank_window_columns_dense_and_sparse(cb, sr):
+    """Heavy rows whose rank windows are dense (on average 8 or more output
+    columns per bitmap word: columns read out a word per warp step) and
+    sparse (fewer: a word per thread), on one span of 8192 columns and on a
+    row spread over two spans, against the oracle."""
+    rng = np.random.default_rng(71)
+    n, ncols = 2000, 8192
+    lens = rng.integers(50, 400, n)
+    cols = [np.sort(rng.choice(ncols, size=l, replace=False)) for l in lens]
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = np.cumsum(lens)
+    B = gen.CSR(n, ncols, rp, np.concatenate(cols).astype(np.int32))
+    B = B.with_values(gen.random_values(sr, B.nnz, 72))
+    # A rows of 3 .. 300 entries: 600 .. 8192 distinct output columns
+    a_lens = [3, 4, 5, 6, 8, 10, 14, 20, 40, 80, 300, 0, 1]
+    a_cols = [np.sort(rng.choice(n, size=l, replace=False)) for l in a_lens]
+    arp = np.zeros(len(a_lens) + 1, np.int64)
+    arp[1:] = np.cumsum(a_lens)
+    A = gen.CSR(len(a_lens), n, arp, np.concatenate(a_cols).astype(np.int32))
+    A = A.with_values(gen.random_values(sr, A.nnz, 73))
+    want = oracle.spgemm(sr, A, B)
+    nnz = np.diff(want[0])
+    words = ncols // 32          # one window per row: every row holds < kWcut entries
+    heavy = nnz > 512            # rows past the hash tiers
+    assert np.any(heavy & (nnz >= 8 * words)) and np.any(heavy & (nnz < 8 * words))
+    got = run_pair(cb, sr, A, B)
+    check_structure(got[0], got[1], B.ncols)
+    compare_rows(sr, got, want)
+    assert cb.context().stats()["heavy_units"] >= int(heavy.sum())
+    # the same rows with their columns spread over two spans (sparse windows)
+    B2 = gen.CSR(n, 2 * (1 << 18), rp, (B.col.astype(np.int64) * 61).astype(np.int32), B.val)
+    assert_parity(cb, sr, A, B2)
+
+
 def test_single_hot_column(cb):
     # every product of every row lands in column 7: maximal atomic contention
     n = 5000
